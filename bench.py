@@ -1,0 +1,409 @@
+"""Benchmark of the element-integration hot path on GB300.
+
+A step is one pass of the whole hot path (geometry, Jacobians, point
+operators, contraction, load vectors, stores) over one batch of synthetic
+prisms already resident in HBM.  Default workload: p = 4, 100 000 jittered
+prisms (the single-degree configuration), precision = the fastest path that
+meets 1e-6 relative error.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload p4]
+                    [--precision tc_f16x3|fp32|fp64] [--impl reference]
+
+Prints one JSON line (rank 0).  Under torchrun every rank integrates its own
+copy of the workload (weak scaling, no data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1310_1194_gb300 import inputs  # noqa: E402
+
+WORKLOAD_TEXT = {
+    "pr1": "PR1: 4096 prisms (16x16x8 grid, 2 prisms per hex, jitter 10% h), p=1",
+    "p4": "single degree: 100000 prisms (50x50x20 grid, jitter 10% h), p=4, N_sh=75, N_q=125",
+    "mixed": "mixed degree: 200000 prisms (50x50x40 grid), p in 1..7 with probabilities .25/.2/.15/.15/.1/.1/.05",
+    "diff": "differentiation: 20000 prisms (25x20x20), p=5, per-point coefficient fields",
+    "p7": "high order: 32768 prisms (32x32x16 grid, jitter 25% h, det J > 0 certified), p=7",
+}
+
+
+def nsh(p):
+    return (p + 1) * (p + 1) * (p + 2) // 2
+
+
+def nq(p):
+    return (p + 1) ** 3
+
+
+def flops_per_element(p):
+    """Algorithmic flops per element: 8 N_sh^2 N_q (contraction with the 4x4
+    point operator) + 2 N_sh N_q (load vector) + 220 N_q (geometry, the
+    paper's constant per point, Table 2)."""
+    s, q = nsh(p), nq(p)
+    return 8 * s * s * q + 2 * s * q + 220 * q
+
+
+def bytes_per_element(p, out_bytes, per_qp=False):
+    """Algorithmic HBM bytes: geometry 144 B + coefficients 112 B (per
+    element) or 112 N_q B (per point) + outputs (N_sh^2 + N_sh) * s."""
+    s = nsh(p)
+    coef = 112 * (nq(p) if per_qp else 1)
+    return 144 + coef + (s * s + s) * out_bytes
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+        time.sleep(0.25)
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl != "reference" else "gloo"
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def cpu_sample_size(w, per_qp, target_s):
+    """Elements the oracle integrates in about target_s seconds on all host
+    cores (calibrated on a small prefix)."""
+    n0 = 64 if (w["p"] or 7) >= 6 else 256
+    rate, _, _, _ = cpu_oracle_rate(w, None, n0, per_qp)
+    return int(max(n0, min(len(w["geom"]), rate * target_s)))
+
+
+def cpu_oracle_rate(w, p_or_degree, n_sample, per_qp):
+    """Oracle (FP64 C, all host cores) on the first n_sample elements."""
+    import oracle
+    n = min(n_sample, len(w["geom"]))
+    sl = slice(0, n)
+    degree = None if w["p"] is not None else w["degree"][:n]
+    p = w["p"]
+    if per_qp:
+        q = nq(p)
+        K, b, c, f = w["K"][: n * q], w["b"][: n * q], w["c"][: n * q], w["f"][: n * q]
+    else:
+        K, b, c, f = w["K"][sl], w["b"][sl], w["c"][sl], w["f"][sl]
+    oracle.build()
+    cores = len(os.sched_getaffinity(0))
+    t0 = time.perf_counter()
+    oracle.integrate(w["geom"][sl], K, b, c, f, p=p, degree=degree, per_qp=per_qp, nthreads=cores)
+    dt = time.perf_counter() - t0
+    return n / dt, cores, n, dt
+
+
+def run_reference(args, world, rank):
+    """Reference arm: the FP64 oracle on the host cores, on a bounded sample
+    of the same workload per step."""
+    if rank != 0:
+        return
+    w = inputs.workload(args.workload)
+    per_qp = bool(w["per_qp"])
+    n_sample = args.cpu_sample or cpu_sample_size(w, per_qp, max(1.0, 60.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        cpu_oracle_rate(w, None, max(64, n_sample // 8), per_qp)
+    rates, times = [], []
+    cores = None
+    for _ in range(args.steps):
+        r, cores, n, dt = cpu_oracle_rate(w, None, n_sample, per_qp)
+        rates.append(r)
+        times.append(dt)
+    value = statistics.median(rates)
+    line = {
+        "impl": "reference", "metric": metric_name(args), "value": value, "unit": "elements/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * statistics.median(times), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_TEXT[args.workload], "precision": "fp64 CPU oracle"},
+        "cpu_baseline": {"value": value, "unit": "elements/s", "cores": cores, "kind": "oracle",
+                         "sample": f"first {n_sample} elements of the workload per step"},
+        "e2e": {"value": value, "unit": "elements/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def metric_name(args):
+    return f"elements/s ({args.workload}), at rel. error <= 1e-6 vs the FP64 oracle"
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="p4", choices=sorted(WORKLOAD_TEXT))
+    ap.add_argument("--precision", default=None)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--cpu-sample", type=int, default=0, help="elements; 0 = about --cpu-seconds of work")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    import torch
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    from paper_1310_1194_gb300 import api, _lib
+
+    w = inputs.workload(args.workload)
+    per_qp = bool(w["per_qp"])
+    dev = torch.device("cuda", local)
+    g = {k: torch.from_numpy(np.ascontiguousarray(w[k])).to(dev) for k in ("geom", "K", "b", "c", "f")}
+    deg = None if w["p"] is not None else torch.from_numpy(w["degree"]).to(dev)
+    p = w["p"]
+    n = g["geom"].shape[0]
+
+    precision = args.precision
+    if precision is None:
+        precision = "tc_f16x3"
+        try:
+            api.fei_integrate(g["geom"][:1], g["K"][: (nq(p) if per_qp else 1)], g["b"][: (nq(p) if per_qp else 1)],
+                              g["c"][: (nq(p) if per_qp else 1)], g["f"][: (nq(p) if per_qp else 1)],
+                              p=p if p is not None else 3, precision=precision)
+        except _lib.FeiError:
+            precision = "fp32"
+    layout = api.fei_plan_offsets(deg) if deg is not None else api.uniform_layout(n, p)
+    refs = [api.fei_reference_create(d) for d in ([p] if p is not None else range(1, 8))]
+    out_dtype = torch.float64 if precision == "fp64" else torch.float32
+    A = torch.empty(layout.A_total, dtype=out_dtype, device=dev)
+    bv = torch.empty(layout.b_total, dtype=out_dtype, device=dev)
+    st = torch.empty(n, dtype=torch.int32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > L2
+    stream = torch.cuda.current_stream()
+
+    def step(prec=precision, outs=(A, bv, st)):
+        api.fei_integrate(g["geom"], g["K"], g["b"], g["c"], g["f"], p=p, degree=deg, per_qp=per_qp,
+                          precision=prec, refs=refs, layout=layout, out=outs)
+
+    launches_per_step = 1 if deg is None else 2 + len(refs)  # memset is not a kernel; bucket + per degree
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    for k in range(args.steps):
+        flush.fill_(float(k))  # evict L2 between steps (outside the events)
+        evs[k][0].record(stream)
+        step()
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    ms = sum(step_ms) / len(step_ms)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * n / (ms * 1e-3)
+
+    # algorithmic flops / bytes of one step
+    degs = np.full(n, p) if p is not None else w["degree"]
+    counts = np.bincount(degs, minlength=8)
+    out_b = 8 if precision == "fp64" else 4
+    F = sum(int(counts[d]) * flops_per_element(d) for d in range(1, 8))
+    Bts = sum(int(counts[d]) * bytes_per_element(d, out_b, per_qp) for d in range(1, 8))
+    peaks, peak_src = load_peaks()
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    if precision == "tc_f16x3":
+        bound, peak, unit, achieved = "tensor", peaks["bf16_tflops"], "TFLOP/s", F / (ms * 1e-3) / 1e12
+        peak_note = f"bf16/fp16 dense, {peak_src}"
+    elif precision == "fp32":
+        peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12
+        bound, unit, achieved = "alu", "TFLOP/s", F / (ms * 1e-3) / 1e12
+        peak_note = "FP32 FMA: 152 SMs x 128 lanes x 2 flops x max SM clock"
+    else:
+        peak = 152 * 2 * 2 * sm_max * 1e6 / 1e12
+        bound, unit, achieved = "alu", "TFLOP/s", F / (ms * 1e-3) / 1e12
+        peak_note = "FP64 FMA: 152 SMs x 2 DFMA/clk x 2 flops x max SM clock"
+    roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
+                "traffic": None, "peak_source": peak_note,
+                "hbm_gbs_achieved": Bts / (ms * 1e-3) / 1e9, "hbm_frac": Bts / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"]}
+
+    # accuracy of this path against the FP64 GPU path on sampled elements,
+    # and the FP64 GPU path's own throughput (the comparison the metric asks for)
+    fp64 = None
+    rel_err = None
+    if precision != "fp64" and rank == 0:
+        A64 = torch.empty(layout.A_total, dtype=torch.float64, device=dev)
+        b64 = torch.empty(layout.b_total, dtype=torch.float64, device=dev)
+        st64 = torch.empty(n, dtype=torch.int32, device=dev)
+        step("fp64", (A64, b64, st64))
+        torch.cuda.synchronize()
+        t64 = []
+        for _ in range(args.fp64_steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            flush.fill_(1.0)
+            e0.record(stream)
+            step("fp64", (A64, b64, st64))
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t64.append(e0.elapsed_time(e1))
+        fp64 = {"elements_per_s": n / (statistics.median(t64) * 1e-3), "ms_per_step": statistics.median(t64)}
+        step()
+        torch.cuda.synchronize()
+        Aoff = layout.A_offset.cpu().numpy() if layout.A_offset is not None else None
+        errs = []
+        for e in np.linspace(0, n - 1, 64).astype(np.int64):
+            d = int(degs[e])
+            s2 = nsh(d) ** 2
+            o = int(Aoff[e]) if Aoff is not None else int(e) * s2
+            x = A[o:o + s2].double()
+            y = A64[o:o + s2]
+            errs.append(float(torch.linalg.norm(x - y) / torch.linalg.norm(y)))
+        rel_err = max(errs)
+        del A64, b64, st64
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        hin = {k: torch.from_numpy(np.ascontiguousarray(w[k])).pin_memory() for k in ("geom", "K", "b", "c", "f")}
+        hA = torch.empty(layout.A_total, dtype=out_dtype).pin_memory()
+        hb = torch.empty(layout.b_total, dtype=out_dtype).pin_memory()
+        h2d = sum(t.numel() * t.element_size() for t in hin.values())
+        d2h = hA.numel() * hA.element_size() + hb.numel() * hb.element_size()
+        e2e_steps = max(2, min(args.steps, 5))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            for k in hin:
+                g[k].copy_(hin[k], non_blocking=True)
+            step()
+            hA.copy_(A, non_blocking=True)
+            hb.copy_(bv, non_blocking=True)
+            torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / e2e_steps
+        e2e = {"value": world * n / dt, "unit": "elements/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": dt * 1e3}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        n_sample = args.cpu_sample or cpu_sample_size(w, per_qp, args.cpu_seconds)
+        rate, cores, ns, dt = cpu_oracle_rate(w, None, n_sample, per_qp)
+        cpu = {"value": rate, "unit": "elements/s", "cores": cores, "kind": "oracle",
+               "sample": f"first {ns} elements of the workload ({dt:.1f} s on the host cores)"}
+
+    if rank == 0:
+        line = {
+            "metric": metric_name(args), "value": value, "unit": "elements/s", "n_gpus": world,
+            "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp64": "f64", "fp32": "f32", "tc_f16x3": "f16x3->f32"}[precision],
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD_TEXT[args.workload], "precision": precision,
+                       "l2": "256 MB buffer written between timed steps (outside the events); "
+                             "each step also writes its outputs (> L2)",
+                       "gflops_algorithmic": F / (ms * 1e-3) / 1e9,
+                       "rel_err_vs_fp64_path_max_of_64_sampled": rel_err},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches_per_step * args.steps, "clocks": clk,
+            "fp64_path": fp64,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,194 @@
+/*
+ * fei.h -- C ABI of the GB300 element-integration library (libfei.so).
+ *
+ * The library computes, for a batch of bilinear prismatic finite elements of
+ * degree p = 1..7, the element stiffness matrices and load vectors of the
+ * weak form
+ *
+ *     a(u, v) = int  grad v . K grad u  +  v b . grad u  +  c u v,
+ *     l(v)    = int  f v,
+ *
+ * by the standard quadrature of Sec. 2 (Eq. wzor1 generalised, Eq. wzor2):
+ *
+ *     A_e[i][j] = sum_q w_q det J(xi_q) ( grad phi_i . K_q grad phi_j
+ *                                        + phi_i b_q . grad phi_j
+ *                                        + c_q phi_i phi_j )
+ *     b_e[i]    = sum_q w_q det J(xi_q) f_q phi_i
+ *
+ * i = test function (row), j = trial function (column), grad phi = J^{-T}
+ * grad_ref phi.  Basis: orthonormal Dubiner triangle polynomials times
+ * normalised Legendre polynomials in zeta (Table 1: N_sh = (p+1)^2 (p+2)/2),
+ * index = k * (p+1)(p+2)/2 + t, k the zeta degree, t over triangle total
+ * degree d = m + n ascending then n ascending.  Quadrature: Duffy-collapsed
+ * Gauss-Legendre with (p+1)^3 points, point q = (iz*(p+1) + iv)*(p+1) + iu,
+ * xi1 = (1+u)(1-v)/4, xi2 = (1+v)/2, zeta = z, w = w_u w_v (1-v)/8 w_z.
+ * Reference prism: {xi1, xi2 >= 0, xi1 + xi2 <= 1} x [-1, 1].  Geometry
+ * (Sec. 4, bilinear prism): vertices 0, 1, 2 span the bottom triangle at
+ * zeta = -1 (counter-clockwise seen from the top), vertex a+3 lies above a.
+ *
+ * Conventions for every entry point:
+ *  - "device" pointers are CUDA device (or managed) memory of the current
+ *    device; "host" pointers are ordinary host memory.
+ *  - All work is enqueued on the given stream (NULL = legacy default stream)
+ *    and is asynchronous unless stated; a return of FEI_OK only means the
+ *    work was enqueued.
+ *  - The caller owns every buffer it passes; the library never frees them
+ *    and keeps no pointer to them after the call returns.
+ *  - Failures return a status code; fei_last_error_string() (thread-local)
+ *    describes the last failure of the calling thread.  Nothing in the
+ *    library aborts the process or traps on the GPU.
+ */
+#ifndef FEI_H_
+#define FEI_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same object as cudaStream_t. */
+typedef struct CUstream_st *fei_stream_t;
+
+typedef enum {
+  FEI_OK = 0,
+  FEI_ERR_INVALID_ARG = 1,       /* null pointer, bad size, bad enum      */
+  FEI_ERR_INVALID_DEGREE = 2,    /* p outside 1..7, or no reference for p */
+  FEI_ERR_NEGATIVE_JACOBIAN = 3, /* per element: det J <= 0 at a point    */
+  FEI_ERR_NONFINITE = 4,         /* per element: NaN/Inf input or det J   */
+  FEI_ERR_CUDA = 5,              /* a CUDA runtime call failed            */
+  FEI_ERR_TIMEOUT = 6,           /* a bounded device wait gave up         */
+  FEI_ERR_UNSUPPORTED = 7,       /* combination not implemented           */
+  FEI_ERR_OOM = 8                /* device allocation failed              */
+} fei_status;
+
+typedef enum {
+  /* Everything in FP64 on the CUDA cores: the plain FP64 GPU path. */
+  FEI_FP64 = 0,
+  /* FP64 Jacobian columns and w det J; FP32 point operator, FP32
+   * contraction on the CUDA cores.  Output FP32. */
+  FEI_FP32 = 1,
+  /* As FEI_FP32 for the geometry and point operator; the contraction runs
+   * on the tcgen05 tensor cores with each operand split into fp16 hi + lo
+   * (3 products: hi*hi + hi*lo + lo*hi) and FP32 accumulation in TMEM.
+   * Degrees 1 and 2 fall back to the FEI_FP32 kernels.  Output FP32. */
+  FEI_TC_F16X3 = 2
+} fei_precision;
+
+typedef enum {
+  FEI_COEF_PER_ELEMENT = 0, /* one (K, b, c, f) record per element        */
+  FEI_COEF_PER_POINT = 1    /* one record per quadrature point            */
+} fei_coef_mode;
+
+/* Opaque per-degree reference data (quadrature, basis tables, tensor-core
+ * operand images), resident on the device where it was created. */
+typedef struct fei_reference *fei_reference_t;
+
+/* A batch of elements.  All pointers are device pointers.
+ *  geom      double [n_elem][6][3]  vertex coordinates (layout above).
+ *  degree    int32  [n_elem] per-element degree, or NULL: every element has
+ *            degree uniform_degree.
+ *  coef_mode fei_coef_mode.
+ *  K, b, c, f  double [n_rec][3][3], [n_rec][3], [n_rec], [n_rec]; n_rec =
+ *            n_elem (per element) or the total number of points (per point,
+ *            element e's records start at q_offset[e], point order as above).
+ *            K is used as given (row k, column l multiplies d/dx_l of the
+ *            trial function in the k-th component); it need not be symmetric.
+ *  A_offset, b_offset, q_offset  int64 [n_elem + 1] start of element e in
+ *            A_out (scalars), b_out, and the per-point records; NULL means
+ *            the contiguous layout of a uniform degree (e*N_sh^2, e*N_sh,
+ *            e*N_q).  Required when degree != NULL (see fei_plan_offsets). */
+typedef struct {
+  int64_t n_elem;
+  const double *geom;
+  const int32_t *degree;
+  int32_t uniform_degree;
+  int32_t coef_mode;
+  const double *K;
+  const double *b;
+  const double *c;
+  const double *f;
+  const int64_t *A_offset;
+  const int64_t *b_offset;
+  const int64_t *q_offset;
+} fei_batch;
+
+/* Gradient outputs of fei_integrate_backward, same layouts as the inputs
+ * (device pointers, all required). */
+typedef struct {
+  double *K;
+  double *b;
+  double *c;
+  double *f;
+} fei_coef_grad;
+
+/* --------------------------------------------------------------------- */
+
+/* Tabulate the reference data of degree p (Sec. 2.2: quadrature data and
+ * shape functions are the same for every element of one type and degree,
+ * so they are computed once and kept in fast memory; Table 3 sizes).
+ * Runs FP64 kernels on the current device and waits for them.
+ * p outside 1..7 -> FEI_ERR_INVALID_DEGREE; out == NULL -> INVALID_ARG.
+ * The handle is owned by the caller and released with
+ * fei_reference_destroy; it may be shared by threads for reading. */
+fei_status fei_reference_create(int p, fei_reference_t *out);
+fei_status fei_reference_destroy(fei_reference_t ref);
+/* Query degree, N_sh and N_q of a handle (host pointers, any may be NULL). */
+fei_status fei_reference_info(fei_reference_t ref, int *p, int *nsh, int *nq);
+/* Copy the FP64 reference table to host memory (Table 3 rows 1-2 and 4):
+ * pts [N_q][4] = (xi1, xi2, zeta, w), G [N_q][4][N_sh] = phi, dphi/dxi1,
+ * dphi/dxi2, dphi/dzeta.  Either pointer may be NULL.  Synchronous. */
+fei_status fei_reference_copy_table(fei_reference_t ref, double *pts, double *G);
+
+/* Forward integration (Algorithm 1; the loops over points and shape
+ * functions of Sec. 2.1 run in the kernels).
+ *  refs/nrefs  host array of handles; the one whose degree matches each
+ *              element is used (INVALID_DEGREE if one is missing).
+ *  batch       host pointer to the batch description (device data).
+ *  A_out       device [sum N_sh^2] output, FP64 for FEI_FP64, FP32 else,
+ *              row-major A_e (row i = test function) at A_offset[e].
+ *  b_out       device [sum N_sh] output, same precision, at b_offset[e].
+ *  elem_status device int32 [n_elem] (required): 0, or
+ *              FEI_ERR_NEGATIVE_JACOBIAN / FEI_ERR_NONFINITE for an element
+ *              whose outputs are then zero (NONFINITE takes precedence).
+ * Uniform-degree batches use no scratch memory.  A batch with a degree
+ * array needs a bucketing workspace, which this call allocates on first
+ * use per device and keeps; use a plan (below) to allocate up front. */
+fei_status fei_integrate(const fei_reference_t *refs, int nrefs,
+                         const fei_batch *batch, fei_precision prec,
+                         void *A_out, void *b_out, int32_t *elem_status,
+                         fei_stream_t stream);
+
+/* Reverse pass: given gA (same layout/precision as A_out) and gb, writes
+ * (overwrites) the gradient of L = <gA, A> + <gb, b> with respect to the
+ * vertex coordinates g_geom [n_elem][6][3] (FP64) and the coefficients
+ * (g_coef, same layout and mode as the inputs, FP64).  Per-point
+ * coefficient values are held fixed when differentiating by the geometry.
+ * Jacobians are recomputed, not stored.  Precision FEI_FP64 or FEI_FP32
+ * (the contraction W = gA G^T in FP64 or FP32; the Jacobian chain in FP64).
+ * Elements with a nonzero elem_status from the forward get zero gradients
+ * (this call recomputes the status itself). */
+fei_status fei_integrate_backward(const fei_reference_t *refs, int nrefs,
+                                  const fei_batch *batch, fei_precision prec,
+                                  const void *gA, const void *gb,
+                                  double *g_geom, const fei_coef_grad *g_coef,
+                                  fei_stream_t stream);
+
+/* Contiguous offsets for a degree array (device pointers): A_offset,
+ * b_offset, q_offset [n_elem + 1] (any may be NULL).  Also validates the
+ * degrees: an element with p outside 1..7 sets *bad_count (device int32,
+ * may be NULL) nonzero.  Runs on the stream, asynchronous. */
+fei_status fei_plan_offsets(const int32_t *degree, int64_t n_elem,
+                            int64_t *A_offset, int64_t *b_offset,
+                            int64_t *q_offset, int32_t *bad_count,
+                            fei_stream_t stream);
+
+/* Thread-local description of the last failure of the calling thread. */
+const char *fei_last_error_string(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FEI_H_ */

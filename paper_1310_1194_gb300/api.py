@@ -1,0 +1,239 @@
+"""Python binding with the C ABI's names (include/fei.h).
+
+PyTorch provides device memory and the current CUDA stream; every step of
+the integration runs in libfei's kernels.  All tensors are CUDA tensors on
+the current device; inputs are FP64 and contiguous.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import torch
+
+from . import _lib
+from ._lib import check, lib
+
+
+def nsh(p: int) -> int:
+    return (p + 1) * (p + 1) * (p + 2) // 2
+
+
+def nq(p: int) -> int:
+    return (p + 1) ** 3
+
+
+class Reference:
+    """Owning wrapper of a fei_reference_t (reference data of degree p)."""
+
+    def __init__(self, p: int):
+        h = ctypes.c_void_p()
+        check(lib.fei_reference_create(int(p), ctypes.byref(h)), "fei_reference_create")
+        self.handle = h
+        self.p = int(p)
+        self.nsh = nsh(p)
+        self.nq = nq(p)
+        self.device = torch.cuda.current_device()
+
+    def table(self):
+        """(pts [N_q, 4], G [N_q, 4, N_sh]) as FP64 host tensors."""
+        pts = torch.zeros(self.nq, 4, dtype=torch.float64)
+        G = torch.zeros(self.nq, 4, self.nsh, dtype=torch.float64)
+        check(lib.fei_reference_copy_table(self.handle, pts.data_ptr(), G.data_ptr()),
+              "fei_reference_copy_table")
+        return pts, G
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            lib.fei_reference_destroy(h)
+            self.handle = None
+
+
+_ref_cache: dict[tuple[int, int], Reference] = {}
+
+
+def fei_reference_create(p: int) -> Reference:
+    """Reference data of degree p on the current device (cached per device)."""
+    key = (torch.cuda.current_device(), int(p))
+    r = _ref_cache.get(key)
+    if r is None:
+        r = Reference(p)
+        _ref_cache[key] = r
+    return r
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _need(t, name, dtype=torch.float64):
+    if t is None:
+        raise ValueError(f"{name} is required")
+    if not t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous CUDA {dtype} tensor")
+    return t
+
+
+@dataclass
+class Layout:
+    """Output layout of a batch: per-element offsets (device int64 [n+1],
+    or None for the contiguous uniform-degree layout) and total sizes."""
+    A_offset: torch.Tensor | None
+    b_offset: torch.Tensor | None
+    q_offset: torch.Tensor | None
+    A_total: int
+    b_total: int
+    q_total: int
+
+
+def fei_plan_offsets(degree: torch.Tensor) -> Layout:
+    """Contiguous offsets of a degree array (computed by a kernel)."""
+    degree = _need(degree, "degree", torch.int32)
+    n = degree.numel()
+    dev = degree.device
+    Ao = torch.empty(n + 1, dtype=torch.int64, device=dev)
+    bo = torch.empty(n + 1, dtype=torch.int64, device=dev)
+    qo = torch.empty(n + 1, dtype=torch.int64, device=dev)
+    bad = torch.zeros(1, dtype=torch.int32, device=dev)
+    check(lib.fei_plan_offsets(_ptr(degree), n, _ptr(Ao), _ptr(bo), _ptr(qo), _ptr(bad), _stream()),
+          "fei_plan_offsets")
+    tail = torch.stack([Ao[-1], bo[-1], qo[-1], bad[0].to(torch.int64)]).cpu().tolist()
+    if tail[3]:
+        raise ValueError(f"{tail[3]} elements have a degree outside 1..7")
+    return Layout(Ao, bo, qo, int(tail[0]), int(tail[1]), int(tail[2]))
+
+
+def uniform_layout(n: int, p: int) -> Layout:
+    s = nsh(p)
+    return Layout(None, None, None, n * s * s, n * s, n * nq(p))
+
+
+def _batch(geom, K, b, c, f, degree, p, per_qp, layout):
+    n = geom.shape[0]
+    bt = _lib.fei_batch()
+    bt.n_elem = n
+    bt.geom = geom.data_ptr()
+    bt.degree = degree.data_ptr() if degree is not None else None
+    bt.uniform_degree = int(p) if p is not None else 0
+    bt.coef_mode = _lib.FEI_COEF_PER_POINT if per_qp else _lib.FEI_COEF_PER_ELEMENT
+    bt.K = K.data_ptr()
+    bt.b = b.data_ptr()
+    bt.c = c.data_ptr()
+    bt.f = f.data_ptr()
+    bt.A_offset = layout.A_offset.data_ptr() if layout.A_offset is not None else None
+    bt.b_offset = layout.b_offset.data_ptr() if layout.b_offset is not None else None
+    bt.q_offset = layout.q_offset.data_ptr() if layout.q_offset is not None else None
+    return bt
+
+
+def _refs_array(refs):
+    arr = (ctypes.c_void_p * len(refs))(*[r.handle.value for r in refs])
+    return arr
+
+
+def _inputs(geom, K, b, c, f, degree, p, per_qp, layout):
+    geom = _need(geom, "geom")
+    if geom.dim() != 3 or geom.shape[1:] != (6, 3):
+        raise ValueError("geom must be [n, 6, 3]")
+    for t, name in ((K, "K"), (b, "b"), (c, "c"), (f, "f")):
+        _need(t, name)
+    if degree is not None:
+        _need(degree, "degree", torch.int32)
+        if layout is None:
+            layout = fei_plan_offsets(degree)
+    else:
+        if p is None:
+            raise ValueError("give p or degree")
+        if layout is None:
+            layout = uniform_layout(geom.shape[0], p)
+    return geom, layout
+
+
+def fei_integrate(geom, K, b, c, f, p=None, degree=None, per_qp=False, precision="fp32",
+                  refs=None, layout=None, out=None):
+    """Element matrices and load vectors (forward, Algorithm 1).
+
+    Returns (A, b_vec, status, layout): A [A_total] and b_vec [b_total] in
+    FP64 for precision "fp64" and FP32 otherwise, laid out by ``layout``;
+    status int32 [n]."""
+    geom, layout = _inputs(geom, K, b, c, f, degree, p, per_qp, layout)
+    prec = _lib.PRECISIONS[precision]
+    dtype = torch.float64 if prec == _lib.FEI_FP64 else torch.float32
+    n = geom.shape[0]
+    if refs is None:
+        degs = [int(p)] if degree is None else list(range(1, 8))
+        refs = [fei_reference_create(d) for d in degs]
+    if out is None:
+        A = torch.empty(layout.A_total, dtype=dtype, device=geom.device)
+        bv = torch.empty(layout.b_total, dtype=dtype, device=geom.device)
+        st = torch.empty(n, dtype=torch.int32, device=geom.device)
+    else:
+        A, bv, st = out
+    bt = _batch(geom, K, b, c, f, degree, p, per_qp, layout)
+    check(lib.fei_integrate(_refs_array(refs), len(refs), ctypes.byref(bt), prec,
+                            _ptr(A), _ptr(bv), _ptr(st), _stream()), "fei_integrate")
+    return A, bv, st, layout
+
+
+def fei_integrate_backward(geom, K, b, c, f, gA, gb, p=None, degree=None, per_qp=False,
+                           precision="fp64", refs=None, layout=None):
+    """Gradients of <gA, A> + <gb, b>: (g_geom, gK, gb_coef, gc, gf), FP64."""
+    geom, layout = _inputs(geom, K, b, c, f, degree, p, per_qp, layout)
+    prec = _lib.PRECISIONS[precision]
+    dtype = torch.float64 if prec == _lib.FEI_FP64 else torch.float32
+    _need(gA, "gA", dtype)
+    _need(gb, "gb", dtype)
+    if refs is None:
+        degs = [int(p)] if degree is None else list(range(1, 8))
+        refs = [fei_reference_create(d) for d in degs]
+    g_geom = torch.empty_like(geom)
+    gK = torch.empty_like(K)
+    gbc = torch.empty_like(b)
+    gc = torch.empty_like(c)
+    gf = torch.empty_like(f)
+    cg = _lib.fei_coef_grad(gK.data_ptr(), gbc.data_ptr(), gc.data_ptr(), gf.data_ptr())
+    bt = _batch(geom, K, b, c, f, degree, p, per_qp, layout)
+    check(lib.fei_integrate_backward(_refs_array(refs), len(refs), ctypes.byref(bt), prec,
+                                     _ptr(gA), _ptr(gb), _ptr(g_geom), ctypes.byref(cg), _stream()),
+          "fei_integrate_backward")
+    return g_geom, gK, gbc, gc, gf
+
+
+class _IntegrateFn(torch.autograd.Function):
+    """A, b = integrate(geom, K, b, c, f) with the library's adjoint kernel
+    as the backward; the Jacobians are recomputed in the backward."""
+
+    @staticmethod
+    def forward(ctx, geom, K, bc, c, f, p, degree, per_qp, precision, layout):
+        A, bv, st, layout = fei_integrate(geom, K, bc, c, f, p=p, degree=degree, per_qp=per_qp,
+                                          precision=precision, layout=layout)
+        ctx.save_for_backward(geom, K, bc, c, f)
+        ctx.cfg = (p, degree, per_qp, precision, layout)
+        ctx.mark_non_differentiable(st)
+        return A, bv, st
+
+    @staticmethod
+    def backward(ctx, gA, gb, _gst):
+        geom, K, bc, c, f = ctx.saved_tensors
+        p, degree, per_qp, precision, layout = ctx.cfg
+        bprec = "fp64" if precision == "fp64" else "fp32"
+        dt = torch.float64 if bprec == "fp64" else torch.float32
+        gA = torch.zeros(layout.A_total, dtype=dt, device=geom.device) if gA is None else gA.to(dt).contiguous()
+        gb = torch.zeros(layout.b_total, dtype=dt, device=geom.device) if gb is None else gb.to(dt).contiguous()
+        g = fei_integrate_backward(geom, K, bc, c, f, gA, gb, p=p, degree=degree, per_qp=per_qp,
+                                   precision=bprec, layout=layout)
+        return (*g, None, None, None, None, None)
+
+
+def integrate(geom, K, b, c, f, p=None, degree=None, per_qp=False, precision="fp32", layout=None):
+    """Differentiable element integration: returns (A, b_vec, status)."""
+    if degree is not None and layout is None:
+        layout = fei_plan_offsets(degree)
+    if degree is None and layout is None:
+        layout = uniform_layout(geom.shape[0], p)
+    return _IntegrateFn.apply(geom, K, b, c, f, p, degree, per_qp, precision, layout)

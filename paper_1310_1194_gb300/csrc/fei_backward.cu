@@ -1,0 +1,400 @@
+// fei_backward.cu -- reverse pass of the element integration.
+//
+// L = <gA, A> + <gb, b>.  With A_e = sum_q G_q^T Dt_q G_q (fei_geom.cuh):
+//   dL/dDt_q[a][b] = (G_q gA G_q^T)[a][b] = sum_i G[q][a][i] W[i][(q,b)],
+//   W = gA G^T  (N_sh x 4 N_q, the same contraction size as the forward),
+//   dL/d(w det J f)_q = sum_i gb_i phi_i(q).
+// The Jacobian is recomputed at every point (never stored) and the chain
+// from dL/dDt to the coefficients, to the adjugate rows and det J, to the
+// Jacobian columns c1, c2, c3, to the element vectors and finally to the 18
+// vertex coordinates runs in FP64:
+//   Dt00 = w det c, Dt0l = w adj_l.b, Dt_lm = (w/det) adj_l K adj_m^T,
+//   adj_0 = c2 x c3, adj_1 = c3 x c1, adj_2 = c1 x c2, det = adj_2 . c3,
+//   c1 = A1 + zeta B1, c2 = A2 + zeta B2, c3 = C + xi1 D1 + xi2 D2.
+// One thread block per element; rows of gA are processed in blocks of 32 and
+// points in chunks of 8, with dL/dDt accumulated in shared memory.
+#include <type_traits>
+
+#include "fei_geom.cuh"
+#include "fei_internal.cuh"
+
+namespace fei {
+namespace {
+
+template <typename T>
+__device__ __forceinline__ const T *gtab_b(const BwdArgs &a);
+template <>
+__device__ __forceinline__ const double *gtab_b<double>(const BwdArgs &a) { return a.G64; }
+template <>
+__device__ __forceinline__ const float *gtab_b<float>(const BwdArgs &a) { return a.G32; }
+
+template <typename T, int P>
+struct BwdCfg {
+  static constexpr int NSH = nsh_of(P), NQ = nq_of(P), NZ = P + 1, NT = (P + 1) * (P + 1);
+  static constexpr int BI = 32, QC = 8, KC = 4 * QC;
+  static constexpr int NRB = (NSH + BI - 1) / BI;
+  // dynamic shared memory layout (bytes)
+  static constexpr size_t OFF_GA = 0;                                        // T [BI][NSH]
+  static constexpr size_t OFF_GC = OFF_GA + sizeof(T) * BI * NSH;            // T [KC][NSH]
+  static constexpr size_t OFF_W = OFF_GC + sizeof(T) * KC * NSH;             // T [BI][KC]
+  static constexpr size_t OFF_GD = OFF_W + sizeof(T) * BI * KC;              // T [NQ][16]
+  static constexpr size_t OFF_GSF = OFF_GD + sizeof(T) * NQ * 16;            // T [NQ]
+  static constexpr size_t OFF_END = ((OFF_GSF + sizeof(T) * NQ + 15) / 16) * 16;
+  static constexpr size_t SMEM = OFF_END;
+};
+
+struct BwdStatic {
+  double X[18];
+  double ev[21];
+  double cd[14];
+  double zc1[8][3], zc2[8][3], zn3[8][3], zz[8], zw[8];
+  double tc3[64][3], txi[64][2], tw[64];
+  double gev[21];   // gradient of the element vectors
+  double gcoef[14]; // per-element coefficient gradient
+  int status;
+};
+
+__device__ __forceinline__ bool load_coef_b(const BwdArgs &a, int64_t r, double *cd) {
+  bool ok = true;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    cd[k] = a.K[9 * r + k];
+    ok &= isfinite(cd[k]);
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    cd[9 + k] = a.b[3 * r + k];
+    ok &= isfinite(cd[9 + k]);
+  }
+  cd[12] = a.c[r];
+  cd[13] = a.f[r];
+  ok &= isfinite(cd[12]) && isfinite(cd[13]);
+  return ok;
+}
+
+template <typename T, int P>
+__global__ void __launch_bounds__(256) cc_backward_kernel(BwdArgs a) {
+  using C = BwdCfg<T, P>;
+  constexpr int NSH = C::NSH, NQ = C::NQ, NT = C::NT, BI = C::BI, QC = C::QC, KC = C::KC;
+  extern __shared__ __align__(16) unsigned char dsm[];
+  __shared__ BwdStatic sm;
+  T *gAs = reinterpret_cast<T *>(dsm + C::OFF_GA);
+  T *Gc = reinterpret_cast<T *>(dsm + C::OFF_GC);
+  T *Wc = reinterpret_cast<T *>(dsm + C::OFF_W);
+  T *gD = reinterpret_cast<T *>(dsm + C::OFF_GD);
+  T *gsf = reinterpret_cast<T *>(dsm + C::OFF_GSF);
+  const int tid = threadIdx.x;
+  const T *Gg = gtab_b<T>(a);
+  const T *gAg = reinterpret_cast<const T *>(a.gA);
+  const T *gbg = reinterpret_cast<const T *>(a.gb);
+  const int64_t items = a.count ? (int64_t)(*a.count) : a.n_work;
+
+  for (int64_t item = blockIdx.x; item < items; item += gridDim.x) {
+    const int64_t e = a.list ? (int64_t)a.list[item] : item;
+    const int64_t aoff = a.A_off ? a.A_off[e] : e * (int64_t)(NSH * NSH);
+    const int64_t boff = a.b_off ? a.b_off[e] : e * (int64_t)NSH;
+    const int64_t qoff = a.q_off ? a.q_off[e] : e * (int64_t)NQ;
+    if (tid == 0) sm.status = 0;
+    if (tid < 21) sm.gev[tid] = 0.0;
+    if (tid >= 32 && tid < 46) sm.gcoef[tid - 32] = 0.0;
+    __syncthreads();
+    bool ok = true;
+    if (tid < 18) {
+      sm.X[tid] = a.geom[18 * e + tid];
+      ok = isfinite(sm.X[tid]);
+    }
+    if (a.coef_mode == FEI_COEF_PER_ELEMENT && tid == 32) ok = load_coef_b(a, e, sm.cd);
+    if (!ok) sm.status = FEI_ERR_NONFINITE;
+    __syncthreads();
+    if (tid == 0) elem_vectors(sm.X, sm.ev);
+    __syncthreads();
+    if (tid < C::NZ) {
+      const double z = a.znode[2 * tid];
+      znode_columns(sm.ev, z, sm.zc1[tid], sm.zc2[tid], sm.zn3[tid]);
+      sm.zz[tid] = z;
+      sm.zw[tid] = a.znode[2 * tid + 1];
+    } else if (tid >= 32 && tid < 32 + NT) {
+      const int t = tid - 32;
+      const double x1 = a.tnode[4 * t], x2 = a.tnode[4 * t + 1];
+      tnode_column(sm.ev, x1, x2, sm.tc3[t]);
+      sm.txi[t][0] = x1;
+      sm.txi[t][1] = x2;
+      sm.tw[t] = a.tnode[4 * t + 2];
+    }
+    // zero the dL/dDt accumulators; dL/d(w det f) per point
+    for (int k = tid; k < NQ * 16; k += 256) gD[k] = T(0);
+    for (int q = tid; q < NQ; q += 256) {
+      T s = T(0);
+      for (int i = 0; i < NSH; ++i) s += gbg[boff + i] * Gg[(size_t)(4 * q) * NSH + i];
+      gsf[q] = s;
+    }
+    __syncthreads();
+
+    // dL/dDt_q = G_q gA G_q^T, row block by row block
+    for (int r0 = 0; r0 < NSH; r0 += BI) {
+      for (int k = tid; k < BI * NSH; k += 256) {
+        const int ii = k / NSH, j = k - ii * NSH;
+        gAs[k] = (r0 + ii < NSH) ? gAg[aoff + (int64_t)(r0 + ii) * NSH + j] : T(0);
+      }
+      for (int q0 = 0; q0 < NQ; q0 += QC) {
+        for (int k = tid; k < KC * NSH; k += 256) {
+          const int kk = k / NSH, j = k - kk * NSH;
+          const int q = q0 + kk / 4;
+          Gc[k] = (q < NQ) ? Gg[(size_t)(4 * q0 + kk) * NSH + j] : T(0);
+        }
+        __syncthreads();
+        // W[ii][kk] = sum_j gA[r0+ii][j] G[(q0,kk)][j], 2 x 2 outputs per thread
+        {
+          const int ii0 = (tid >> 4) * 2, kk0 = (tid & 15) * 2;
+          T w00 = T(0), w01 = T(0), w10 = T(0), w11 = T(0);
+#pragma unroll 4
+          for (int j = 0; j < NSH; ++j) {
+            const T a0 = gAs[ii0 * NSH + j], a1 = gAs[(ii0 + 1) * NSH + j];
+            const T b0 = Gc[kk0 * NSH + j], b1 = Gc[(kk0 + 1) * NSH + j];
+            w00 += a0 * b0;
+            w01 += a0 * b1;
+            w10 += a1 * b0;
+            w11 += a1 * b1;
+          }
+          Wc[ii0 * KC + kk0] = w00;
+          Wc[ii0 * KC + kk0 + 1] = w01;
+          Wc[(ii0 + 1) * KC + kk0] = w10;
+          Wc[(ii0 + 1) * KC + kk0 + 1] = w11;
+        }
+        __syncthreads();
+        // gD[q][a][b] += sum_ii G[q][a][r0+ii] W[ii][(q,b)]
+        if (tid < QC * 16) {
+          const int qq = tid >> 4, ab = tid & 15, aa = ab >> 2, bb = ab & 3;
+          const int q = q0 + qq;
+          if (q < NQ) {
+            T s = T(0);
+            const int lim = (NSH - r0 < BI) ? NSH - r0 : BI;
+            for (int ii = 0; ii < lim; ++ii) s += Gc[(4 * qq + aa) * NSH + r0 + ii] * Wc[ii * KC + 4 * qq + bb];
+            gD[q * 16 + ab] += s;
+          }
+        }
+        __syncthreads();
+      }
+    }
+
+    // FP64 chain, one thread per point
+    double gev[21];
+#pragma unroll
+    for (int k = 0; k < 21; ++k) gev[k] = 0.0;
+    double gco[14];
+#pragma unroll
+    for (int k = 0; k < 14; ++k) gco[k] = 0.0;
+    int pst = 0;
+    for (int q = tid; q < NQ; q += 256) {
+      const int iz = q / NT, t = q - iz * NT;
+      const double *c1 = sm.zc1[iz], *c2 = sm.zc2[iz], *n3 = sm.zn3[iz], *c3 = sm.tc3[t];
+      const double w = sm.zw[iz] * sm.tw[t];
+      const double det = dot3(n3, c3);
+      pst = merge_status(pst, point_status(w * det));
+      double cq[14];
+      const double *cp = sm.cd;
+      if (a.coef_mode == FEI_COEF_PER_POINT) {
+        if (!load_coef_b(a, qoff + q, cq)) pst = FEI_ERR_NONFINITE;
+        cp = cq;
+      }
+      const double *K = cp, *bvec = cp + 9;
+      const double cc = cp[12], ff = cp[13];
+      double adj[3][3];
+      cross3(c2, c3, adj[0]);
+      cross3(c3, c1, adj[1]);
+      adj[2][0] = n3[0];
+      adj[2][1] = n3[1];
+      adj[2][2] = n3[2];
+      const double gD00 = (double)gD[q * 16 + 0];
+      double gD0[3], gDm[3][3];
+#pragma unroll
+      for (int l = 0; l < 3; ++l) {
+        gD0[l] = (double)gD[q * 16 + 1 + l];
+#pragma unroll
+        for (int m = 0; m < 3; ++m) gDm[l][m] = (double)gD[q * 16 + 4 * (l + 1) + (m + 1)];
+      }
+      const double gs = (double)gsf[q];
+      const double s = w * det, wd = w / det;
+      // coefficient gradients at this point
+      double gKq[9], gbq[3];
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          double acc = 0.0;
+#pragma unroll
+          for (int l = 0; l < 3; ++l)
+#pragma unroll
+            for (int m = 0; m < 3; ++m) acc += gDm[l][m] * adj[l][r] * adj[m][c];
+          gKq[3 * r + c] = wd * acc;
+        }
+#pragma unroll
+      for (int k = 0; k < 3; ++k) gbq[k] = w * (gD0[0] * adj[0][k] + gD0[1] * adj[1][k] + gD0[2] * adj[2][k]);
+      const double gcq = s * gD00, gfq = s * gs;
+      if (a.coef_mode == FEI_COEF_PER_POINT) {
+        const int64_t r = qoff + q;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) a.gK[9 * r + k] = gKq[k];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) a.gbc[3 * r + k] = gbq[k];
+        a.gc[r] = gcq;
+        a.gf[r] = gfq;
+      } else {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) gco[k] += gKq[k];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) gco[9 + k] += gbq[k];
+        gco[12] += gcq;
+        gco[13] += gfq;
+      }
+      // through det J and the adjugate rows
+      double Ka[3][3], Kta[3][3];
+#pragma unroll
+      for (int m = 0; m < 3; ++m)
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+          Ka[m][r] = K[3 * r] * adj[m][0] + K[3 * r + 1] * adj[m][1] + K[3 * r + 2] * adj[m][2];
+          Kta[m][r] = K[r] * adj[m][0] + K[3 + r] * adj[m][1] + K[6 + r] * adj[m][2];
+        }
+      double quad = 0.0;
+#pragma unroll
+      for (int l = 0; l < 3; ++l)
+#pragma unroll
+        for (int m = 0; m < 3; ++m) quad += gDm[l][m] * dot3(adj[l], Ka[m]);
+      const double gdet = w * (cc * gD00 + ff * gs) - wd / det * quad;
+      double gadj[3][3];
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          double acc = w * gD0[r] * bvec[k];
+#pragma unroll
+          for (int m = 0; m < 3; ++m) acc += wd * (gDm[r][m] * Ka[m][k] + gDm[m][r] * Kta[m][k]);
+          gadj[r][k] = acc;
+        }
+      double gc1[3] = {0, 0, 0}, gc2[3] = {0, 0, 0}, gc3[3], tmp[3], gn3[3];
+      cross3(c3, gadj[0], gc2);   // adj0 = c2 x c3
+      cross3(gadj[0], c2, gc3);
+      cross3(c1, gadj[1], tmp);   // adj1 = c3 x c1
+#pragma unroll
+      for (int k = 0; k < 3; ++k) gc3[k] += tmp[k];
+      cross3(gadj[1], c3, gc1);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        gn3[k] = gadj[2][k] + gdet * c3[k];  // adj2 = n3, det = n3 . c3
+        gc3[k] += gdet * n3[k];
+      }
+      cross3(c2, gn3, tmp);       // n3 = c1 x c2
+#pragma unroll
+      for (int k = 0; k < 3; ++k) gc1[k] += tmp[k];
+      cross3(gn3, c1, tmp);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) gc2[k] += tmp[k];
+      const double z = sm.zz[iz], x1 = sm.txi[t][0], x2 = sm.txi[t][1];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        gev[0 + k] += gc1[k];
+        gev[3 + k] += z * gc1[k];
+        gev[6 + k] += gc2[k];
+        gev[9 + k] += z * gc2[k];
+        gev[12 + k] += gc3[k];
+        gev[15 + k] += x1 * gc3[k];
+        gev[18 + k] += x2 * gc3[k];
+      }
+    }
+    if (pst) atomicMax(&sm.status, pst);
+#pragma unroll
+    for (int k = 0; k < 21; ++k) {
+      double v = gev[k];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if ((tid & 31) == 0) atomicAdd(&sm.gev[k], v);
+    }
+    if (a.coef_mode == FEI_COEF_PER_ELEMENT) {
+#pragma unroll
+      for (int k = 0; k < 14; ++k) {
+        double v = gco[k];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((tid & 31) == 0) atomicAdd(&sm.gcoef[k], v);
+      }
+    }
+    __syncthreads();
+    const int st = sm.status;
+    // element vectors -> vertices (transpose of elem_vectors)
+    if (tid < 3) {
+      const int k = tid;
+      const double *g = sm.gev;
+      const double gA1 = g[0 + k], gB1 = g[3 + k], gA2 = g[6 + k], gB2 = g[9 + k];
+      const double gC = g[12 + k], gD1 = g[15 + k], gD2 = g[18 + k];
+      double gP0 = 0.5 * (-gA1 + gB1 - gA2 + gB2 - gC + gD1 + gD2);
+      double gQ0 = 0.5 * (-gA1 - gB1 - gA2 - gB2 + gC - gD1 - gD2);
+      double gP1 = 0.5 * (gA1 - gB1 - gD1);
+      double gQ1 = 0.5 * (gA1 + gB1 + gD1);
+      double gP2 = 0.5 * (gA2 - gB2 - gD2);
+      double gQ2 = 0.5 * (gA2 + gB2 + gD2);
+      double *out = a.g_geom + 18 * e;
+      out[0 + k] = st ? 0.0 : gP0;
+      out[3 + k] = st ? 0.0 : gP1;
+      out[6 + k] = st ? 0.0 : gP2;
+      out[9 + k] = st ? 0.0 : gQ0;
+      out[12 + k] = st ? 0.0 : gQ1;
+      out[15 + k] = st ? 0.0 : gQ2;
+    }
+    if (a.coef_mode == FEI_COEF_PER_ELEMENT && tid >= 32 && tid < 46) {
+      const int k = tid - 32;
+      const double v = st ? 0.0 : sm.gcoef[k];
+      if (k < 9) a.gK[9 * e + k] = v;
+      else if (k < 12) a.gbc[3 * e + (k - 9)] = v;
+      else if (k == 12) a.gc[e] = v;
+      else a.gf[e] = v;
+    }
+    if (a.coef_mode == FEI_COEF_PER_POINT && st) {
+      // flagged element: overwrite the per-point gradients with zeros
+      for (int q = tid; q < NQ; q += 256) {
+        const int64_t r = qoff + q;
+        for (int k = 0; k < 9; ++k) a.gK[9 * r + k] = 0.0;
+        for (int k = 0; k < 3; ++k) a.gbc[3 * r + k] = 0.0;
+        a.gc[r] = 0.0;
+        a.gf[r] = 0.0;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T, int P>
+fei_status launch_bwd(const BwdArgs &a, int64_t grid_work, cudaStream_t s) {
+  using C = BwdCfg<T, P>;
+  FEI_CUDA_TRY(cudaFuncSetAttribute(cc_backward_kernel<T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)C::SMEM),
+               "cudaFuncSetAttribute(cc_backward)");
+  int64_t blocks = grid_work;
+  if (a.count) blocks = blocks < 152 * 4 ? blocks : 152 * 4;
+  if (blocks > 2147483647LL) blocks = 2147483647LL;
+  if (blocks < 1) blocks = 1;
+  cc_backward_kernel<T, P><<<(unsigned)blocks, 256, C::SMEM, s>>>(a);
+  FEI_CUDA_TRY(cudaGetLastError(), "cc_backward_kernel launch");
+  return FEI_OK;
+}
+
+template <typename T>
+fei_status launch_bwd_typed(int p, const BwdArgs &a, int64_t grid_work, cudaStream_t s) {
+  switch (p) {
+    case 1: return launch_bwd<T, 1>(a, grid_work, s);
+    case 2: return launch_bwd<T, 2>(a, grid_work, s);
+    case 3: return launch_bwd<T, 3>(a, grid_work, s);
+    case 4: return launch_bwd<T, 4>(a, grid_work, s);
+    case 5: return launch_bwd<T, 5>(a, grid_work, s);
+    case 6: return launch_bwd<T, 6>(a, grid_work, s);
+    case 7: return launch_bwd<T, 7>(a, grid_work, s);
+  }
+  return set_error(FEI_ERR_INVALID_DEGREE, "degree %d outside 1..7", p);
+}
+
+}  // namespace
+
+fei_status launch_cc_backward(int p, bool fp64, const BwdArgs &a, int64_t grid_work, cudaStream_t s) {
+  if (grid_work <= 0) return FEI_OK;
+  return fp64 ? launch_bwd_typed<double>(p, a, grid_work, s) : launch_bwd_typed<float>(p, a, grid_work, s);
+}
+
+}  // namespace fei

@@ -1,0 +1,116 @@
+// fei_geom.cuh -- geometry of the bilinear prism and the point operator.
+//
+// Geometry (Sec. 4, the geometrically bilinear prism; Algorithm 1 step 7):
+// with bottom vertices P_a = X_a and top vertices Q_a = X_{a+3} (a = 0,1,2),
+//   x(xi, zeta) = sum_a lambda_a(xi) [ (1-zeta)/2 P_a + (1+zeta)/2 Q_a ],
+// the Jacobian columns are
+//   c1 = dx/dxi1  = A1 + zeta B1,      c2 = dx/dxi2 = A2 + zeta B2,
+//   c3 = dx/dzeta = C + xi1 D1 + xi2 D2,
+// A1 = ((P1-P0) + (Q1-Q0))/2, B1 = ((Q1-Q0) - (P1-P0))/2 (same with 2),
+// C = (Q0-P0)/2, D1 = ((Q1-P1) - (Q0-P0))/2, D2 = ((Q2-P2) - (Q0-P0))/2.
+// So c1, c2 depend only on the vertical node and c3 only on the triangle
+// node; det J = (c1 x c2) . c3 and J^{-1} has rows
+//   adj_0 = c2 x c3, adj_1 = c3 x c1, adj_2 = c1 x c2, divided by det J.
+// The element vectors are differences of vertex coordinates and are always
+// formed in FP64 (this is where FP32 would lose the most: |x| ~ 1, h ~ 1/50).
+//
+// Point operator (Eq. wzor2 with the general weak form): with
+// T = blockdiag(1, J^{-T}) and D = [[c, b^T], [0, K]] (row = test
+// component (value, d/dx), column = trial component),
+//   Dt_q = w det J  T^T D T
+//        = [[ w det J c,  w (adj_l . b) ], [ 0, (w/det J) adj_l K adj_m^T ]],
+// and A_e[i][j] = sum_q sum_{a,b} G[q][a][i] Dt_q[a][b] G[q][b][j] with
+// G[q] = (phi, dphi/dxi1, dphi/dxi2, dphi/dzeta).  Layout of Dt in memory:
+//   [0] = Dt00, [1..3] = Dt0l, [4..12] = Dt_lm (row-major l, m),
+//   [13] = w det J f (load-vector weight), [14] = w det J, [15] unused.
+#pragma once
+
+#include <math.h>
+
+#include "fei_internal.cuh"
+
+namespace fei {
+
+__device__ __forceinline__ void elem_vectors(const double *X, double *ev) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const double p0 = X[0 + k], p1 = X[3 + k], p2 = X[6 + k];
+    const double q0 = X[9 + k], q1 = X[12 + k], q2 = X[15 + k];
+    const double e1p = p1 - p0, e1q = q1 - q0, e2p = p2 - p0, e2q = q2 - q0;
+    const double v0 = q0 - p0, v1 = q1 - p1, v2 = q2 - p2;
+    ev[0 + k] = 0.5 * (e1p + e1q);   // A1
+    ev[3 + k] = 0.5 * (e1q - e1p);   // B1
+    ev[6 + k] = 0.5 * (e2p + e2q);   // A2
+    ev[9 + k] = 0.5 * (e2q - e2p);   // B2
+    ev[12 + k] = 0.5 * v0;           // C
+    ev[15 + k] = 0.5 * (v1 - v0);    // D1
+    ev[18 + k] = 0.5 * (v2 - v0);    // D2
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void cross3(const T *a, const T *b, T *r) {
+  r[0] = a[1] * b[2] - a[2] * b[1];
+  r[1] = a[2] * b[0] - a[0] * b[2];
+  r[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+template <typename T>
+__device__ __forceinline__ T dot3(const T *a, const T *b) {
+  return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+
+// Vertical-node quantities: c1, c2 and n3 = c1 x c2 (FP64).
+__device__ __forceinline__ void znode_columns(const double *ev, double z, double *c1, double *c2,
+                                              double *n3) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    c1[k] = fma(z, ev[3 + k], ev[0 + k]);
+    c2[k] = fma(z, ev[9 + k], ev[6 + k]);
+  }
+  cross3(c1, c2, n3);
+}
+
+// Triangle-node quantity: c3 (FP64).
+__device__ __forceinline__ void tnode_column(const double *ev, double xi1, double xi2, double *c3) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) c3[k] = fma(xi2, ev[18 + k], fma(xi1, ev[15 + k], ev[12 + k]));
+}
+
+// Dt from adjugate rows, w, s = w det J and the coefficients, in type T.
+// winv_det = w / det J.
+template <typename T>
+__device__ __forceinline__ void dt_from_adj(const T *a0, const T *a1, const T *a2, T w, T s,
+                                            T winv_det, const T *K, const T *b, T c, T f, T *D) {
+  const T *adj[3] = {a0, a1, a2};
+  D[0] = s * c;
+#pragma unroll
+  for (int l = 0; l < 3; ++l) D[1 + l] = w * dot3(adj[l], b);
+  T Ka[3][3];  // Ka[m] = K adj_m^T
+#pragma unroll
+  for (int m = 0; m < 3; ++m)
+#pragma unroll
+    for (int r = 0; r < 3; ++r) Ka[m][r] = K[3 * r + 0] * adj[m][0] + K[3 * r + 1] * adj[m][1] + K[3 * r + 2] * adj[m][2];
+#pragma unroll
+  for (int l = 0; l < 3; ++l)
+#pragma unroll
+    for (int m = 0; m < 3; ++m) D[4 + 3 * l + m] = winv_det * dot3(adj[l], Ka[m]);
+  D[13] = s * f;
+  D[14] = s;
+  D[15] = T(0);
+}
+
+// Status of one point from s = w det J: 0 ok, 3 det <= 0, 4 non-finite.
+__device__ __forceinline__ int point_status(double s) {
+  if (!isfinite(s)) return FEI_ERR_NONFINITE;
+  if (!(s > 0.0)) return FEI_ERR_NEGATIVE_JACOBIAN;
+  return 0;
+}
+
+__device__ __forceinline__ int merge_status(int a, int b) {
+  // NONFINITE takes precedence over NEGATIVE_JACOBIAN
+  if (a == FEI_ERR_NONFINITE || b == FEI_ERR_NONFINITE) return FEI_ERR_NONFINITE;
+  return a ? a : b;
+}
+
+}  // namespace fei

@@ -1,0 +1,100 @@
+// fei_internal.cuh -- shared declarations of the libfei CUDA sources.
+//
+// Layout of the device reference data of one degree p (N_sh shape
+// functions, N_q = (p+1)^3 points, Sec. 2.2 / Table 3):
+//   pts   double [N_q][4]        (xi1, xi2, zeta, w)
+//   G64   double [N_q][4][N_sh]  row 0 = phi, rows 1..3 = d phi / d(xi1, xi2, zeta)
+//   G32   float  [N_q][4][N_sh]  the same rounded to FP32
+//   znode double [p+1][2]        (zeta, w_zeta)        vertical Gauss nodes
+//   tnode double [(p+1)^2][4]    (xi1, xi2, w_tri, 0)  collapsed triangle nodes
+//   point q = iz * (p+1)^2 + t, t = iv * (p+1) + iu, w_q = w_tri[t] w_zeta[iz].
+//   tcB   uint16 image of the tensor-core B operand (see fei_tc.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/fei.h"
+
+namespace fei {
+
+constexpr int kPMax = 7;
+
+__host__ __device__ constexpr int nsh_of(int p) { return (p + 1) * (p + 1) * (p + 2) / 2; }
+__host__ __device__ constexpr int nq_of(int p) { return (p + 1) * (p + 1) * (p + 1); }
+__host__ __device__ constexpr int ntri_of(int p) { return (p + 1) * (p + 2) / 2; }
+
+struct TcImage;  // tensor-core operand image, fei_tc.cu
+
+}  // namespace fei
+
+struct fei_reference {
+  int p, nsh, nq;
+  int device;
+  double *pts;
+  double *G64;
+  float *G32;
+  double *znode;
+  double *tnode;
+  fei::TcImage *tc;  // null until built (degree >= 3)
+};
+
+namespace fei {
+
+// Arguments of every forward kernel.  A "work item" is one element; with a
+// bucket list the work items are list[0 .. *count) (device count), else
+// elements 0 .. n_work.
+struct FwdArgs {
+  int64_t n_work;
+  const int32_t *count;  // device, or null
+  const int32_t *list;   // device, or null
+  const double *geom;
+  int coef_mode;
+  const double *K, *b, *c, *f;
+  const int64_t *A_off, *b_off, *q_off;
+  void *A;
+  void *bv;
+  int32_t *status;
+  const double *G64;
+  const float *G32;
+  const double *znode;
+  const double *tnode;
+};
+
+struct BwdArgs {
+  int64_t n_work;
+  const int32_t *count;
+  const int32_t *list;
+  const double *geom;
+  int coef_mode;
+  const double *K, *b, *c, *f;
+  const int64_t *A_off, *b_off, *q_off;
+  const void *gA;
+  const void *gb;
+  double *g_geom;
+  double *gK, *gbc, *gc, *gf;
+  const double *G64;
+  const float *G32;
+  const double *znode;
+  const double *tnode;
+};
+
+// Error reporting (fei_api.cu).
+fei_status set_error(fei_status st, const char *fmt, ...);
+fei_status cuda_error(cudaError_t e, const char *what);
+
+// Kernel launchers (each returns FEI_OK or an error already recorded).
+fei_status launch_cc_forward(int p, bool fp64, const FwdArgs &a, int64_t grid_work, cudaStream_t s);
+fei_status launch_cc_backward(int p, bool fp64, const BwdArgs &a, int64_t grid_work, cudaStream_t s);
+fei_status launch_tc_forward(int p, const fei_reference *ref, const FwdArgs &a, int64_t grid_work,
+                             cudaStream_t s);
+fei_status build_tc_image(fei_reference *ref);
+void free_tc_image(fei_reference *ref);
+
+}  // namespace fei
+
+#define FEI_CUDA_TRY(call, what)                               \
+  do {                                                         \
+    cudaError_t e_ = (call);                                   \
+    if (e_ != cudaSuccess) return ::fei::cuda_error(e_, what); \
+  } while (0)

@@ -1,0 +1,57 @@
+"""The C-ABI library builds, loads and exports every declared symbol (CPU
+only: no compute call reaches a GPU here; only argument checks that return
+before any CUDA call are exercised)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "fei.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1310_1194_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(fei_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("fei_reference_create", "fei_reference_destroy", "fei_integrate",
+                 "fei_integrate_backward", "fei_plan_offsets", "fei_last_error_string"):
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_argument_errors_before_any_cuda_call(lib):
+    lib.fei_reference_create.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]
+    lib.fei_last_error_string.restype = ctypes.c_char_p
+    h = ctypes.c_void_p()
+    assert lib.fei_reference_create(0, ctypes.byref(h)) == 2
+    assert b"degree" in lib.fei_last_error_string()
+    assert lib.fei_reference_create(8, ctypes.byref(h)) == 2
+    assert lib.fei_reference_create(3, None) == 1
+    lib.fei_integrate.argtypes = [ctypes.c_void_p] * 2 + [ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 4
+    assert lib.fei_integrate(None, 1, None, 0, None, None, None, None) == 1
+    lib.fei_plan_offsets.argtypes = [ctypes.c_void_p, ctypes.c_int64] + [ctypes.c_void_p] * 5
+    assert lib.fei_plan_offsets(None, 5, None, None, None, None, None) == 1
+    assert lib.fei_reference_destroy(None) == 0
+
+
+def test_python_binding_loads():
+    from paper_1310_1194_gb300 import _lib
+    assert _lib.lib is not None
+    assert _lib.PRECISIONS["fp64"] == 0

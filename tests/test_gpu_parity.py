@@ -1,0 +1,192 @@
+"""CUDA path against the FP64 oracle, element by element, through the C ABI.
+
+Tolerances (relative Frobenius norm per element, max over the batch; load
+vectors by the 2-norm): FP64 path 1e-12, FP32 path 1e-5, split-precision
+tensor-core path 1e-6, gradients 1e-6 (FP32 contraction) / 1e-10 (FP64).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1310_1194_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "fp32": 1e-5, "tc_f16x3": 1e-6}
+# elements per degree: several thread blocks / tiles and a ragged tail
+N_PER_P = {1: 517, 2: 133, 3: 45, 4: 21, 5: 9, 6: 5, 7: 3}
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1310_1194_gb300 import api as a
+    return a
+
+
+def dev(x, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(x))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+def per_elem_err(flat_gpu, flat_ref, offsets, sizes):
+    errs = []
+    for e in range(len(sizes)):
+        o, s = int(offsets[e]), int(sizes[e])
+        a, r = flat_gpu[o:o + s], flat_ref[o:o + s]
+        nr = np.linalg.norm(r)
+        errs.append(np.linalg.norm(a - r) / nr if nr > 0 else np.linalg.norm(a))
+    return np.array(errs)
+
+
+def run_gpu(api, w, p=None, degree=None, precision="fp64", per_qp=False):
+    g = dev(w["geom"])
+    A, bv, st, lay = api.fei_integrate(g, dev(w["K"]), dev(w["b"]), dev(w["c"]), dev(w["f"]),
+                                       p=p, degree=None if degree is None else dev(degree),
+                                       per_qp=per_qp, precision=precision)
+    torch.cuda.synchronize()
+    return A.double().cpu().numpy(), bv.double().cpu().numpy(), st.cpu().numpy()
+
+
+def compare(api, w, p, precision, per_qp=False, degree=None):
+    A, bv, st = run_gpu(api, w, p=p, degree=degree, precision=precision, per_qp=per_qp)
+    Ao, bo, so, (Aoff, boff, _) = oracle.integrate(w["geom"], w["K"], w["b"], w["c"], w["f"],
+                                                  p=p, degree=degree, per_qp=per_qp)
+    assert np.array_equal(st, so), (st[st != so][:5], so[st != so][:5])
+    degs = np.full(len(w["geom"]), p) if degree is None else np.asarray(degree)
+    s = (degs + 1) ** 2 * (degs + 2) // 2
+    ea = per_elem_err(A, Ao, Aoff, s * s)
+    eb = per_elem_err(bv, bo, boff, s)
+    return ea, eb
+
+
+def workload_for(p, n):
+    return inputs.workload("p7", n_max=n) if p >= 6 else inputs.workload("pr1", n_max=n)
+
+
+@pytest.mark.parametrize("p", range(1, 8))
+def test_reference_tables_match_oracle(api, p):
+    ref = api.fei_reference_create(p)
+    pts, G = ref.table()
+    pts_o = oracle.quadrature(p)
+    assert np.max(np.abs(pts.numpy() - pts_o)) < 1e-15
+    phi, dphi = oracle.basis(p, pts_o[:, :3])
+    Go = np.concatenate([phi[:, None, :], dphi.transpose(0, 2, 1)], axis=1)
+    scale = np.max(np.abs(Go))
+    assert np.max(np.abs(G.numpy() - Go)) < 1e-13 * scale
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("p", range(1, 8))
+def test_forward_uniform_degree(api, p, precision):
+    w = workload_for(p, N_PER_P[p])
+    ea, eb = compare(api, w, p, precision)
+    assert ea.max() < TOL[precision], (p, precision, ea.max())
+    assert eb.max() < TOL[precision], (p, precision, eb.max())
+
+
+def test_pr1_full_fp64(api):
+    """PR1: 4096 prisms, p = 1, FP64 -- the whole batch."""
+    w = inputs.workload("pr1")
+    ea, eb = compare(api, w, 1, "fp64")
+    assert ea.max() < 1e-12 and eb.max() < 1e-12
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_mixed_degree_batch(api, precision):
+    w = inputs.workload("mixed", n_max=240)
+    ea, eb = compare(api, w, None, precision, degree=w["degree"])
+    assert ea.max() < TOL[precision] and eb.max() < TOL[precision]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_per_point_coefficients(api, precision):
+    w = inputs.workload("diff", n_max=6)
+    ea, eb = compare(api, w, 5, precision, per_qp=True)
+    assert ea.max() < TOL[precision] and eb.max() < TOL[precision]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("p", [1, 4])
+def test_status_flags_and_zero_outputs(api, p, precision):
+    w = workload_for(p, 7)
+    geom = w["geom"].copy()
+    geom[2] = geom[2][[0, 2, 1, 3, 5, 4]]  # mirrored: det J < 0
+    c = w["c"].copy()
+    c[4] = np.nan
+    geom[5, 3, 1] = np.inf
+    w2 = dict(w, geom=geom, c=c)
+    A, bv, st = run_gpu(api, w2, p=p, precision=precision)
+    s = api.nsh(p)
+    assert list(st) == [0, 0, 3, 0, 4, 4, 0]
+    for e in (2, 4, 5):
+        assert np.all(A[e * s * s:(e + 1) * s * s] == 0) and np.all(bv[e * s:(e + 1) * s] == 0)
+    ea, eb = compare(api, w2, p, precision)
+    assert ea.max() < TOL[precision]
+
+
+def test_custom_offsets_leave_gaps_untouched(api):
+    """Caller-provided offsets with gaps between elements."""
+    w = inputs.workload("pr1", n_max=5)
+    p, s = 2, api.nsh(2)
+    Aoff = np.arange(6, dtype=np.int64) * (s * s + 7)
+    boff = np.arange(6, dtype=np.int64) * (s + 3)
+    qoff = np.arange(6, dtype=np.int64) * api.nq(p)
+    lay = api.Layout(dev(Aoff), dev(boff), dev(qoff), int(Aoff[-1]), int(boff[-1]), int(qoff[-1]))
+    A = torch.full((lay.A_total,), 7.0, dtype=torch.float64, device="cuda")
+    bv = torch.full((lay.b_total,), 7.0, dtype=torch.float64, device="cuda")
+    st = torch.empty(5, dtype=torch.int32, device="cuda")
+    deg = np.full(5, p, dtype=np.int32)
+    api.fei_integrate(dev(w["geom"]), dev(w["K"]), dev(w["b"]), dev(w["c"]), dev(w["f"]),
+                      degree=dev(deg), precision="fp64", layout=lay, out=(A, bv, st))
+    A = A.cpu().numpy()
+    Ao, bo, _, _ = oracle.integrate(w["geom"], w["K"], w["b"], w["c"], w["f"], p=p)
+    for e in range(5):
+        a = A[Aoff[e]:Aoff[e] + s * s]
+        assert np.linalg.norm(a - Ao[e * s * s:(e + 1) * s * s]) < 1e-12 * np.linalg.norm(a)
+        assert np.all(A[Aoff[e] + s * s:Aoff[e + 1]] == 7.0)
+
+
+def test_empty_batch(api):
+    z = torch.zeros((0, 6, 3), dtype=torch.float64, device="cuda")
+    zK = torch.zeros((0, 3, 3), dtype=torch.float64, device="cuda")
+    zb = torch.zeros((0, 3), dtype=torch.float64, device="cuda")
+    zc = torch.zeros((0,), dtype=torch.float64, device="cuda")
+    A, bv, st, _ = api.fei_integrate(z, zK, zb, zc, zc, p=3, precision="fp32")
+    assert A.numel() == 0 and st.numel() == 0
+
+
+def test_invalid_degree_reported(api):
+    w = inputs.workload("pr1", n_max=4)
+    with pytest.raises(api._lib.FeiError) as ei:
+        api.fei_integrate(dev(w["geom"]), dev(w["K"]), dev(w["b"]), dev(w["c"]), dev(w["f"]), p=9)
+    assert ei.value.status == 2
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32", 1e-6)])
+@pytest.mark.parametrize("p,per_qp", [(2, False), (3, False), (5, True)])
+def test_backward_matches_oracle_adjoint(api, p, per_qp, precision, tol):
+    w = inputs.workload("diff", n_max=3) if per_qp else inputs.workload("p7", n_max=4)
+    n = len(w["geom"])
+    s = api.nsh(p)
+    rng = np.random.default_rng(p)
+    gA = rng.standard_normal(n * s * s)
+    gb = rng.standard_normal(n * s)
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    out = api.fei_integrate_backward(dev(w["geom"]), dev(w["K"]), dev(w["b"]), dev(w["c"]), dev(w["f"]),
+                                     dev(gA, dt), dev(gb, dt), p=p, per_qp=per_qp, precision=precision)
+    torch.cuda.synchronize()
+    if precision == "fp32":  # the oracle sees the same rounded cotangents
+        gA = gA.astype(np.float32).astype(np.float64)
+        gb = gb.astype(np.float32).astype(np.float64)
+    ref = oracle.integrate_backward(w["geom"], w["K"], w["b"], w["c"], w["f"], gA, gb, p=p, per_qp=per_qp)
+    for name, got, want in zip(("geom", "K", "b", "c", "f"), out, ref):
+        got = got.cpu().numpy().reshape(want.shape)
+        e = np.linalg.norm(got - want) / np.linalg.norm(want)
+        assert e < tol, (name, e)
