@@ -1,22 +1,917 @@
-// fei_tc.cu -- tensor-core (tcgen05) contraction for p >= 3.  Placeholder
-// until the kernel lands: FEI_TC_F16X3 reports FEI_ERR_UNSUPPORTED.
+// fei_tc.cu -- the contraction on the 5th-generation tensor cores (p >= 3).
+//
+// The double loop over shape functions of Algorithm 1 (steps 9-13, "the
+// dominant cost", Sec. 2.2) is, for every element e, the product
+//     A_e = H'_e^T G,   H'_e[(q,b)][i] = sum_a Dt_q[a][b] G[q][a][i],
+// over the K = 4 N_q dimension (q = point, b = value / 3 derivatives).  G is
+// the same for every element of one degree (Sec. 2.2), so the batch is ONE
+// GEMM: the rows (e, i) of all elements are stacked along M in tiles of
+// 128 rows that run across element boundaries, N = N_sh (the shared G), and
+// K = 4 N_q.  This is the GPU counterpart of the paper's vectorisation over
+// the entries of A_e (Algorithm 2 "DD", four consecutive j per float4): here
+// one tcgen05.mma produces a 128 x N tile.
+//
+// Precision (FEI_TC_F16X3).  Each operand x is split into two fp16 numbers
+// hi = rn(x), lo = rn(x - hi); hi*hi + hi*lo + lo*hi is x*y to about 2^-21
+// relative.  To keep fp16 in range, G is scaled by 2^tau (per degree) and
+// H'_e by 2^sigma_e (per element), chosen from the exact bound
+// max |H'| <= max_{q,b} sum_a |Dt[a][b]| max |G|, so every operand value is
+// at most 2^14.  The producers build H' from the scaled table, so the
+// accumulator holds A_e 2^(sigma_e + 2 tau); the epilogue scales back
+// exactly.  The tensor core adds into its FP32 accumulator with truncation,
+// so a long chain of MMAs drifts by about half an ulp of the accumulator per
+// instruction; to keep the error independent of K, each K chunk (and N half)
+// accumulates into a fresh partial buffer in tensor memory, and the epilogue
+// warps add the partial into a running FP32 sum with round-to-nearest
+// ("promotion") while the MMAs fill the other partial buffer.  The point
+// operators are formed as in the FEI_FP32 path (element vectors, node
+// columns and w det J in FP64).
+//
+// One thread block per SM walks 128-row tiles; nothing synchronises the
+// whole block between tiles.  Roles (warp = 32 threads):
+//   warp 0       TMEM owner; lane 0 streams the pre-swizzled B operand (the
+//                split G image) into shared memory with cp.async.bulk;
+//   warp 1       lane 0 issues tcgen05.mma (M = 128, N = N_pad or 2 halves);
+//   warps 2..9   producers: per tile, the point operators of the touched
+//                elements and their scales; per K chunk, H' for the 128
+//                rows, split into hi/lo, written in the swizzled K-major
+//                operand layout; the load vector b_e and the statuses;
+//   warps 10..13 epilogue: promotion of every partial accumulator, then
+//                scaling and coalesced stores of A_e.
+// All hand-offs are mbarriers; every wait is bounded by a time limit after
+// which the block raises an abort flag, marks its remaining elements with
+// FEI_ERR_TIMEOUT, drains its MMAs, frees its TMEM and exits.
+#include <cuda_fp16.h>
+#include <math.h>
+#include <string.h>
+
+#include "fei_geom.cuh"
 #include "fei_internal.cuh"
 
 namespace fei {
 
 struct TcImage {
-  int dummy;
+  __half *img;  // [NCHUNK][2][NPAD][ROWB/2], each [NPAD][ROWB/2] block swizzled
+  int npad, nchunk, rowb, tau;
 };
 
-fei_status build_tc_image(fei_reference *ref) {
-  ref->tc = nullptr;
+namespace {
+
+constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s per wait
+
+// ---------------------------------------------------------------------------
+// PTX wrappers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t a) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t a, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t a, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(a), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: false (and the abort flag raised) after kWaitLimitNs, or as
+// soon as another role raised the flag.
+__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int *abort_flag) {
+  if (mbar_try_wait(a, parity)) return true;
+  const uint64_t t0 = global_ns();
+  while (true) {
+    if (mbar_try_wait(a, parity)) return true;
+    if (*abort_flag) return false;
+    if (global_ns() - t0 > kWaitLimitNs) {
+      *abort_flag = 1;
+      return false;
+    }
+  }
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(mbar)
+               : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
+}
+__device__ __forceinline__ void tc_mma_f16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void named_bar(int id, int count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+// 32 lanes x 16 columns of 32-bit values; thread t owns its lane's columns.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
+}
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float *v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16};" ::"r"(taddr),
+      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
+      "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
+      "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+      "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15]))
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ float exp2i(int k) {  // exact 2^k for |k| < 126
+  return __int_as_float((127 + k) << 23);
+}
+
+// ---------------------------------------------------------------------------
+// Configuration
+// ---------------------------------------------------------------------------
+// ROWB = bytes of one swizzled operand row = K values per chunk * 2 (fp16):
+// 128 (128-byte swizzle, 16 points per chunk) or 64 (64-byte swizzle,
+// 8 points per chunk, used for p = 7 to leave room for three stages).
+template <int P>
+struct TcCfg {
+  static constexpr int NSH = nsh_of(P), NQ = nq_of(P), NZ = P + 1, NT = (P + 1) * (P + 1);
+  static constexpr int NPAD = P == 6 ? 224 : (NSH + 15) / 16 * 16;
+  static constexpr int NHALF = P >= 6 ? 2 : 1;
+  static constexpr int NMMA = NPAD / NHALF;  // N of one MMA = one partial buffer
+  static constexpr int ROWB = P == 7 ? 64 : 128;
+  static constexpr int KCH = ROWB / 2;        // K values per chunk
+  static constexpr int PPC = KCH / 4;         // points per chunk
+  static constexpr int KSL = KCH / 16;        // 16-wide K slices per chunk
+  static constexpr int NCHUNK = (NQ + PPC - 1) / PPC;
+  static constexpr int TMEM_COLS = 3 * NPAD <= 256 ? 256 : 512;
+  // running sum: columns [0, RT) in TMEM after the two partial buffers, the
+  // rest (RREG columns) in registers of the epilogue threads
+  static constexpr int RT = (512 - 2 * NMMA) < NPAD ? (512 - 2 * NMMA) : NPAD;
+  static constexpr int RREG = NPAD - RT;
+  static constexpr int EMAX = (128 + NSH - 1) / NSH + 1;
+  static constexpr int NPW = 8;  // producer warps
+  static constexpr int NEW = 4;  // epilogue warps
+  static constexpr int NTHREADS = (2 + NPW + NEW) * 32;
+  static constexpr int QPG = PPC / 2;  // points per producer thread per chunk
+  static constexpr int A_BYTES = 128 * ROWB;
+  static constexpr int B_BYTES = NPAD * ROWB;
+  static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+  static constexpr int STAGES = P == 3 ? 4 : P == 4 ? 3 : P == 5 ? 3 : P == 6 ? 2 : 3;
+  static constexpr int DYN_SMEM = STAGES * STAGE_BYTES + 1024;
+  static_assert(NMMA % 16 == 0 && NMMA <= 256, "MMA N");
+  static_assert(RT % 16 == 0 && RREG % 16 == 0 && RT >= 0, "running-sum split");
+  static_assert(2 * NMMA + RT <= TMEM_COLS, "tensor memory");
+  static_assert(QPG % 2 == 0, "two points per 16-byte chunk");
+};
+
+template <int P>
+struct TcElem {
+  using C = TcCfg<P>;
+  double X[18];
+  double ev[21];
+  double cd[14];
+  double zn3w[C::NZ][3];
+  double tc3w[C::NT][3];
+  float zc1f[C::NZ][3], zc2f[C::NZ][3], zn3f[C::NZ][3], zwf[C::NZ];
+  float tc3f[C::NT][3], twf[C::NT];
+  int64_t e, aoff, boff, qoff;
+  int status;
+  int mbits;   // float bits of max_{q,b} sum_a |Dt[a][b]|
+  float up;    // 2^sigma (applied to Dt before H')
+  float down;  // 2^-(sigma + 2 tau)
+};
+
+struct TcMeta {
+  int64_t row_off[128];  // start of the row in A_out, -1 for rows past the end
+  float row_down[128];   // exact scale back of the row's element
+  int row_zero[128];     // element flagged: write zeros
+};
+
+template <int P>
+struct TcAux {
+  using C = TcCfg<P>;
+  uint64_t full[C::STAGES];   // producers wrote A of the stage
+  uint64_t bfull[C::STAGES];  // B of the stage landed
+  uint64_t empty[C::STAGES];  // MMAs of the stage completed
+  uint64_t part_full[2];      // partial accumulator ready for promotion
+  uint64_t promo_done[2];     // partial accumulator promoted (free again)
+  uint64_t meta_full[2];
+  uint64_t meta_empty[2];
+  uint64_t drain;
+  uint32_t tmem_base;
+  int abort_flag;
+  int psnap;
+  int n_el;
+  int64_t k_first;
+  TcElem<P> el[C::EMAX];
+  alignas(16) float Dc[2][C::EMAX][C::PPC][16];
+  float sp[C::EMAX][C::NQ];  // w det J per point (FP32, from FP64)
+  TcMeta meta[2];
+  float bsum[128];
+  alignas(16) float stg[C::NEW][32][17];  // epilogue transpose staging
+};
+
+__device__ __forceinline__ bool load_coef_tc(const FwdArgs &a, int64_t r, double *cd) {
+  bool ok = true;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    cd[k] = a.K[9 * r + k];
+    ok &= isfinite(cd[k]);
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    cd[9 + k] = a.b[3 * r + k];
+    ok &= isfinite(cd[9 + k]);
+  }
+  cd[12] = a.c[r];
+  cd[13] = a.f[r];
+  ok &= isfinite(cd[12]) && isfinite(cd[13]);
+  return ok;
+}
+
+// FP32 point operator of element slot E at point q from the node tables;
+// sf = w det J (formed in FP64, rounded once).
+template <int P>
+__device__ __forceinline__ void tc_point(const TcElem<P> &E, const double *cd, int q, float sf, float *D) {
+  using C = TcCfg<P>;
+  const int iz = q / C::NT, t = q - iz * C::NT;
+  float a0[3], a1[3];
+  cross3(E.zc2f[iz], E.tc3f[t], a0);
+  cross3(E.tc3f[t], E.zc1f[iz], a1);
+  const float wf = E.zwf[iz] * E.twf[t];
+  float K[9], b[3];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) K[k] = (float)cd[k];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) b[k] = (float)cd[9 + k];
+  dt_from_adj<float>(a0, a1, E.zn3f[iz], wf, sf, wf * wf / sf, K, b, (float)cd[12], (float)cd[13], D);
+}
+
+// Shared-memory matrix descriptor of a K-major operand with ROWB-byte rows
+// in the ROWB-byte swizzle layout; 8-row groups 8 * ROWB bytes apart.
+template <int ROWB>
+__device__ __forceinline__ uint64_t sw_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);    // start address
+  d |= (uint64_t)1 << 16;                      // leading byte offset (unused)
+  d |= (uint64_t)((8 * ROWB) >> 4) << 32;      // stride byte offset
+  d |= (uint64_t)1 << 46;                      // descriptor version
+  d |= (uint64_t)(ROWB == 128 ? 2 : 4) << 61;  // 128- or 64-byte swizzle
+  return d;
+}
+// Byte offset of 16-byte chunk c of row r in a swizzled operand tile whose
+// base is 1024-byte aligned: the chunk index is XORed with address bits
+// [9:7] (128-byte rows) or [8:7] (64-byte rows).
+template <int ROWB>
+__host__ __device__ __forceinline__ uint32_t sw_off(int r, int c) {
+  const int x = ROWB == 128 ? (r & 7) : ((r >> 1) & 3);
+  return (uint32_t)(r * ROWB + ((c ^ x) << 4));
+}
+// Instruction descriptor, kind::f16: fp16 A and B (K-major), FP32 D.
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+template <int P>
+__global__ void __launch_bounds__(TcCfg<P>::NTHREADS, 1) tc_forward_kernel(FwdArgs a, const __half *img, int tau) {
+  using C = TcCfg<P>;
+  constexpr int NSH = C::NSH, NQ = C::NQ, NT = C::NT, NZ = C::NZ, S = C::STAGES, NCH = C::NCHUNK;
+  constexpr int NP = C::NPW * 32, PPC = C::PPC, ROWB = C::ROWB;
+  extern __shared__ __align__(1024) unsigned char dsm_raw[];
+  __shared__ TcAux<P> ax;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t dbase = (smem_u32(dsm_raw) + 1023u) & ~1023u;
+  auto stageA = [&](int s, int piece) { return dbase + s * C::STAGE_BYTES + piece * C::A_BYTES; };
+  auto stageB = [&](int s) { return dbase + s * C::STAGE_BYTES + 2 * C::A_BYTES; };
+  volatile int *abort_flag = &ax.abort_flag;
+
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(smem_u32(&ax.full[s]), C::NPW);
+      mbar_init(smem_u32(&ax.bfull[s]), 1);
+      mbar_init(smem_u32(&ax.empty[s]), 1);
+    }
+    for (int k = 0; k < 2; ++k) {
+      mbar_init(smem_u32(&ax.part_full[k]), 1);
+      mbar_init(smem_u32(&ax.promo_done[k]), C::NEW);
+      mbar_init(smem_u32(&ax.meta_full[k]), 1);
+      mbar_init(smem_u32(&ax.meta_empty[k]), C::NEW);
+    }
+    mbar_init(smem_u32(&ax.drain), 1);
+    ax.abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&ax.tmem_base)),
+                 "r"(C::TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = ax.tmem_base;
+
+  const int64_t items = a.count ? (int64_t)(*a.count) : a.n_work;
+  const int64_t rows_total = items * NSH;
+  const int64_t tiles = (rows_total + 127) / 128;
+
+  if (warp >= 2 && warp < 2 + C::NPW) {
+    // ================================================================ producers
+    const int tp = tid - 64;  // 0 .. NP-1
+    const int r = tp & 127, grp = tp >> 7;
+    int it = 0;
+    int64_t tile = blockIdx.x;
+    for (; tile < tiles; tile += gridDim.x, ++it) {
+      const int64_t r0 = tile * 128;
+      if (tp == 0) {
+        ax.psnap = *abort_flag;
+        const int64_t k0 = r0 / NSH;
+        int64_t k1 = (r0 + 127) / NSH;
+        if (k1 > items - 1) k1 = items - 1;
+        ax.k_first = k0;
+        ax.n_el = (int)(k1 - k0 + 1);
+      }
+      named_bar(1, NP);
+      if (ax.psnap) break;
+      const int nel = ax.n_el;
+      const int64_t k0 = ax.k_first;
+      // geometry and coefficients of the touched elements
+      if (tp < nel * 32) {
+        const int el = tp >> 5, ln = tp & 31;
+        TcElem<P> &E = ax.el[el];
+        const int64_t e = a.list ? (int64_t)a.list[k0 + el] : k0 + el;
+        bool ok = true;
+        if (ln < 18) {
+          E.X[ln] = a.geom[18 * e + ln];
+          ok = isfinite(E.X[ln]);
+        }
+        if (ln == 20) {
+          E.e = e;
+          E.aoff = a.A_off ? a.A_off[e] : e * (int64_t)(NSH * NSH);
+          E.boff = a.b_off ? a.b_off[e] : e * (int64_t)NSH;
+          E.qoff = a.q_off ? a.q_off[e] : e * (int64_t)NQ;
+          E.mbits = 0;
+          if (a.coef_mode == FEI_COEF_PER_ELEMENT) ok = load_coef_tc(a, e, E.cd);
+        }
+        ok = __all_sync(0xffffffffu, ok);
+        if (ln == 0) E.status = ok ? 0 : FEI_ERR_NONFINITE;
+      }
+      named_bar(1, NP);
+      if (tp < nel) elem_vectors(ax.el[tp].X, ax.el[tp].ev);
+      named_bar(1, NP);
+      // node tables: vertical nodes (c1, c2, n3) and triangle nodes (c3)
+      for (int idx = tp; idx < nel * (NZ + NT); idx += NP) {
+        const int el = idx / (NZ + NT), nd = idx - el * (NZ + NT);
+        TcElem<P> &E = ax.el[el];
+        if (nd < NZ) {
+          double c1[3], c2[3], n3[3];
+          const double z = a.znode[2 * nd], wz = a.znode[2 * nd + 1];
+          znode_columns(E.ev, z, c1, c2, n3);
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            E.zc1f[nd][k] = (float)c1[k];
+            E.zc2f[nd][k] = (float)c2[k];
+            E.zn3f[nd][k] = (float)n3[k];
+            E.zn3w[nd][k] = wz * n3[k];
+          }
+          E.zwf[nd] = (float)wz;
+        } else {
+          const int t = nd - NZ;
+          double c3[3];
+          const double wt = a.tnode[4 * t + 2];
+          tnode_column(E.ev, a.tnode[4 * t], a.tnode[4 * t + 1], c3);
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            E.tc3f[t][k] = (float)c3[k];
+            E.tc3w[t][k] = wt * c3[k];
+          }
+          E.twf[t] = (float)wt;
+        }
+      }
+      named_bar(1, NP);
+      // pre-pass over all points: w det J (FP64 -> FP32), status, and the
+      // bound max_{q,b} sum_a |Dt[a][b]| that sets the element's scale
+      for (int idx = tp; idx < nel * NQ; idx += NP) {
+        const int el = idx / NQ, q = idx - el * NQ;
+        TcElem<P> &E = ax.el[el];
+        const int iz = q / NT, t = q - iz * NT;
+        const double s = dot3(E.zn3w[iz], E.tc3w[t]);
+        int st = point_status(s);
+        double cq[14];
+        const double *cp = E.cd;
+        if (a.coef_mode == FEI_COEF_PER_POINT) {
+          if (!load_coef_tc(a, E.qoff + q, cq)) st = FEI_ERR_NONFINITE;
+          cp = cq;
+        }
+        const float sf = (float)s;
+        ax.sp[el][q] = sf;
+        if (st) {
+          atomicMax(&E.status, st);
+        } else {
+          float D[16];
+          tc_point<P>(E, cp, q, sf, D);
+          float m0 = fabsf(D[0]);
+          float m1 = fabsf(D[1]) + fabsf(D[4]) + fabsf(D[7]) + fabsf(D[10]);
+          float m2 = fabsf(D[2]) + fabsf(D[5]) + fabsf(D[8]) + fabsf(D[11]);
+          float m3 = fabsf(D[3]) + fabsf(D[6]) + fabsf(D[9]) + fabsf(D[12]);
+          const float m = fmaxf(fmaxf(m0, m1), fmaxf(m2, m3));
+          if (!(m <= 3.0e38f)) atomicMax(&E.status, FEI_ERR_NONFINITE);
+          else atomicMax(&E.mbits, __float_as_int(m));
+        }
+      }
+      named_bar(1, NP);
+      if (tp < nel) {
+        TcElem<P> &E = ax.el[tp];
+        // The A operand is H' 2^sigma built from the scaled table G 2^tau,
+        // so |A| <= M 2^sigma max|G 2^tau| <= M 2^sigma 2^14: sigma = -ex
+        // with M <= 2^ex keeps it within 2^14.  D = A_e 2^(sigma + 2 tau).
+        const float M = __int_as_float(E.mbits);
+        int ex = 0;
+        if (M > 0.f) (void)frexpf(M, &ex);  // M <= 2^ex
+        int sigma = -ex;
+        sigma = sigma > 100 ? 100 : (sigma < -100 ? -100 : sigma);
+        E.up = exp2i(sigma);
+        const int dn = -(sigma + 2 * tau);
+        E.down = dn >= -126 && dn <= 126 ? exp2i(dn) : ldexpf(1.0f, dn);
+      }
+      // row metadata, double-buffered for the epilogue of this tile
+      const int slot = it & 1;
+      if (tp == 0) {
+        const uint32_t k = (uint32_t)(it >> 1);
+        ax.psnap = mbar_wait(smem_u32(&ax.meta_empty[slot]), (k & 1u) ^ 1u, abort_flag) ? 0 : 1;
+      }
+      named_bar(1, NP);
+      const bool live = ax.psnap == 0;
+      const int64_t grow = r0 + r;
+      const bool rvalid = grow < rows_total && live;
+      int rel = 0, ri = 0;
+      if (grow < rows_total) {
+        const int64_t k = grow / NSH;
+        ri = (int)(grow - k * NSH);
+        rel = (int)(k - k0);
+      }
+      if (grp == 0 && live) {
+        TcMeta &M = ax.meta[slot];
+        if (rvalid) {
+          const TcElem<P> &E = ax.el[rel];
+          M.row_off[r] = E.aoff + (int64_t)ri * NSH;
+          M.row_down[r] = E.down;
+          M.row_zero[r] = E.status != 0;
+        } else {
+          M.row_off[r] = -1;
+          M.row_down[r] = 0.f;
+          M.row_zero[r] = 1;
+        }
+      }
+      named_bar(1, NP);
+      if (tp == 0 && live) mbar_arrive(smem_u32(&ax.meta_full[slot]));
+      float bpart = 0.f;
+      // K chunks
+      for (int c = 0; c < NCH; ++c) {
+        const int g = it * NCH + c, s = g % S;
+        const uint32_t u = (uint32_t)(g / S);
+        const int buf = c & 1;
+        // point operators of this chunk, pre-scaled by 2^sigma (entry 13,
+        // w det J f for the load vector, unscaled)
+        if (tp < nel * PPC) {
+          const int el = tp / PPC, qq = tp - el * PPC, q = c * PPC + qq;
+          const TcElem<P> &E = ax.el[el];
+          float *D = ax.Dc[buf][el][qq];
+          if (q < NQ && E.status == 0) {
+            double cq[14];
+            const double *cp = E.cd;
+            if (a.coef_mode == FEI_COEF_PER_POINT) {
+              load_coef_tc(a, E.qoff + q, cq);
+              cp = cq;
+            }
+            float Dt[16];
+            tc_point<P>(E, cp, q, ax.sp[el][q], Dt);
+#pragma unroll
+            for (int k = 0; k < 13; ++k) D[k] = Dt[k] * E.up;
+            D[13] = Dt[13];
+            D[14] = 0.f;
+            D[15] = 0.f;
+          } else {
+#pragma unroll
+            for (int k = 0; k < 16; ++k) D[k] = 0.f;
+          }
+        }
+        named_bar(1, NP);
+        // wait for this stage: B landed (G is read from it) and A free.  A
+        // failed wait does not leave the loop (every producer must reach the
+        // named barriers); the warp only stops producing.
+        bool ok = live && mbar_wait(smem_u32(&ax.bfull[s]), u & 1u, abort_flag);
+        ok = ok && mbar_wait(smem_u32(&ax.empty[s]), (u & 1u) ^ 1u, abort_flag);
+        ok = __all_sync(0xffffffffu, ok);
+        if (!ok) continue;
+        const uint32_t bh = stageB(s), bl = bh + C::B_BYTES;
+        const uint32_t ah = stageA(s, 0), alo = stageA(s, 1);
+        // this thread: row r, points grp*QPG .. of the chunk = 16-byte chunks
+        // grp*QPG/2 .. of the operand row (two points each)
+#pragma unroll
+        for (int pc = 0; pc < C::QPG / 2; ++pc) {
+          const int chunk = grp * (C::QPG / 2) + pc;
+          uint32_t hw[4], lw[4];
+          if (rvalid) {
+            const uint32_t goff = sw_off<ROWB>(ri, chunk);
+            uint4 gh, gl;
+            asm volatile("ld.shared.v4.b32 {%0,%1,%2,%3}, [%4];"
+                         : "=r"(gh.x), "=r"(gh.y), "=r"(gh.z), "=r"(gh.w)
+                         : "r"(bh + goff));
+            asm volatile("ld.shared.v4.b32 {%0,%1,%2,%3}, [%4];"
+                         : "=r"(gl.x), "=r"(gl.y), "=r"(gl.z), "=r"(gl.w)
+                         : "r"(bl + goff));
+            const uint32_t ghw[4] = {gh.x, gh.y, gh.z, gh.w}, glw[4] = {gl.x, gl.y, gl.z, gl.w};
+#pragma unroll
+            for (int h2 = 0; h2 < 2; ++h2) {  // two points per 16-byte chunk
+              const int qq = chunk * 2 + h2;  // point within the chunk
+              const float *D = ax.Dc[buf][rel][qq];
+              float gv[4];
+#pragma unroll
+              for (int ab = 0; ab < 2; ++ab) {
+                __half2 hh, ll;
+                memcpy(&hh, &ghw[2 * h2 + ab], 4);
+                memcpy(&ll, &glw[2 * h2 + ab], 4);
+                const float2 fh = __half22float2(hh), fl = __half22float2(ll);
+                gv[2 * ab] = fh.x + fl.x;
+                gv[2 * ab + 1] = fh.y + fl.y;
+              }
+              // gv = G 2^tau; D carries 2^sigma
+              const float4 d0 = *reinterpret_cast<const float4 *>(D);
+              const float4 d1 = *reinterpret_cast<const float4 *>(D + 4);
+              const float4 d2 = *reinterpret_cast<const float4 *>(D + 8);
+              const float4 d3 = *reinterpret_cast<const float4 *>(D + 12);
+              float hv[4];
+              hv[0] = d0.x * gv[0];
+              hv[1] = d0.y * gv[0] + d1.x * gv[1] + d1.w * gv[2] + d2.z * gv[3];
+              hv[2] = d0.z * gv[0] + d1.y * gv[1] + d2.x * gv[2] + d2.w * gv[3];
+              hv[3] = d0.w * gv[0] + d1.z * gv[1] + d2.y * gv[2] + d3.x * gv[3];
+              bpart += d3.y * gv[0];  // (w det J f) phi 2^tau
+              const __half2 h01 = __floats2half2_rn(hv[0], hv[1]);
+              const __half2 h23 = __floats2half2_rn(hv[2], hv[3]);
+              const float2 f01 = __half22float2(h01), f23 = __half22float2(h23);
+              const __half2 l01 = __floats2half2_rn(hv[0] - f01.x, hv[1] - f01.y);
+              const __half2 l23 = __floats2half2_rn(hv[2] - f23.x, hv[3] - f23.y);
+              memcpy(&hw[2 * h2], &h01, 4);
+              memcpy(&hw[2 * h2 + 1], &h23, 4);
+              memcpy(&lw[2 * h2], &l01, 4);
+              memcpy(&lw[2 * h2 + 1], &l23, 4);
+            }
+          } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) hw[k] = lw[k] = 0u;
+          }
+          const uint32_t aoff = sw_off<ROWB>(r, chunk);
+          asm volatile("st.shared.v4.b32 [%0], {%1,%2,%3,%4};" ::"r"(ah + aoff), "r"(hw[0]), "r"(hw[1]), "r"(hw[2]),
+                       "r"(hw[3])
+                       : "memory");
+          asm volatile("st.shared.v4.b32 [%0], {%1,%2,%3,%4};" ::"r"(alo + aoff), "r"(lw[0]), "r"(lw[1]), "r"(lw[2]),
+                       "r"(lw[3])
+                       : "memory");
+        }
+        fence_proxy_async();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&ax.full[s]));
+      }
+      // load vector: combine the point groups, write b_e rows and statuses
+      ax.bsum[r] = 0.f;
+      named_bar(1, NP);
+      atomicAdd(&ax.bsum[r], bpart);
+      named_bar(1, NP);
+      if (grp == 0 && rvalid) {
+        const TcElem<P> &E = ax.el[rel];
+        const float bval = E.status ? 0.f : ax.bsum[r] * exp2i(-tau);
+        reinterpret_cast<float *>(a.bv)[E.boff + ri] = bval;
+        if (ri == 0) a.status[E.e] = E.status;
+      }
+    }
+    // an aborted block marks every element of its remaining tiles
+    if (*abort_flag) {
+      for (int64_t t2 = tile; t2 < tiles; t2 += gridDim.x)
+        for (int rr = tp; rr < 128; rr += NP) {
+          const int64_t grow = t2 * 128 + rr;
+          if (grow >= rows_total) continue;
+          const int64_t k = grow / NSH;
+          if (grow - k * NSH != 0 && rr != 0) continue;
+          const int64_t e = a.list ? (int64_t)a.list[k] : k;
+          a.status[e] = FEI_ERR_TIMEOUT;
+        }
+    }
+  } else if (warp >= 2 + C::NPW) {
+    // ================================================================ epilogue
+    const int ew = warp - (2 + C::NPW);  // 0..3
+    const int quarter = warp & 3;        // TMEM lanes 32*quarter ..
+    const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
+    const int myrow = quarter * 32 + lane;
+    float rreg[C::RREG > 0 ? C::RREG : 1];
+    int it = 0;
+    uint32_t unit = 0;
+    bool dead = false;
+    for (int64_t tile = blockIdx.x; tile < tiles && !dead; tile += gridDim.x, ++it) {
+      for (int c = 0; c < NCH && !dead; ++c) {
+#pragma unroll
+        for (int nh = 0; nh < C::NHALF; ++nh) {
+          const uint32_t pb = unit & 1u, k = unit >> 1;
+          ++unit;
+          const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&ax.part_full[pb]), k & 1u, abort_flag));
+          if (!ok) {
+            dead = true;
+            break;
+          }
+          tc_fence_after();
+#pragma unroll
+          for (int b = 0; b < C::NMMA / 16; ++b) {
+            const int ncol = nh * C::NMMA + b * 16;  // column of A_e (and of R)
+            float v[16];
+            tmem_ld16(tmem + lane_base + pb * C::NMMA + b * 16, v);
+            if (ncol < C::RT) {
+              const uint32_t raddr = tmem + lane_base + 2 * C::NMMA + ncol;
+              if (c > 0) {
+                float rv[16];
+                tmem_ld16(raddr, rv);
+#pragma unroll
+                for (int k2 = 0; k2 < 16; ++k2) v[k2] += rv[k2];
+              }
+              tmem_st16(raddr, v);
+            } else if constexpr (C::RREG > 0) {
+              const int ro = ncol - C::RT;
+#pragma unroll
+              for (int k2 = 0; k2 < 16; ++k2) rreg[ro + k2] = (c > 0 ? rreg[ro + k2] : 0.f) + v[k2];
+            }
+          }
+          tmem_wait_st();
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(smem_u32(&ax.promo_done[pb]));
+        }
+      }
+      if (dead) break;
+      // final: scale the running sum and store the tile's rows of A_e
+      const int slot = it & 1;
+      const uint32_t km = (uint32_t)(it >> 1);
+      if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&ax.meta_full[slot]), km & 1u, abort_flag))) break;
+      const TcMeta &M = ax.meta[slot];
+      const float dn = M.row_zero[myrow] ? 0.f : M.row_down[myrow];
+      float(*stg)[17] = ax.stg[ew];
+#pragma unroll
+      for (int b = 0; b < C::NPAD / 16; ++b) {
+        const int ncol = b * 16;
+        if (ncol < NSH) {
+          float v[16];
+          if (ncol < C::RT) {
+            tmem_ld16(tmem + lane_base + 2 * C::NMMA + ncol, v);
+          } else if constexpr (C::RREG > 0) {
+#pragma unroll
+            for (int k2 = 0; k2 < 16; ++k2) v[k2] = rreg[ncol - C::RT + k2];
+          }
+#pragma unroll
+          for (int k2 = 0; k2 < 16; ++k2) stg[lane][k2] = v[k2] * dn;
+          __syncwarp();
+          // two rows per store instruction: lanes 0-15 row rr, 16-31 row rr+1
+          const int half = lane >> 4, col = ncol + (lane & 15);
+          for (int rr = 0; rr < 32; rr += 2) {
+            const int row = quarter * 32 + rr + half;
+            const int64_t off = M.row_off[row];
+            if (off >= 0 && col < NSH) reinterpret_cast<float *>(a.A)[off + col] = stg[rr + half][lane & 15];
+          }
+          __syncwarp();
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&ax.meta_empty[slot]));
+    }
+  } else if (warp == 0) {
+    // ================================================================ B stream
+    if (lane == 0) {
+      int it = 0;
+      for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++it) {
+        bool ok = true;
+        for (int c = 0; c < NCH; ++c) {
+          const int g = it * NCH + c, s = g % S;
+          const uint32_t u = (uint32_t)(g / S);
+          if (!mbar_wait(smem_u32(&ax.empty[s]), (u & 1u) ^ 1u, abort_flag)) {
+            ok = false;
+            break;
+          }
+          const uint32_t bar = smem_u32(&ax.bfull[s]);
+          mbar_expect_tx(bar, 2u * C::B_BYTES);
+          bulk_g2s(stageB(s), img + (size_t)c * 2 * C::NPAD * (ROWB / 2), 2u * C::B_BYTES, bar);
+        }
+        if (!ok) break;
+      }
+    }
+  } else {
+    // ================================================================ MMA issue
+    if (lane == 0) {
+      constexpr uint32_t IDESC = idesc_f16(128, C::NMMA);
+      bool ok = true;
+      uint32_t unit = 0;
+      int it = 0;
+      for (int64_t tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x, ++it) {
+        for (int c = 0; c < NCH && ok; ++c) {
+          const int g = it * NCH + c, s = g % S;
+          const uint32_t u = (uint32_t)(g / S);
+          ok = mbar_wait(smem_u32(&ax.bfull[s]), u & 1u, abort_flag) &&
+               mbar_wait(smem_u32(&ax.full[s]), u & 1u, abort_flag);
+          if (!ok) break;
+          tc_fence_after();
+          const uint32_t ah = stageA(s, 0), alo = stageA(s, 1), bh = stageB(s), bl = bh + C::B_BYTES;
+#pragma unroll
+          for (int nh = 0; nh < C::NHALF; ++nh) {
+            const uint32_t pb = unit & 1u, k = unit >> 1;
+            ++unit;
+            ok = mbar_wait(smem_u32(&ax.promo_done[pb]), (k & 1u) ^ 1u, abort_flag);
+            if (!ok) break;
+            tc_fence_after();
+            const uint32_t d = tmem + pb * C::NMMA;
+#pragma unroll
+            for (int kk = 0; kk < C::KSL; ++kk) {
+              const uint32_t boff = (uint32_t)(nh * C::NMMA * ROWB + kk * 32);
+              const uint64_t Ah = sw_desc<ROWB>(ah + kk * 32), Al = sw_desc<ROWB>(alo + kk * 32);
+              const uint64_t Bh = sw_desc<ROWB>(bh + boff), Bl = sw_desc<ROWB>(bl + boff);
+              tc_mma_f16(d, Ah, Bh, IDESC, kk != 0);
+              tc_mma_f16(d, Ah, Bl, IDESC, 1u);
+              tc_mma_f16(d, Al, Bh, IDESC, 1u);
+            }
+            tc_commit(smem_u32(&ax.part_full[pb]));
+          }
+          if (ok) tc_commit(smem_u32(&ax.empty[s]));
+        }
+      }
+      if (!ok) {
+        // make sure no MMA is in flight before the block leaves
+        tc_commit(smem_u32(&ax.drain));
+        const uint64_t t0 = global_ns();
+        while (!mbar_try_wait(smem_u32(&ax.drain), 0) && global_ns() - t0 < kWaitLimitNs) {
+        }
+      }
+    }
+  }
+  // in-flight bulk copies of an aborted block land within microseconds
+  if (*abort_flag) {
+    const uint64_t t0 = global_ns();
+    while (global_ns() - t0 < 200000ull) {
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::TMEM_COLS) : "memory");
+  }
+}
+
+// ---------------------------------------------------------------------------
+// B operand image: G * 2^tau split into fp16 hi/lo, K-major swizzled rows
+// ---------------------------------------------------------------------------
+__global__ void gmax_kernel(const double *G, int n, unsigned long long *out) {
+  double m = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) m = fmax(m, fabs(G[i]));
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
+
+__global__ void image_kernel(const double *G, int nsh, int nq, int npad, int nchunk, int rowb, double scale,
+                             __half *img) {
+  const int kch = rowb / 2, ppc = kch / 4;
+  const int64_t total = (int64_t)nchunk * npad * kch;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int k = (int)(idx % kch);
+    const int n = (int)((idx / kch) % npad);
+    const int c = (int)(idx / (kch * (int64_t)npad));
+    const int q = c * ppc + k / 4, b = k % 4;
+    const double x = (q < nq && n < nsh) ? G[(size_t)(4 * q + b) * nsh + n] * scale : 0.0;
+    const __half hi = __double2half(x);
+    const __half lo = __double2half(x - (double)__half2float(hi));
+    const uint32_t byte = rowb == 128 ? sw_off<128>(n, k >> 3) : sw_off<64>(n, k >> 3);
+    const size_t pos = byte / 2 + (k & 7);  // halves from the start of the block
+    img[(size_t)(c * 2 + 0) * npad * kch + pos] = hi;
+    img[(size_t)(c * 2 + 1) * npad * kch + pos] = lo;
+  }
+}
+
+template <int P>
+fei_status launch_tc(const fei_reference *ref, const FwdArgs &a, int64_t grid_work, cudaStream_t s) {
+  using C = TcCfg<P>;
+  const TcImage *im = ref->tc;
+  if (!im) return set_error(FEI_ERR_UNSUPPORTED, "no tensor-core image for degree %d", P);
+  FEI_CUDA_TRY(cudaFuncSetAttribute(tc_forward_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::DYN_SMEM),
+               "cudaFuncSetAttribute(tc_forward)");
+  int dev, sms;
+  FEI_CUDA_TRY(cudaGetDevice(&dev), "cudaGetDevice");
+  FEI_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "cudaDeviceGetAttribute");
+  const int64_t tiles = (grid_work * C::NSH + 127) / 128;
+  int64_t blocks = tiles < sms ? tiles : sms;
+  if (blocks < 1) blocks = 1;
+  tc_forward_kernel<P><<<(unsigned)blocks, C::NTHREADS, C::DYN_SMEM, s>>>(a, im->img, im->tau);
+  FEI_CUDA_TRY(cudaGetLastError(), "tc_forward_kernel launch");
   return FEI_OK;
 }
 
-void free_tc_image(fei_reference *ref) { ref->tc = nullptr; }
+template <int P>
+void tc_dims(int &npad, int &nchunk, int &rowb) {
+  npad = TcCfg<P>::NPAD;
+  nchunk = TcCfg<P>::NCHUNK;
+  rowb = TcCfg<P>::ROWB;
+}
 
-fei_status launch_tc_forward(int p, const fei_reference *, const FwdArgs &, int64_t, cudaStream_t) {
-  return set_error(FEI_ERR_UNSUPPORTED, "tensor-core path for degree %d not built", p);
+}  // namespace
+
+fei_status build_tc_image(fei_reference *ref) {
+  ref->tc = nullptr;
+  if (ref->p < 3) return FEI_OK;
+  int npad = 0, nchunk = 0, rowb = 0;
+  switch (ref->p) {
+    case 3: tc_dims<3>(npad, nchunk, rowb); break;
+    case 4: tc_dims<4>(npad, nchunk, rowb); break;
+    case 5: tc_dims<5>(npad, nchunk, rowb); break;
+    case 6: tc_dims<6>(npad, nchunk, rowb); break;
+    case 7: tc_dims<7>(npad, nchunk, rowb); break;
+  }
+  TcImage *im = new TcImage();
+  im->npad = npad;
+  im->nchunk = nchunk;
+  im->rowb = rowb;
+  im->img = nullptr;
+  unsigned long long *dmax = nullptr;
+  const size_t halves = (size_t)nchunk * 2 * npad * (rowb / 2);
+  cudaError_t e = cudaMalloc(&im->img, sizeof(__half) * halves);
+  if (e == cudaSuccess) e = cudaMalloc(&dmax, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemset(dmax, 0, sizeof(unsigned long long));
+  if (e == cudaSuccess) {
+    const int n = 4 * ref->nq * ref->nsh;
+    gmax_kernel<<<64, 256>>>(ref->G64, n, dmax);
+    e = cudaGetLastError();
+  }
+  unsigned long long bits = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&bits, dmax, sizeof(bits), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) {
+    double gmax;
+    memcpy(&gmax, &bits, sizeof(gmax));
+    int ex = 0;
+    frexp(gmax, &ex);  // gmax <= 2^ex
+    im->tau = 14 - ex;
+    image_kernel<<<256, 256>>>(ref->G64, ref->nsh, ref->nq, npad, nchunk, rowb, ldexp(1.0, im->tau), im->img);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  }
+  if (dmax) cudaFree(dmax);
+  if (e != cudaSuccess) {
+    if (im->img) cudaFree(im->img);
+    delete im;
+    return cuda_error(e, "tensor-core image");
+  }
+  ref->tc = im;
+  return FEI_OK;
+}
+
+void free_tc_image(fei_reference *ref) {
+  if (ref->tc) {
+    cudaFree(ref->tc->img);
+    delete ref->tc;
+    ref->tc = nullptr;
+  }
+}
+
+fei_status launch_tc_forward(int p, const fei_reference *ref, const FwdArgs &a, int64_t grid_work, cudaStream_t s) {
+  if (grid_work <= 0) return FEI_OK;
+  switch (p) {
+    case 3: return launch_tc<3>(ref, a, grid_work, s);
+    case 4: return launch_tc<4>(ref, a, grid_work, s);
+    case 5: return launch_tc<5>(ref, a, grid_work, s);
+    case 6: return launch_tc<6>(ref, a, grid_work, s);
+    case 7: return launch_tc<7>(ref, a, grid_work, s);
+  }
+  return set_error(FEI_ERR_UNSUPPORTED, "tensor-core path for degree %d", p);
 }
 
 }  // namespace fei
