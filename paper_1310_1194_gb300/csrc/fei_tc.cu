@@ -93,13 +93,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t a, uint32_t parity) {
 __device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int *abort_flag) {
   if (mbar_try_wait(a, parity)) return true;
   const uint64_t t0 = global_ns();
-  while (true) {
+  for (int spin = 0;; ++spin) {
     if (mbar_try_wait(a, parity)) return true;
     if (*abort_flag) return false;
     if (global_ns() - t0 > kWaitLimitNs) {
       *abort_flag = 1;
       return false;
     }
+    if (spin > 8) __nanosleep(64);  // leave issue slots to the working warps
   }
 }
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t mbar) {
@@ -147,6 +148,16 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const float *v) {
       : "memory");
 }
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+// Issue-only variants (no wait): the caller waits once for a batch.
+__device__ __forceinline__ void tmem_ld16_nw(uint32_t taddr, uint32_t *r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
 
 __device__ __forceinline__ float exp2i(int k) {  // exact 2^k for |k| < 126
   return __int_as_float((127 + k) << 23);
@@ -196,6 +207,7 @@ struct TcElem {
   double X[18];
   double ev[21];
   double cd[14];
+  float cf[14];  // the per-element coefficients rounded once to FP32
   double zn3w[C::NZ][3];
   double tc3w[C::NT][3];
   float zc1f[C::NZ][3], zc2f[C::NZ][3], zn3f[C::NZ][3], zwf[C::NZ];
@@ -256,21 +268,20 @@ __device__ __forceinline__ bool load_coef_tc(const FwdArgs &a, int64_t r, double
 }
 
 // FP32 point operator of element slot E at point q from the node tables;
-// sf = w det J (formed in FP64, rounded once).
+// sf = w det J (formed in FP64, rounded once); cf = coefficients in FP32.
 template <int P>
-__device__ __forceinline__ void tc_point(const TcElem<P> &E, const double *cd, int q, float sf, float *D) {
+__device__ __forceinline__ void tc_point(const TcElem<P> &E, const float *cf, int q, float sf, float *D) {
   using C = TcCfg<P>;
   const int iz = q / C::NT, t = q - iz * C::NT;
   float a0[3], a1[3];
   cross3(E.zc2f[iz], E.tc3f[t], a0);
   cross3(E.tc3f[t], E.zc1f[iz], a1);
   const float wf = E.zwf[iz] * E.twf[t];
-  float K[9], b[3];
+  dt_from_adj<float>(a0, a1, E.zn3f[iz], wf, sf, wf * wf / sf, cf, cf + 9, cf[12], cf[13], D);
+}
+__device__ __forceinline__ void coef_to_float(const double *cd, float *cf) {
 #pragma unroll
-  for (int k = 0; k < 9; ++k) K[k] = (float)cd[k];
-#pragma unroll
-  for (int k = 0; k < 3; ++k) b[k] = (float)cd[9 + k];
-  dt_from_adj<float>(a0, a1, E.zn3f[iz], wf, sf, wf * wf / sf, K, b, (float)cd[12], (float)cd[13], D);
+  for (int k = 0; k < 14; ++k) cf[k] = (float)cd[k];
 }
 
 // Shared-memory matrix descriptor of a K-major operand with ROWB-byte rows
@@ -378,7 +389,10 @@ __global__ void __launch_bounds__(TcCfg<P>::NTHREADS, 1) tc_forward_kernel(FwdAr
           E.boff = a.b_off ? a.b_off[e] : e * (int64_t)NSH;
           E.qoff = a.q_off ? a.q_off[e] : e * (int64_t)NQ;
           E.mbits = 0;
-          if (a.coef_mode == FEI_COEF_PER_ELEMENT) ok = load_coef_tc(a, e, E.cd);
+          if (a.coef_mode == FEI_COEF_PER_ELEMENT) {
+            ok = load_coef_tc(a, e, E.cd);
+            coef_to_float(E.cd, E.cf);
+          }
         }
         ok = __all_sync(0xffffffffu, ok);
         if (ln == 0) E.status = ok ? 0 : FEI_ERR_NONFINITE;
@@ -424,10 +438,12 @@ __global__ void __launch_bounds__(TcCfg<P>::NTHREADS, 1) tc_forward_kernel(FwdAr
         const int iz = q / NT, t = q - iz * NT;
         const double s = dot3(E.zn3w[iz], E.tc3w[t]);
         int st = point_status(s);
-        double cq[14];
-        const double *cp = E.cd;
+        float cq[14];
+        const float *cp = E.cf;
         if (a.coef_mode == FEI_COEF_PER_POINT) {
-          if (!load_coef_tc(a, E.qoff + q, cq)) st = FEI_ERR_NONFINITE;
+          double cdq[14];
+          if (!load_coef_tc(a, E.qoff + q, cdq)) st = FEI_ERR_NONFINITE;
+          coef_to_float(cdq, cq);
           cp = cq;
         }
         const float sf = (float)s;
@@ -505,10 +521,12 @@ __global__ void __launch_bounds__(TcCfg<P>::NTHREADS, 1) tc_forward_kernel(FwdAr
           const TcElem<P> &E = ax.el[el];
           float *D = ax.Dc[buf][el][qq];
           if (q < NQ && E.status == 0) {
-            double cq[14];
-            const double *cp = E.cd;
+            float cq[14];
+            const float *cp = E.cf;
             if (a.coef_mode == FEI_COEF_PER_POINT) {
-              load_coef_tc(a, E.qoff + q, cq);
+              double cdq[14];
+              load_coef_tc(a, E.qoff + q, cdq);
+              coef_to_float(cdq, cq);
               cp = cq;
             }
             float Dt[16];
@@ -646,24 +664,41 @@ __global__ void __launch_bounds__(TcCfg<P>::NTHREADS, 1) tc_forward_kernel(FwdAr
             break;
           }
           tc_fence_after();
+          // groups of two 16-column blocks: issue the loads of the partial
+          // (and of the running sum), wait once, add, store
 #pragma unroll
-          for (int b = 0; b < C::NMMA / 16; ++b) {
-            const int ncol = nh * C::NMMA + b * 16;  // column of A_e (and of R)
-            float v[16];
-            tmem_ld16(tmem + lane_base + pb * C::NMMA + b * 16, v);
-            if (ncol < C::RT) {
-              const uint32_t raddr = tmem + lane_base + 2 * C::NMMA + ncol;
-              if (c > 0) {
-                float rv[16];
-                tmem_ld16(raddr, rv);
+          for (int b0 = 0; b0 < C::NMMA / 16; b0 += 2) {
+            uint32_t pv[2][16], rv[2][16];
 #pragma unroll
-                for (int k2 = 0; k2 < 16; ++k2) v[k2] += rv[k2];
+            for (int j = 0; j < 2; ++j) {
+              const int b = b0 + j;
+              if (b < C::NMMA / 16) {
+                const int ncol = nh * C::NMMA + b * 16;
+                tmem_ld16_nw(tmem + lane_base + pb * C::NMMA + b * 16, pv[j]);
+                if (ncol < C::RT && c > 0) tmem_ld16_nw(tmem + lane_base + 2 * C::NMMA + ncol, rv[j]);
               }
-              tmem_st16(raddr, v);
-            } else if constexpr (C::RREG > 0) {
-              const int ro = ncol - C::RT;
+            }
+            tmem_wait_ld();
 #pragma unroll
-              for (int k2 = 0; k2 < 16; ++k2) rreg[ro + k2] = (c > 0 ? rreg[ro + k2] : 0.f) + v[k2];
+            for (int j = 0; j < 2; ++j) {
+              const int b = b0 + j;
+              if (b < C::NMMA / 16) {
+                const int ncol = nh * C::NMMA + b * 16;
+                float v[16];
+#pragma unroll
+                for (int k2 = 0; k2 < 16; ++k2) v[k2] = __uint_as_float(pv[j][k2]);
+                if (ncol < C::RT) {
+                  if (c > 0) {
+#pragma unroll
+                    for (int k2 = 0; k2 < 16; ++k2) v[k2] += __uint_as_float(rv[j][k2]);
+                  }
+                  tmem_st16(tmem + lane_base + 2 * C::NMMA + ncol, v);
+                } else if constexpr (C::RREG > 0) {
+                  const int ro = ncol - C::RT;
+#pragma unroll
+                  for (int k2 = 0; k2 < 16; ++k2) rreg[ro + k2] = (c > 0 ? rreg[ro + k2] : 0.f) + v[k2];
+                }
+              }
             }
           }
           tmem_wait_st();
