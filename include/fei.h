@@ -184,6 +184,31 @@ fei_status fei_plan_offsets(const int32_t *degree, int64_t n_elem,
                             int64_t *q_offset, int32_t *bad_count,
                             fei_stream_t stream);
 
+/* Largest batch fei_integrate_noalloc accepts. */
+#define FEI_NOALLOC_MAX_ELEM 262144
+
+/* fei_integrate without any device allocation (the paper has no
+ * counterpart; this serves callers that cannot allocate).  fei_integrate
+ * allocates scratch with cudaMalloc for a batch with a degree array (the
+ * per-degree element lists).  Callers that cannot have a library allocate
+ * -- code running while a stream is captured into a CUDA graph, code that
+ * must never block the device, applications whose device memory belongs to
+ * a pool or budget the library must not bypass -- call this instead.  Same
+ * arguments, layout, outputs and statuses as fei_integrate; the scratch is
+ * a fixed device array inside libfei (4 * (8 + 7 * FEI_NOALLOC_MAX_ELEM)
+ * bytes, about 7.3 MB, reserved on every GPU that loads the library until
+ * the process exits); no cudaMalloc, cudaFree or allocating routine is
+ * called.  n_elem > FEI_NOALLOC_MAX_ELEM -> FEI_ERR_INVALID_ARG.  Every
+ * call on a device shares that array and leaves its contents behind (the
+ * call clears the counts it needs); calls whose work overlaps on the GPU
+ * race on it, so order them on one stream.  The first call on a device
+ * looks the array's address up (cudaGetSymbolAddress): make it before any
+ * stream capture starts. */
+fei_status fei_integrate_noalloc(const fei_reference_t *refs, int nrefs,
+                                 const fei_batch *batch, fei_precision prec,
+                                 void *A_out, void *b_out, int32_t *elem_status,
+                                 fei_stream_t stream);
+
 /* Thread-local description of the last failure of the calling thread. */
 const char *fei_last_error_string(void);
 

@@ -32,6 +32,8 @@ FEI_COEF_PER_POINT = 1
 
 PRECISIONS = {"fp64": FEI_FP64, "fp32": FEI_FP32, "tc_f16x3": FEI_TC_F16X3}
 
+FEI_NOALLOC_MAX_ELEM = 262144
+
 
 class fei_batch(ctypes.Structure):
     _fields_ = [
@@ -78,11 +80,13 @@ def _load():
     lib.fei_integrate_backward.argtypes = [ref_p, ctypes.c_int, ctypes.POINTER(fei_batch), ctypes.c_int,
                                            vp, vp, vp, ctypes.POINTER(fei_coef_grad), vp]
     lib.fei_plan_offsets.argtypes = [vp, i64, vp, vp, vp, vp, vp]
+    lib.fei_integrate_noalloc.argtypes = [ref_p, ctypes.c_int, ctypes.POINTER(fei_batch), ctypes.c_int,
+                                          vp, vp, vp, vp]
     lib.fei_last_error_string.argtypes = []
     lib.fei_last_error_string.restype = ctypes.c_char_p
     for name in ("fei_reference_create", "fei_reference_destroy", "fei_reference_info",
                  "fei_reference_copy_table", "fei_integrate", "fei_integrate_backward",
-                 "fei_plan_offsets"):
+                 "fei_plan_offsets", "fei_integrate_noalloc"):
         getattr(lib, name).restype = i32
     return lib
 
