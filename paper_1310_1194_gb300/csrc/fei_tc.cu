@@ -32,12 +32,15 @@
 //   warp 0       TMEM owner; lane 0 streams the pre-swizzled B operand (the
 //                split G image) into shared memory with cp.async.bulk;
 //   warp 1       lane 0 issues tcgen05.mma (M = 128, N = N_pad or 2 halves);
-//   warps 2..9   producers: per tile, the point operators of the touched
-//                elements and their scales; per K chunk, H' for the 128
-//                rows, split into hi/lo, written in the swizzled K-major
-//                operand layout; the load vector b_e and the statuses;
-//   warps 10..13 epilogue: promotion of every partial accumulator, then
-//                scaling and coalesced stores of A_e.
+//   warps 2..3   point operators: per tile, the touched elements' geometry
+//                (FP64 node columns, w det J at every point), their scales
+//                and the row data; per K chunk, the point operators of its
+//                points into a ring that runs ahead of the producers;
+//   warps 4..11  producers: per K chunk, H' for the 128 rows, split into
+//                hi/lo, written in the swizzled K-major operand layout, and
+//                the partial load vectors;
+//   warps 12..15 epilogue: promotion of every partial accumulator, then
+//                scaling and coalesced stores of A_e, b_e and the statuses.
 // All hand-offs are mbarriers; every wait is bounded by a time limit after
 // which the block raises an abort flag, marks its remaining elements with
 // FEI_ERR_TIMEOUT, drains its MMAs, frees its TMEM and exits.
@@ -180,38 +183,45 @@ struct TcCfg {
   static constexpr int PPC = KCH / 4;         // points per chunk
   static constexpr int KSL = KCH / 16;        // 16-wide K slices per chunk
   static constexpr int NCHUNK = (NQ + PPC - 1) / PPC;
+  // chunks per promotion unit: a partial accumulator collects 4 K slices
+  // (12 MMAs) before the epilogue adds it into the running sum
+  static constexpr int UC = KSL == 2 ? 2 : 1;
   static constexpr int TMEM_COLS = 3 * NPAD <= 256 ? 256 : 512;
   // running sum: columns [0, RT) in TMEM after the two partial buffers, the
   // rest (RREG columns) in registers of the epilogue threads
   static constexpr int RT = (512 - 2 * NMMA) < NPAD ? (512 - 2 * NMMA) : NPAD;
   static constexpr int RREG = NPAD - RT;
   static constexpr int EMAX = (128 + NSH - 1) / NSH + 1;
+  static constexpr int NDW = 2;  // point-operator warps
   static constexpr int NPW = 8;  // producer warps
   static constexpr int NEW = 4;  // epilogue warps
-  static constexpr int NTHREADS = (2 + NPW + NEW) * 32;
+  static constexpr int W_DW = 2, W_PW = W_DW + NDW, W_EW = W_PW + NPW;
+  static constexpr int NTHREADS = (2 + NDW + NPW + NEW) * 32;
   static constexpr int QPG = PPC / 2;  // points per producer thread per chunk
+  static constexpr int DRING = 4;      // chunks of point operators ahead
   static constexpr int A_BYTES = 128 * ROWB;
   static constexpr int B_BYTES = NPAD * ROWB;
   static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
-  static constexpr int STAGES = P == 3 ? 4 : P == 4 ? 3 : P == 5 ? 3 : P == 6 ? 2 : 3;
+  static constexpr int STAGES = P == 3 ? 4 : P == 4 ? 3 : P == 5 ? 2 : P == 6 ? 2 : 3;
   static constexpr int DYN_SMEM = STAGES * STAGE_BYTES + 1024;
   static_assert(NMMA % 16 == 0 && NMMA <= 256, "MMA N");
   static_assert(RT % 16 == 0 && RREG % 16 == 0 && RT >= 0, "running-sum split");
   static_assert(2 * NMMA + RT <= TMEM_COLS, "tensor memory");
   static_assert(QPG % 2 == 0, "two points per 16-byte chunk");
+  static_assert(STAGES > UC, "a promotion unit must leave a stage for the producers");
+  static_assert(W_EW % 4 == 0, "epilogue warps cover the four TMEM lane quarters in order");
 };
 
 template <int P>
 struct TcElem {
   using C = TcCfg<P>;
   double X[18];
-  double ev[21];
-  double cd[14];
-  float cf[14];  // the per-element coefficients rounded once to FP32
-  double zn3w[C::NZ][3];
-  double tc3w[C::NT][3];
-  float zc1f[C::NZ][3], zc2f[C::NZ][3], zn3f[C::NZ][3], zwf[C::NZ];
-  float tc3f[C::NT][3], twf[C::NT];
+  double ev[21];          // element vectors A1, B1, A2, B2, C, D1, D2 (FP64)
+  float evf[21];          // the same rounded once to FP32
+  float cf[14];           // the per-element coefficients rounded once to FP32
+  double zabg[C::NZ][3];  // w_z (n3.C, n3.D1, n3.D2) per vertical node (FP64)
+  float zc1f[C::NZ][3], zc2f[C::NZ][3], zn3f[C::NZ][3];
+  float tc3f[C::NT][3];
   int64_t e, aoff, boff, qoff;
   int status;
   int mbits;   // float bits of max_{q,b} sum_a |Dt[a][b]|
@@ -219,10 +229,14 @@ struct TcElem {
   float down;  // 2^-(sigma + 2 tau)
 };
 
+// Per-tile row data handed from the point-operator warps to the producers
+// (load vector, statuses) and to the epilogue (stores of A_e).
 struct TcMeta {
-  int64_t row_off[128];  // start of the row in A_out, -1 for rows past the end
-  float row_down[128];   // exact scale back of the row's element
-  int row_zero[128];     // element flagged: write zeros
+  int64_t row_off[128];   // start of the row in A_out, -1 for rows past the end
+  int64_t row_boff[128];  // position of the row in b_out
+  int64_t row_eid[128];   // element id of the row
+  float row_down[128];    // exact scale back of the row's element
+  int row_status[128];    // status of the row's element (nonzero: write zeros)
 };
 
 template <int P>
@@ -231,21 +245,25 @@ struct TcAux {
   uint64_t full[C::STAGES];   // producers wrote A of the stage
   uint64_t bfull[C::STAGES];  // B of the stage landed
   uint64_t empty[C::STAGES];  // MMAs of the stage completed
+  uint64_t dfull[C::DRING];   // point operators of a chunk ready
+  uint64_t dempty[C::DRING];  // producers done with them
   uint64_t part_full[2];      // partial accumulator ready for promotion
   uint64_t promo_done[2];     // partial accumulator promoted (free again)
   uint64_t meta_full[2];
   uint64_t meta_empty[2];
+  uint64_t bsum_full[2];      // producers' load-vector partials of a tile
   uint64_t drain;
   uint32_t tmem_base;
   int abort_flag;
-  int psnap;
-  int n_el;
-  int64_t k_first;
+  int dsnap;
   TcElem<P> el[C::EMAX];
-  alignas(16) float Dc[2][C::EMAX][C::PPC][16];
   float sp[C::EMAX][C::NQ];  // w det J per point (FP32, from FP64)
+  double ttab[C::NT][3];     // (w_t, w_t xi1, w_t xi2) per triangle node
+  float ttabf[C::NT][3];     // (w_t, xi1, xi2) in FP32
+  float ztabf[C::NZ][2];     // (zeta, w_z) in FP32
+  alignas(16) float Dc[C::DRING][C::EMAX][C::PPC][16];
   TcMeta meta[2];
-  float bsum[128];
+  float bsum[2][C::NPW * 32 / 128][128];
   alignas(16) float stg[C::NEW][32][17];  // epilogue transpose staging
 };
 
@@ -270,14 +288,34 @@ __device__ __forceinline__ bool load_coef_tc(const FwdArgs &a, int64_t r, double
 // FP32 point operator of element slot E at point q from the node tables;
 // sf = w det J (formed in FP64, rounded once); cf = coefficients in FP32.
 template <int P>
-__device__ __forceinline__ void tc_point(const TcElem<P> &E, const float *cf, int q, float sf, float *D) {
+__device__ __forceinline__ void tc_point(const TcElem<P> &E, const TcAux<P> &ax, const float *cf, int q, float sf,
+                                         float *D) {
   using C = TcCfg<P>;
   const int iz = q / C::NT, t = q - iz * C::NT;
   float a0[3], a1[3];
   cross3(E.zc2f[iz], E.tc3f[t], a0);
   cross3(E.tc3f[t], E.zc1f[iz], a1);
-  const float wf = E.zwf[iz] * E.twf[t];
+  const float wf = ax.ztabf[iz][1] * ax.ttabf[t][0];
   dt_from_adj<float>(a0, a1, E.zn3f[iz], wf, sf, wf * wf / sf, cf, cf + 9, cf[12], cf[13], D);
+}
+// finite test by the exponent bits (integer pipe; FP64 compares are slow here)
+__device__ __forceinline__ bool finite_bits(double x) {
+  return ((__double_as_longlong(x) >> 52) & 0x7ff) != 0x7ff;
+}
+// One component (j = vector * 3 + axis) of the element vectors, FP64:
+// A1, B1, A2, B2, C, D1, D2 from the bottom (P) and top (Q) vertices.
+__device__ __forceinline__ double elem_vector_component(const double *X, int j) {
+  const int v = j / 3, k = j - 3 * v;
+  const double p0 = X[k], p1 = X[3 + k], p2 = X[6 + k], q0 = X[9 + k], q1 = X[12 + k], q2 = X[15 + k];
+  switch (v) {
+    case 0: return 0.5 * ((p1 - p0) + (q1 - q0));
+    case 1: return 0.5 * ((q1 - q0) - (p1 - p0));
+    case 2: return 0.5 * ((p2 - p0) + (q2 - q0));
+    case 3: return 0.5 * ((q2 - q0) - (p2 - p0));
+    case 4: return 0.5 * (q0 - p0);
+    case 5: return 0.5 * ((q1 - p1) - (q0 - p0));
+    default: return 0.5 * ((q2 - p2) - (q0 - p0));
+  }
 }
 __device__ __forceinline__ void coef_to_float(const double *cd, float *cf) {
 #pragma unroll
@@ -313,7 +351,7 @@ template <int P>
 __global__ void __launch_bounds__(TcCfg<P>::NTHREADS, 1) tc_forward_kernel(FwdArgs a, const __half *img, int tau) {
   using C = TcCfg<P>;
   constexpr int NSH = C::NSH, NQ = C::NQ, NT = C::NT, NZ = C::NZ, S = C::STAGES, NCH = C::NCHUNK;
-  constexpr int NP = C::NPW * 32, PPC = C::PPC, ROWB = C::ROWB;
+  constexpr int NP = C::NPW * 32, ND = C::NDW * 32, PPC = C::PPC, ROWB = C::ROWB, DR = C::DRING;
   extern __shared__ __align__(1024) unsigned char dsm_raw[];
   __shared__ TcAux<P> ax;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -328,11 +366,16 @@ __global__ void __launch_bounds__(TcCfg<P>::NTHREADS, 1) tc_forward_kernel(FwdAr
       mbar_init(smem_u32(&ax.bfull[s]), 1);
       mbar_init(smem_u32(&ax.empty[s]), 1);
     }
+    for (int k = 0; k < DR; ++k) {
+      mbar_init(smem_u32(&ax.dfull[k]), 1);
+      mbar_init(smem_u32(&ax.dempty[k]), C::NPW);
+    }
     for (int k = 0; k < 2; ++k) {
       mbar_init(smem_u32(&ax.part_full[k]), 1);
       mbar_init(smem_u32(&ax.promo_done[k]), C::NEW);
       mbar_init(smem_u32(&ax.meta_full[k]), 1);
       mbar_init(smem_u32(&ax.meta_empty[k]), C::NEW);
+      mbar_init(smem_u32(&ax.bsum_full[k]), C::NPW);
     }
     mbar_init(smem_u32(&ax.drain), 1);
     ax.abort_flag = 0;
@@ -344,6 +387,20 @@ __global__ void __launch_bounds__(TcCfg<P>::NTHREADS, 1) tc_forward_kernel(FwdAr
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
+  // quadrature node tables of this degree, once per block
+  for (int t = tid; t < NT; t += blockDim.x) {
+    const double x1 = a.tnode[4 * t], x2 = a.tnode[4 * t + 1], wt = a.tnode[4 * t + 2];
+    ax.ttab[t][0] = wt;
+    ax.ttab[t][1] = wt * x1;
+    ax.ttab[t][2] = wt * x2;
+    ax.ttabf[t][0] = (float)wt;
+    ax.ttabf[t][1] = (float)x1;
+    ax.ttabf[t][2] = (float)x2;
+  }
+  for (int z = tid; z < NZ; z += blockDim.x) {
+    ax.ztabf[z][0] = (float)a.znode[2 * z];
+    ax.ztabf[z][1] = (float)a.znode[2 * z + 1];
+  }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -353,118 +410,146 @@ __global__ void __launch_bounds__(TcCfg<P>::NTHREADS, 1) tc_forward_kernel(FwdAr
   const int64_t rows_total = items * NSH;
   const int64_t tiles = (rows_total + 127) / 128;
 
-  if (warp >= 2 && warp < 2 + C::NPW) {
-    // ================================================================ producers
-    const int tp = tid - 64;  // 0 .. NP-1
-    const int r = tp & 127, grp = tp >> 7;
+  if (warp >= C::W_DW && warp < C::W_PW) {
+    // ======================================================== point operators
+    // Per tile: the touched elements' geometry, FP64 node columns, w det J
+    // at every point, the scale bound and the row data; per chunk: the
+    // point operators of its points (pre-scaled by 2^sigma) into a ring.
+    const int td = tid - C::W_DW * 32;  // 0 .. ND-1
     int it = 0;
-    int64_t tile = blockIdx.x;
-    for (; tile < tiles; tile += gridDim.x, ++it) {
+    for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++it) {
+      // both point-operator warps leave together (they share named barriers)
+      if (td == 0) ax.dsnap = *abort_flag;
+      named_bar(2, ND);
+      if (ax.dsnap) break;
       const int64_t r0 = tile * 128;
-      if (tp == 0) {
-        ax.psnap = *abort_flag;
-        const int64_t k0 = r0 / NSH;
-        int64_t k1 = (r0 + 127) / NSH;
-        if (k1 > items - 1) k1 = items - 1;
-        ax.k_first = k0;
-        ax.n_el = (int)(k1 - k0 + 1);
-      }
-      named_bar(1, NP);
-      if (ax.psnap) break;
-      const int nel = ax.n_el;
-      const int64_t k0 = ax.k_first;
-      // geometry and coefficients of the touched elements
-      if (tp < nel * 32) {
-        const int el = tp >> 5, ln = tp & 31;
+      const int64_t k0 = r0 / NSH;
+      int64_t k1 = (r0 + 127) / NSH;
+      if (k1 > items - 1) k1 = items - 1;
+      const int nel = (int)(k1 - k0 + 1);
+      // geometry and coefficients of the touched elements (one warp per
+      // element: lanes 0-17 the vertices, 18-31 the coefficients).  FP64 is
+      // slow per instruction on this part, so every FP64 step below runs
+      // across lanes rather than in one thread.
+      for (int el = warp - C::W_DW; el < nel; el += C::NDW) {
         TcElem<P> &E = ax.el[el];
         const int64_t e = a.list ? (int64_t)a.list[k0 + el] : k0 + el;
         bool ok = true;
-        if (ln < 18) {
-          E.X[ln] = a.geom[18 * e + ln];
-          ok = isfinite(E.X[ln]);
+        if (lane < 18) {
+          const double x = a.geom[18 * e + lane];
+          E.X[lane] = x;
+          ok = finite_bits(x);
+        } else if (a.coef_mode == FEI_COEF_PER_ELEMENT) {
+          const int k = lane - 18;
+          const double x = k < 9 ? a.K[9 * e + k] : k < 12 ? a.b[3 * e + (k - 9)] : k == 12 ? a.c[e] : a.f[e];
+          E.cf[k] = (float)x;
+          ok = finite_bits(x);
         }
-        if (ln == 20) {
+        if (lane == 0) {
           E.e = e;
           E.aoff = a.A_off ? a.A_off[e] : e * (int64_t)(NSH * NSH);
           E.boff = a.b_off ? a.b_off[e] : e * (int64_t)NSH;
           E.qoff = a.q_off ? a.q_off[e] : e * (int64_t)NQ;
           E.mbits = 0;
-          if (a.coef_mode == FEI_COEF_PER_ELEMENT) {
-            ok = load_coef_tc(a, e, E.cd);
-            coef_to_float(E.cd, E.cf);
-          }
         }
         ok = __all_sync(0xffffffffu, ok);
-        if (ln == 0) E.status = ok ? 0 : FEI_ERR_NONFINITE;
+        if (lane == 0) E.status = ok ? 0 : FEI_ERR_NONFINITE;
       }
-      named_bar(1, NP);
-      if (tp < nel) elem_vectors(ax.el[tp].X, ax.el[tp].ev);
-      named_bar(1, NP);
-      // node tables: vertical nodes (c1, c2, n3) and triangle nodes (c3)
-      for (int idx = tp; idx < nel * (NZ + NT); idx += NP) {
+      named_bar(2, ND);
+      // element vectors, one component per thread (FP64, and rounded once)
+      for (int idx = td; idx < nel * 21; idx += ND) {
+        const int el = idx / 21, j = idx - el * 21;
+        const double v = elem_vector_component(ax.el[el].X, j);
+        ax.el[el].ev[j] = v;
+        ax.el[el].evf[j] = (float)v;
+      }
+      named_bar(2, ND);
+      // vertical nodes: c1, c2, n3 = c1 x c2 and w_z (n3.C, n3.D1, n3.D2) in
+      // FP64 (so that w det J = w_t (..) below is FP64), the columns for the
+      // FP32 adjugate from the FP32 element vectors; triangle nodes: c3 in FP32
+      for (int idx = td; idx < nel * (NZ + NT); idx += ND) {
         const int el = idx / (NZ + NT), nd = idx - el * (NZ + NT);
         TcElem<P> &E = ax.el[el];
         if (nd < NZ) {
-          double c1[3], c2[3], n3[3];
           const double z = a.znode[2 * nd], wz = a.znode[2 * nd + 1];
+          double c1[3], c2[3], n3[3];
           znode_columns(E.ev, z, c1, c2, n3);
+          E.zabg[nd][0] = wz * dot3(n3, E.ev + 12);
+          E.zabg[nd][1] = wz * dot3(n3, E.ev + 15);
+          E.zabg[nd][2] = wz * dot3(n3, E.ev + 18);
+          const float zf = ax.ztabf[nd][0];
+          float f1[3], f2[3], fn[3];
 #pragma unroll
           for (int k = 0; k < 3; ++k) {
-            E.zc1f[nd][k] = (float)c1[k];
-            E.zc2f[nd][k] = (float)c2[k];
-            E.zn3f[nd][k] = (float)n3[k];
-            E.zn3w[nd][k] = wz * n3[k];
+            f1[k] = fmaf(zf, E.evf[3 + k], E.evf[0 + k]);
+            f2[k] = fmaf(zf, E.evf[9 + k], E.evf[6 + k]);
           }
-          E.zwf[nd] = (float)wz;
+          cross3(f1, f2, fn);
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            E.zc1f[nd][k] = f1[k];
+            E.zc2f[nd][k] = f2[k];
+            E.zn3f[nd][k] = fn[k];
+          }
         } else {
           const int t = nd - NZ;
-          double c3[3];
-          const double wt = a.tnode[4 * t + 2];
-          tnode_column(E.ev, a.tnode[4 * t], a.tnode[4 * t + 1], c3);
+          const float x1 = ax.ttabf[t][1], x2 = ax.ttabf[t][2];
 #pragma unroll
-          for (int k = 0; k < 3; ++k) {
-            E.tc3f[t][k] = (float)c3[k];
-            E.tc3w[t][k] = wt * c3[k];
+          for (int k = 0; k < 3; ++k) E.tc3f[t][k] = fmaf(x2, E.evf[18 + k], fmaf(x1, E.evf[15 + k], E.evf[12 + k]));
+        }
+      }
+      named_bar(2, ND);
+      // pre-pass over all points: w det J = w_t (a + xi1 b + xi2 g) in FP64
+      // (rounded once), status, and the bound max_{q,b} sum_a |Dt[a][b]|
+      // that sets the element's scale
+      for (int base = 0; base < nel * NQ; base += ND) {
+        const int idx = base + td;
+        int el = -1;
+        float m = 0.f;
+        if (idx < nel * NQ) {
+          el = idx / NQ;
+          const int q = idx - el * NQ;
+          TcElem<P> &E = ax.el[el];
+          const int iz = q / NT, t = q - iz * NT;
+          const double s = ax.ttab[t][0] * E.zabg[iz][0] + ax.ttab[t][1] * E.zabg[iz][1] + ax.ttab[t][2] * E.zabg[iz][2];
+          const float sf = (float)s;
+          int st = !finite_bits(s) ? FEI_ERR_NONFINITE : (!(sf > 0.f) ? FEI_ERR_NEGATIVE_JACOBIAN : 0);
+          float cq[14];
+          const float *cp = E.cf;
+          if (a.coef_mode == FEI_COEF_PER_POINT) {
+            double cdq[14];
+            if (!load_coef_tc(a, E.qoff + q, cdq)) st = FEI_ERR_NONFINITE;
+            coef_to_float(cdq, cq);
+            cp = cq;
           }
-          E.twf[t] = (float)wt;
+          ax.sp[el][q] = sf;
+          if (st) {
+            atomicMax(&E.status, st);
+          } else {
+            float D[16];
+            tc_point<P>(E, ax, cp, q, sf, D);
+            const float m0 = fabsf(D[0]);
+            const float m1 = fabsf(D[1]) + fabsf(D[4]) + fabsf(D[7]) + fabsf(D[10]);
+            const float m2 = fabsf(D[2]) + fabsf(D[5]) + fabsf(D[8]) + fabsf(D[11]);
+            const float m3 = fabsf(D[3]) + fabsf(D[6]) + fabsf(D[9]) + fabsf(D[12]);
+            m = fmaxf(fmaxf(m0, m1), fmaxf(m2, m3));
+            if (!(m <= 3.0e38f)) {
+              atomicMax(&E.status, FEI_ERR_NONFINITE);
+              m = 0.f;
+            }
+          }
+        }
+        // one atomic per element per warp (the bound is a max of
+        // non-negative floats, so their bit patterns order as integers)
+        const int el0 = __shfl_sync(0xffffffffu, el, 0), el1 = __shfl_sync(0xffffffffu, el, 31);
+        for (int e2 = el0 < 0 ? 0 : el0; e2 <= el1 && e2 < nel; ++e2) {
+          const unsigned mb = __reduce_max_sync(0xffffffffu, el == e2 ? __float_as_uint(m) : 0u);
+          if (lane == 0 && mb) atomicMax(&ax.el[e2].mbits, (int)mb);
         }
       }
-      named_bar(1, NP);
-      // pre-pass over all points: w det J (FP64 -> FP32), status, and the
-      // bound max_{q,b} sum_a |Dt[a][b]| that sets the element's scale
-      for (int idx = tp; idx < nel * NQ; idx += NP) {
-        const int el = idx / NQ, q = idx - el * NQ;
-        TcElem<P> &E = ax.el[el];
-        const int iz = q / NT, t = q - iz * NT;
-        const double s = dot3(E.zn3w[iz], E.tc3w[t]);
-        int st = point_status(s);
-        float cq[14];
-        const float *cp = E.cf;
-        if (a.coef_mode == FEI_COEF_PER_POINT) {
-          double cdq[14];
-          if (!load_coef_tc(a, E.qoff + q, cdq)) st = FEI_ERR_NONFINITE;
-          coef_to_float(cdq, cq);
-          cp = cq;
-        }
-        const float sf = (float)s;
-        ax.sp[el][q] = sf;
-        if (st) {
-          atomicMax(&E.status, st);
-        } else {
-          float D[16];
-          tc_point<P>(E, cp, q, sf, D);
-          float m0 = fabsf(D[0]);
-          float m1 = fabsf(D[1]) + fabsf(D[4]) + fabsf(D[7]) + fabsf(D[10]);
-          float m2 = fabsf(D[2]) + fabsf(D[5]) + fabsf(D[8]) + fabsf(D[11]);
-          float m3 = fabsf(D[3]) + fabsf(D[6]) + fabsf(D[9]) + fabsf(D[12]);
-          const float m = fmaxf(fmaxf(m0, m1), fmaxf(m2, m3));
-          if (!(m <= 3.0e38f)) atomicMax(&E.status, FEI_ERR_NONFINITE);
-          else atomicMax(&E.mbits, __float_as_int(m));
-        }
-      }
-      named_bar(1, NP);
-      if (tp < nel) {
-        TcElem<P> &E = ax.el[tp];
+      named_bar(2, ND);
+      if (td < nel) {
+        TcElem<P> &E = ax.el[td];
         // The A operand is H' 2^sigma built from the scaled table G 2^tau,
         // so |A| <= M 2^sigma max|G 2^tau| <= M 2^sigma 2^14: sigma = -ex
         // with M <= 2^ex keeps it within 2^14.  D = A_e 2^(sigma + 2 tau).
@@ -477,86 +562,106 @@ __global__ void __launch_bounds__(TcCfg<P>::NTHREADS, 1) tc_forward_kernel(FwdAr
         const int dn = -(sigma + 2 * tau);
         E.down = dn >= -126 && dn <= 126 ? exp2i(dn) : ldexpf(1.0f, dn);
       }
-      // row metadata, double-buffered for the epilogue of this tile
+      named_bar(2, ND);
+      // row data of this tile (double-buffered by tile parity)
       const int slot = it & 1;
-      if (tp == 0) {
-        const uint32_t k = (uint32_t)(it >> 1);
-        ax.psnap = mbar_wait(smem_u32(&ax.meta_empty[slot]), (k & 1u) ^ 1u, abort_flag) ? 0 : 1;
+      const bool mok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&ax.meta_empty[slot]), ((uint32_t)(it >> 1) & 1u) ^ 1u, abort_flag));
+      if (mok) {
+        TcMeta &M = ax.meta[slot];
+        for (int r = td; r < 128; r += ND) {
+          const int64_t grow = r0 + r;
+          if (grow < rows_total) {
+            const int64_t k = grow / NSH;
+            const int ri = (int)(grow - k * NSH);
+            const TcElem<P> &E = ax.el[k - k0];
+            M.row_off[r] = E.aoff + (int64_t)ri * NSH;
+            M.row_boff[r] = E.boff + ri;
+            M.row_eid[r] = ri == 0 ? E.e : -1;
+            M.row_down[r] = E.down;
+            M.row_status[r] = E.status;
+          } else {
+            M.row_off[r] = -1;
+            M.row_boff[r] = -1;
+            M.row_eid[r] = -1;
+            M.row_down[r] = 0.f;
+            M.row_status[r] = 0;
+          }
+        }
       }
-      named_bar(1, NP);
-      const bool live = ax.psnap == 0;
+      named_bar(2, ND);
+      if (td == 0 && mok) mbar_arrive(smem_u32(&ax.meta_full[slot]));
+      // point operators, chunk by chunk, into the ring
+      for (int c = 0; c < NCH; ++c) {
+        const int g = it * NCH + c, dr = g % DR;
+        const uint32_t u = (uint32_t)(g / DR);
+        const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&ax.dempty[dr]), (u & 1u) ^ 1u, abort_flag));
+        if (ok) {
+          for (int idx = td; idx < nel * PPC; idx += ND) {
+            const int el = idx / PPC, qq = idx - el * PPC, q = c * PPC + qq;
+            const TcElem<P> &E = ax.el[el];
+            float *D = ax.Dc[dr][el][qq];
+            if (q < NQ && E.status == 0) {
+              float cq[14];
+              const float *cp = E.cf;
+              if (a.coef_mode == FEI_COEF_PER_POINT) {
+                double cdq[14];
+                load_coef_tc(a, E.qoff + q, cdq);
+                coef_to_float(cdq, cq);
+                cp = cq;
+              }
+              float Dt[16];
+              tc_point<P>(E, ax, cp, q, ax.sp[el][q], Dt);
+#pragma unroll
+              for (int k = 0; k < 13; ++k) D[k] = Dt[k] * E.up;
+              D[13] = Dt[13];
+              D[14] = 0.f;
+              D[15] = 0.f;
+            } else {
+#pragma unroll
+              for (int k = 0; k < 16; ++k) D[k] = 0.f;
+            }
+          }
+        }
+        named_bar(2, ND);
+        if (td == 0 && ok) mbar_arrive(smem_u32(&ax.dfull[dr]));
+      }
+    }
+  } else if (warp >= C::W_PW && warp < C::W_EW) {
+    // ================================================================ producers
+    const int tp = tid - C::W_PW * 32;  // 0 .. NP-1
+    const int r = tp & 127, grp = tp >> 7;
+    int it = 0;
+    int64_t tile = blockIdx.x;
+    for (; tile < tiles; tile += gridDim.x, ++it) {
+      if (*abort_flag) break;
+      const int64_t r0 = tile * 128;
+      const int64_t k0 = r0 / NSH;
       const int64_t grow = r0 + r;
-      const bool rvalid = grow < rows_total && live;
+      const bool rvalid = grow < rows_total;
       int rel = 0, ri = 0;
-      if (grow < rows_total) {
+      if (rvalid) {
         const int64_t k = grow / NSH;
         ri = (int)(grow - k * NSH);
         rel = (int)(k - k0);
       }
-      if (grp == 0 && live) {
-        TcMeta &M = ax.meta[slot];
-        if (rvalid) {
-          const TcElem<P> &E = ax.el[rel];
-          M.row_off[r] = E.aoff + (int64_t)ri * NSH;
-          M.row_down[r] = E.down;
-          M.row_zero[r] = E.status != 0;
-        } else {
-          M.row_off[r] = -1;
-          M.row_down[r] = 0.f;
-          M.row_zero[r] = 1;
-        }
-      }
-      named_bar(1, NP);
-      if (tp == 0 && live) mbar_arrive(smem_u32(&ax.meta_full[slot]));
       float bpart = 0.f;
-      // K chunks
       for (int c = 0; c < NCH; ++c) {
-        const int g = it * NCH + c, s = g % S;
-        const uint32_t u = (uint32_t)(g / S);
-        const int buf = c & 1;
-        // point operators of this chunk, pre-scaled by 2^sigma (entry 13,
-        // w det J f for the load vector, unscaled)
-        if (tp < nel * PPC) {
-          const int el = tp / PPC, qq = tp - el * PPC, q = c * PPC + qq;
-          const TcElem<P> &E = ax.el[el];
-          float *D = ax.Dc[buf][el][qq];
-          if (q < NQ && E.status == 0) {
-            float cq[14];
-            const float *cp = E.cf;
-            if (a.coef_mode == FEI_COEF_PER_POINT) {
-              double cdq[14];
-              load_coef_tc(a, E.qoff + q, cdq);
-              coef_to_float(cdq, cq);
-              cp = cq;
-            }
-            float Dt[16];
-            tc_point<P>(E, cp, q, ax.sp[el][q], Dt);
-#pragma unroll
-            for (int k = 0; k < 13; ++k) D[k] = Dt[k] * E.up;
-            D[13] = Dt[13];
-            D[14] = 0.f;
-            D[15] = 0.f;
-          } else {
-#pragma unroll
-            for (int k = 0; k < 16; ++k) D[k] = 0.f;
-          }
-        }
-        named_bar(1, NP);
-        // wait for this stage: B landed (G is read from it) and A free.  A
-        // failed wait does not leave the loop (every producer must reach the
-        // named barriers); the warp only stops producing.
-        bool ok = live && mbar_wait(smem_u32(&ax.bfull[s]), u & 1u, abort_flag);
+        const int g = it * NCH + c, s = g % S, dr = g % DR;
+        const uint32_t u = (uint32_t)(g / S), ud = (uint32_t)(g / DR);
+        // B landed (G is read from it), A slot free, point operators ready
+        bool ok = mbar_wait(smem_u32(&ax.bfull[s]), u & 1u, abort_flag);
         ok = ok && mbar_wait(smem_u32(&ax.empty[s]), (u & 1u) ^ 1u, abort_flag);
+        ok = ok && mbar_wait(smem_u32(&ax.dfull[dr]), ud & 1u, abort_flag);
         ok = __all_sync(0xffffffffu, ok);
-        if (!ok) continue;
+        if (!ok) break;
         const uint32_t bh = stageB(s), bl = bh + C::B_BYTES;
         const uint32_t ah = stageA(s, 0), alo = stageA(s, 1);
         // this thread: row r, points grp*QPG .. of the chunk = 16-byte chunks
         // grp*QPG/2 .. of the operand row (two points each)
+        uint32_t hw[C::QPG / 2][4], lw[C::QPG / 2][4];
 #pragma unroll
         for (int pc = 0; pc < C::QPG / 2; ++pc) {
           const int chunk = grp * (C::QPG / 2) + pc;
-          uint32_t hw[4], lw[4];
           if (rvalid) {
             const uint32_t goff = sw_off<ROWB>(ri, chunk);
             uint4 gh, gl;
@@ -570,7 +675,7 @@ __global__ void __launch_bounds__(TcCfg<P>::NTHREADS, 1) tc_forward_kernel(FwdAr
 #pragma unroll
             for (int h2 = 0; h2 < 2; ++h2) {  // two points per 16-byte chunk
               const int qq = chunk * 2 + h2;  // point within the chunk
-              const float *D = ax.Dc[buf][rel][qq];
+              const float *D = ax.Dc[dr][rel][qq];
               float gv[4];
 #pragma unroll
               for (int ab = 0; ab < 2; ++ab) {
@@ -597,38 +702,44 @@ __global__ void __launch_bounds__(TcCfg<P>::NTHREADS, 1) tc_forward_kernel(FwdAr
               const float2 f01 = __half22float2(h01), f23 = __half22float2(h23);
               const __half2 l01 = __floats2half2_rn(hv[0] - f01.x, hv[1] - f01.y);
               const __half2 l23 = __floats2half2_rn(hv[2] - f23.x, hv[3] - f23.y);
-              memcpy(&hw[2 * h2], &h01, 4);
-              memcpy(&hw[2 * h2 + 1], &h23, 4);
-              memcpy(&lw[2 * h2], &l01, 4);
-              memcpy(&lw[2 * h2 + 1], &l23, 4);
+              memcpy(&hw[pc][2 * h2], &h01, 4);
+              memcpy(&hw[pc][2 * h2 + 1], &h23, 4);
+              memcpy(&lw[pc][2 * h2], &l01, 4);
+              memcpy(&lw[pc][2 * h2 + 1], &l23, 4);
             }
           } else {
 #pragma unroll
-            for (int k = 0; k < 4; ++k) hw[k] = lw[k] = 0u;
+            for (int k = 0; k < 4; ++k) hw[pc][k] = lw[pc][k] = 0u;
           }
+        }
+        // the point operators of this chunk are consumed
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&ax.dempty[dr]));
+#pragma unroll
+        for (int pc = 0; pc < C::QPG / 2; ++pc) {
+          const int chunk = grp * (C::QPG / 2) + pc;
           const uint32_t aoff = sw_off<ROWB>(r, chunk);
-          asm volatile("st.shared.v4.b32 [%0], {%1,%2,%3,%4};" ::"r"(ah + aoff), "r"(hw[0]), "r"(hw[1]), "r"(hw[2]),
-                       "r"(hw[3])
+          asm volatile("st.shared.v4.b32 [%0], {%1,%2,%3,%4};" ::"r"(ah + aoff), "r"(hw[pc][0]), "r"(hw[pc][1]),
+                       "r"(hw[pc][2]), "r"(hw[pc][3])
                        : "memory");
-          asm volatile("st.shared.v4.b32 [%0], {%1,%2,%3,%4};" ::"r"(alo + aoff), "r"(lw[0]), "r"(lw[1]), "r"(lw[2]),
-                       "r"(lw[3])
+          asm volatile("st.shared.v4.b32 [%0], {%1,%2,%3,%4};" ::"r"(alo + aoff), "r"(lw[pc][0]), "r"(lw[pc][1]),
+                       "r"(lw[pc][2]), "r"(lw[pc][3])
                        : "memory");
         }
         fence_proxy_async();
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_u32(&ax.full[s]));
       }
-      // load vector: combine the point groups, write b_e rows and statuses
-      ax.bsum[r] = 0.f;
-      named_bar(1, NP);
-      atomicAdd(&ax.bsum[r], bpart);
-      named_bar(1, NP);
-      if (grp == 0 && rvalid) {
-        const TcElem<P> &E = ax.el[rel];
-        const float bval = E.status ? 0.f : ax.bsum[r] * exp2i(-tau);
-        reinterpret_cast<float *>(a.bv)[E.boff + ri] = bval;
-        if (ri == 0) a.status[E.e] = E.status;
-      }
+      if (*abort_flag) break;
+      // load-vector partials of this tile for the epilogue (the slot is free
+      // once the epilogue finished the tile two before)
+      const int slot = it & 1;
+      const bool mok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&ax.meta_empty[slot]),
+                                                         ((uint32_t)(it >> 1) & 1u) ^ 1u, abort_flag));
+      if (!mok) break;
+      ax.bsum[slot][grp][r] = bpart;
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&ax.bsum_full[slot]));
     }
     // an aborted block marks every element of its remaining tiles
     if (*abort_flag) {
@@ -642,10 +753,10 @@ __global__ void __launch_bounds__(TcCfg<P>::NTHREADS, 1) tc_forward_kernel(FwdAr
           a.status[e] = FEI_ERR_TIMEOUT;
         }
     }
-  } else if (warp >= 2 + C::NPW) {
+  } else if (warp >= C::W_EW) {
     // ================================================================ epilogue
-    const int ew = warp - (2 + C::NPW);  // 0..3
-    const int quarter = warp & 3;        // TMEM lanes 32*quarter ..
+    const int ew = warp - C::W_EW;    // 0..3
+    const int quarter = warp & 3;     // TMEM lanes 32*quarter ..
     const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
     const int myrow = quarter * 32 + lane;
     float rreg[C::RREG > 0 ? C::RREG : 1];
@@ -653,7 +764,7 @@ __global__ void __launch_bounds__(TcCfg<P>::NTHREADS, 1) tc_forward_kernel(FwdAr
     uint32_t unit = 0;
     bool dead = false;
     for (int64_t tile = blockIdx.x; tile < tiles && !dead; tile += gridDim.x, ++it) {
-      for (int c = 0; c < NCH && !dead; ++c) {
+      for (int c = 0; c < NCH && !dead; c += C::UC) {
 #pragma unroll
         for (int nh = 0; nh < C::NHALF; ++nh) {
           const uint32_t pb = unit & 1u, k = unit >> 1;
@@ -711,9 +822,20 @@ __global__ void __launch_bounds__(TcCfg<P>::NTHREADS, 1) tc_forward_kernel(FwdAr
       // final: scale the running sum and store the tile's rows of A_e
       const int slot = it & 1;
       const uint32_t km = (uint32_t)(it >> 1);
-      if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&ax.meta_full[slot]), km & 1u, abort_flag))) break;
+      bool mok = mbar_wait(smem_u32(&ax.meta_full[slot]), km & 1u, abort_flag);
+      mok = mok && mbar_wait(smem_u32(&ax.bsum_full[slot]), km & 1u, abort_flag);
+      if (!__all_sync(0xffffffffu, mok)) break;
       const TcMeta &M = ax.meta[slot];
-      const float dn = M.row_zero[myrow] ? 0.f : M.row_down[myrow];
+      const float dn = M.row_status[myrow] ? 0.f : M.row_down[myrow];
+      // load vector and status of this lane's row
+      if (M.row_boff[myrow] >= 0) {
+        float bsum = 0.f;
+#pragma unroll
+        for (int gq = 0; gq < C::NPW * 32 / 128; ++gq) bsum += ax.bsum[slot][gq][myrow];
+        const int st = M.row_status[myrow];
+        reinterpret_cast<float *>(a.bv)[M.row_boff[myrow]] = st ? 0.f : bsum * exp2i(-tau);
+        if (M.row_eid[myrow] >= 0) a.status[M.row_eid[myrow]] = st;
+      }
       float(*stg)[17] = ax.stg[ew];
 #pragma unroll
       for (int b = 0; b < C::NPAD / 16; ++b) {
@@ -771,14 +893,18 @@ __global__ void __launch_bounds__(TcCfg<P>::NTHREADS, 1) tc_forward_kernel(FwdAr
       uint32_t unit = 0;
       int it = 0;
       for (int64_t tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x, ++it) {
-        for (int c = 0; c < NCH && ok; ++c) {
-          const int g = it * NCH + c, s = g % S;
-          const uint32_t u = (uint32_t)(g / S);
-          ok = mbar_wait(smem_u32(&ax.bfull[s]), u & 1u, abort_flag) &&
-               mbar_wait(smem_u32(&ax.full[s]), u & 1u, abort_flag);
+        for (int c0 = 0; c0 < NCH && ok; c0 += C::UC) {
+          const int cn = NCH - c0 < C::UC ? NCH - c0 : C::UC;
+          int st[C::UC];
+          for (int j = 0; j < cn && ok; ++j) {
+            const int g = it * NCH + c0 + j;
+            st[j] = g % S;
+            const uint32_t u = (uint32_t)(g / S);
+            ok = mbar_wait(smem_u32(&ax.bfull[st[j]]), u & 1u, abort_flag) &&
+                 mbar_wait(smem_u32(&ax.full[st[j]]), u & 1u, abort_flag);
+          }
           if (!ok) break;
           tc_fence_after();
-          const uint32_t ah = stageA(s, 0), alo = stageA(s, 1), bh = stageB(s), bl = bh + C::B_BYTES;
 #pragma unroll
           for (int nh = 0; nh < C::NHALF; ++nh) {
             const uint32_t pb = unit & 1u, k = unit >> 1;
@@ -787,18 +913,23 @@ __global__ void __launch_bounds__(TcCfg<P>::NTHREADS, 1) tc_forward_kernel(FwdAr
             if (!ok) break;
             tc_fence_after();
             const uint32_t d = tmem + pb * C::NMMA;
+            for (int j = 0; j < cn; ++j) {
+              const uint32_t ah = stageA(st[j], 0), alo = stageA(st[j], 1);
+              const uint32_t bh = stageB(st[j]), bl = bh + C::B_BYTES;
 #pragma unroll
-            for (int kk = 0; kk < C::KSL; ++kk) {
-              const uint32_t boff = (uint32_t)(nh * C::NMMA * ROWB + kk * 32);
-              const uint64_t Ah = sw_desc<ROWB>(ah + kk * 32), Al = sw_desc<ROWB>(alo + kk * 32);
-              const uint64_t Bh = sw_desc<ROWB>(bh + boff), Bl = sw_desc<ROWB>(bl + boff);
-              tc_mma_f16(d, Ah, Bh, IDESC, kk != 0);
-              tc_mma_f16(d, Ah, Bl, IDESC, 1u);
-              tc_mma_f16(d, Al, Bh, IDESC, 1u);
+              for (int kk = 0; kk < C::KSL; ++kk) {
+                const uint32_t boff = (uint32_t)(nh * C::NMMA * ROWB + kk * 32);
+                const uint64_t Ah = sw_desc<ROWB>(ah + kk * 32), Al = sw_desc<ROWB>(alo + kk * 32);
+                const uint64_t Bh = sw_desc<ROWB>(bh + boff), Bl = sw_desc<ROWB>(bl + boff);
+                tc_mma_f16(d, Ah, Bh, IDESC, (j | kk) != 0);
+                tc_mma_f16(d, Ah, Bl, IDESC, 1u);
+                tc_mma_f16(d, Al, Bh, IDESC, 1u);
+              }
             }
             tc_commit(smem_u32(&ax.part_full[pb]));
           }
-          if (ok) tc_commit(smem_u32(&ax.empty[s]));
+          if (ok)
+            for (int j = 0; j < cn; ++j) tc_commit(smem_u32(&ax.empty[st[j]]));
         }
       }
       if (!ok) {
