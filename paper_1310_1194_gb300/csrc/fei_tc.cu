@@ -192,24 +192,24 @@ struct TcCfg {
   static constexpr int RT = (512 - 2 * NMMA) < NPAD ? (512 - 2 * NMMA) : NPAD;
   static constexpr int RREG = NPAD - RT;
   static constexpr int EMAX = (128 + NSH - 1) / NSH + 1;
-  static constexpr int NDW = 2;  // point-operator warps
+  static constexpr int NDW = P == 7 ? 2 : 4;  // point-operator warps
   static constexpr int NPW = 8;  // producer warps
   static constexpr int NEW = 4;  // epilogue warps
   static constexpr int W_DW = 2, W_PW = W_DW + NDW, W_EW = W_PW + NPW;
   static constexpr int NTHREADS = (2 + NDW + NPW + NEW) * 32;
   static constexpr int QPG = PPC / 2;  // points per producer thread per chunk
-  static constexpr int DRING = 4;      // chunks of point operators ahead
+  static constexpr int DRING = P <= 4 ? 8 : 4;  // chunks of point operators ahead
   static constexpr int A_BYTES = 128 * ROWB;
   static constexpr int B_BYTES = NPAD * ROWB;
   static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
-  static constexpr int STAGES = P == 3 ? 4 : P == 4 ? 3 : P == 5 ? 2 : P == 6 ? 2 : 3;
+  static constexpr int STAGES = P == 3 ? 3 : P == 4 ? 3 : P == 5 ? 2 : P == 6 ? 2 : 3;
   static constexpr int DYN_SMEM = STAGES * STAGE_BYTES + 1024;
   static_assert(NMMA % 16 == 0 && NMMA <= 256, "MMA N");
   static_assert(RT % 16 == 0 && RREG % 16 == 0 && RT >= 0, "running-sum split");
   static_assert(2 * NMMA + RT <= TMEM_COLS, "tensor memory");
   static_assert(QPG % 2 == 0, "two points per 16-byte chunk");
   static_assert(STAGES > UC, "a promotion unit must leave a stage for the producers");
-  static_assert(W_EW % 4 == 0, "epilogue warps cover the four TMEM lane quarters in order");
+  static_assert(NEW == 4, "four consecutive epilogue warps cover the four TMEM lane quarters");
 };
 
 template <int P>
@@ -465,18 +465,42 @@ __global__ void __launch_bounds__(TcCfg<P>::NTHREADS, 1) tc_forward_kernel(FwdAr
       }
       named_bar(2, ND);
       // vertical nodes: c1, c2, n3 = c1 x c2 and w_z (n3.C, n3.D1, n3.D2) in
-      // FP64 (so that w det J = w_t (..) below is FP64), the columns for the
-      // FP32 adjugate from the FP32 element vectors; triangle nodes: c3 in FP32
+      // FP64 (so that w det J = w_t (..) below is FP64), one lane per vector
+      // component and node (shuffles give the cross product); the columns
+      // for the FP32 adjugate from the FP32 element vectors.
+      {
+        constexpr int ZPW = 30;  // 10 nodes x 3 components per warp
+        const int ntask = nel * NZ;
+        for (int base = (warp - C::W_DW) * 10; base < ntask; base += C::NDW * 10) {
+          const int node = base + lane / 3, k = lane % 3;
+          const bool act = lane < ZPW && node < ntask;
+          const int el = act ? node / NZ : 0, iz = act ? node - (node / NZ) * NZ : 0;
+          const TcElem<P> &E = ax.el[el];
+          const double z = a.znode[2 * iz], wz = a.znode[2 * iz + 1];
+          const double c1 = fma(z, E.ev[3 + k], E.ev[0 + k]);
+          const double c2 = fma(z, E.ev[9 + k], E.ev[6 + k]);
+          // components k+1, k+2 (mod 3) from the neighbouring lanes of the node
+          const int g0 = lane - k, l1 = g0 + (k + 1) % 3, l2 = g0 + (k + 2) % 3;
+          const double c1a = __shfl_sync(0xffffffffu, c1, l1), c1b = __shfl_sync(0xffffffffu, c1, l2);
+          const double c2a = __shfl_sync(0xffffffffu, c2, l1), c2b = __shfl_sync(0xffffffffu, c2, l2);
+          const double n3 = c1a * c2b - c1b * c2a;  // (c1 x c2)_k
+          double ab = n3 * E.ev[12 + k], bb = n3 * E.ev[15 + k], gb = n3 * E.ev[18 + k];
+          ab += __shfl_sync(0xffffffffu, ab, l1) + __shfl_sync(0xffffffffu, ab, l2);
+          bb += __shfl_sync(0xffffffffu, bb, l1) + __shfl_sync(0xffffffffu, bb, l2);
+          gb += __shfl_sync(0xffffffffu, gb, l1) + __shfl_sync(0xffffffffu, gb, l2);
+          if (act && k == 0) {
+            TcElem<P> &Ew = ax.el[el];
+            Ew.zabg[iz][0] = wz * ab;
+            Ew.zabg[iz][1] = wz * bb;
+            Ew.zabg[iz][2] = wz * gb;
+          }
+        }
+      }
+      // FP32 columns: vertical nodes (c1, c2, n3) and triangle nodes (c3)
       for (int idx = td; idx < nel * (NZ + NT); idx += ND) {
         const int el = idx / (NZ + NT), nd = idx - el * (NZ + NT);
         TcElem<P> &E = ax.el[el];
         if (nd < NZ) {
-          const double z = a.znode[2 * nd], wz = a.znode[2 * nd + 1];
-          double c1[3], c2[3], n3[3];
-          znode_columns(E.ev, z, c1, c2, n3);
-          E.zabg[nd][0] = wz * dot3(n3, E.ev + 12);
-          E.zabg[nd][1] = wz * dot3(n3, E.ev + 15);
-          E.zabg[nd][2] = wz * dot3(n3, E.ev + 18);
           const float zf = ax.ztabf[nd][0];
           float f1[3], f2[3], fn[3];
 #pragma unroll
