@@ -196,6 +196,7 @@ void fill_fwd(FwdArgs &a, const fei_batch *b, const fei_reference *r, void *A, v
   a.G32 = r->G32;
   a.znode = r->znode;
   a.tnode = r->tnode;
+  a.G32T = r->G32T;
 }
 
 fei_status launch_forward(int p, fei_precision prec, const fei_reference *r, const FwdArgs &a,

@@ -5,6 +5,8 @@
 //   pts   double [N_q][4]        (xi1, xi2, zeta, w)
 //   G64   double [N_q][4][N_sh]  row 0 = phi, rows 1..3 = d phi / d(xi1, xi2, zeta)
 //   G32   float  [N_q][4][N_sh]  the same rounded to FP32
+//   G32T  float  [N_q][N_sh][4]  the same, components adjacent (one 16-byte
+//                                load per point and shape function)
 //   znode double [p+1][2]        (zeta, w_zeta)        vertical Gauss nodes
 //   tnode double [(p+1)^2][4]    (xi1, xi2, w_tri, 0)  collapsed triangle nodes
 //   point q = iz * (p+1)^2 + t, t = iv * (p+1) + iu, w_q = w_tri[t] w_zeta[iz].
@@ -36,6 +38,7 @@ struct fei_reference {
   float *G32;
   double *znode;
   double *tnode;
+  float *G32T;       // [N_q][N_sh][4] the FP32 table with the 4 components adjacent
   fei::TcImage *tc;  // null until built (degree >= 3)
 };
 
@@ -59,6 +62,7 @@ struct FwdArgs {
   const float *G32;
   const double *znode;
   const double *tnode;
+  const float *G32T;
 };
 
 struct BwdArgs {

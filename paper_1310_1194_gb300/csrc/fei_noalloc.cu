@@ -156,6 +156,7 @@ extern "C" fei_status fei_integrate_noalloc(const fei_reference_t *refs, int nre
     a.G32 = r->G32;
     a.znode = r->znode;
     a.tnode = r->tnode;
+    a.G32T = r->G32T;
     st = launch_one(p, prec, r, a, batch->n_elem, s);
     if (st) return st;
   }

@@ -147,7 +147,7 @@ __device__ void legendre_norm_eval(int k, double z, double &L, double &dL) {
 
 // One thread per (point q, shape function i).
 __global__ void tabulate_kernel(int p, const double *znode, const double *tnode, double *pts,
-                                double *G64, float *G32) {
+                                double *G64, float *G32, float *G32T) {
   const int nsh = nsh_of(p), nq = nq_of(p), T = ntri_of(p), n1 = p + 1;
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= nq * nsh) return;
@@ -172,6 +172,7 @@ __global__ void tabulate_kernel(int p, const double *znode, const double *tnode,
   for (int a = 0; a < 4; ++a) {
     G64[(size_t)(q * 4 + a) * nsh + i] = g[a];
     G32[(size_t)(q * 4 + a) * nsh + i] = (float)g[a];
+    G32T[((size_t)q * nsh + i) * 4 + a] = (float)g[a];
   }
 }
 
@@ -196,12 +197,12 @@ extern "C" fei_status fei_reference_create(int p, fei_reference_t *out) {
     return cuda_error(e, "cudaGetDevice");
   }
   const int n1 = p + 1;
-  size_t bytes[5] = {sizeof(double) * 4 * r->nq, sizeof(double) * 4 * r->nq * r->nsh,
+  size_t bytes[6] = {sizeof(double) * 4 * r->nq, sizeof(double) * 4 * r->nq * r->nsh,
                      sizeof(float) * 4 * r->nq * r->nsh, sizeof(double) * 2 * n1,
-                     sizeof(double) * 4 * n1 * n1};
-  void **ptrs[5] = {(void **)&r->pts, (void **)&r->G64, (void **)&r->G32, (void **)&r->znode,
-                    (void **)&r->tnode};
-  for (int k = 0; k < 5; ++k) {
+                     sizeof(double) * 4 * n1 * n1, sizeof(float) * 4 * r->nq * r->nsh};
+  void **ptrs[6] = {(void **)&r->pts, (void **)&r->G64, (void **)&r->G32, (void **)&r->znode,
+                    (void **)&r->tnode, (void **)&r->G32T};
+  for (int k = 0; k < 6; ++k) {
     e = cudaMalloc(ptrs[k], bytes[k]);
     if (e != cudaSuccess) {
       fei_reference_destroy(r);
@@ -218,7 +219,7 @@ extern "C" fei_status fei_reference_create(int p, fei_reference_t *out) {
   gauss_legendre_kernel<<<1, 32, 0, s>>>(n1, r->znode);
   triangle_nodes_kernel<<<1, 64, 0, s>>>(n1, r->znode, r->tnode);
   const int total = r->nq * r->nsh;
-  tabulate_kernel<<<(total + 255) / 256, 256, 0, s>>>(p, r->znode, r->tnode, r->pts, r->G64, r->G32);
+  tabulate_kernel<<<(total + 255) / 256, 256, 0, s>>>(p, r->znode, r->tnode, r->pts, r->G64, r->G32, r->G32T);
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   cudaStreamDestroy(s);
@@ -245,6 +246,7 @@ extern "C" fei_status fei_reference_destroy(fei_reference_t r) {
   cudaFree(r->G32);
   cudaFree(r->znode);
   cudaFree(r->tnode);
+  cudaFree(r->G32T);
   free(r);
   return FEI_OK;
 }

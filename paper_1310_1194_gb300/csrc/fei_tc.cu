@@ -16,9 +16,8 @@
 // relative.  To keep fp16 in range, G is scaled by 2^tau (per degree) and
 // H'_e by 2^sigma_e (per element), chosen from the exact bound
 // max |H'| <= max_{q,b} sum_a |Dt[a][b]| max |G|, so every operand value is
-// at most 2^14.  The producers build H' from the scaled table, so the
-// accumulator holds A_e 2^(sigma_e + 2 tau); the epilogue scales back
-// exactly.  The tensor core adds into its FP32 accumulator with truncation,
+// at most 2^14; the accumulator holds A_e 2^(sigma_e + tau) and the
+// epilogue scales back exactly.  The tensor core adds into its FP32 accumulator with truncation,
 // so a long chain of MMAs drifts by about half an ulp of the accumulator per
 // instruction; to keep the error independent of K, each K chunk (and N half)
 // accumulates into a fresh partial buffer in tensor memory, and the epilogue
@@ -32,14 +31,15 @@
 //   warp 0       TMEM owner; lane 0 streams the pre-swizzled B operand (the
 //                split G image) into shared memory with cp.async.bulk;
 //   warp 1       lane 0 issues tcgen05.mma (M = 128, N = N_pad or 2 halves);
-//   warps 2..3   point operators: per tile, the touched elements' geometry
+//   next warps   point operators: per tile, the touched elements' geometry
 //                (FP64 node columns, w det J at every point), their scales
 //                and the row data; per K chunk, the point operators of its
 //                points into a ring that runs ahead of the producers;
-//   warps 4..11  producers: per K chunk, H' for the 128 rows, split into
-//                hi/lo, written in the swizzled K-major operand layout, and
-//                the partial load vectors;
-//   warps 12..15 epilogue: promotion of every partial accumulator, then
+//   producers    per K chunk, H' for the 128 rows from the FP32 table (read
+//                through L2, 16 bytes per row and point), split into hi/lo,
+//                written in the swizzled K-major operand layout, and the
+//                partial load vectors;
+//   last 4 warps epilogue: promotion of every partial accumulator, then
 //                scaling and coalesced stores of A_e, b_e and the statuses.
 // All hand-offs are mbarriers; every wait is bounded by a time limit after
 // which the block raises an abort flag, marks its remaining elements with
@@ -192,13 +192,14 @@ struct TcCfg {
   static constexpr int RT = (512 - 2 * NMMA) < NPAD ? (512 - 2 * NMMA) : NPAD;
   static constexpr int RREG = NPAD - RT;
   static constexpr int EMAX = (128 + NSH - 1) / NSH + 1;
-  static constexpr int NDW = P == 7 ? 2 : 4;  // point-operator warps
+  static constexpr int NDW = P == 7 ? 2 : P == 6 ? 4 : 6;  // point-operator warps
   static constexpr int NPW = 8;  // producer warps
   static constexpr int NEW = 4;  // epilogue warps
   static constexpr int W_DW = 2, W_PW = W_DW + NDW, W_EW = W_PW + NPW;
   static constexpr int NTHREADS = (2 + NDW + NPW + NEW) * 32;
   static constexpr int QPG = PPC / 2;  // points per producer thread per chunk
   static constexpr int DRING = P <= 4 ? 8 : 4;  // chunks of point operators ahead
+  static constexpr int DB = 2;                  // chunks of point operators per round
   static constexpr int A_BYTES = 128 * ROWB;
   static constexpr int B_BYTES = NPAD * ROWB;
   static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
@@ -209,6 +210,7 @@ struct TcCfg {
   static_assert(2 * NMMA + RT <= TMEM_COLS, "tensor memory");
   static_assert(QPG % 2 == 0, "two points per 16-byte chunk");
   static_assert(STAGES > UC, "a promotion unit must leave a stage for the producers");
+  static_assert(DRING >= 2 * DB, "the operator ring holds two rounds");
   static_assert(NEW == 4, "four consecutive epilogue warps cover the four TMEM lane quarters");
 };
 
@@ -226,7 +228,7 @@ struct TcElem {
   int status;
   int mbits;   // float bits of max_{q,b} sum_a |Dt[a][b]|
   float up;    // 2^sigma (applied to Dt before H')
-  float down;  // 2^-(sigma + 2 tau)
+  float down;  // 2^-(sigma + tau)
 };
 
 // Per-tile row data handed from the point-operator warps to the producers
@@ -574,16 +576,17 @@ __global__ void __launch_bounds__(TcCfg<P>::NTHREADS, 1) tc_forward_kernel(FwdAr
       named_bar(2, ND);
       if (td < nel) {
         TcElem<P> &E = ax.el[td];
-        // The A operand is H' 2^sigma built from the scaled table G 2^tau,
-        // so |A| <= M 2^sigma max|G 2^tau| <= M 2^sigma 2^14: sigma = -ex
-        // with M <= 2^ex keeps it within 2^14.  D = A_e 2^(sigma + 2 tau).
+        // The A operand is H' 2^sigma and max|G| <= 2^(14 - tau), so
+        // |A| <= M 2^sigma 2^(14 - tau): sigma = tau - ex with M <= 2^ex
+        // keeps it within 2^14.  The B operand is G 2^tau, so the
+        // accumulator holds A_e 2^(sigma + tau).
         const float M = __int_as_float(E.mbits);
         int ex = 0;
         if (M > 0.f) (void)frexpf(M, &ex);  // M <= 2^ex
-        int sigma = -ex;
+        int sigma = tau - ex;
         sigma = sigma > 100 ? 100 : (sigma < -100 ? -100 : sigma);
         E.up = exp2i(sigma);
-        const int dn = -(sigma + 2 * tau);
+        const int dn = -(sigma + tau);
         E.down = dn >= -126 && dn <= 126 ? exp2i(dn) : ldexpf(1.0f, dn);
       }
       named_bar(2, ND);
@@ -614,14 +617,21 @@ __global__ void __launch_bounds__(TcCfg<P>::NTHREADS, 1) tc_forward_kernel(FwdAr
       }
       named_bar(2, ND);
       if (td == 0 && mok) mbar_arrive(smem_u32(&ax.meta_full[slot]));
-      // point operators, chunk by chunk, into the ring
-      for (int c = 0; c < NCH; ++c) {
-        const int g = it * NCH + c, dr = g % DR;
-        const uint32_t u = (uint32_t)(g / DR);
-        const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&ax.dempty[dr]), (u & 1u) ^ 1u, abort_flag));
+      // point operators into the ring, DB chunks per round (one wait and
+      // one pass over the threads for several chunks)
+      for (int c0 = 0; c0 < NCH; c0 += C::DB) {
+        const int cn = NCH - c0 < C::DB ? NCH - c0 : C::DB;
+        bool ok = true;
+        for (int j = 0; j < cn; ++j) {
+          const int g = it * NCH + c0 + j;
+          ok = ok && mbar_wait(smem_u32(&ax.dempty[g % DR]), ((uint32_t)(g / DR) & 1u) ^ 1u, abort_flag);
+        }
+        ok = __all_sync(0xffffffffu, ok);
         if (ok) {
-          for (int idx = td; idx < nel * PPC; idx += ND) {
-            const int el = idx / PPC, qq = idx - el * PPC, q = c * PPC + qq;
+          for (int idx = td; idx < cn * nel * PPC; idx += ND) {
+            const int j = idx / (nel * PPC), rem = idx - j * (nel * PPC);
+            const int el = rem / PPC, qq = rem - el * PPC, q = (c0 + j) * PPC + qq;
+            const int dr = (it * NCH + c0 + j) % DR;
             const TcElem<P> &E = ax.el[el];
             float *D = ax.Dc[dr][el][qq];
             if (q < NQ && E.status == 0) {
@@ -647,7 +657,7 @@ __global__ void __launch_bounds__(TcCfg<P>::NTHREADS, 1) tc_forward_kernel(FwdAr
           }
         }
         named_bar(2, ND);
-        if (td == 0 && ok) mbar_arrive(smem_u32(&ax.dfull[dr]));
+        if (td < cn && ok) mbar_arrive(smem_u32(&ax.dfull[(it * NCH + c0 + td) % DR]));
       }
     }
   } else if (warp >= C::W_PW && warp < C::W_EW) {
@@ -669,16 +679,23 @@ __global__ void __launch_bounds__(TcCfg<P>::NTHREADS, 1) tc_forward_kernel(FwdAr
         rel = (int)(k - k0);
       }
       float bpart = 0.f;
+      const float4 *G4 = reinterpret_cast<const float4 *>(a.G32T);
       for (int c = 0; c < NCH; ++c) {
         const int g = it * NCH + c, s = g % S, dr = g % DR;
         const uint32_t u = (uint32_t)(g / S), ud = (uint32_t)(g / DR);
-        // B landed (G is read from it), A slot free, point operators ready
-        bool ok = mbar_wait(smem_u32(&ax.bfull[s]), u & 1u, abort_flag);
-        ok = ok && mbar_wait(smem_u32(&ax.empty[s]), (u & 1u) ^ 1u, abort_flag);
+        // the FP32 table values of this row at this thread's points, fetched
+        // before the waits so that their latency overlaps them
+        float4 gq[C::QPG];
+#pragma unroll
+        for (int j = 0; j < C::QPG; ++j) {
+          const int q = c * PPC + grp * C::QPG + j;
+          gq[j] = (rvalid && q < NQ) ? __ldg(G4 + (size_t)q * NSH + ri) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        // A slot free, point operators ready
+        bool ok = mbar_wait(smem_u32(&ax.empty[s]), (u & 1u) ^ 1u, abort_flag);
         ok = ok && mbar_wait(smem_u32(&ax.dfull[dr]), ud & 1u, abort_flag);
         ok = __all_sync(0xffffffffu, ok);
         if (!ok) break;
-        const uint32_t bh = stageB(s), bl = bh + C::B_BYTES;
         const uint32_t ah = stageA(s, 0), alo = stageA(s, 1);
         // this thread: row r, points grp*QPG .. of the chunk = 16-byte chunks
         // grp*QPG/2 .. of the operand row (two points each)
@@ -687,30 +704,13 @@ __global__ void __launch_bounds__(TcCfg<P>::NTHREADS, 1) tc_forward_kernel(FwdAr
         for (int pc = 0; pc < C::QPG / 2; ++pc) {
           const int chunk = grp * (C::QPG / 2) + pc;
           if (rvalid) {
-            const uint32_t goff = sw_off<ROWB>(ri, chunk);
-            uint4 gh, gl;
-            asm volatile("ld.shared.v4.b32 {%0,%1,%2,%3}, [%4];"
-                         : "=r"(gh.x), "=r"(gh.y), "=r"(gh.z), "=r"(gh.w)
-                         : "r"(bh + goff));
-            asm volatile("ld.shared.v4.b32 {%0,%1,%2,%3}, [%4];"
-                         : "=r"(gl.x), "=r"(gl.y), "=r"(gl.z), "=r"(gl.w)
-                         : "r"(bl + goff));
-            const uint32_t ghw[4] = {gh.x, gh.y, gh.z, gh.w}, glw[4] = {gl.x, gl.y, gl.z, gl.w};
 #pragma unroll
             for (int h2 = 0; h2 < 2; ++h2) {  // two points per 16-byte chunk
               const int qq = chunk * 2 + h2;  // point within the chunk
               const float *D = ax.Dc[dr][rel][qq];
-              float gv[4];
-#pragma unroll
-              for (int ab = 0; ab < 2; ++ab) {
-                __half2 hh, ll;
-                memcpy(&hh, &ghw[2 * h2 + ab], 4);
-                memcpy(&ll, &glw[2 * h2 + ab], 4);
-                const float2 fh = __half22float2(hh), fl = __half22float2(ll);
-                gv[2 * ab] = fh.x + fl.x;
-                gv[2 * ab + 1] = fh.y + fl.y;
-              }
-              // gv = G 2^tau; D carries 2^sigma
+              const float4 gg = gq[pc * 2 + h2];
+              const float gv[4] = {gg.x, gg.y, gg.z, gg.w};
+              // D carries 2^sigma; the operand is H' 2^sigma
               const float4 d0 = *reinterpret_cast<const float4 *>(D);
               const float4 d1 = *reinterpret_cast<const float4 *>(D + 4);
               const float4 d2 = *reinterpret_cast<const float4 *>(D + 8);
@@ -720,7 +720,7 @@ __global__ void __launch_bounds__(TcCfg<P>::NTHREADS, 1) tc_forward_kernel(FwdAr
               hv[1] = d0.y * gv[0] + d1.x * gv[1] + d1.w * gv[2] + d2.z * gv[3];
               hv[2] = d0.z * gv[0] + d1.y * gv[1] + d2.x * gv[2] + d2.w * gv[3];
               hv[3] = d0.w * gv[0] + d1.z * gv[1] + d2.y * gv[2] + d3.x * gv[3];
-              bpart += d3.y * gv[0];  // (w det J f) phi 2^tau
+              bpart += d3.y * gv[0];  // (w det J f) phi
               const __half2 h01 = __floats2half2_rn(hv[0], hv[1]);
               const __half2 h23 = __floats2half2_rn(hv[2], hv[3]);
               const float2 f01 = __half22float2(h01), f23 = __half22float2(h23);
@@ -857,7 +857,7 @@ __global__ void __launch_bounds__(TcCfg<P>::NTHREADS, 1) tc_forward_kernel(FwdAr
 #pragma unroll
         for (int gq = 0; gq < C::NPW * 32 / 128; ++gq) bsum += ax.bsum[slot][gq][myrow];
         const int st = M.row_status[myrow];
-        reinterpret_cast<float *>(a.bv)[M.row_boff[myrow]] = st ? 0.f : bsum * exp2i(-tau);
+        reinterpret_cast<float *>(a.bv)[M.row_boff[myrow]] = st ? 0.f : bsum;
         if (M.row_eid[myrow] >= 0) a.status[M.row_eid[myrow]] = st;
       }
       float(*stg)[17] = ax.stg[ew];
