@@ -191,7 +191,8 @@ struct TcCfg {
   // rest (RREG columns) in registers of the epilogue threads
   static constexpr int RT = (512 - 2 * NMMA) < NPAD ? (512 - 2 * NMMA) : NPAD;
   static constexpr int RREG = NPAD - RT;
-  static constexpr int EMAX = (128 + NSH - 1) / NSH + 1;
+  static constexpr int EMAX = (128 + NSH - 1) / NSH + 1;  // elements a tile can touch
+  static constexpr int NSLOT = EMAX + 1;  // element slots: a tile's elements plus the one it shares
   static constexpr int NDW = P == 7 ? 2 : P == 6 ? 4 : 6;  // point-operator warps
   static constexpr int NPW = 8;  // producer warps
   static constexpr int NEW = 4;  // epilogue warps
@@ -224,6 +225,8 @@ struct TcElem {
   double zabg[C::NZ][3];  // w_z (n3.C, n3.D1, n3.D2) per vertical node (FP64)
   float zc1f[C::NZ][3], zc2f[C::NZ][3], zn3f[C::NZ][3];
   float tc3f[C::NT][3];
+  float zn[C::NZ][3];  // |c1|, |c2|, |c1 x c2| per vertical node (FP32)
+  float tn[C::NT];     // |c3| per triangle node
   int64_t e, aoff, boff, qoff;
   int status;
   int mbits;   // float bits of max_{q,b} sum_a |Dt[a][b]|
@@ -258,12 +261,15 @@ struct TcAux {
   uint32_t tmem_base;
   int abort_flag;
   int dsnap;
-  TcElem<P> el[C::EMAX];
-  float sp[C::EMAX][C::NQ];  // w det J per point (FP32, from FP64)
+  TcElem<P> el[C::NSLOT];    // element k lives in slot k % NSLOT
+  float sp[C::NSLOT][C::NQ];  // w det J per point (FP32, from FP64)
   double ttab[C::NT][3];     // (w_t, w_t xi1, w_t xi2) per triangle node
   float ttabf[C::NT][3];     // (w_t, xi1, xi2) in FP32
   float ztabf[C::NZ][2];     // (zeta, w_z) in FP32
-  alignas(16) float Dc[C::DRING][C::EMAX][C::PPC][16];
+  // point operators of a chunk: [tile-relative element][16-byte group][point],
+  // so that consecutive points are consecutive 16-byte words (conflict-free
+  // stores by the point-operator warps, broadcast loads by the producers)
+  float4 Dc[C::DRING][C::EMAX][4][C::PPC];
   TcMeta meta[2];
   float bsum[2][C::NPW * 32 / 128][128];
   alignas(16) float stg[C::NEW][32][17];  // epilogue transpose staging
@@ -299,6 +305,30 @@ __device__ __forceinline__ void tc_point(const TcElem<P> &E, const TcAux<P> &ax,
   cross3(E.tc3f[t], E.zc1f[iz], a1);
   const float wf = ax.ztabf[iz][1] * ax.ttabf[t][0];
   dt_from_adj<float>(a0, a1, E.zn3f[iz], wf, sf, wf * wf / sf, cf, cf + 9, cf[12], cf[13], D);
+}
+__device__ __forceinline__ float norm3f(const float *v) { return sqrtf(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]); }
+// Upper bound of max_b sum_a |Dt[a][b]| at one point, from norms only:
+// |adj_0| <= |c2||c3|, |adj_1| <= |c3||c1|, |adj_2| = |c1 x c2|, so
+//   sum_a |Dt[a][0]| = s |c|,
+//   sum_a |Dt[a][m]| <= w |adj_m| |b| + (w / det J) |adj_m| ||K||_2 sum_l |adj_l|,
+// with w / det J = w^2 / s and ||K||_2 <= sqrt(||K||_1 ||K||_inf).  It sets
+// the element's power-of-two operand scale, which only has to keep the fp16
+// operands in range; an over-estimate costs at most a few bits of headroom.
+template <int P>
+__device__ __forceinline__ float tc_bound(const TcElem<P> &E, const TcAux<P> &ax, const float *cf, int iz, int t,
+                                          float sf) {
+  const float w = ax.ztabf[iz][1] * ax.ttabf[t][0];
+  const float n3 = E.tn[t];
+  const float a0 = E.zn[iz][1] * n3, a1 = n3 * E.zn[iz][0], a2 = E.zn[iz][2];
+  const float amax = fmaxf(fmaxf(a0, a1), a2), asum = a0 + a1 + a2;
+  float r1 = 0.f, ri = 0.f;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    r1 = fmaxf(r1, fabsf(cf[k]) + fabsf(cf[3 + k]) + fabsf(cf[6 + k]));
+    ri = fmaxf(ri, fabsf(cf[3 * k]) + fabsf(cf[3 * k + 1]) + fabsf(cf[3 * k + 2]));
+  }
+  const float kn = sqrtf(r1 * ri), bn = norm3f(cf + 9);
+  return fmaxf(sf * fabsf(cf[12]), w * amax * (bn + (w / sf) * kn * asum));
 }
 // finite test by the exponent bits (integer pipe; FP64 compares are slow here)
 __device__ __forceinline__ bool finite_bits(double x) {
@@ -411,16 +441,23 @@ __global__ void __launch_bounds__(TcCfg<P>::NTHREADS, 1) tc_forward_kernel(FwdAr
   const int64_t items = a.count ? (int64_t)(*a.count) : a.n_work;
   const int64_t rows_total = items * NSH;
   const int64_t tiles = (rows_total + 127) / 128;
+  // this block's tiles: a contiguous range (consecutive tiles share elements)
+  const int64_t t_per = tiles / gridDim.x, t_extra = tiles % gridDim.x;
+  const int64_t t_begin = blockIdx.x * t_per + (blockIdx.x < t_extra ? blockIdx.x : t_extra);
+  const int64_t t_end = t_begin + t_per + (blockIdx.x < t_extra ? 1 : 0);
 
   if (warp >= C::W_DW && warp < C::W_PW) {
     // ======================================================== point operators
-    // Per tile: the touched elements' geometry, FP64 node columns, w det J
-    // at every point, the scale bound and the row data; per chunk: the
-    // point operators of its points (pre-scaled by 2^sigma) into a ring.
+    // Per tile: set up the elements not seen before (geometry, FP64 node
+    // columns, w det J at every point, the scale), then the row data; per
+    // chunk: the point operators of its points (pre-scaled by 2^sigma) into
+    // a ring that runs ahead of the producers.  A block walks consecutive
+    // tiles, so an element split between two tiles is set up once.
     const int td = tid - C::W_DW * 32;  // 0 .. ND-1
     int it = 0;
-    for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++it) {
-      // both point-operator warps leave together (they share named barriers)
+    int64_t kdone = -1;  // elements 0 .. kdone of this block are set up
+    for (int64_t tile = t_begin; tile < t_end; ++tile, ++it) {
+      // the point-operator warps leave together (they share named barriers)
       if (td == 0) ax.dsnap = *abort_flag;
       named_bar(2, ND);
       if (ax.dsnap) break;
@@ -429,13 +466,17 @@ __global__ void __launch_bounds__(TcCfg<P>::NTHREADS, 1) tc_forward_kernel(FwdAr
       int64_t k1 = (r0 + 127) / NSH;
       if (k1 > items - 1) k1 = items - 1;
       const int nel = (int)(k1 - k0 + 1);
-      // geometry and coefficients of the touched elements (one warp per
+      const int64_t kn0 = kdone + 1 > k0 ? kdone + 1 : k0;  // first new element
+      const int nnew = (int)(k1 - kn0 + 1);
+      kdone = k1;
+      auto slot_of = [&](int64_t k) { return (int)(k % C::NSLOT); };
+      // geometry and coefficients of the new elements (one warp per
       // element: lanes 0-17 the vertices, 18-31 the coefficients).  FP64 is
       // slow per instruction on this part, so every FP64 step below runs
       // across lanes rather than in one thread.
-      for (int el = warp - C::W_DW; el < nel; el += C::NDW) {
-        TcElem<P> &E = ax.el[el];
-        const int64_t e = a.list ? (int64_t)a.list[k0 + el] : k0 + el;
+      for (int i = warp - C::W_DW; i < nnew; i += C::NDW) {
+        TcElem<P> &E = ax.el[slot_of(kn0 + i)];
+        const int64_t e = a.list ? (int64_t)a.list[kn0 + i] : kn0 + i;
         bool ok = true;
         if (lane < 18) {
           const double x = a.geom[18 * e + lane];
@@ -459,11 +500,12 @@ __global__ void __launch_bounds__(TcCfg<P>::NTHREADS, 1) tc_forward_kernel(FwdAr
       }
       named_bar(2, ND);
       // element vectors, one component per thread (FP64, and rounded once)
-      for (int idx = td; idx < nel * 21; idx += ND) {
-        const int el = idx / 21, j = idx - el * 21;
-        const double v = elem_vector_component(ax.el[el].X, j);
-        ax.el[el].ev[j] = v;
-        ax.el[el].evf[j] = (float)v;
+      for (int idx = td; idx < nnew * 21; idx += ND) {
+        const int i = idx / 21, j = idx - i * 21;
+        TcElem<P> &E = ax.el[slot_of(kn0 + i)];
+        const double v = elem_vector_component(E.X, j);
+        E.ev[j] = v;
+        E.evf[j] = (float)v;
       }
       named_bar(2, ND);
       // vertical nodes: c1, c2, n3 = c1 x c2 and w_z (n3.C, n3.D1, n3.D2) in
@@ -472,12 +514,12 @@ __global__ void __launch_bounds__(TcCfg<P>::NTHREADS, 1) tc_forward_kernel(FwdAr
       // for the FP32 adjugate from the FP32 element vectors.
       {
         constexpr int ZPW = 30;  // 10 nodes x 3 components per warp
-        const int ntask = nel * NZ;
+        const int ntask = nnew * NZ;
         for (int base = (warp - C::W_DW) * 10; base < ntask; base += C::NDW * 10) {
           const int node = base + lane / 3, k = lane % 3;
           const bool act = lane < ZPW && node < ntask;
-          const int el = act ? node / NZ : 0, iz = act ? node - (node / NZ) * NZ : 0;
-          const TcElem<P> &E = ax.el[el];
+          const int i = act ? node / NZ : 0, iz = act ? node - (node / NZ) * NZ : 0;
+          TcElem<P> &E = ax.el[slot_of(kn0 + i)];
           const double z = a.znode[2 * iz], wz = a.znode[2 * iz + 1];
           const double c1 = fma(z, E.ev[3 + k], E.ev[0 + k]);
           const double c2 = fma(z, E.ev[9 + k], E.ev[6 + k]);
@@ -491,17 +533,17 @@ __global__ void __launch_bounds__(TcCfg<P>::NTHREADS, 1) tc_forward_kernel(FwdAr
           bb += __shfl_sync(0xffffffffu, bb, l1) + __shfl_sync(0xffffffffu, bb, l2);
           gb += __shfl_sync(0xffffffffu, gb, l1) + __shfl_sync(0xffffffffu, gb, l2);
           if (act && k == 0) {
-            TcElem<P> &Ew = ax.el[el];
-            Ew.zabg[iz][0] = wz * ab;
-            Ew.zabg[iz][1] = wz * bb;
-            Ew.zabg[iz][2] = wz * gb;
+            E.zabg[iz][0] = wz * ab;
+            E.zabg[iz][1] = wz * bb;
+            E.zabg[iz][2] = wz * gb;
           }
         }
       }
-      // FP32 columns: vertical nodes (c1, c2, n3) and triangle nodes (c3)
-      for (int idx = td; idx < nel * (NZ + NT); idx += ND) {
-        const int el = idx / (NZ + NT), nd = idx - el * (NZ + NT);
-        TcElem<P> &E = ax.el[el];
+      // FP32 columns and their norms: vertical nodes (c1, c2, n3) and
+      // triangle nodes (c3)
+      for (int idx = td; idx < nnew * (NZ + NT); idx += ND) {
+        const int i = idx / (NZ + NT), nd = idx - i * (NZ + NT);
+        TcElem<P> &E = ax.el[slot_of(kn0 + i)];
         if (nd < NZ) {
           const float zf = ax.ztabf[nd][0];
           float f1[3], f2[3], fn[3];
@@ -517,25 +559,34 @@ __global__ void __launch_bounds__(TcCfg<P>::NTHREADS, 1) tc_forward_kernel(FwdAr
             E.zc2f[nd][k] = f2[k];
             E.zn3f[nd][k] = fn[k];
           }
+          E.zn[nd][0] = norm3f(f1);
+          E.zn[nd][1] = norm3f(f2);
+          E.zn[nd][2] = norm3f(fn);
         } else {
           const int t = nd - NZ;
           const float x1 = ax.ttabf[t][1], x2 = ax.ttabf[t][2];
+          float c3[3];
 #pragma unroll
-          for (int k = 0; k < 3; ++k) E.tc3f[t][k] = fmaf(x2, E.evf[18 + k], fmaf(x1, E.evf[15 + k], E.evf[12 + k]));
+          for (int k = 0; k < 3; ++k) {
+            c3[k] = fmaf(x2, E.evf[18 + k], fmaf(x1, E.evf[15 + k], E.evf[12 + k]));
+            E.tc3f[t][k] = c3[k];
+          }
+          E.tn[t] = norm3f(c3);
         }
       }
       named_bar(2, ND);
-      // pre-pass over all points: w det J = w_t (a + xi1 b + xi2 g) in FP64
-      // (rounded once), status, and the bound max_{q,b} sum_a |Dt[a][b]|
-      // that sets the element's scale
-      for (int base = 0; base < nel * NQ; base += ND) {
+      // pre-pass over the points of the new elements: w det J = w_t (a +
+      // xi1 b + xi2 g) in FP64 (rounded once), status, and the bound of
+      // max_{q,b} sum_a |Dt[a][b]| that sets the element's scale
+      for (int base = 0; base < nnew * NQ; base += ND) {
         const int idx = base + td;
-        int el = -1;
+        int i = -1;
         float m = 0.f;
-        if (idx < nel * NQ) {
-          el = idx / NQ;
-          const int q = idx - el * NQ;
-          TcElem<P> &E = ax.el[el];
+        if (idx < nnew * NQ) {
+          i = idx / NQ;
+          const int q = idx - i * NQ;
+          const int sl = slot_of(kn0 + i);
+          TcElem<P> &E = ax.el[sl];
           const int iz = q / NT, t = q - iz * NT;
           const double s = ax.ttab[t][0] * E.zabg[iz][0] + ax.ttab[t][1] * E.zabg[iz][1] + ax.ttab[t][2] * E.zabg[iz][2];
           const float sf = (float)s;
@@ -548,17 +599,11 @@ __global__ void __launch_bounds__(TcCfg<P>::NTHREADS, 1) tc_forward_kernel(FwdAr
             coef_to_float(cdq, cq);
             cp = cq;
           }
-          ax.sp[el][q] = sf;
+          ax.sp[sl][q] = sf;
           if (st) {
             atomicMax(&E.status, st);
           } else {
-            float D[16];
-            tc_point<P>(E, ax, cp, q, sf, D);
-            const float m0 = fabsf(D[0]);
-            const float m1 = fabsf(D[1]) + fabsf(D[4]) + fabsf(D[7]) + fabsf(D[10]);
-            const float m2 = fabsf(D[2]) + fabsf(D[5]) + fabsf(D[8]) + fabsf(D[11]);
-            const float m3 = fabsf(D[3]) + fabsf(D[6]) + fabsf(D[9]) + fabsf(D[12]);
-            m = fmaxf(fmaxf(m0, m1), fmaxf(m2, m3));
+            m = tc_bound<P>(E, ax, cp, iz, t, sf);
             if (!(m <= 3.0e38f)) {
               atomicMax(&E.status, FEI_ERR_NONFINITE);
               m = 0.f;
@@ -567,15 +612,15 @@ __global__ void __launch_bounds__(TcCfg<P>::NTHREADS, 1) tc_forward_kernel(FwdAr
         }
         // one atomic per element per warp (the bound is a max of
         // non-negative floats, so their bit patterns order as integers)
-        const int el0 = __shfl_sync(0xffffffffu, el, 0), el1 = __shfl_sync(0xffffffffu, el, 31);
-        for (int e2 = el0 < 0 ? 0 : el0; e2 <= el1 && e2 < nel; ++e2) {
-          const unsigned mb = __reduce_max_sync(0xffffffffu, el == e2 ? __float_as_uint(m) : 0u);
-          if (lane == 0 && mb) atomicMax(&ax.el[e2].mbits, (int)mb);
+        const int i0 = __shfl_sync(0xffffffffu, i, 0), i1 = __shfl_sync(0xffffffffu, i, 31);
+        for (int i2 = i0 < 0 ? 0 : i0; i2 <= i1 && i2 < nnew; ++i2) {
+          const unsigned mb = __reduce_max_sync(0xffffffffu, i == i2 ? __float_as_uint(m) : 0u);
+          if (lane == 0 && mb) atomicMax(&ax.el[slot_of(kn0 + i2)].mbits, (int)mb);
         }
       }
       named_bar(2, ND);
-      if (td < nel) {
-        TcElem<P> &E = ax.el[td];
+      if (td < nnew) {
+        TcElem<P> &E = ax.el[slot_of(kn0 + td)];
         // The A operand is H' 2^sigma and max|G| <= 2^(14 - tau), so
         // |A| <= M 2^sigma 2^(14 - tau): sigma = tau - ex with M <= 2^ex
         // keeps it within 2^14.  The B operand is G 2^tau, so the
@@ -600,7 +645,7 @@ __global__ void __launch_bounds__(TcCfg<P>::NTHREADS, 1) tc_forward_kernel(FwdAr
           if (grow < rows_total) {
             const int64_t k = grow / NSH;
             const int ri = (int)(grow - k * NSH);
-            const TcElem<P> &E = ax.el[k - k0];
+            const TcElem<P> &E = ax.el[slot_of(k)];
             M.row_off[r] = E.aoff + (int64_t)ri * NSH;
             M.row_boff[r] = E.boff + ri;
             M.row_eid[r] = ri == 0 ? E.e : -1;
@@ -632,8 +677,9 @@ __global__ void __launch_bounds__(TcCfg<P>::NTHREADS, 1) tc_forward_kernel(FwdAr
             const int j = idx / (nel * PPC), rem = idx - j * (nel * PPC);
             const int el = rem / PPC, qq = rem - el * PPC, q = (c0 + j) * PPC + qq;
             const int dr = (it * NCH + c0 + j) % DR;
-            const TcElem<P> &E = ax.el[el];
-            float *D = ax.Dc[dr][el][qq];
+            const int sl = slot_of(k0 + el);
+            const TcElem<P> &E = ax.el[sl];
+            float4 *D4 = &ax.Dc[dr][el][0][qq];
             if (q < NQ && E.status == 0) {
               float cq[14];
               const float *cp = E.cf;
@@ -644,15 +690,18 @@ __global__ void __launch_bounds__(TcCfg<P>::NTHREADS, 1) tc_forward_kernel(FwdAr
                 cp = cq;
               }
               float Dt[16];
-              tc_point<P>(E, ax, cp, q, ax.sp[el][q], Dt);
-#pragma unroll
-              for (int k = 0; k < 13; ++k) D[k] = Dt[k] * E.up;
-              D[13] = Dt[13];
-              D[14] = 0.f;
-              D[15] = 0.f;
+              tc_point<P>(E, ax, cp, q, ax.sp[sl][q], Dt);
+              const float up = E.up;
+              D4[0] = make_float4(Dt[0] * up, Dt[1] * up, Dt[2] * up, Dt[3] * up);
+              D4[PPC] = make_float4(Dt[4] * up, Dt[5] * up, Dt[6] * up, Dt[7] * up);
+              D4[2 * PPC] = make_float4(Dt[8] * up, Dt[9] * up, Dt[10] * up, Dt[11] * up);
+              D4[3 * PPC] = make_float4(Dt[12] * up, Dt[13], 0.f, 0.f);
             } else {
-#pragma unroll
-              for (int k = 0; k < 16; ++k) D[k] = 0.f;
+              const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+              D4[0] = z4;
+              D4[PPC] = z4;
+              D4[2 * PPC] = z4;
+              D4[3 * PPC] = z4;
             }
           }
         }
@@ -665,8 +714,8 @@ __global__ void __launch_bounds__(TcCfg<P>::NTHREADS, 1) tc_forward_kernel(FwdAr
     const int tp = tid - C::W_PW * 32;  // 0 .. NP-1
     const int r = tp & 127, grp = tp >> 7;
     int it = 0;
-    int64_t tile = blockIdx.x;
-    for (; tile < tiles; tile += gridDim.x, ++it) {
+    int64_t tile = t_begin;
+    for (; tile < t_end; ++tile, ++it) {
       if (*abort_flag) break;
       const int64_t r0 = tile * 128;
       const int64_t k0 = r0 / NSH;
@@ -707,14 +756,11 @@ __global__ void __launch_bounds__(TcCfg<P>::NTHREADS, 1) tc_forward_kernel(FwdAr
 #pragma unroll
             for (int h2 = 0; h2 < 2; ++h2) {  // two points per 16-byte chunk
               const int qq = chunk * 2 + h2;  // point within the chunk
-              const float *D = ax.Dc[dr][rel][qq];
+              const float4 *D4 = &ax.Dc[dr][rel][0][qq];
               const float4 gg = gq[pc * 2 + h2];
               const float gv[4] = {gg.x, gg.y, gg.z, gg.w};
               // D carries 2^sigma; the operand is H' 2^sigma
-              const float4 d0 = *reinterpret_cast<const float4 *>(D);
-              const float4 d1 = *reinterpret_cast<const float4 *>(D + 4);
-              const float4 d2 = *reinterpret_cast<const float4 *>(D + 8);
-              const float4 d3 = *reinterpret_cast<const float4 *>(D + 12);
+              const float4 d0 = D4[0], d1 = D4[PPC], d2 = D4[2 * PPC], d3 = D4[3 * PPC];
               float hv[4];
               hv[0] = d0.x * gv[0];
               hv[1] = d0.y * gv[0] + d1.x * gv[1] + d1.w * gv[2] + d2.z * gv[3];
@@ -767,7 +813,7 @@ __global__ void __launch_bounds__(TcCfg<P>::NTHREADS, 1) tc_forward_kernel(FwdAr
     }
     // an aborted block marks every element of its remaining tiles
     if (*abort_flag) {
-      for (int64_t t2 = tile; t2 < tiles; t2 += gridDim.x)
+      for (int64_t t2 = tile; t2 < t_end; ++t2)
         for (int rr = tp; rr < 128; rr += NP) {
           const int64_t grow = t2 * 128 + rr;
           if (grow >= rows_total) continue;
@@ -787,7 +833,7 @@ __global__ void __launch_bounds__(TcCfg<P>::NTHREADS, 1) tc_forward_kernel(FwdAr
     int it = 0;
     uint32_t unit = 0;
     bool dead = false;
-    for (int64_t tile = blockIdx.x; tile < tiles && !dead; tile += gridDim.x, ++it) {
+    for (int64_t tile = t_begin; tile < t_end && !dead; ++tile, ++it) {
       for (int c = 0; c < NCH && !dead; c += C::UC) {
 #pragma unroll
         for (int nh = 0; nh < C::NHALF; ++nh) {
@@ -893,7 +939,7 @@ __global__ void __launch_bounds__(TcCfg<P>::NTHREADS, 1) tc_forward_kernel(FwdAr
     // ================================================================ B stream
     if (lane == 0) {
       int it = 0;
-      for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++it) {
+      for (int64_t tile = t_begin; tile < t_end; ++tile, ++it) {
         bool ok = true;
         for (int c = 0; c < NCH; ++c) {
           const int g = it * NCH + c, s = g % S;
@@ -916,7 +962,7 @@ __global__ void __launch_bounds__(TcCfg<P>::NTHREADS, 1) tc_forward_kernel(FwdAr
       bool ok = true;
       uint32_t unit = 0;
       int it = 0;
-      for (int64_t tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x, ++it) {
+      for (int64_t tile = t_begin; tile < t_end && ok; ++tile, ++it) {
         for (int c0 = 0; c0 < NCH && ok; c0 += C::UC) {
           const int cn = NCH - c0 < C::UC ? NCH - c0 : C::UC;
           int st[C::UC];
