@@ -50,7 +50,7 @@ def nq(p):
 def flops_per_element(p):
     """Algorithmic flops per element: 8 N_sh^2 N_q (contraction with the 4x4
     point operator) + 2 N_sh N_q (load vector) + 220 N_q (geometry, the
-    paper's constant per point, Table 2)."""
+    paper's constant per point, Table 3)."""
     s, q = nsh(p), nq(p)
     return 8 * s * s * q + 2 * s * q + 220 * q
 

@@ -8,7 +8,7 @@
  *     a(u, v) = int  grad v . K grad u  +  v b . grad u  +  c u v,
  *     l(v)    = int  f v,
  *
- * by the standard quadrature of Sec. 2 (Eq. wzor1 generalised, Eq. wzor2):
+ * by the standard quadrature of Sec. 2 (Eq. (1) generalised, Eq. (2)):
  *
  *     A_e[i][j] = sum_q w_q det J(xi_q) ( grad phi_i . K_q grad phi_j
  *                                        + phi_i b_q . grad phi_j
@@ -127,7 +127,7 @@ typedef struct {
 
 /* Tabulate the reference data of degree p (Sec. 2.2: quadrature data and
  * shape functions are the same for every element of one type and degree,
- * so they are computed once and kept in fast memory; Table 3 sizes).
+ * so they are computed once and kept in fast memory; Table 2 sizes).
  * Runs FP64 kernels on the current device and waits for them.
  * p outside 1..7 -> FEI_ERR_INVALID_DEGREE; out == NULL -> INVALID_ARG.
  * The handle is owned by the caller and released with
@@ -136,7 +136,7 @@ fei_status fei_reference_create(int p, fei_reference_t *out);
 fei_status fei_reference_destroy(fei_reference_t ref);
 /* Query degree, N_sh and N_q of a handle (host pointers, any may be NULL). */
 fei_status fei_reference_info(fei_reference_t ref, int *p, int *nsh, int *nq);
-/* Copy the FP64 reference table to host memory (Table 3 rows 1-2 and 4):
+/* Copy the FP64 reference table to host memory (Table 2 rows 1-2 and 4):
  * pts [N_q][4] = (xi1, xi2, zeta, w), G [N_q][4][N_sh] = phi, dphi/dxi1,
  * dphi/dxi2, dphi/dzeta.  Either pointer may be NULL.  Synchronous. */
 fei_status fei_reference_copy_table(fei_reference_t ref, double *pts, double *G);
@@ -183,6 +183,53 @@ fei_status fei_plan_offsets(const int32_t *degree, int64_t n_elem,
                             int64_t *A_offset, int64_t *b_offset,
                             int64_t *q_offset, int32_t *bad_count,
                             fei_stream_t stream);
+
+/* --------------------------------------------------------------------- */
+/* Plans: a mixed-degree batch as one CUDA graph, with the kernel shape of
+ * every degree chosen by measurement.  Elements are grouped by degree so
+ * that each degree's tables stay resident (Sec. 2.2); a plan owns the
+ * grouping scratch, per degree a kernel variant and grid (defaults, or the
+ * fastest measured by fei_plan_tune), and the CUDA graph of its last
+ * argument set. */
+typedef struct fei_plan *fei_plan_t;
+
+/* refs/nrefs as for fei_integrate (host array, handles of the current
+ * device; the plan keeps pointers to them: destroy the plan first).
+ * max_elem: largest n_elem of a batch with a degree array (the scratch,
+ * 4 * (8 + 7 * max_elem) bytes of device memory, is allocated here and never
+ * again).  prec: as for fei_integrate.  Errors: INVALID_ARG (NULL pointers,
+ * max_elem outside 0..2^31-1, bad precision, a handle of another device),
+ * CUDA/OOM. */
+fei_status fei_plan_create(const fei_reference_t *refs, int nrefs, int64_t max_elem,
+                           fei_precision prec, fei_plan_t *out);
+fei_status fei_plan_destroy(fei_plan_t plan);
+
+/* Same arguments, outputs and statuses as fei_integrate.  The first call
+ * with a given (batch contents, A_out, b_out, elem_status) captures the
+ * grouping kernel and one kernel per degree into a CUDA graph on `stream`
+ * and launches it; later calls with the same pointers replay the graph
+ * (one cudaGraphLaunch); different pointers re-capture (updating the
+ * graph in place when possible).  The legacy default stream (NULL) cannot
+ * be captured: there the kernels are launched directly.  No device memory
+ * is allocated.  Calls on one plan must not overlap on the GPU (they share
+ * its scratch) and must come from one host thread at a time. */
+fei_status fei_plan_execute(fei_plan_t plan, const fei_batch *batch, void *A_out,
+                            void *b_out, int32_t *elem_status, fei_stream_t stream);
+
+/* Autotuner: runs every candidate kernel shape of every degree present in
+ * `batch` on that degree's elements (writing the same outputs a normal call
+ * writes), times each with CUDA events (best of two after one warm-up run)
+ * and keeps the fastest per degree.  Candidates: the tensor-core kernel's
+ * warp-role variants (p >= 3 under FEI_TC_F16X3), or 2/4/8/16 blocks per
+ * SM for the CUDA-core kernels.  Synchronous (waits for the stream). */
+fei_status fei_plan_tune(fei_plan_t plan, const fei_batch *batch, void *A_out,
+                         void *b_out, int32_t *elem_status, fei_stream_t stream);
+
+/* The plan's choice for degree p (host pointers, any may be NULL):
+ * variant index, grid cap in blocks (0 = the kernel's default) and the
+ * time fei_plan_tune measured for that degree (ms, -1 if not tuned). */
+fei_status fei_plan_choice(fei_plan_t plan, int p, int *variant, int64_t *grid_cap,
+                           float *tuned_ms);
 
 /* Largest batch fei_integrate_noalloc accepts. */
 #define FEI_NOALLOC_MAX_ELEM 262144

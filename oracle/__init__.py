@@ -14,7 +14,7 @@ Each function names the passage of the paper it follows:
   reference prism (Sec. 2; the point count is this build's reading).
 * ``basis``            -- prism shape functions: complete triangle basis times
   1D functions along the vertical direction (Table 1 and its text).
-* ``integrate``        -- Eq. wzor2 generalised to
+* ``integrate``        -- Eq. (2) generalised to
   int grad v.K grad u + v b.grad u + c u v  and  int f v, Algorithm 1.
 * ``integrate_backward`` -- the reverse pass of ``integrate`` (hand-derived
   adjoint, FP64); derivative formulas are in the C source.

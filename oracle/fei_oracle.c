@@ -8,7 +8,7 @@
  * by the CPU-baseline leg of the benchmark, and it shares no code, header,
  * table or constant with the CUDA path.
  *
- * What it computes (Sec. 2, Eq. wzor1 / Eq. wzor2, generalised to the
+ * What it computes (Sec. 2, Eq. (1) / Eq. (2), generalised to the
  * convection-diffusion-reaction form):
  *
  *   A_e[i][j] = sum_q w_q det J(xi_q) * ( grad phi_i . K_q grad phi_j

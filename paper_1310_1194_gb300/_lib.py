@@ -82,11 +82,18 @@ def _load():
     lib.fei_plan_offsets.argtypes = [vp, i64, vp, vp, vp, vp, vp]
     lib.fei_integrate_noalloc.argtypes = [ref_p, ctypes.c_int, ctypes.POINTER(fei_batch), ctypes.c_int,
                                           vp, vp, vp, vp]
+    lib.fei_plan_create.argtypes = [ref_p, ctypes.c_int, i64, ctypes.c_int, ref_p]
+    lib.fei_plan_destroy.argtypes = [vp]
+    lib.fei_plan_execute.argtypes = [vp, ctypes.POINTER(fei_batch), vp, vp, vp, vp]
+    lib.fei_plan_tune.argtypes = [vp, ctypes.POINTER(fei_batch), vp, vp, vp, vp]
+    lib.fei_plan_choice.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(i64),
+                                    ctypes.POINTER(ctypes.c_float)]
     lib.fei_last_error_string.argtypes = []
     lib.fei_last_error_string.restype = ctypes.c_char_p
     for name in ("fei_reference_create", "fei_reference_destroy", "fei_reference_info",
                  "fei_reference_copy_table", "fei_integrate", "fei_integrate_backward",
-                 "fei_plan_offsets", "fei_integrate_noalloc"):
+                 "fei_plan_offsets", "fei_integrate_noalloc", "fei_plan_create", "fei_plan_destroy",
+                 "fei_plan_execute", "fei_plan_tune", "fei_plan_choice"):
         getattr(lib, name).restype = i32
     return lib
 

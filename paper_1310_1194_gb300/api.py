@@ -204,6 +204,60 @@ def fei_integrate_backward(geom, K, b, c, f, gA, gb, p=None, degree=None, per_qp
     return g_geom, gK, gbc, gc, gf
 
 
+class Plan:
+    """Owning wrapper of a fei_plan_t: a (mixed-degree) batch executed as one
+    CUDA graph, with per-degree kernel shapes from the autotuner.
+
+    ``execute`` takes the same arguments as :func:`fei_integrate` (outputs
+    must be given with ``out`` for the graph to be replayed: a new output
+    buffer means a new capture)."""
+
+    def __init__(self, degrees=range(1, 8), max_elem: int = 0, precision: str = "tc_f16x3"):
+        self.precision = precision
+        self.refs = [fei_reference_create(d) for d in degrees]
+        self.max_elem = int(max_elem)
+        h = ctypes.c_void_p()
+        check(lib.fei_plan_create(_refs_array(self.refs), len(self.refs), self.max_elem,
+                                  _lib.PRECISIONS[precision], ctypes.byref(h)), "fei_plan_create")
+        self.handle = h
+
+    def _call(self, fn, name, geom, K, b, c, f, p, degree, per_qp, layout, out):
+        geom, layout = _inputs(geom, K, b, c, f, degree, p, per_qp, layout)
+        prec = _lib.PRECISIONS[self.precision]
+        dtype = torch.float64 if prec == _lib.FEI_FP64 else torch.float32
+        n = geom.shape[0]
+        if out is None:
+            A = torch.empty(layout.A_total, dtype=dtype, device=geom.device)
+            bv = torch.empty(layout.b_total, dtype=dtype, device=geom.device)
+            st = torch.empty(n, dtype=torch.int32, device=geom.device)
+        else:
+            A, bv, st = out
+        bt = _batch(geom, K, b, c, f, degree, p, per_qp, layout)
+        check(fn(self.handle, ctypes.byref(bt), _ptr(A), _ptr(bv), _ptr(st), _stream()), name)
+        return A, bv, st, layout
+
+    def execute(self, geom, K, b, c, f, p=None, degree=None, per_qp=False, layout=None, out=None):
+        return self._call(lib.fei_plan_execute, "fei_plan_execute", geom, K, b, c, f, p, degree, per_qp,
+                          layout, out)
+
+    def tune(self, geom, K, b, c, f, p=None, degree=None, per_qp=False, layout=None, out=None):
+        return self._call(lib.fei_plan_tune, "fei_plan_tune", geom, K, b, c, f, p, degree, per_qp,
+                          layout, out)
+
+    def choice(self, p: int):
+        """(variant, grid cap in blocks, tuned ms) chosen for degree p."""
+        v, g, t = ctypes.c_int(), ctypes.c_int64(), ctypes.c_float()
+        check(lib.fei_plan_choice(self.handle, int(p), ctypes.byref(v), ctypes.byref(g), ctypes.byref(t)),
+              "fei_plan_choice")
+        return v.value, g.value, t.value
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            lib.fei_plan_destroy(h)
+            self.handle = None
+
+
 class _IntegrateFn(torch.autograd.Function):
     """A, b = integrate(geom, K, b, c, f) with the library's adjoint kernel
     as the backward; the Jacobians are recomputed in the backward."""

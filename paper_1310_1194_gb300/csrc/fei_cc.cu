@@ -405,12 +405,13 @@ __global__ void __launch_bounds__(256) cc_tile_kernel(FwdArgs a) {
 }
 
 template <typename T, int P>
-fei_status launch_small(const FwdArgs &a, int64_t grid_work, cudaStream_t s) {
+fei_status launch_small(const FwdArgs &a, int64_t grid_work, cudaStream_t s, int64_t grid_cap) {
   using C = SmallCfg<T, P>;
   FEI_CUDA_TRY(cudaFuncSetAttribute(cc_small_kernel<T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM),
                "cudaFuncSetAttribute(cc_small)");
   int64_t blocks = (grid_work + C::WPB - 1) / C::WPB;
-  if (a.count) blocks = blocks < 152 * 4 ? blocks : 152 * 4;
+  const int64_t cap = grid_cap > 0 ? grid_cap : (a.count ? 152 * 4 : 0);
+  if (cap > 0 && blocks > cap) blocks = cap;
   if (blocks > 2147483647LL) blocks = 2147483647LL;
   if (blocks < 1) blocks = 1;
   cc_small_kernel<T, P><<<(unsigned)blocks, C::WPB * 32, C::SMEM, s>>>(a);
@@ -419,10 +420,11 @@ fei_status launch_small(const FwdArgs &a, int64_t grid_work, cudaStream_t s) {
 }
 
 template <typename T, int P>
-fei_status launch_tile(const FwdArgs &a, int64_t grid_work, cudaStream_t s) {
+fei_status launch_tile(const FwdArgs &a, int64_t grid_work, cudaStream_t s, int64_t grid_cap) {
   using C = TileCfg<T, P>;
   int64_t blocks = grid_work * C::NB * C::NB;
-  if (a.count) blocks = blocks < 152 * 8 ? blocks : 152 * 8;
+  const int64_t cap = grid_cap > 0 ? grid_cap : (a.count ? 152 * 8 : 0);
+  if (cap > 0 && blocks > cap) blocks = cap;
   if (blocks > 2147483647LL) blocks = 2147483647LL;
   if (blocks < 1) blocks = 1;
   cc_tile_kernel<T, P><<<(unsigned)blocks, 256, 0, s>>>(a);
@@ -431,24 +433,26 @@ fei_status launch_tile(const FwdArgs &a, int64_t grid_work, cudaStream_t s) {
 }
 
 template <typename T>
-fei_status launch_typed(int p, const FwdArgs &a, int64_t grid_work, cudaStream_t s) {
+fei_status launch_typed(int p, const FwdArgs &a, int64_t grid_work, cudaStream_t s, int64_t cap) {
   switch (p) {
-    case 1: return launch_small<T, 1>(a, grid_work, s);
-    case 2: return launch_small<T, 2>(a, grid_work, s);
-    case 3: return launch_tile<T, 3>(a, grid_work, s);
-    case 4: return launch_tile<T, 4>(a, grid_work, s);
-    case 5: return launch_tile<T, 5>(a, grid_work, s);
-    case 6: return launch_tile<T, 6>(a, grid_work, s);
-    case 7: return launch_tile<T, 7>(a, grid_work, s);
+    case 1: return launch_small<T, 1>(a, grid_work, s, cap);
+    case 2: return launch_small<T, 2>(a, grid_work, s, cap);
+    case 3: return launch_tile<T, 3>(a, grid_work, s, cap);
+    case 4: return launch_tile<T, 4>(a, grid_work, s, cap);
+    case 5: return launch_tile<T, 5>(a, grid_work, s, cap);
+    case 6: return launch_tile<T, 6>(a, grid_work, s, cap);
+    case 7: return launch_tile<T, 7>(a, grid_work, s, cap);
   }
   return set_error(FEI_ERR_INVALID_DEGREE, "degree %d outside 1..7", p);
 }
 
 }  // namespace
 
-fei_status launch_cc_forward(int p, bool fp64, const FwdArgs &a, int64_t grid_work, cudaStream_t s) {
+fei_status launch_cc_forward(int p, bool fp64, const FwdArgs &a, int64_t grid_work, cudaStream_t s,
+                             int64_t grid_cap) {
   if (grid_work <= 0) return FEI_OK;
-  return fp64 ? launch_typed<double>(p, a, grid_work, s) : launch_typed<float>(p, a, grid_work, s);
+  return fp64 ? launch_typed<double>(p, a, grid_work, s, grid_cap)
+              : launch_typed<float>(p, a, grid_work, s, grid_cap);
 }
 
 }  // namespace fei

@@ -14,7 +14,7 @@
 // The element vectors are differences of vertex coordinates and are always
 // formed in FP64 (this is where FP32 would lose the most: |x| ~ 1, h ~ 1/50).
 //
-// Point operator (Eq. wzor2 with the general weak form): with
+// Point operator (Eq. (2) with the general weak form): with
 // T = blockdiag(1, J^{-T}) and D = [[c, b^T], [0, K]] (row = test
 // component (value, d/dx), column = trial component),
 //   Dt_q = w det J  T^T D T

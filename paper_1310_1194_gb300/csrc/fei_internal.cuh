@@ -1,7 +1,7 @@
 // fei_internal.cuh -- shared declarations of the libfei CUDA sources.
 //
 // Layout of the device reference data of one degree p (N_sh shape
-// functions, N_q = (p+1)^3 points, Sec. 2.2 / Table 3):
+// functions, N_q = (p+1)^3 points, Sec. 2.2 / Table 2):
 //   pts   double [N_q][4]        (xi1, xi2, zeta, w)
 //   G64   double [N_q][4][N_sh]  row 0 = phi, rows 1..3 = d phi / d(xi1, xi2, zeta)
 //   G32   float  [N_q][4][N_sh]  the same rounded to FP32
@@ -88,10 +88,15 @@ fei_status set_error(fei_status st, const char *fmt, ...);
 fei_status cuda_error(cudaError_t e, const char *what);
 
 // Kernel launchers (each returns FEI_OK or an error already recorded).
-fei_status launch_cc_forward(int p, bool fp64, const FwdArgs &a, int64_t grid_work, cudaStream_t s);
+// grid_cap: largest grid (blocks) of the grid-stride kernels, 0 = default
+// (all work items for a known count, 152 x 4 or 152 x 8 for a device count)
+fei_status launch_cc_forward(int p, bool fp64, const FwdArgs &a, int64_t grid_work, cudaStream_t s,
+                             int64_t grid_cap = 0);
 fei_status launch_cc_backward(int p, bool fp64, const BwdArgs &a, int64_t grid_work, cudaStream_t s);
+// variant: 0 .. tc_variant_count(p) - 1 (warp-role variants of one kernel)
 fei_status launch_tc_forward(int p, const fei_reference *ref, const FwdArgs &a, int64_t grid_work,
-                             cudaStream_t s);
+                             cudaStream_t s, int variant = 0);
+int tc_variant_count(int p);
 fei_status build_tc_image(fei_reference *ref);
 void free_tc_image(fei_reference *ref);
 

@@ -3,7 +3,7 @@
 // Sec. 2.2: quadrature data and the values of the shape functions and their
 // reference derivatives are identical for all elements of one type and
 // degree, so they are computed once and kept resident (the paper's "SR"
-// variant; Table 3 gives their sizes).  Everything here is computed by
+// variant; Table 2 gives their sizes).  Everything here is computed by
 // kernels; the host only allocates and launches.
 //
 // Basis (Table 1 and its text: complete triangle basis times 1D functions in

@@ -172,7 +172,10 @@ __device__ __forceinline__ float exp2i(int k) {  // exact 2^k for |k| < 126
 // ROWB = bytes of one swizzled operand row = K values per chunk * 2 (fp16):
 // 128 (128-byte swizzle, 16 points per chunk) or 64 (64-byte swizzle,
 // 8 points per chunk, used for p = 7 to leave room for three stages).
-template <int P>
+// V selects a variant of the warp roles (the autotuner of a plan times
+// them): 0 = 8 producer warps, 1 = 16 producer warps with half the points
+// each (more warps in flight, fewer registers per thread).
+template <int P, int V = 0>
 struct TcCfg {
   static constexpr int NSH = nsh_of(P), NQ = nq_of(P), NZ = P + 1, NT = (P + 1) * (P + 1);
   static constexpr int NPAD = P == 6 ? 224 : (NSH + 15) / 16 * 16;
@@ -194,11 +197,11 @@ struct TcCfg {
   static constexpr int EMAX = (128 + NSH - 1) / NSH + 1;  // elements a tile can touch
   static constexpr int NSLOT = EMAX + 1;  // element slots: a tile's elements plus the one it shares
   static constexpr int NDW = P == 7 ? 2 : P == 6 ? 4 : 6;  // point-operator warps
-  static constexpr int NPW = 8;  // producer warps
+  static constexpr int NPW = V == 1 ? 16 : 8;  // producer warps
   static constexpr int NEW = 4;  // epilogue warps
   static constexpr int W_DW = 2, W_PW = W_DW + NDW, W_EW = W_PW + NPW;
   static constexpr int NTHREADS = (2 + NDW + NPW + NEW) * 32;
-  static constexpr int QPG = PPC / 2;  // points per producer thread per chunk
+  static constexpr int QPG = PPC / (NPW / 4);  // points per producer thread per chunk
   static constexpr int DRING = P <= 4 ? 8 : 4;  // chunks of point operators ahead
   static constexpr int DB = 2;                  // chunks of point operators per round
   static constexpr int A_BYTES = 128 * ROWB;
@@ -244,9 +247,9 @@ struct TcMeta {
   int row_status[128];    // status of the row's element (nonzero: write zeros)
 };
 
-template <int P>
+template <int P, int V>
 struct TcAux {
-  using C = TcCfg<P>;
+  using C = TcCfg<P, V>;
   uint64_t full[C::STAGES];   // producers wrote A of the stage
   uint64_t bfull[C::STAGES];  // B of the stage landed
   uint64_t empty[C::STAGES];  // MMAs of the stage completed
@@ -295,8 +298,8 @@ __device__ __forceinline__ bool load_coef_tc(const FwdArgs &a, int64_t r, double
 
 // FP32 point operator of element slot E at point q from the node tables;
 // sf = w det J (formed in FP64, rounded once); cf = coefficients in FP32.
-template <int P>
-__device__ __forceinline__ void tc_point(const TcElem<P> &E, const TcAux<P> &ax, const float *cf, int q, float sf,
+template <int P, class AX>
+__device__ __forceinline__ void tc_point(const TcElem<P> &E, const AX &ax, const float *cf, int q, float sf,
                                          float *D) {
   using C = TcCfg<P>;
   const int iz = q / C::NT, t = q - iz * C::NT;
@@ -314,8 +317,8 @@ __device__ __forceinline__ float norm3f(const float *v) { return sqrtf(v[0] * v[
 // with w / det J = w^2 / s and ||K||_2 <= sqrt(||K||_1 ||K||_inf).  It sets
 // the element's power-of-two operand scale, which only has to keep the fp16
 // operands in range; an over-estimate costs at most a few bits of headroom.
-template <int P>
-__device__ __forceinline__ float tc_bound(const TcElem<P> &E, const TcAux<P> &ax, const float *cf, int iz, int t,
+template <int P, class AX>
+__device__ __forceinline__ float tc_bound(const TcElem<P> &E, const AX &ax, const float *cf, int iz, int t,
                                           float sf) {
   const float w = ax.ztabf[iz][1] * ax.ttabf[t][0];
   const float n3 = E.tn[t];
@@ -379,13 +382,13 @@ __host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
   return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-template <int P>
-__global__ void __launch_bounds__(TcCfg<P>::NTHREADS, 1) tc_forward_kernel(FwdArgs a, const __half *img, int tau) {
-  using C = TcCfg<P>;
+template <int P, int V>
+__global__ void __launch_bounds__(TcCfg<P, V>::NTHREADS, 1) tc_forward_kernel(FwdArgs a, const __half *img, int tau) {
+  using C = TcCfg<P, V>;
   constexpr int NSH = C::NSH, NQ = C::NQ, NT = C::NT, NZ = C::NZ, S = C::STAGES, NCH = C::NCHUNK;
   constexpr int NP = C::NPW * 32, ND = C::NDW * 32, PPC = C::PPC, ROWB = C::ROWB, DR = C::DRING;
   extern __shared__ __align__(1024) unsigned char dsm_raw[];
-  __shared__ TcAux<P> ax;
+  __shared__ TcAux<P, V> ax;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t dbase = (smem_u32(dsm_raw) + 1023u) & ~1023u;
   auto stageA = [&](int s, int piece) { return dbase + s * C::STAGE_BYTES + piece * C::A_BYTES; };
@@ -745,13 +748,17 @@ __global__ void __launch_bounds__(TcCfg<P>::NTHREADS, 1) tc_forward_kernel(FwdAr
         ok = ok && mbar_wait(smem_u32(&ax.dfull[dr]), ud & 1u, abort_flag);
         ok = __all_sync(0xffffffffu, ok);
         if (!ok) break;
-        const uint32_t ah = stageA(s, 0), alo = stageA(s, 1);
+        // generic pointers to the stage's hi and lo operand tiles
+        unsigned char *const ahp = dsm_raw + (stageA(s, 0) - smem_u32(dsm_raw));
+        unsigned char *const alp = ahp + C::A_BYTES;
         // this thread: row r, points grp*QPG .. of the chunk = 16-byte chunks
-        // grp*QPG/2 .. of the operand row (two points each)
-        uint32_t hw[C::QPG / 2][4], lw[C::QPG / 2][4];
+        // grp*QPG/2 .. of the operand row (two points each); each 16-byte
+        // chunk is stored as soon as it is formed (plain stores, so the
+        // compiler may overlap them with the next points' loads)
 #pragma unroll
         for (int pc = 0; pc < C::QPG / 2; ++pc) {
           const int chunk = grp * (C::QPG / 2) + pc;
+          uint32_t hw[4], lw[4];
           if (rvalid) {
 #pragma unroll
             for (int h2 = 0; h2 < 2; ++h2) {  // two points per 16-byte chunk
@@ -772,30 +779,22 @@ __global__ void __launch_bounds__(TcCfg<P>::NTHREADS, 1) tc_forward_kernel(FwdAr
               const float2 f01 = __half22float2(h01), f23 = __half22float2(h23);
               const __half2 l01 = __floats2half2_rn(hv[0] - f01.x, hv[1] - f01.y);
               const __half2 l23 = __floats2half2_rn(hv[2] - f23.x, hv[3] - f23.y);
-              memcpy(&hw[pc][2 * h2], &h01, 4);
-              memcpy(&hw[pc][2 * h2 + 1], &h23, 4);
-              memcpy(&lw[pc][2 * h2], &l01, 4);
-              memcpy(&lw[pc][2 * h2 + 1], &l23, 4);
+              memcpy(&hw[2 * h2], &h01, 4);
+              memcpy(&hw[2 * h2 + 1], &h23, 4);
+              memcpy(&lw[2 * h2], &l01, 4);
+              memcpy(&lw[2 * h2 + 1], &l23, 4);
             }
           } else {
 #pragma unroll
-            for (int k = 0; k < 4; ++k) hw[pc][k] = lw[pc][k] = 0u;
+            for (int k = 0; k < 4; ++k) hw[k] = lw[k] = 0u;
           }
+          const uint32_t aoff = sw_off<ROWB>(r, chunk);
+          *reinterpret_cast<uint4 *>(ahp + aoff) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+          *reinterpret_cast<uint4 *>(alp + aoff) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
         }
         // the point operators of this chunk are consumed
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_u32(&ax.dempty[dr]));
-#pragma unroll
-        for (int pc = 0; pc < C::QPG / 2; ++pc) {
-          const int chunk = grp * (C::QPG / 2) + pc;
-          const uint32_t aoff = sw_off<ROWB>(r, chunk);
-          asm volatile("st.shared.v4.b32 [%0], {%1,%2,%3,%4};" ::"r"(ah + aoff), "r"(hw[pc][0]), "r"(hw[pc][1]),
-                       "r"(hw[pc][2]), "r"(hw[pc][3])
-                       : "memory");
-          asm volatile("st.shared.v4.b32 [%0], {%1,%2,%3,%4};" ::"r"(alo + aoff), "r"(lw[pc][0]), "r"(lw[pc][1]),
-                       "r"(lw[pc][2]), "r"(lw[pc][3])
-                       : "memory");
-        }
         fence_proxy_async();
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_u32(&ax.full[s]));
@@ -1055,12 +1054,12 @@ __global__ void image_kernel(const double *G, int nsh, int nq, int npad, int nch
   }
 }
 
-template <int P>
+template <int P, int V>
 fei_status launch_tc(const fei_reference *ref, const FwdArgs &a, int64_t grid_work, cudaStream_t s) {
-  using C = TcCfg<P>;
+  using C = TcCfg<P, V>;
   const TcImage *im = ref->tc;
   if (!im) return set_error(FEI_ERR_UNSUPPORTED, "no tensor-core image for degree %d", P);
-  FEI_CUDA_TRY(cudaFuncSetAttribute(tc_forward_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::DYN_SMEM),
+  FEI_CUDA_TRY(cudaFuncSetAttribute(tc_forward_kernel<P, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::DYN_SMEM),
                "cudaFuncSetAttribute(tc_forward)");
   int dev, sms;
   FEI_CUDA_TRY(cudaGetDevice(&dev), "cudaGetDevice");
@@ -1068,7 +1067,7 @@ fei_status launch_tc(const fei_reference *ref, const FwdArgs &a, int64_t grid_wo
   const int64_t tiles = (grid_work * C::NSH + 127) / 128;
   int64_t blocks = tiles < sms ? tiles : sms;
   if (blocks < 1) blocks = 1;
-  tc_forward_kernel<P><<<(unsigned)blocks, C::NTHREADS, C::DYN_SMEM, s>>>(a, im->img, im->tau);
+  tc_forward_kernel<P, V><<<(unsigned)blocks, C::NTHREADS, C::DYN_SMEM, s>>>(a, im->img, im->tau);
   FEI_CUDA_TRY(cudaGetLastError(), "tc_forward_kernel launch");
   return FEI_OK;
 }
@@ -1138,14 +1137,23 @@ void free_tc_image(fei_reference *ref) {
   }
 }
 
-fei_status launch_tc_forward(int p, const fei_reference *ref, const FwdArgs &a, int64_t grid_work, cudaStream_t s) {
+int tc_variant_count(int p) { return p >= 3 && p <= 6 ? 2 : p == 7 ? 1 : 0; }
+
+fei_status launch_tc_forward(int p, const fei_reference *ref, const FwdArgs &a, int64_t grid_work, cudaStream_t s,
+                             int variant) {
   if (grid_work <= 0) return FEI_OK;
-  switch (p) {
-    case 3: return launch_tc<3>(ref, a, grid_work, s);
-    case 4: return launch_tc<4>(ref, a, grid_work, s);
-    case 5: return launch_tc<5>(ref, a, grid_work, s);
-    case 6: return launch_tc<6>(ref, a, grid_work, s);
-    case 7: return launch_tc<7>(ref, a, grid_work, s);
+  if (variant < 0 || variant >= tc_variant_count(p))
+    return set_error(FEI_ERR_UNSUPPORTED, "tensor-core variant %d for degree %d", variant, p);
+  switch (p * 2 + variant) {
+    case 6: return launch_tc<3, 0>(ref, a, grid_work, s);
+    case 7: return launch_tc<3, 1>(ref, a, grid_work, s);
+    case 8: return launch_tc<4, 0>(ref, a, grid_work, s);
+    case 9: return launch_tc<4, 1>(ref, a, grid_work, s);
+    case 10: return launch_tc<5, 0>(ref, a, grid_work, s);
+    case 11: return launch_tc<5, 1>(ref, a, grid_work, s);
+    case 12: return launch_tc<6, 0>(ref, a, grid_work, s);
+    case 13: return launch_tc<6, 1>(ref, a, grid_work, s);
+    case 14: return launch_tc<7, 0>(ref, a, grid_work, s);
   }
   return set_error(FEI_ERR_UNSUPPORTED, "tensor-core path for degree %d", p);
 }

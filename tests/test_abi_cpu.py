@@ -49,6 +49,20 @@ def test_argument_errors_before_any_cuda_call(lib):
     lib.fei_plan_offsets.argtypes = [ctypes.c_void_p, ctypes.c_int64] + [ctypes.c_void_p] * 5
     assert lib.fei_plan_offsets(None, 5, None, None, None, None, None) == 1
     assert lib.fei_reference_destroy(None) == 0
+    # plans: argument errors are reported before any CUDA call
+    vp = ctypes.c_void_p
+    lib.fei_plan_create.argtypes = [vp, ctypes.c_int, ctypes.c_int64, ctypes.c_int, vp]
+    assert lib.fei_plan_create(None, 1, 10, 0, None) == 1
+    out = vp()
+    assert lib.fei_plan_create(None, 1, 10, 0, ctypes.byref(out)) == 1
+    assert out.value is None
+    lib.fei_plan_execute.argtypes = [vp] * 6
+    assert lib.fei_plan_execute(None, None, None, None, None, None) == 1
+    lib.fei_plan_tune.argtypes = [vp] * 6
+    assert lib.fei_plan_tune(None, None, None, None, None, None) == 1
+    lib.fei_plan_choice.argtypes = [vp, ctypes.c_int, vp, vp, vp]
+    assert lib.fei_plan_choice(None, 3, None, None, None) == 1
+    assert lib.fei_plan_destroy(None) == 0
 
 
 def test_python_binding_loads():

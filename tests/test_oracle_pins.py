@@ -17,8 +17,8 @@ def test_pin(name, fn):
 
 
 def test_table_sizes_match_paper():
-    """Table 1 / Table 3 (shape-function counts and stored sizes per p)."""
-    with open(os.path.join(GOLDEN, "table3_sizes.json")) as fh:
+    """Table 1 / Table 2 (shape-function counts and stored sizes per p)."""
+    with open(os.path.join(GOLDEN, "table2_sizes.json")) as fh:
         g = json.load(fh)
     for i, p in enumerate(g["p"]):
         s = oracle.nsh(p)
