@@ -65,6 +65,15 @@ def tc_hw_flops(p):
     return 3 * 2 * s * npad * kpad
 
 
+def bwd_flops_per_element(p):
+    """Algorithmic flops of the adjoint per element: W = gA G^T (8 N_sh^2
+    N_q), dL/dDt = G_q W_q (32 N_sh N_q), the load-vector adjoint (2 N_sh
+    N_q) and the per-point chain to the coefficients and vertices (about
+    600 flops per point)."""
+    s, q = nsh(p), nq(p)
+    return 8 * s * s * q + 34 * s * q + 600 * q
+
+
 def bytes_per_element(p, out_bytes, per_qp=False):
     """Algorithmic HBM bytes: geometry 144 B + coefficients 112 B (per
     element) or 112 N_q B (per point) + outputs (N_sh^2 + N_sh) * s."""
@@ -254,6 +263,10 @@ def main():
     w = inputs.workload(args.workload, n_max=args.elements or None)
     per_qp = bool(w["per_qp"])
     dev = torch.device("cuda", local)
+    # a non-default stream for everything (a plan captures its launches into
+    # a CUDA graph, which the legacy default stream does not allow)
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
     g = {k: torch.from_numpy(np.ascontiguousarray(w[k])).to(dev) for k in ("geom", "K", "b", "c", "f")}
     deg = None if w["p"] is not None else torch.from_numpy(w["degree"]).to(dev)
     p = w["p"]
@@ -275,13 +288,46 @@ def main():
     bv = torch.empty(layout.b_total, dtype=out_dtype, device=dev)
     st = torch.empty(n, dtype=torch.int32, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > L2
-    stream = torch.cuda.current_stream()
 
-    def step(prec=precision, outs=(A, bv, st)):
-        api.fei_integrate(g["geom"], g["K"], g["b"], g["c"], g["f"], p=p, degree=deg, per_qp=per_qp,
-                          precision=prec, refs=refs, layout=layout, out=outs)
+    # mixed degree: a plan (bucketing + one kernel per degree in one CUDA
+    # graph), its per-degree kernel shapes tuned once before timing
+    plan = None
+    plan_choices = None
+    if deg is not None:
+        plan = api.Plan(degrees=range(1, 8), max_elem=n, precision=precision)
+        plan.tune(g["geom"], g["K"], g["b"], g["c"], g["f"], degree=deg, per_qp=per_qp, layout=layout,
+                  out=(A, bv, st))
+        plan_choices = {f"p{d}": dict(zip(("variant", "grid_cap", "tuned_ms"), plan.choice(d)))
+                        for d in range(1, 8) if (w["degree"] == d).any()}
 
-    launches_per_step = 1 if deg is None else 2 + len(refs)  # memset is not a kernel; bucket + per degree
+    # differentiation: the step is the forward and the adjoint of
+    # L = sum_e u_e^T A_e u_e - u_e^T b_e (gA_e = u_e u_e^T, gb_e = -u_e)
+    grads = None
+    if args.workload == "diff":
+        u = torch.from_numpy(inputs.loss_weights(layout.b_total, 4)).to(dev)
+        s_ = nsh(p)
+        uu = u.view(n, s_)
+        gA = (uu[:, :, None] * uu[:, None, :]).reshape(-1).to(torch.float32)
+        gb = (-u).to(torch.float32)
+        grads = (gA, gb)
+
+    def step(prec=precision, outs=(A, bv, st), mid=None):
+        if plan is not None and prec == precision:
+            plan.execute(g["geom"], g["K"], g["b"], g["c"], g["f"], degree=deg, per_qp=per_qp, layout=layout,
+                         out=outs)
+        else:
+            api.fei_integrate(g["geom"], g["K"], g["b"], g["c"], g["f"], p=p, degree=deg, per_qp=per_qp,
+                              precision=prec, refs=refs, layout=layout, out=outs)
+        if grads is not None and prec == precision:
+            if mid is not None:
+                mid.record(stream)
+            api.fei_integrate_backward(g["geom"], g["K"], g["b"], g["c"], g["f"], grads[0], grads[1], p=p,
+                                       degree=deg, per_qp=per_qp, precision="fp32", refs=refs, layout=layout)
+
+    # kernels of one step: bucketing + one per degree (a plan), or one
+    launches_per_step = (1 + len(refs)) if deg is not None else 1
+    if grads is not None:
+        launches_per_step += 1
     for _ in range(max(3, args.warmup)):
         step()
     torch.cuda.synchronize()
@@ -290,13 +336,14 @@ def main():
     clocks = ClockSampler(local)
     clocks.start()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    mids = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)] if grads is not None else None
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
     for k in range(args.steps):
         flush.fill_(float(k))  # evict L2 between steps (outside the events)
         evs[k][0].record(stream)
-        step()
+        step(mid=mids[k] if mids else None)
         evs[k][1].record(stream)
     torch.cuda.synchronize()
     if world > 1:
@@ -318,7 +365,30 @@ def main():
     Bts = sum(int(counts[d]) * bytes_per_element(d, out_b, per_qp) for d in range(1, 8))
     peaks, peak_src = load_peaks()
     sm_max = peaks.get("sm_max_mhz", 2070.0)
+    # the dominant kernel and its own duration (CUDA events on its stream):
+    # the one kernel of a uniform forward step; the slowest degree of a
+    # plan (timed per degree by the plan's tuner above); the adjoint kernel
+    # of a differentiation step (events around it)
+    dom = {"kernel": "forward", "ms": ms, "F": F, "precision": precision, "counts": counts}
+    if plan is not None:
+        per_deg = {d: plan.choice(d)[2] for d in range(1, 8) if counts[d]}
+        d_star = max(per_deg, key=per_deg.get)
+        c1 = np.zeros(8, dtype=np.int64)
+        c1[d_star] = counts[d_star]
+        dom = {"kernel": f"forward, p={d_star} bucket", "ms": per_deg[d_star],
+               "F": int(counts[d_star]) * flops_per_element(d_star),
+               "precision": precision if (precision != "tc_f16x3" or d_star >= 3) else "fp32", "counts": c1}
+    elif grads is not None:
+        bwd_ms = statistics.median([mids[k].elapsed_time(evs[k][1]) for k in range(args.steps)])
+        fwd_ms = statistics.median([evs[k][0].elapsed_time(mids[k]) for k in range(args.steps)])
+        dom = {"kernel": "adjoint (fp32 contraction, fp64 chain)", "ms": bwd_ms, "F": n * bwd_flops_per_element(p),
+               "precision": "fp32", "counts": counts, "fwd_ms": fwd_ms}
     hw = None
+    F, ms_all = dom["F"], ms
+    ms = dom["ms"]
+    counts = dom["counts"]
+    precision_all = precision
+    precision = dom["precision"]
     if precision == "tc_f16x3":
         # every algorithmic multiply-add is three fp16 tensor products (hi*hi,
         # hi*lo, lo*hi), so the peak for algorithmic flops is a third of the
@@ -338,9 +408,13 @@ def main():
         bound, unit, achieved = "alu", "TFLOP/s", F / (ms * 1e-3) / 1e12
         peak_note = "FP64 FMA: 152 SMs x 2 DFMA/clk x 2 flops x max SM clock"
     roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
-                "traffic": None, "peak_source": peak_note,
-                "hbm_gbs_achieved": Bts / (ms * 1e-3) / 1e9, "hbm_frac": Bts / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
+                "traffic": None, "peak_source": peak_note, "kernel": dom["kernel"], "kernel_ms": ms,
+                "step_hbm_gbs": Bts / (ms_all * 1e-3) / 1e9,
+                "step_hbm_frac": Bts / (ms_all * 1e-3) / 1e9 / peaks["hbm_gbs"],
                 "hardware": hw}
+    if "fwd_ms" in dom:
+        roofline["forward_ms"] = dom["fwd_ms"]
+    precision, ms = precision_all, ms_all
 
     # accuracy of this path against the FP64 GPU path on sampled elements,
     # and the FP64 GPU path's own throughput (the comparison the metric asks for)
@@ -420,6 +494,7 @@ def main():
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches_per_step * args.steps, "clocks": clk,
             "fp64_path": fp64,
+            "plan": plan_choices,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

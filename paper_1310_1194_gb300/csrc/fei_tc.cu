@@ -91,19 +91,30 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t a, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+// try_wait that lets the thread sleep until the phase completes or about
+// 0.5 ms pass (the hardware wakes it when the phase completes, so a waiting
+// warp neither spins nor misses the completion)
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint32_t a, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(a), "r"(parity), "r"(500000u)
+      : "memory");
+  return ok != 0;
+}
 // Bounded wait: false (and the abort flag raised) after kWaitLimitNs, or as
-// soon as another role raised the flag.
+// soon as another role raised the flag (checked between sleeps).
 __device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int *abort_flag) {
   if (mbar_try_wait(a, parity)) return true;
   const uint64_t t0 = global_ns();
-  for (int spin = 0;; ++spin) {
-    if (mbar_try_wait(a, parity)) return true;
+  for (;;) {
+    if (mbar_try_wait_sleep(a, parity)) return true;
     if (*abort_flag) return false;
     if (global_ns() - t0 > kWaitLimitNs) {
       *abort_flag = 1;
       return false;
     }
-    if (spin > 8) __nanosleep(64);  // leave issue slots to the working warps
   }
 }
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t mbar) {
@@ -920,12 +931,26 @@ __global__ void __launch_bounds__(TcCfg<P, V>::NTHREADS, 1) tc_forward_kernel(Fw
 #pragma unroll
           for (int k2 = 0; k2 < 16; ++k2) stg[lane][k2] = v[k2] * dn;
           __syncwarp();
-          // two rows per store instruction: lanes 0-15 row rr, 16-31 row rr+1
+          // two rows per store instruction: lanes 0-15 row rr, 16-31 row rr+1;
+          // eight rows' values and offsets are read before their stores (a
+          // global store could alias the staging buffer as far as the
+          // compiler knows, so interleaving would serialise every load
+          // behind the previous store)
           const int half = lane >> 4, col = ncol + (lane & 15);
-          for (int rr = 0; rr < 32; rr += 2) {
-            const int row = quarter * 32 + rr + half;
-            const int64_t off = M.row_off[row];
-            if (off >= 0 && col < NSH) reinterpret_cast<float *>(a.A)[off + col] = stg[rr + half][lane & 15];
+          float *const Aout = reinterpret_cast<float *>(a.A);
+#pragma unroll
+          for (int r16 = 0; r16 < 32; r16 += 16) {
+            float vv[8];
+            int64_t oo[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              const int rr = r16 + 2 * j;
+              oo[j] = M.row_off[quarter * 32 + rr + half];
+              vv[j] = stg[rr + half][lane & 15];
+            }
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+              if (oo[j] >= 0 && col < NSH) Aout[oo[j] + col] = vv[j];
           }
           __syncwarp();
         }
