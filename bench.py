@@ -82,6 +82,25 @@ def bytes_per_element(p, out_bytes, per_qp=False):
     return 144 + coef + (s * s + s) * out_bytes
 
 
+def measured_traffic(kernel_key, p, n_elem):
+    """DRAM bytes of one launch of the dominant kernel from the committed ncu
+    capture (profiles/traffic.json, per element, scaled by the elements of
+    this launch), or None when the capture is of another kernel source."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    src = os.path.join(ROOT, "paper_1310_1194_gb300", "csrc", "fei_tc.cu")
+    if kernel_key != "tc_forward_kernel" or not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        d = json.load(fh)
+    with open(src, "rb") as fh:
+        sha = hashlib.sha256(fh.read()).hexdigest()
+    if d.get("fei_tc_cu_sha256") != sha:
+        return None
+    rec = d.get(kernel_key, {}).get(str(p))
+    return None if rec is None else rec["bytes_per_element"] * n_elem
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -407,8 +426,11 @@ def main():
         peak = 152 * 2 * 2 * sm_max * 1e6 / 1e12
         bound, unit, achieved = "alu", "TFLOP/s", F / (ms * 1e-3) / 1e12
         peak_note = "FP64 FMA: 152 SMs x 2 DFMA/clk x 2 flops x max SM clock"
+    traffic = None
+    if precision == "tc_f16x3" and dom["kernel"] == "forward" and p is not None and p >= 3:
+        traffic = measured_traffic("tc_forward_kernel", p, n)
     roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
-                "traffic": None, "peak_source": peak_note, "kernel": dom["kernel"], "kernel_ms": ms,
+                "traffic": traffic, "peak_source": peak_note, "kernel": dom["kernel"], "kernel_ms": ms,
                 "step_hbm_gbs": Bts / (ms_all * 1e-3) / 1e9,
                 "step_hbm_frac": Bts / (ms_all * 1e-3) / 1e9 / peaks["hbm_gbs"],
                 "hardware": hw}

@@ -1162,7 +1162,7 @@ void free_tc_image(fei_reference *ref) {
   }
 }
 
-int tc_variant_count(int p) { return p >= 3 && p <= 6 ? 2 : p == 7 ? 1 : 0; }
+int tc_variant_count(int p) { return p >= 3 && p <= 5 ? 2 : p >= 6 && p <= 7 ? 1 : 0; }
 
 fei_status launch_tc_forward(int p, const fei_reference *ref, const FwdArgs &a, int64_t grid_work, cudaStream_t s,
                              int variant) {
@@ -1177,7 +1177,6 @@ fei_status launch_tc_forward(int p, const fei_reference *ref, const FwdArgs &a, 
     case 10: return launch_tc<5, 0>(ref, a, grid_work, s);
     case 11: return launch_tc<5, 1>(ref, a, grid_work, s);
     case 12: return launch_tc<6, 0>(ref, a, grid_work, s);
-    case 13: return launch_tc<6, 1>(ref, a, grid_work, s);
     case 14: return launch_tc<7, 0>(ref, a, grid_work, s);
   }
   return set_error(FEI_ERR_UNSUPPORTED, "tensor-core path for degree %d", p);
