@@ -28,15 +28,22 @@ __device__ __forceinline__ const double *gtab_b<double>(const BwdArgs &a) { retu
 template <>
 __device__ __forceinline__ const float *gtab_b<float>(const BwdArgs &a) { return a.G32; }
 
+// W = gA G^T is computed in tiles of BI rows x KC columns (QC points x 4),
+// TM x TN outputs per thread; the operand rows are stored with a padded
+// stride NSHP (a multiple of 4, plus 4) so that the 16-byte loads of the
+// threads of a warp fall into distinct banks.
 template <typename T, int P>
 struct BwdCfg {
+  static constexpr bool F32 = std::is_same<T, float>::value;
   static constexpr int NSH = nsh_of(P), NQ = nq_of(P), NZ = P + 1, NT = (P + 1) * (P + 1);
-  static constexpr int BI = 32, QC = 8, KC = 4 * QC;
+  static constexpr int BI = F32 ? 64 : 32, QC = F32 ? 16 : 8, KC = 4 * QC;
+  static constexpr int TM = BI / 16, TN = KC / 16;  // outputs per thread (16 x 16 threads)
+  static constexpr int NSHP = F32 ? (NSH + 3) / 4 * 4 + 4 : NSH;
   static constexpr int NRB = (NSH + BI - 1) / BI;
   // dynamic shared memory layout (bytes)
-  static constexpr size_t OFF_GA = 0;                                        // T [BI][NSH]
-  static constexpr size_t OFF_GC = OFF_GA + sizeof(T) * BI * NSH;            // T [KC][NSH]
-  static constexpr size_t OFF_W = OFF_GC + sizeof(T) * KC * NSH;             // T [BI][KC]
+  static constexpr size_t OFF_GA = 0;                                        // T [BI][NSHP]
+  static constexpr size_t OFF_GC = OFF_GA + sizeof(T) * BI * NSHP;           // T [KC][NSHP]
+  static constexpr size_t OFF_W = OFF_GC + sizeof(T) * KC * NSHP;            // T [BI][KC]
   static constexpr size_t OFF_GD = OFF_W + sizeof(T) * BI * KC;              // T [NQ][16]
   static constexpr size_t OFF_GSF = OFF_GD + sizeof(T) * NQ * 16;            // T [NQ]
   static constexpr size_t OFF_END = ((OFF_GSF + sizeof(T) * NQ + 15) / 16) * 16;
@@ -75,7 +82,7 @@ __device__ __forceinline__ bool load_coef_b(const BwdArgs &a, int64_t r, double 
 template <typename T, int P>
 __global__ void __launch_bounds__(256) cc_backward_kernel(BwdArgs a) {
   using C = BwdCfg<T, P>;
-  constexpr int NSH = C::NSH, NQ = C::NQ, NT = C::NT, BI = C::BI, QC = C::QC, KC = C::KC;
+  constexpr int NSH = C::NSH, NQ = C::NQ, NT = C::NT, BI = C::BI, QC = C::QC, KC = C::KC, NSHP = C::NSHP;
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ BwdStatic sm;
   T *gAs = reinterpret_cast<T *>(dsm + C::OFF_GA);
@@ -132,45 +139,73 @@ __global__ void __launch_bounds__(256) cc_backward_kernel(BwdArgs a) {
 
     // dL/dDt_q = G_q gA G_q^T, row block by row block
     for (int r0 = 0; r0 < NSH; r0 += BI) {
-      for (int k = tid; k < BI * NSH; k += 256) {
-        const int ii = k / NSH, j = k - ii * NSH;
-        gAs[k] = (r0 + ii < NSH) ? gAg[aoff + (int64_t)(r0 + ii) * NSH + j] : T(0);
+      for (int k = tid; k < BI * NSHP; k += 256) {
+        const int ii = k / NSHP, j = k - ii * NSHP;
+        gAs[k] = (r0 + ii < NSH && j < NSH) ? gAg[aoff + (int64_t)(r0 + ii) * NSH + j] : T(0);
       }
       for (int q0 = 0; q0 < NQ; q0 += QC) {
-        for (int k = tid; k < KC * NSH; k += 256) {
-          const int kk = k / NSH, j = k - kk * NSH;
+        for (int k = tid; k < KC * NSHP; k += 256) {
+          const int kk = k / NSHP, j = k - kk * NSHP;
           const int q = q0 + kk / 4;
-          Gc[k] = (q < NQ) ? Gg[(size_t)(4 * q0 + kk) * NSH + j] : T(0);
+          Gc[k] = (q < NQ && j < NSH) ? Gg[(size_t)(4 * q0 + kk) * NSH + j] : T(0);
         }
         __syncthreads();
-        // W[ii][kk] = sum_j gA[r0+ii][j] G[(q0,kk)][j], 2 x 2 outputs per thread
+        // W[ii][kk] = sum_j gA[r0+ii][j] G[(q0,kk)][j]; thread (ty, tx) owns
+        // rows ty + 16 r and columns tx + 16 c (r < TM, c < TN)
         {
-          const int ii0 = (tid >> 4) * 2, kk0 = (tid & 15) * 2;
-          T w00 = T(0), w01 = T(0), w10 = T(0), w11 = T(0);
+          const int ty = tid >> 4, tx = tid & 15;
+          T acc[C::TM][C::TN];
+#pragma unroll
+          for (int r = 0; r < C::TM; ++r)
+#pragma unroll
+            for (int c = 0; c < C::TN; ++c) acc[r][c] = T(0);
+          if constexpr (C::F32) {
+#pragma unroll 2
+            for (int j = 0; j < NSHP; j += 4) {
+              float4 av[C::TM], bv[C::TN];
+#pragma unroll
+              for (int r = 0; r < C::TM; ++r) av[r] = *reinterpret_cast<const float4 *>(&gAs[(ty + 16 * r) * NSHP + j]);
+#pragma unroll
+              for (int c = 0; c < C::TN; ++c) bv[c] = *reinterpret_cast<const float4 *>(&Gc[(tx + 16 * c) * NSHP + j]);
+#pragma unroll
+              for (int r = 0; r < C::TM; ++r)
+#pragma unroll
+                for (int c = 0; c < C::TN; ++c) {
+                  acc[r][c] = fmaf(av[r].x, bv[c].x, acc[r][c]);
+                  acc[r][c] = fmaf(av[r].y, bv[c].y, acc[r][c]);
+                  acc[r][c] = fmaf(av[r].z, bv[c].z, acc[r][c]);
+                  acc[r][c] = fmaf(av[r].w, bv[c].w, acc[r][c]);
+                }
+            }
+          } else {
 #pragma unroll 4
-          for (int j = 0; j < NSH; ++j) {
-            const T a0 = gAs[ii0 * NSH + j], a1 = gAs[(ii0 + 1) * NSH + j];
-            const T b0 = Gc[kk0 * NSH + j], b1 = Gc[(kk0 + 1) * NSH + j];
-            w00 += a0 * b0;
-            w01 += a0 * b1;
-            w10 += a1 * b0;
-            w11 += a1 * b1;
+            for (int j = 0; j < NSH; ++j) {
+              T av[C::TM], bv[C::TN];
+#pragma unroll
+              for (int r = 0; r < C::TM; ++r) av[r] = gAs[(ty + 16 * r) * NSHP + j];
+#pragma unroll
+              for (int c = 0; c < C::TN; ++c) bv[c] = Gc[(tx + 16 * c) * NSHP + j];
+#pragma unroll
+              for (int r = 0; r < C::TM; ++r)
+#pragma unroll
+                for (int c = 0; c < C::TN; ++c) acc[r][c] += av[r] * bv[c];
+            }
           }
-          Wc[ii0 * KC + kk0] = w00;
-          Wc[ii0 * KC + kk0 + 1] = w01;
-          Wc[(ii0 + 1) * KC + kk0] = w10;
-          Wc[(ii0 + 1) * KC + kk0 + 1] = w11;
+#pragma unroll
+          for (int r = 0; r < C::TM; ++r)
+#pragma unroll
+            for (int c = 0; c < C::TN; ++c) Wc[(ty + 16 * r) * KC + tx + 16 * c] = acc[r][c];
         }
         __syncthreads();
         // gD[q][a][b] += sum_ii G[q][a][r0+ii] W[ii][(q,b)]
-        if (tid < QC * 16) {
-          const int qq = tid >> 4, ab = tid & 15, aa = ab >> 2, bb = ab & 3;
+        for (int task = tid; task < QC * 16; task += 256) {
+          const int qq = task >> 4, ab = task & 15, aa = ab >> 2, bb = ab & 3;
           const int q = q0 + qq;
           if (q < NQ) {
-            T s = T(0);
+            T sacc = T(0);
             const int lim = (NSH - r0 < BI) ? NSH - r0 : BI;
-            for (int ii = 0; ii < lim; ++ii) s += Gc[(4 * qq + aa) * NSH + r0 + ii] * Wc[ii * KC + 4 * qq + bb];
-            gD[q * 16 + ab] += s;
+            for (int ii = 0; ii < lim; ++ii) sacc += Gc[(4 * qq + aa) * NSHP + r0 + ii] * Wc[ii * KC + 4 * qq + bb];
+            gD[q * 16 + ab] += sacc;
           }
         }
         __syncthreads();

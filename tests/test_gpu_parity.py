@@ -170,7 +170,8 @@ def test_invalid_degree_reported(api):
 
 
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32", 1e-6)])
-@pytest.mark.parametrize("p,per_qp", [(2, False), (3, False), (5, True)])
+@pytest.mark.parametrize("p,per_qp", [(1, False), (2, False), (3, False), (4, False), (5, True), (6, False),
+                                     (7, False)])
 def test_backward_matches_oracle_adjoint(api, p, per_qp, precision, tol):
     w = inputs.workload("diff", n_max=3) if per_qp else inputs.workload("p7", n_max=4)
     n = len(w["geom"])
@@ -190,3 +191,35 @@ def test_backward_matches_oracle_adjoint(api, p, per_qp, precision, tol):
         got = got.cpu().numpy().reshape(want.shape)
         e = np.linalg.norm(got - want) / np.linalg.norm(want)
         assert e < tol, (name, e)
+
+
+def test_autograd_matches_central_differences(api):
+    """integrate() as a torch.autograd.Function: dL/dX and dL/dK of
+    L = sum_e u_e^T A_e u_e - u_e^T b_e against central differences
+    (h = 1e-6) of the FP64 GPU forward."""
+    p, n = 3, 5
+    w = inputs.workload("p7", n_max=n)
+    s = api.nsh(p)
+    u = torch.from_numpy(np.random.default_rng(7).standard_normal(n * s)).cuda()
+
+    def loss(geom, K):
+        A, bv, st = api.integrate(geom, K, dev(w["b"]), dev(w["c"]), dev(w["f"]), p=p, precision="fp64")
+        Ae = A.view(n, s, s)
+        ue = u.view(n, s)
+        return (torch.einsum("ei,eij,ej->", ue, Ae, ue) - (ue * bv.view(n, s)).sum())
+
+    geom = dev(w["geom"]).clone().requires_grad_(True)
+    K = dev(w["K"]).clone().requires_grad_(True)
+    L = loss(geom, K)
+    L.backward()
+    h = 1e-6
+    for (t, idx) in [(geom, (0, 1, 2)), (geom, (3, 4, 0)), (geom, (4, 0, 1)), (K, (2, 0, 1)), (K, (1, 2, 2))]:
+        base = (geom.detach(), K.detach())
+        plus = [x.clone() for x in base]
+        minus = [x.clone() for x in base]
+        k = 0 if t is geom else 1
+        plus[k][idx] += h
+        minus[k][idx] -= h
+        fd = (loss(*plus).item() - loss(*minus).item()) / (2 * h)
+        got = t.grad[idx].item()
+        assert abs(got - fd) <= 1e-6 * max(1.0, abs(fd)), (idx, got, fd)
