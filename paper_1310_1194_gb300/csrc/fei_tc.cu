@@ -217,8 +217,15 @@ struct TcCfg {
   static constexpr int DB = 2;                  // chunks of point operators per round
   static constexpr int A_BYTES = 128 * ROWB;
   static constexpr int B_BYTES = NPAD * ROWB;
-  static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
-  static constexpr int STAGES = P == 3 ? 3 : P == 4 ? 3 : P == 5 ? 2 : P == 6 ? 2 : 3;
+  // GS: the chunk's rows of the FP32 table (PPC points x N_sh x 16 bytes)
+  // travel with the B operand into the stage (copy engine), so the
+  // producers read them from shared memory instead of L2 (p <= 4, where
+  // they fit beside two stages)
+  static constexpr bool GS = P <= 4;
+  static constexpr int G_BYTES = GS ? PPC * NSH * 16 : 0;
+  static constexpr int G_AREA = (G_BYTES + 1023) / 1024 * 1024;
+  static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES + G_AREA;
+  static constexpr int STAGES = P == 7 ? 3 : 2;
   static constexpr int DYN_SMEM = STAGES * STAGE_BYTES + 1024;
   static_assert(NMMA % 16 == 0 && NMMA <= 256, "MMA N");
   static_assert(RT % 16 == 0 && RREG % 16 == 0 && RT >= 0, "running-sum split");
@@ -404,6 +411,7 @@ __global__ void __launch_bounds__(TcCfg<P, V>::NTHREADS, 1) tc_forward_kernel(Fw
   const uint32_t dbase = (smem_u32(dsm_raw) + 1023u) & ~1023u;
   auto stageA = [&](int s, int piece) { return dbase + s * C::STAGE_BYTES + piece * C::A_BYTES; };
   auto stageB = [&](int s) { return dbase + s * C::STAGE_BYTES + 2 * C::A_BYTES; };
+  auto stageG = [&](int s) { return dbase + s * C::STAGE_BYTES + 2 * C::A_BYTES + 2 * C::B_BYTES; };
   volatile int *abort_flag = &ax.abort_flag;
 
   if (tid == 0) {
@@ -746,19 +754,31 @@ __global__ void __launch_bounds__(TcCfg<P, V>::NTHREADS, 1) tc_forward_kernel(Fw
       for (int c = 0; c < NCH; ++c) {
         const int g = it * NCH + c, s = g % S, dr = g % DR;
         const uint32_t u = (uint32_t)(g / S), ud = (uint32_t)(g / DR);
-        // the FP32 table values of this row at this thread's points, fetched
+        // the FP32 table values of this row at this thread's points: from
+        // the stage (copied there with the B operand), or from L2, fetched
         // before the waits so that their latency overlaps them
         float4 gq[C::QPG];
+        if constexpr (!C::GS) {
 #pragma unroll
-        for (int j = 0; j < C::QPG; ++j) {
-          const int q = c * PPC + grp * C::QPG + j;
-          gq[j] = (rvalid && q < NQ) ? __ldg(G4 + (size_t)q * NSH + ri) : make_float4(0.f, 0.f, 0.f, 0.f);
+          for (int j = 0; j < C::QPG; ++j) {
+            const int q = c * PPC + grp * C::QPG + j;
+            gq[j] = (rvalid && q < NQ) ? __ldg(G4 + (size_t)q * NSH + ri) : make_float4(0.f, 0.f, 0.f, 0.f);
+          }
         }
-        // A slot free, point operators ready
+        // A slot free, point operators ready (and the table chunk landed)
         bool ok = mbar_wait(smem_u32(&ax.empty[s]), (u & 1u) ^ 1u, abort_flag);
         ok = ok && mbar_wait(smem_u32(&ax.dfull[dr]), ud & 1u, abort_flag);
+        if constexpr (C::GS) ok = ok && mbar_wait(smem_u32(&ax.bfull[s]), u & 1u, abort_flag);
         ok = __all_sync(0xffffffffu, ok);
         if (!ok) break;
+        if constexpr (C::GS) {
+          const float4 *Gs = reinterpret_cast<const float4 *>(dsm_raw + (stageG(s) - smem_u32(dsm_raw)));
+#pragma unroll
+          for (int j = 0; j < C::QPG; ++j) {
+            const int qq = grp * C::QPG + j, q = c * PPC + qq;
+            gq[j] = (rvalid && q < NQ) ? Gs[qq * NSH + ri] : make_float4(0.f, 0.f, 0.f, 0.f);
+          }
+        }
         // generic pointers to the stage's hi and lo operand tiles
         unsigned char *const ahp = dsm_raw + (stageA(s, 0) - smem_u32(dsm_raw));
         unsigned char *const alp = ahp + C::A_BYTES;
@@ -973,8 +993,12 @@ __global__ void __launch_bounds__(TcCfg<P, V>::NTHREADS, 1) tc_forward_kernel(Fw
             break;
           }
           const uint32_t bar = smem_u32(&ax.bfull[s]);
-          mbar_expect_tx(bar, 2u * C::B_BYTES);
+          // points of this chunk that exist (the last chunk may be short)
+          const int npts = NQ - c * PPC < PPC ? NQ - c * PPC : PPC;
+          const uint32_t gbytes = C::GS ? (uint32_t)(npts * NSH * 16) : 0u;
+          mbar_expect_tx(bar, 2u * C::B_BYTES + gbytes);
           bulk_g2s(stageB(s), img + (size_t)c * 2 * C::NPAD * (ROWB / 2), 2u * C::B_BYTES, bar);
+          if (C::GS) bulk_g2s(stageG(s), a.G32T + (size_t)c * PPC * NSH * 4, gbytes, bar);
         }
         if (!ok) break;
       }
