@@ -175,6 +175,22 @@ fei_status fei_integrate_backward(const fei_reference_t *refs, int nrefs,
                                   double *g_geom, const fei_coef_grad *g_coef,
                                   fei_stream_t stream);
 
+/* Adjoint of the quadratic loss L = sum_e u_e^T A_e u_e - u_e^T b_e (the
+ * energy of a field u; not in the paper): the gradients fei_integrate_backward
+ * gives for gA_e = u_e u_e^T and gb_e = -u_e, computed without forming gA.
+ * With v_q = G_q u_e (value and reference gradient of the field at point q),
+ * dL/dDt_q = v_q v_q^T and dL/d(w det J f)_q = -v_q[0], so the cost per
+ * element is O(N_sh N_q) instead of O(N_sh^2 N_q).
+ *  u  device double [b_total]: u_e at b_offset[e] (the layout of b_out).
+ * Other arguments, outputs, precisions and errors as for
+ * fei_integrate_backward (FEI_FP32: v_q in FP32, the Jacobian chain in
+ * FP64). */
+fei_status fei_integrate_backward_quadratic(const fei_reference_t *refs, int nrefs,
+                                            const fei_batch *batch, fei_precision prec,
+                                            const double *u, double *g_geom,
+                                            const fei_coef_grad *g_coef,
+                                            fei_stream_t stream);
+
 /* Contiguous offsets for a degree array (device pointers): A_offset,
  * b_offset, q_offset [n_elem + 1] (any may be NULL).  Also validates the
  * degrees: an element with p outside 1..7 sets *bad_count (device int32,

@@ -11,7 +11,8 @@ and raise ImportError if it is not built.
 from . import inputs  # noqa: F401
 
 _API_NAMES = ("fei_integrate", "fei_integrate_backward", "fei_reference_create",
-              "fei_plan_offsets", "integrate", "Reference", "Layout", "uniform_layout", "nsh", "nq", "Plan")
+              "fei_plan_offsets", "integrate", "Reference", "Layout", "uniform_layout", "nsh", "nq", "Plan",
+              "fei_integrate_backward_quadratic")
 
 
 def __getattr__(name):

@@ -79,6 +79,8 @@ def _load():
                                   vp, vp, vp, vp]
     lib.fei_integrate_backward.argtypes = [ref_p, ctypes.c_int, ctypes.POINTER(fei_batch), ctypes.c_int,
                                            vp, vp, vp, ctypes.POINTER(fei_coef_grad), vp]
+    lib.fei_integrate_backward_quadratic.argtypes = [ref_p, ctypes.c_int, ctypes.POINTER(fei_batch), ctypes.c_int,
+                                                     vp, vp, ctypes.POINTER(fei_coef_grad), vp]
     lib.fei_plan_offsets.argtypes = [vp, i64, vp, vp, vp, vp, vp]
     lib.fei_integrate_noalloc.argtypes = [ref_p, ctypes.c_int, ctypes.POINTER(fei_batch), ctypes.c_int,
                                           vp, vp, vp, vp]
@@ -92,6 +94,7 @@ def _load():
     lib.fei_last_error_string.restype = ctypes.c_char_p
     for name in ("fei_reference_create", "fei_reference_destroy", "fei_reference_info",
                  "fei_reference_copy_table", "fei_integrate", "fei_integrate_backward",
+                 "fei_integrate_backward_quadratic",
                  "fei_plan_offsets", "fei_integrate_noalloc", "fei_plan_create", "fei_plan_destroy",
                  "fei_plan_execute", "fei_plan_tune", "fei_plan_choice"):
         getattr(lib, name).restype = i32

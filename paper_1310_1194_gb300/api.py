@@ -204,6 +204,30 @@ def fei_integrate_backward(geom, K, b, c, f, gA, gb, p=None, degree=None, per_qp
     return g_geom, gK, gbc, gc, gf
 
 
+def fei_integrate_backward_quadratic(geom, K, b, c, f, u, p=None, degree=None, per_qp=False,
+                                     precision="fp64", refs=None, layout=None):
+    """Gradients of L = sum_e u_e^T A_e u_e - u_e^T b_e with respect to the
+    geometry and the coefficients, (g_geom, gK, gb_coef, gc, gf) in FP64,
+    without forming gA (u: FP64 [b_total] in the layout of b)."""
+    geom, layout = _inputs(geom, K, b, c, f, degree, p, per_qp, layout)
+    prec = _lib.PRECISIONS[precision]
+    _need(u, "u")
+    if refs is None:
+        degs = [int(p)] if degree is None else list(range(1, 8))
+        refs = [fei_reference_create(d) for d in degs]
+    g_geom = torch.empty_like(geom)
+    gK = torch.empty_like(K)
+    gbc = torch.empty_like(b)
+    gc = torch.empty_like(c)
+    gf = torch.empty_like(f)
+    cg = _lib.fei_coef_grad(gK.data_ptr(), gbc.data_ptr(), gc.data_ptr(), gf.data_ptr())
+    bt = _batch(geom, K, b, c, f, degree, p, per_qp, layout)
+    check(lib.fei_integrate_backward_quadratic(_refs_array(refs), len(refs), ctypes.byref(bt), prec, _ptr(u),
+                                               _ptr(g_geom), ctypes.byref(cg), _stream()),
+          "fei_integrate_backward_quadratic")
+    return g_geom, gK, gbc, gc, gf
+
+
 class Plan:
     """Owning wrapper of a fei_plan_t: a (mixed-degree) batch executed as one
     CUDA graph, with per-degree kernel shapes from the autotuner.

@@ -270,23 +270,27 @@ extern "C" fei_status fei_integrate(const fei_reference_t *refs, int nrefs, cons
   return FEI_OK;
 }
 
-extern "C" fei_status fei_integrate_backward(const fei_reference_t *refs, int nrefs, const fei_batch *batch,
-                                             fei_precision prec, const void *gA, const void *gb,
-                                             double *g_geom, const fei_coef_grad *g_coef,
-                                             fei_stream_t stream) {
+namespace fei {
+namespace {
+
+// Shared by the general adjoint (gA, gb given) and the quadratic-loss
+// adjoint (u given, gA = u u^T and gb = -u implied).
+fei_status backward_impl(const char *who, const fei_reference_t *refs, int nrefs, const fei_batch *batch,
+                         fei_precision prec, const void *gA, const void *gb, const double *u, double *g_geom,
+                         const fei_coef_grad *g_coef, fei_stream_t stream) {
+  const bool quad = u != nullptr;
   fei_status st = check_batch(batch);
   if (st) return st;
   if (prec != FEI_FP64 && prec != FEI_FP32)
-    return set_error(FEI_ERR_UNSUPPORTED, "fei_integrate_backward: precision %d (FP64 or FP32 only)", (int)prec);
+    return set_error(FEI_ERR_UNSUPPORTED, "%s: precision %d (FP64 or FP32 only)", who, (int)prec);
   if (batch->n_elem == 0) return FEI_OK;
-  if (!gA || !gb || !g_geom || !g_coef || !g_coef->K || !g_coef->b || !g_coef->c || !g_coef->f)
-    return set_error(FEI_ERR_INVALID_ARG, "fei_integrate_backward: NULL gradient pointer");
+  if ((!quad && (!gA || !gb)) || !g_geom || !g_coef || !g_coef->K || !g_coef->b || !g_coef->c || !g_coef->f)
+    return set_error(FEI_ERR_INVALID_ARG, "%s: NULL gradient pointer", who);
   int dev;
   FEI_CUDA_TRY(cudaGetDevice(&dev), "cudaGetDevice");
   const fei_reference *by_p[kPMax + 1];
   st = check_refs(refs, nrefs, dev, by_p);
   if (st) return st;
-  if (batch->n_elem == 0) return FEI_OK;
   cudaStream_t s = (cudaStream_t)stream;
   BwdArgs a;
   memset(&a, 0, sizeof(a));
@@ -302,6 +306,7 @@ extern "C" fei_status fei_integrate_backward(const fei_reference_t *refs, int nr
   a.q_off = batch->q_offset;
   a.gA = gA;
   a.gb = gb;
+  a.u = u;
   a.g_geom = g_geom;
   a.gK = g_coef->K;
   a.gbc = g_coef->b;
@@ -315,7 +320,7 @@ extern "C" fei_status fei_integrate_backward(const fei_reference_t *refs, int nr
     a.G32 = r->G32;
     a.znode = r->znode;
     a.tnode = r->tnode;
-    return launch_cc_backward(p, prec == FEI_FP64, a, batch->n_elem, s);
+    return launch_cc_backward(p, prec == FEI_FP64, a, batch->n_elem, s, quad);
   }
   Workspace *ws;
   st = workspace_for(dev, batch->n_elem, &ws);
@@ -341,8 +346,35 @@ extern "C" fei_status fei_integrate_backward(const fei_reference_t *refs, int nr
     ap.tnode = r->tnode;
     ap.count = ws->counts + p;
     ap.list = ws->lists + (int64_t)(p - 1) * ws->capacity;
-    st = launch_cc_backward(p, prec == FEI_FP64, ap, batch->n_elem, s);
+    st = launch_cc_backward(p, prec == FEI_FP64, ap, batch->n_elem, s, quad);
     if (st) return st;
   }
   return FEI_OK;
+}
+
+}  // namespace
+}  // namespace fei
+
+extern "C" fei_status fei_integrate_backward(const fei_reference_t *refs, int nrefs, const fei_batch *batch,
+                                             fei_precision prec, const void *gA, const void *gb,
+                                             double *g_geom, const fei_coef_grad *g_coef,
+                                             fei_stream_t stream) {
+  if (!gA || !gb) {
+    if (batch && batch->n_elem == 0) return FEI_OK;
+    return set_error(FEI_ERR_INVALID_ARG, "fei_integrate_backward: NULL gradient pointer");
+  }
+  return backward_impl("fei_integrate_backward", refs, nrefs, batch, prec, gA, gb, nullptr, g_geom, g_coef,
+                       stream);
+}
+
+extern "C" fei_status fei_integrate_backward_quadratic(const fei_reference_t *refs, int nrefs,
+                                                       const fei_batch *batch, fei_precision prec,
+                                                       const double *u, double *g_geom,
+                                                       const fei_coef_grad *g_coef, fei_stream_t stream) {
+  if (!u) {
+    if (batch && batch->n_elem == 0) return FEI_OK;
+    return set_error(FEI_ERR_INVALID_ARG, "fei_integrate_backward_quadratic: u is NULL");
+  }
+  return backward_impl("fei_integrate_backward_quadratic", refs, nrefs, batch, prec, nullptr, nullptr, u, g_geom,
+                       g_coef, stream);
 }

@@ -32,19 +32,19 @@ __device__ __forceinline__ const float *gtab_b<float>(const BwdArgs &a) { return
 // TM x TN outputs per thread; the operand rows are stored with a padded
 // stride NSHP (a multiple of 4, plus 4) so that the 16-byte loads of the
 // threads of a warp fall into distinct banks.
-template <typename T, int P>
+template <typename T, int P, bool Q = false>
 struct BwdCfg {
   static constexpr bool F32 = std::is_same<T, float>::value;
   static constexpr int NSH = nsh_of(P), NQ = nq_of(P), NZ = P + 1, NT = (P + 1) * (P + 1);
   static constexpr int BI = F32 ? 64 : 32, QC = F32 ? 16 : 8, KC = 4 * QC;
   static constexpr int TM = BI / 16, TN = KC / 16;  // outputs per thread (16 x 16 threads)
   static constexpr int NSHP = F32 ? (NSH + 3) / 4 * 4 + 4 : NSH;
-  static constexpr int NRB = (NSH + BI - 1) / BI;
-  // dynamic shared memory layout (bytes)
-  static constexpr size_t OFF_GA = 0;                                        // T [BI][NSHP]
-  static constexpr size_t OFF_GC = OFF_GA + sizeof(T) * BI * NSHP;           // T [KC][NSHP]
-  static constexpr size_t OFF_W = OFF_GC + sizeof(T) * KC * NSHP;            // T [BI][KC]
-  static constexpr size_t OFF_GD = OFF_W + sizeof(T) * BI * KC;              // T [NQ][16]
+  // dynamic shared memory layout (bytes); the quadratic-loss adjoint (Q)
+  // needs only u (in the gA area) and the per-point results
+  static constexpr size_t OFF_GA = 0;                                        // T [BI][NSHP] (Q: u [NSH])
+  static constexpr size_t OFF_GC = OFF_GA + (Q ? sizeof(T) * ((NSH + 3) / 4 * 4) : sizeof(T) * BI * NSHP);
+  static constexpr size_t OFF_W = OFF_GC + (Q ? 0 : sizeof(T) * KC * NSHP);  // T [BI][KC]
+  static constexpr size_t OFF_GD = OFF_W + (Q ? 0 : sizeof(T) * BI * KC);    // T [NQ][16]
   static constexpr size_t OFF_GSF = OFF_GD + sizeof(T) * NQ * 16;            // T [NQ]
   static constexpr size_t OFF_END = ((OFF_GSF + sizeof(T) * NQ + 15) / 16) * 16;
   static constexpr size_t SMEM = OFF_END;
@@ -79,9 +79,9 @@ __device__ __forceinline__ bool load_coef_b(const BwdArgs &a, int64_t r, double 
   return ok;
 }
 
-template <typename T, int P>
-__global__ void __launch_bounds__(256) cc_backward_kernel(BwdArgs a) {
-  using C = BwdCfg<T, P>;
+template <typename T, int P, bool Q>
+__global__ void __launch_bounds__(256, 2) cc_backward_kernel(BwdArgs a) {
+  using C = BwdCfg<T, P, Q>;
   constexpr int NSH = C::NSH, NQ = C::NQ, NT = C::NT, BI = C::BI, QC = C::QC, KC = C::KC, NSHP = C::NSHP;
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ BwdStatic sm;
@@ -128,6 +128,31 @@ __global__ void __launch_bounds__(256) cc_backward_kernel(BwdArgs a) {
       sm.txi[t][1] = x2;
       sm.tw[t] = a.tnode[4 * t + 2];
     }
+    if constexpr (Q) {
+      // L_e = u^T A_e u - u^T b_e: with v_q = G_q u (4 values per point),
+      // dL/dDt_q = v_q v_q^T and dL/d(w det f)_q = -v_q[0] (row 0 of G_q
+      // is phi), so gA = u u^T is never formed.  One warp per point.
+      T *us = gAs;
+      for (int i = tid; i < NSH; i += 256) us[i] = (T)a.u[boff + i];
+      __syncthreads();
+      const int warp = tid >> 5, lane = tid & 31;
+      for (int q = warp; q < NQ; q += 8) {
+        T v[4];
+#pragma unroll
+        for (int aa = 0; aa < 4; ++aa) {
+          const T *row = Gg + (size_t)(4 * q + aa) * NSH;
+          T s = T(0);
+          for (int i = lane; i < NSH; i += 32) s += row[i] * us[i];
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+          v[aa] = s;
+        }
+        if (lane < 16) gD[q * 16 + lane] = v[lane >> 2] * v[lane & 3];
+        if (lane == 0) gsf[q] = -v[0];
+      }
+      __syncthreads();
+    }
+    if constexpr (!Q) {
     // zero the dL/dDt accumulators; dL/d(w det f) per point
     for (int k = tid; k < NQ * 16; k += 256) gD[k] = T(0);
     for (int q = tid; q < NQ; q += 256) {
@@ -212,7 +237,13 @@ __global__ void __launch_bounds__(256) cc_backward_kernel(BwdArgs a) {
       }
     }
 
-    // FP64 chain, one thread per point
+    }  // !Q
+
+    // The chain to the coefficients and the vertices, one thread per point.
+    // det J, w det J, w / det J and the sums over points are FP64; the 3 x 3
+    // products that carry dL/dDt through the adjugate run in the contraction's
+    // type CT (FP64 for FEI_FP64, FP32 for FEI_FP32, whose dL/dDt is FP32 already)
+    using CT = T;
     double gev[21];
 #pragma unroll
     for (int k = 0; k < 21; ++k) gev[k] = 0.0;
@@ -232,39 +263,62 @@ __global__ void __launch_bounds__(256) cc_backward_kernel(BwdArgs a) {
         if (!load_coef_b(a, qoff + q, cq)) pst = FEI_ERR_NONFINITE;
         cp = cq;
       }
-      const double *K = cp, *bvec = cp + 9;
+      CT K[9], bvec[3];
+#pragma unroll
+      for (int k = 0; k < 9; ++k) K[k] = (CT)cp[k];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) bvec[k] = (CT)cp[9 + k];
       const double cc = cp[12], ff = cp[13];
-      double adj[3][3];
-      cross3(c2, c3, adj[0]);
-      cross3(c3, c1, adj[1]);
-      adj[2][0] = n3[0];
-      adj[2][1] = n3[1];
-      adj[2][2] = n3[2];
+      CT adj[3][3], cx1[3], cx2[3], cx3[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        cx1[k] = (CT)c1[k];
+        cx2[k] = (CT)c2[k];
+        cx3[k] = (CT)c3[k];
+        adj[2][k] = (CT)n3[k];
+      }
+      cross3(cx2, cx3, adj[0]);
+      cross3(cx3, cx1, adj[1]);
       const double gD00 = (double)gD[q * 16 + 0];
-      double gD0[3], gDm[3][3];
+      CT gD0[3], gDm[3][3];
 #pragma unroll
       for (int l = 0; l < 3; ++l) {
-        gD0[l] = (double)gD[q * 16 + 1 + l];
+        gD0[l] = gD[q * 16 + 1 + l];
 #pragma unroll
-        for (int m = 0; m < 3; ++m) gDm[l][m] = (double)gD[q * 16 + 4 * (l + 1) + (m + 1)];
+        for (int m = 0; m < 3; ++m) gDm[l][m] = gD[q * 16 + 4 * (l + 1) + (m + 1)];
       }
       const double gs = (double)gsf[q];
       const double s = w * det, wd = w / det;
-      // coefficient gradients at this point
-      double gKq[9], gbq[3];
+      const CT wc = (CT)w, wdc = (CT)wd;
+      // K adj_m^T and K^T adj_m per adjugate row m, and the products
+      // U = gDm Ka, V = gDm^T Kta, T = gDm adj (3 x 3 each)
+      CT Ka[3][3], Kta[3][3];
+#pragma unroll
+      for (int m = 0; m < 3; ++m)
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+          Ka[m][r] = K[3 * r] * adj[m][0] + K[3 * r + 1] * adj[m][1] + K[3 * r + 2] * adj[m][2];
+          Kta[m][r] = K[r] * adj[m][0] + K[3 + r] * adj[m][1] + K[6 + r] * adj[m][2];
+        }
+      CT U[3][3], V[3][3], Tm[3][3];
 #pragma unroll
       for (int r = 0; r < 3; ++r)
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          double acc = 0.0;
-#pragma unroll
-          for (int l = 0; l < 3; ++l)
-#pragma unroll
-            for (int m = 0; m < 3; ++m) acc += gDm[l][m] * adj[l][r] * adj[m][c];
-          gKq[3 * r + c] = wd * acc;
+        for (int k = 0; k < 3; ++k) {
+          U[r][k] = gDm[r][0] * Ka[0][k] + gDm[r][1] * Ka[1][k] + gDm[r][2] * Ka[2][k];
+          V[r][k] = gDm[0][r] * Kta[0][k] + gDm[1][r] * Kta[1][k] + gDm[2][r] * Kta[2][k];
+          Tm[r][k] = gDm[r][0] * adj[0][k] + gDm[r][1] * adj[1][k] + gDm[r][2] * adj[2][k];
         }
+      // coefficient gradients at this point: dL/dK = (w / det) adj^T gDm adj,
+      // dL/db = w adj^T gD0, dL/dc = w det gD00, dL/df = w det gs
+      CT gKq[9], gbq[3];
 #pragma unroll
-      for (int k = 0; k < 3; ++k) gbq[k] = w * (gD0[0] * adj[0][k] + gD0[1] * adj[1][k] + gD0[2] * adj[2][k]);
+      for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          gKq[3 * r + c] = wdc * (adj[0][r] * Tm[0][c] + adj[1][r] * Tm[1][c] + adj[2][r] * Tm[2][c]);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) gbq[k] = wc * (gD0[0] * adj[0][k] + gD0[1] * adj[1][k] + gD0[2] * adj[2][k]);
       const double gcq = s * gD00, gfq = s * gs;
       if (a.coef_mode == FEI_COEF_PER_POINT) {
         const int64_t r = qoff + q;
@@ -282,47 +336,34 @@ __global__ void __launch_bounds__(256) cc_backward_kernel(BwdArgs a) {
         gco[12] += gcq;
         gco[13] += gfq;
       }
-      // through det J and the adjugate rows
-      double Ka[3][3], Kta[3][3];
+      // through det J and the adjugate rows: with the quadratic form
+      // sum_lm gDm[l][m] adj_l K adj_m^T = sum_{l,r} adj[l][r] U[l][r]
+      CT quad = CT(0);
 #pragma unroll
-      for (int m = 0; m < 3; ++m)
-#pragma unroll
-        for (int r = 0; r < 3; ++r) {
-          Ka[m][r] = K[3 * r] * adj[m][0] + K[3 * r + 1] * adj[m][1] + K[3 * r + 2] * adj[m][2];
-          Kta[m][r] = K[r] * adj[m][0] + K[3 + r] * adj[m][1] + K[6 + r] * adj[m][2];
-        }
-      double quad = 0.0;
-#pragma unroll
-      for (int l = 0; l < 3; ++l)
-#pragma unroll
-        for (int m = 0; m < 3; ++m) quad += gDm[l][m] * dot3(adj[l], Ka[m]);
-      const double gdet = w * (cc * gD00 + ff * gs) - wd / det * quad;
-      double gadj[3][3];
+      for (int l = 0; l < 3; ++l) quad += adj[l][0] * U[l][0] + adj[l][1] * U[l][1] + adj[l][2] * U[l][2];
+      const double gdet = w * (cc * gD00 + ff * gs) - wd / det * (double)quad;
+      const CT gdetc = (CT)gdet;
+      CT gadj[3][3];
 #pragma unroll
       for (int r = 0; r < 3; ++r)
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          double acc = w * gD0[r] * bvec[k];
-#pragma unroll
-          for (int m = 0; m < 3; ++m) acc += wd * (gDm[r][m] * Ka[m][k] + gDm[m][r] * Kta[m][k]);
-          gadj[r][k] = acc;
-        }
-      double gc1[3] = {0, 0, 0}, gc2[3] = {0, 0, 0}, gc3[3], tmp[3], gn3[3];
-      cross3(c3, gadj[0], gc2);   // adj0 = c2 x c3
-      cross3(gadj[0], c2, gc3);
-      cross3(c1, gadj[1], tmp);   // adj1 = c3 x c1
+        for (int k = 0; k < 3; ++k) gadj[r][k] = wc * gD0[r] * bvec[k] + wdc * (U[r][k] + V[r][k]);
+      CT gc1[3] = {0, 0, 0}, gc2[3] = {0, 0, 0}, gc3[3], tmp[3], gn3[3];
+      cross3(cx3, gadj[0], gc2);   // adj0 = c2 x c3
+      cross3(gadj[0], cx2, gc3);
+      cross3(cx1, gadj[1], tmp);   // adj1 = c3 x c1
 #pragma unroll
       for (int k = 0; k < 3; ++k) gc3[k] += tmp[k];
-      cross3(gadj[1], c3, gc1);
+      cross3(gadj[1], cx3, gc1);
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
-        gn3[k] = gadj[2][k] + gdet * c3[k];  // adj2 = n3, det = n3 . c3
-        gc3[k] += gdet * n3[k];
+        gn3[k] = gadj[2][k] + gdetc * cx3[k];  // adj2 = n3, det = n3 . c3
+        gc3[k] += gdetc * adj[2][k];
       }
-      cross3(c2, gn3, tmp);       // n3 = c1 x c2
+      cross3(cx2, gn3, tmp);       // n3 = c1 x c2
 #pragma unroll
       for (int k = 0; k < 3; ++k) gc1[k] += tmp[k];
-      cross3(gn3, c1, tmp);
+      cross3(gn3, cx1, tmp);
 #pragma unroll
       for (int k = 0; k < 3; ++k) gc2[k] += tmp[k];
       const double z = sm.zz[iz], x1 = sm.txi[t][0], x2 = sm.txi[t][1];
@@ -396,40 +437,45 @@ __global__ void __launch_bounds__(256) cc_backward_kernel(BwdArgs a) {
   }
 }
 
-template <typename T, int P>
+template <typename T, int P, bool Q>
 fei_status launch_bwd(const BwdArgs &a, int64_t grid_work, cudaStream_t s) {
-  using C = BwdCfg<T, P>;
-  FEI_CUDA_TRY(cudaFuncSetAttribute(cc_backward_kernel<T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  using C = BwdCfg<T, P, Q>;
+  FEI_CUDA_TRY(cudaFuncSetAttribute(cc_backward_kernel<T, P, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)C::SMEM),
                "cudaFuncSetAttribute(cc_backward)");
   int64_t blocks = grid_work;
   if (a.count) blocks = blocks < 152 * 4 ? blocks : 152 * 4;
   if (blocks > 2147483647LL) blocks = 2147483647LL;
   if (blocks < 1) blocks = 1;
-  cc_backward_kernel<T, P><<<(unsigned)blocks, 256, C::SMEM, s>>>(a);
+  cc_backward_kernel<T, P, Q><<<(unsigned)blocks, 256, C::SMEM, s>>>(a);
   FEI_CUDA_TRY(cudaGetLastError(), "cc_backward_kernel launch");
   return FEI_OK;
 }
 
-template <typename T>
+template <typename T, bool Q>
 fei_status launch_bwd_typed(int p, const BwdArgs &a, int64_t grid_work, cudaStream_t s) {
   switch (p) {
-    case 1: return launch_bwd<T, 1>(a, grid_work, s);
-    case 2: return launch_bwd<T, 2>(a, grid_work, s);
-    case 3: return launch_bwd<T, 3>(a, grid_work, s);
-    case 4: return launch_bwd<T, 4>(a, grid_work, s);
-    case 5: return launch_bwd<T, 5>(a, grid_work, s);
-    case 6: return launch_bwd<T, 6>(a, grid_work, s);
-    case 7: return launch_bwd<T, 7>(a, grid_work, s);
+    case 1: return launch_bwd<T, 1, Q>(a, grid_work, s);
+    case 2: return launch_bwd<T, 2, Q>(a, grid_work, s);
+    case 3: return launch_bwd<T, 3, Q>(a, grid_work, s);
+    case 4: return launch_bwd<T, 4, Q>(a, grid_work, s);
+    case 5: return launch_bwd<T, 5, Q>(a, grid_work, s);
+    case 6: return launch_bwd<T, 6, Q>(a, grid_work, s);
+    case 7: return launch_bwd<T, 7, Q>(a, grid_work, s);
   }
   return set_error(FEI_ERR_INVALID_DEGREE, "degree %d outside 1..7", p);
 }
 
 }  // namespace
 
-fei_status launch_cc_backward(int p, bool fp64, const BwdArgs &a, int64_t grid_work, cudaStream_t s) {
+fei_status launch_cc_backward(int p, bool fp64, const BwdArgs &a, int64_t grid_work, cudaStream_t s,
+                              bool quadratic) {
   if (grid_work <= 0) return FEI_OK;
-  return fp64 ? launch_bwd_typed<double>(p, a, grid_work, s) : launch_bwd_typed<float>(p, a, grid_work, s);
+  if (quadratic)
+    return fp64 ? launch_bwd_typed<double, true>(p, a, grid_work, s)
+                : launch_bwd_typed<float, true>(p, a, grid_work, s);
+  return fp64 ? launch_bwd_typed<double, false>(p, a, grid_work, s)
+              : launch_bwd_typed<float, false>(p, a, grid_work, s);
 }
 
 }  // namespace fei

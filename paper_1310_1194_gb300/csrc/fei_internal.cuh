@@ -75,6 +75,7 @@ struct BwdArgs {
   const int64_t *A_off, *b_off, *q_off;
   const void *gA;
   const void *gb;
+  const double *u;  // quadratic-loss adjoint: u_e at b_off[e] (else unused)
   double *g_geom;
   double *gK, *gbc, *gc, *gf;
   const double *G64;
@@ -92,7 +93,10 @@ fei_status cuda_error(cudaError_t e, const char *what);
 // (all work items for a known count, 152 x 4 or 152 x 8 for a device count)
 fei_status launch_cc_forward(int p, bool fp64, const FwdArgs &a, int64_t grid_work, cudaStream_t s,
                              int64_t grid_cap = 0);
-fei_status launch_cc_backward(int p, bool fp64, const BwdArgs &a, int64_t grid_work, cudaStream_t s);
+// quadratic = true: the adjoint of L = sum_e u_e^T A_e u_e - u_e^T b_e
+// (gA_e = u_e u_e^T and gb_e = -u_e never formed; a.u holds u)
+fei_status launch_cc_backward(int p, bool fp64, const BwdArgs &a, int64_t grid_work, cudaStream_t s,
+                              bool quadratic = false);
 // variant: 0 .. tc_variant_count(p) - 1 (warp-role variants of one kernel)
 fei_status launch_tc_forward(int p, const fei_reference *ref, const FwdArgs &a, int64_t grid_work,
                              cudaStream_t s, int variant = 0);

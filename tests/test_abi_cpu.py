@@ -63,6 +63,8 @@ def test_argument_errors_before_any_cuda_call(lib):
     lib.fei_plan_choice.argtypes = [vp, ctypes.c_int, vp, vp, vp]
     assert lib.fei_plan_choice(None, 3, None, None, None) == 1
     assert lib.fei_plan_destroy(None) == 0
+    lib.fei_integrate_backward_quadratic.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int, vp, vp, vp, vp]
+    assert lib.fei_integrate_backward_quadratic(None, 1, None, 0, None, None, None, None) == 1
 
 
 def test_python_binding_loads():

@@ -223,3 +223,41 @@ def test_autograd_matches_central_differences(api):
         fd = (loss(*plus).item() - loss(*minus).item()) / (2 * h)
         got = t.grad[idx].item()
         assert abs(got - fd) <= 1e-6 * max(1.0, abs(fd)), (idx, got, fd)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32", 1e-6)])
+@pytest.mark.parametrize("p,per_qp", [(1, False), (4, False), (5, True), (7, False)])
+def test_quadratic_adjoint_matches_oracle(api, p, per_qp, precision, tol):
+    """fei_integrate_backward_quadratic equals the general adjoint of the
+    oracle with gA_e = u_e u_e^T and gb_e = -u_e."""
+    w = inputs.workload("diff", n_max=3) if per_qp else inputs.workload("p7", n_max=4)
+    n = len(w["geom"])
+    s = api.nsh(p)
+    u = np.random.default_rng(10 + p).standard_normal(n * s)
+    out = api.fei_integrate_backward_quadratic(dev(w["geom"]), dev(w["K"]), dev(w["b"]), dev(w["c"]), dev(w["f"]),
+                                               dev(u), p=p, per_qp=per_qp, precision=precision)
+    torch.cuda.synchronize()
+    ue = u.reshape(n, s)
+    gA = np.einsum("ei,ej->eij", ue, ue).reshape(-1)
+    ref = oracle.integrate_backward(w["geom"], w["K"], w["b"], w["c"], w["f"], gA, -u, p=p, per_qp=per_qp)
+    for name, got, want in zip(("geom", "K", "b", "c", "f"), out, ref):
+        got = got.cpu().numpy().reshape(want.shape)
+        e = np.linalg.norm(got - want) / np.linalg.norm(want)
+        assert e < tol, (name, e)
+
+
+def test_quadratic_adjoint_mixed_degrees(api):
+    w = inputs.workload("mixed", n_max=60)
+    deg = dev(w["degree"], torch.int32)
+    layout = api.fei_plan_offsets(deg)
+    u = np.random.default_rng(5).standard_normal(layout.b_total)
+    out = api.fei_integrate_backward_quadratic(dev(w["geom"]), dev(w["K"]), dev(w["b"]), dev(w["c"]), dev(w["f"]),
+                                               dev(u), degree=deg, layout=layout, precision="fp64")
+    torch.cuda.synchronize()
+    boff = layout.b_offset.cpu().numpy()
+    gA = np.concatenate([np.outer(u[boff[e]:boff[e + 1]], u[boff[e]:boff[e + 1]]).reshape(-1)
+                         for e in range(len(w["geom"]))])
+    ref = oracle.integrate_backward(w["geom"], w["K"], w["b"], w["c"], w["f"], gA, -u, degree=w["degree"])
+    for name, got, want in zip(("geom", "K", "b", "c", "f"), out, ref):
+        got = got.cpu().numpy().reshape(want.shape)
+        assert np.linalg.norm(got - want) / np.linalg.norm(want) < 1e-10, name
