@@ -123,6 +123,16 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t
                : "memory");
 }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// shared -> global bulk copy (16-byte aligned addresses, size a multiple of 16)
+__device__ __forceinline__ void bulk_s2g(void *dst, uint32_t src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(src), "r"(bytes)
+               : "memory");
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+// wait until the bulk copies of this thread have read their source
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// wait until the bulk copies of this thread have completed
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -224,6 +234,7 @@ struct TcCfg {
   static constexpr bool GS = P <= 4;
   static constexpr int G_BYTES = GS ? PPC * NSH * 16 : 0;
   static constexpr int G_AREA = (G_BYTES + 1023) / 1024 * 1024;
+  static constexpr bool BS = P <= 4;  // bulk stores of staged rows (shared-memory budget)
   static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES + G_AREA;
   static constexpr int STAGES = P == 7 ? 3 : 2;
   static constexpr int DYN_SMEM = STAGES * STAGE_BYTES + 1024;
@@ -294,6 +305,9 @@ struct TcAux {
   TcMeta meta[2];
   float bsum[2][C::NPW * 32 / 128][128];
   alignas(16) float stg[C::NEW][32][17];  // epilogue transpose staging
+  // BS: for a contiguous output layout (p <= 4), each epilogue warp stages
+  // 16 of its rows of A_e here and stores them with one bulk copy
+  alignas(16) float rows16[C::BS ? C::NEW : 1][C::BS ? 16 * C::NSH : 4];
 };
 
 __device__ __forceinline__ bool load_coef_tc(const FwdArgs &a, int64_t r, double *cd) {
@@ -859,6 +873,10 @@ __global__ void __launch_bounds__(TcCfg<P, V>::NTHREADS, 1) tc_forward_kernel(Fw
     const int quarter = warp & 3;     // TMEM lanes 32*quarter ..
     const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
     const int myrow = quarter * 32 + lane;
+    // a contiguous output (uniform degree, no element list, 16-byte aligned):
+    // the tile's rows of A_e are one range of A
+    const bool contiguous = a.A_off == nullptr && a.list == nullptr &&
+                            (reinterpret_cast<uintptr_t>(a.A) & 15u) == 0u;
     float rreg[C::RREG > 0 ? C::RREG : 1];
     int it = 0;
     uint32_t unit = 0;
@@ -936,49 +954,97 @@ __global__ void __launch_bounds__(TcCfg<P, V>::NTHREADS, 1) tc_forward_kernel(Fw
         reinterpret_cast<float *>(a.bv)[M.row_boff[myrow]] = st ? 0.f : bsum;
         if (M.row_eid[myrow] >= 0) a.status[M.row_eid[myrow]] = st;
       }
-      float(*stg)[17] = ax.stg[ew];
-#pragma unroll
-      for (int b = 0; b < C::NPAD / 16; ++b) {
-        const int ncol = b * 16;
-        if (ncol < NSH) {
-          float v[16];
-          if (ncol < C::RT) {
-            tmem_ld16(tmem + lane_base + 2 * C::NMMA + ncol, v);
-          } else if constexpr (C::RREG > 0) {
-#pragma unroll
-            for (int k2 = 0; k2 < 16; ++k2) v[k2] = rreg[ncol - C::RT + k2];
-          }
-#pragma unroll
-          for (int k2 = 0; k2 < 16; ++k2) stg[lane][k2] = v[k2] * dn;
+      // rows of this warp: 32 * quarter + [0, 32) of the tile
+      const int64_t wrow0 = tile * 128 + quarter * 32;
+      const int nvalid = rows_total - wrow0 >= 32 ? 32 : (rows_total - wrow0 > 0 ? (int)(rows_total - wrow0) : 0);
+      if (C::BS && contiguous) {
+        // two halves of 16 rows: lanes 16h .. 16h+15 stage their rows, one
+        // lane stores the half with a bulk copy (A_e rows of consecutive
+        // elements are consecutive in a contiguous layout)
+        float *buf = ax.rows16[ew];
+        for (int h = 0; h < 2; ++h) {
+          const int nh = nvalid - 16 * h >= 16 ? 16 : (nvalid - 16 * h > 0 ? nvalid - 16 * h : 0);
+          if (lane == 0) bulk_wait_read();  // the previous copy has read the buffer
           __syncwarp();
-          // two rows per store instruction: lanes 0-15 row rr, 16-31 row rr+1;
-          // eight rows' values and offsets are read before their stores (a
-          // global store could alias the staging buffer as far as the
-          // compiler knows, so interleaving would serialise every load
-          // behind the previous store)
-          const int half = lane >> 4, col = ncol + (lane & 15);
-          float *const Aout = reinterpret_cast<float *>(a.A);
+          const bool mine = (lane >> 4) == h;
 #pragma unroll
-          for (int r16 = 0; r16 < 32; r16 += 16) {
-            float vv[8];
-            int64_t oo[8];
+          for (int b = 0; b < C::NPAD / 16; ++b) {
+            const int ncol = b * 16;
+            if (ncol < NSH) {
+              float v[16];
+              if (ncol < C::RT) {
+                tmem_ld16(tmem + lane_base + 2 * C::NMMA + ncol, v);
+              } else if constexpr (C::RREG > 0) {
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-              const int rr = r16 + 2 * j;
-              oo[j] = M.row_off[quarter * 32 + rr + half];
-              vv[j] = stg[rr + half][lane & 15];
+                for (int k2 = 0; k2 < 16; ++k2) v[k2] = rreg[ncol - C::RT + k2];
+              }
+              if (mine) {
+                float *dst = buf + (lane & 15) * NSH + ncol;
+#pragma unroll
+                for (int k2 = 0; k2 < 16; ++k2)
+                  if (ncol + k2 < NSH) dst[k2] = v[k2] * dn;
+              }
             }
-#pragma unroll
-            for (int j = 0; j < 8; ++j)
-              if (oo[j] >= 0 && col < NSH) Aout[oo[j] + col] = vv[j];
           }
+          fence_proxy_async();
           __syncwarp();
+          if (lane == 0 && nh > 0) {
+            const uint32_t bytes = (uint32_t)(nh * NSH * 4);
+            float *gdst = reinterpret_cast<float *>(a.A) + (wrow0 + 16 * h) * NSH;
+            if ((bytes & 15u) == 0u) {
+              bulk_s2g(gdst, smem_u32(buf), bytes);
+            } else {
+              // a ragged tail whose size is not a multiple of 16 bytes
+              for (int k = 0; k < nh * NSH; ++k) gdst[k] = buf[k];
+            }
+          }
+        }
+      } else {
+        float(*stg)[17] = ax.stg[ew];
+  #pragma unroll
+        for (int b = 0; b < C::NPAD / 16; ++b) {
+          const int ncol = b * 16;
+          if (ncol < NSH) {
+            float v[16];
+            if (ncol < C::RT) {
+              tmem_ld16(tmem + lane_base + 2 * C::NMMA + ncol, v);
+            } else if constexpr (C::RREG > 0) {
+  #pragma unroll
+              for (int k2 = 0; k2 < 16; ++k2) v[k2] = rreg[ncol - C::RT + k2];
+            }
+  #pragma unroll
+            for (int k2 = 0; k2 < 16; ++k2) stg[lane][k2] = v[k2] * dn;
+            __syncwarp();
+            // two rows per store instruction: lanes 0-15 row rr, 16-31 row rr+1;
+            // eight rows' values and offsets are read before their stores (a
+            // global store could alias the staging buffer as far as the
+            // compiler knows, so interleaving would serialise every load
+            // behind the previous store)
+            const int half = lane >> 4, col = ncol + (lane & 15);
+            float *const Aout = reinterpret_cast<float *>(a.A);
+  #pragma unroll
+            for (int r16 = 0; r16 < 32; r16 += 16) {
+              float vv[8];
+              int64_t oo[8];
+  #pragma unroll
+              for (int j = 0; j < 8; ++j) {
+                const int rr = r16 + 2 * j;
+                oo[j] = M.row_off[quarter * 32 + rr + half];
+                vv[j] = stg[rr + half][lane & 15];
+              }
+  #pragma unroll
+              for (int j = 0; j < 8; ++j)
+                if (oo[j] >= 0 && col < NSH) Aout[oo[j] + col] = vv[j];
+            }
+            __syncwarp();
+          }
         }
       }
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&ax.meta_empty[slot]));
     }
+    if (C::BS && lane == 0) bulk_wait_all();  // this warp's bulk stores have landed
   } else if (warp == 0) {
     // ================================================================ B stream
     if (lane == 0) {
