@@ -36,6 +36,7 @@ WORKLOAD_TEXT = {
     "mixed": "mixed degree: 200000 prisms (50x50x40 grid), p in 1..7 with probabilities .25/.2/.15/.15/.1/.1/.05",
     "diff": "differentiation: 20000 prisms (25x20x20), p=5, per-point coefficient fields",
     "p7": "high order: 32768 prisms (32x32x16 grid, jitter 25% h, det J > 0 certified), p=7",
+    "p1m": "PR1 recipe at 1 000 000 prisms (100x100x50 grid, jitter 10% h), p=1 (supplementary, store-bound)",
 }
 
 
@@ -431,12 +432,18 @@ def main():
             dom = {"kernel": "forward", "ms": fwd_ms, "F": F, "precision": precision, "counts": counts,
                    "adjoint_ms": bwd_ms}
     hw = None
+    low_p = p is not None and p <= 2 and grads is None
     F, ms_all = dom["F"], ms
     ms = dom["ms"]
     counts = dom["counts"]
     precision_all = precision
     precision = dom["precision"]
-    if precision == "tc_f16x3":
+    if low_p:
+        # p <= 2: a few kflops per element against 0.4-0.6 KB of traffic; the
+        # path streams geometry in and element matrices out
+        bound, peak, unit, achieved = "hbm", peaks["hbm_gbs"], "GB/s", Bts / (ms * 1e-3) / 1e9
+        peak_note = f"HBM copy bandwidth ({peak_src})"
+    elif precision == "tc_f16x3":
         # every algorithmic multiply-add is three fp16 tensor products (hi*hi,
         # hi*lo, lo*hi), so the peak for algorithmic flops is a third of the
         # fp16 (= bf16) dense peak

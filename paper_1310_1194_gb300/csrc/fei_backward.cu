@@ -136,13 +136,25 @@ __global__ void __launch_bounds__(256, 2) cc_backward_kernel(BwdArgs a) {
       for (int i = tid; i < NSH; i += 256) us[i] = (T)a.u[boff + i];
       __syncthreads();
       const int warp = tid >> 5, lane = tid & 31;
+      constexpr int NI = (NSH + 31) / 32;  // table entries per lane and row
+      T ul[NI];
+#pragma unroll
+      for (int k = 0; k < NI; ++k) ul[k] = lane + 32 * k < NSH ? us[lane + 32 * k] : T(0);
       for (int q = warp; q < NQ; q += 8) {
-        T v[4];
+        // the four rows of G_q: every load issued before the first use
+        T g[4][NI];
 #pragma unroll
         for (int aa = 0; aa < 4; ++aa) {
           const T *row = Gg + (size_t)(4 * q + aa) * NSH;
+#pragma unroll
+          for (int k = 0; k < NI; ++k) g[aa][k] = lane + 32 * k < NSH ? row[lane + 32 * k] : T(0);
+        }
+        T v[4];
+#pragma unroll
+        for (int aa = 0; aa < 4; ++aa) {
           T s = T(0);
-          for (int i = lane; i < NSH; i += 32) s += row[i] * us[i];
+#pragma unroll
+          for (int k = 0; k < NI; ++k) s += g[aa][k] * ul[k];
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
           v[aa] = s;

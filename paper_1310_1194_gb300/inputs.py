@@ -16,6 +16,8 @@ Workloads (all seeded, numpy PCG64):
   varying per quadrature slot (smooth sin/cos fields of position).
 * ``p7``    -- 32x32x16 grid (32 768 prisms), +-25% h with every element
   certified valid (positive Jacobian determinant), p = 7.
+* ``p1m``   -- 100x100x50 grid (1 000 000 prisms), +-10% h, p = 1: the
+  PR1 recipe at a size where the store-bound low-degree path is measurable.
 
 Coefficients per element: K = Q diag(lam) Q^T with Q from the QR factor of a
 3x3 standard normal matrix (sign-fixed) and lam ~ U[0.5, 2]; b ~ U[-1, 1]^3;
@@ -33,6 +35,7 @@ WORKLOADS = {
     "mixed": dict(grid=(50, 50, 40), jitter=0.10, seed=3, p=None),
     "diff": dict(grid=(25, 20, 20), jitter=0.10, seed=4, p=5),
     "p7": dict(grid=(32, 32, 16), jitter=0.25, seed=5, p=7),
+    "p1m": dict(grid=(100, 100, 50), jitter=0.10, seed=6, p=1),
 }
 
 
