@@ -95,101 +95,158 @@ __device__ __forceinline__ int point_direct(const double *ev, const double *pt, 
 }
 
 // ---------------------------------------------------------------------------
-// Low degree (p <= 2): one warp per element, lanes over the entries of A_e.
+// Low degree (p <= 2): EPW elements per warp (p = 1: four elements of 8
+// points, p = 2: one of 27), so that every lane takes a point in the FP64
+// Jacobian work; lanes then run over the entries of the A_e.
 // ---------------------------------------------------------------------------
+
+// finite test by the exponent bits (integer pipe; FP64 compares are slow here)
+__device__ __forceinline__ bool finite_d(double x) {
+  return ((__double_as_longlong(x) >> 52) & 0x7ff) != 0x7ff;
+}
+
+// One component (j = vector * 3 + axis) of the element vectors A1, B1, A2,
+// B2, C, D1, D2 from the bottom (P) and top (Q) vertices, FP64.
+__device__ __forceinline__ double elem_vec_comp(const double *X, int j) {
+  const int v = j / 3, k = j - 3 * v;
+  const double p0 = X[k], p1 = X[3 + k], p2 = X[6 + k], q0 = X[9 + k], q1 = X[12 + k], q2 = X[15 + k];
+  switch (v) {
+    case 0: return 0.5 * ((p1 - p0) + (q1 - q0));
+    case 1: return 0.5 * ((q1 - q0) - (p1 - p0));
+    case 2: return 0.5 * ((p2 - p0) + (q2 - q0));
+    case 3: return 0.5 * ((q2 - q0) - (p2 - p0));
+    case 4: return 0.5 * (q0 - p0);
+    case 5: return 0.5 * ((q1 - p1) - (q0 - p0));
+    default: return 0.5 * ((q2 - p2) - (q0 - p0));
+  }
+}
 
 template <typename T, int P>
 struct SmallCfg {
   static constexpr int NSH = nsh_of(P), NQ = nq_of(P), K4 = 4 * NQ;
+  static constexpr int EPW = 32 / NQ;  // elements per warp
   static constexpr int WPB = std::is_same<T, double>::value ? 4 : 8;
-  static constexpr int WARP_BYTES =
+  // per element slot: X[18], ev[21], cd[14] (FP64), D[NQ][16], H[K4][NSH] (T), status
+  static constexpr int SLOT_BYTES =
       ((sizeof(double) * (18 + 21 + 14) + sizeof(T) * (NQ * 16 + K4 * NSH) + 16 + 15) / 16) * 16;
-  static constexpr int SMEM = sizeof(T) * K4 * NSH + WPB * WARP_BYTES + 16;
+  static constexpr int WARP_BYTES = EPW * SLOT_BYTES;
+  static constexpr int SMEM = ((sizeof(T) * K4 * NSH + 15) / 16) * 16 + WPB * WARP_BYTES;
 };
 
 template <typename T, int P>
 __global__ void __launch_bounds__(SmallCfg<T, P>::WPB * 32) cc_small_kernel(FwdArgs a) {
   using C = SmallCfg<T, P>;
-  constexpr int NSH = C::NSH, NQ = C::NQ, K4 = C::K4;
+  constexpr int NSH = C::NSH, NQ = C::NQ, K4 = C::K4, EPW = C::EPW;
   static_assert(NQ <= 32, "one point per lane");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *Gs = reinterpret_cast<T *>(smem_raw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   unsigned char *wb = smem_raw + ((sizeof(T) * K4 * NSH + 15) / 16) * 16 + warp * C::WARP_BYTES;
-  double *X = reinterpret_cast<double *>(wb);
-  double *ev = X + 18;
-  double *cd = ev + 21;
-  T *D = reinterpret_cast<T *>(cd + 14);
-  T *H = D + NQ * 16;
+  auto Xs = [&](int sl) { return reinterpret_cast<double *>(wb + sl * C::SLOT_BYTES); };
+  auto evs = [&](int sl) { return Xs(sl) + 18; };
+  auto cds = [&](int sl) { return Xs(sl) + 39; };
+  auto Ds = [&](int sl) { return reinterpret_cast<T *>(Xs(sl) + 53); };
+  auto Hs = [&](int sl) { return Ds(sl) + NQ * 16; };
+  auto Ss = [&](int sl) { return reinterpret_cast<int *>(Hs(sl) + K4 * NSH); };
 
   const T *G = gtab<T>(a);
   for (int k = threadIdx.x; k < K4 * NSH; k += blockDim.x) Gs[k] = G[k];
   __syncthreads();
 
   const int64_t items = n_items(a);
-  for (int64_t item = (int64_t)blockIdx.x * C::WPB + warp; item < items;
-       item += (int64_t)gridDim.x * C::WPB) {
-    const int64_t e = a.list ? (int64_t)a.list[item] : item;
-    bool ok = true;
-    if (lane < 18) {
-      X[lane] = a.geom[18 * e + lane];
-      ok = isfinite(X[lane]);
+  const int64_t nwarps = (int64_t)gridDim.x * C::WPB;
+  for (int64_t item0 = ((int64_t)blockIdx.x * C::WPB + warp) * EPW; item0 < items; item0 += nwarps * EPW) {
+    const int nel = items - item0 < EPW ? (int)(items - item0) : EPW;
+    // geometry and coefficients of the warp's elements, spread over lanes
+    for (int idx = lane; idx < nel * 32; idx += 32) {
+      const int sl = idx >> 5, k = idx & 31;
+      const int64_t e = a.list ? (int64_t)a.list[item0 + sl] : item0 + sl;
+      bool ok = true;
+      if (k < 18) {
+        const double x = a.geom[18 * e + k];
+        Xs(sl)[k] = x;
+        ok = finite_d(x);
+      } else if (a.coef_mode == FEI_COEF_PER_ELEMENT) {
+        const int c = k - 18;
+        const double x = c < 9 ? a.K[9 * e + c] : c < 12 ? a.b[3 * e + (c - 9)] : c == 12 ? a.c[e] : a.f[e];
+        cds(sl)[c] = x;
+        ok = finite_d(x);
+      }
+      // lanes of one element are one aligned group of 32: the whole warp
+      const unsigned bad = __ballot_sync(0xffffffffu, !ok);
+      if (k == 0) Ss(sl)[0] = bad ? FEI_ERR_NONFINITE : 0;
     }
-    if (a.coef_mode == FEI_COEF_PER_ELEMENT && lane == 0) ok &= load_coef(a, e, cd);
-    int st = __any_sync(0xffffffffu, !ok) ? FEI_ERR_NONFINITE : 0;
     __syncwarp();
-    if (lane == 0) elem_vectors(X, ev);
+    // element vectors, one component per lane (FP64)
+    for (int idx = lane; idx < nel * 21; idx += 32) {
+      const int sl = idx / 21, j = idx - sl * 21;
+      evs(sl)[j] = elem_vec_comp(Xs(sl), j);
+    }
     __syncwarp();
+    // point operators: lane = (element slot, point)
+    const int psl = lane / NQ, q = lane - psl * NQ;
     int pst = 0;
-    if (lane < NQ) {
+    if (psl < nel) {
+      const int64_t e = a.list ? (int64_t)a.list[item0 + psl] : item0 + psl;
       double ptv[4];
       // quadrature point from the node tables: q = iz*(p+1)^2 + t
-      const int iz = lane / ((P + 1) * (P + 1)), t = lane % ((P + 1) * (P + 1));
+      const int iz = q / ((P + 1) * (P + 1)), t = q % ((P + 1) * (P + 1));
       ptv[0] = a.tnode[4 * t];
       ptv[1] = a.tnode[4 * t + 1];
       ptv[2] = a.znode[2 * iz];
       ptv[3] = a.tnode[4 * t + 2] * a.znode[2 * iz + 1];
       double cq[14];
-      const double *cp = cd;
+      const double *cp = cds(psl);
       if (a.coef_mode == FEI_COEF_PER_POINT) {
-        const int64_t r = (a.q_off ? a.q_off[e] : e * (int64_t)NQ) + lane;
+        const int64_t r = (a.q_off ? a.q_off[e] : e * (int64_t)NQ) + q;
         if (!load_coef(a, r, cq)) pst = FEI_ERR_NONFINITE;
         cp = cq;
       }
-      pst = merge_status(pst, point_direct<T>(ev, ptv, cp, D + 16 * lane));
+      pst = merge_status(pst, point_direct<T>(evs(psl), ptv, cp, Ds(psl) + 16 * q));
+      if (pst) atomicMax(Ss(psl), pst == FEI_ERR_NONFINITE ? 2 * FEI_ERR_NONFINITE : pst);
     }
-    // warp-wide status with NONFINITE precedence
-    if (__any_sync(0xffffffffu, pst == FEI_ERR_NONFINITE)) st = FEI_ERR_NONFINITE;
-    else if (!st && __any_sync(0xffffffffu, pst == FEI_ERR_NEGATIVE_JACOBIAN)) st = FEI_ERR_NEGATIVE_JACOBIAN;
     __syncwarp();
-    for (int idx = lane; idx < NQ * NSH; idx += 32) {
-      const int q = idx / NSH, i = idx - q * NSH;
-      const T *Dq = D + 16 * q;
-      const T g0 = Gs[(4 * q + 0) * NSH + i], g1 = Gs[(4 * q + 1) * NSH + i];
-      const T g2 = Gs[(4 * q + 2) * NSH + i], g3 = Gs[(4 * q + 3) * NSH + i];
-      H[(4 * q + 0) * NSH + i] = Dq[0] * g0;
+    // H[(q, b)][i] = sum_a Dt_q[a][b] G[q][a][i], per element
+    for (int idx = lane; idx < nel * NQ * NSH; idx += 32) {
+      const int sl = idx / (NQ * NSH), rem = idx - sl * (NQ * NSH);
+      const int qq = rem / NSH, i = rem - qq * NSH;
+      const T *Dq = Ds(sl) + 16 * qq;
+      T *H = Hs(sl);
+      const T g0 = Gs[(4 * qq + 0) * NSH + i], g1 = Gs[(4 * qq + 1) * NSH + i];
+      const T g2 = Gs[(4 * qq + 2) * NSH + i], g3 = Gs[(4 * qq + 3) * NSH + i];
+      H[(4 * qq + 0) * NSH + i] = Dq[0] * g0;
 #pragma unroll
       for (int m = 0; m < 3; ++m)
-        H[(4 * q + 1 + m) * NSH + i] = Dq[1 + m] * g0 + Dq[4 + m] * g1 + Dq[7 + m] * g2 + Dq[10 + m] * g3;
+        H[(4 * qq + 1 + m) * NSH + i] = Dq[1 + m] * g0 + Dq[4 + m] * g1 + Dq[7 + m] * g2 + Dq[10 + m] * g3;
     }
     __syncwarp();
-    const int64_t aoff = a.A_off ? a.A_off[e] : e * (int64_t)(NSH * NSH);
-    const int64_t boff = a.b_off ? a.b_off[e] : e * (int64_t)NSH;
-    T *A = reinterpret_cast<T *>(a.A) + aoff;
-    T *bv = reinterpret_cast<T *>(a.bv) + boff;
-    for (int idx = lane; idx < NSH * NSH; idx += 32) {
-      const int i = idx / NSH, j = idx - i * NSH;
+    // A_e = H^T G and b_e, lanes over (element, entry)
+    for (int idx = lane; idx < nel * NSH * NSH; idx += 32) {
+      const int sl = idx / (NSH * NSH), ij = idx - sl * (NSH * NSH);
+      const int i = ij / NSH, j = ij - i * NSH;
+      const int64_t e = a.list ? (int64_t)a.list[item0 + sl] : item0 + sl;
+      const int64_t aoff = a.A_off ? a.A_off[e] : e * (int64_t)(NSH * NSH);
+      const T *H = Hs(sl);
       T acc = T(0);
 #pragma unroll 4
       for (int k = 0; k < K4; ++k) acc += H[k * NSH + i] * Gs[k * NSH + j];
-      A[idx] = st ? T(0) : acc;
+      reinterpret_cast<T *>(a.A)[aoff + ij] = Ss(sl)[0] ? T(0) : acc;
     }
-    for (int i = lane; i < NSH; i += 32) {
+    for (int idx = lane; idx < nel * NSH; idx += 32) {
+      const int sl = idx / NSH, i = idx - sl * NSH;
+      const int64_t e = a.list ? (int64_t)a.list[item0 + sl] : item0 + sl;
+      const int64_t boff = a.b_off ? a.b_off[e] : e * (int64_t)NSH;
+      const T *D = Ds(sl);
       T acc = T(0);
-      for (int q = 0; q < NQ; ++q) acc += D[16 * q + 13] * Gs[(4 * q) * NSH + i];
-      bv[i] = st ? T(0) : acc;
+      for (int qq = 0; qq < NQ; ++qq) acc += D[16 * qq + 13] * Gs[(4 * qq) * NSH + i];
+      reinterpret_cast<T *>(a.bv)[boff + i] = Ss(sl)[0] ? T(0) : acc;
     }
-    if (lane == 0) a.status[e] = st;
+    for (int sl = lane; sl < nel; sl += 32) {
+      const int64_t e = a.list ? (int64_t)a.list[item0 + sl] : item0 + sl;
+      const int v = Ss(sl)[0];
+      // NONFINITE is recorded as 2 * NONFINITE so that it wins the max
+      a.status[e] = v == 2 * FEI_ERR_NONFINITE ? FEI_ERR_NONFINITE : v;
+    }
     __syncwarp();
   }
 }
@@ -409,7 +466,7 @@ fei_status launch_small(const FwdArgs &a, int64_t grid_work, cudaStream_t s, int
   using C = SmallCfg<T, P>;
   FEI_CUDA_TRY(cudaFuncSetAttribute(cc_small_kernel<T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM),
                "cudaFuncSetAttribute(cc_small)");
-  int64_t blocks = (grid_work + C::WPB - 1) / C::WPB;
+  int64_t blocks = (grid_work + C::WPB * C::EPW - 1) / (C::WPB * C::EPW);
   const int64_t cap = grid_cap > 0 ? grid_cap : (a.count ? 152 * 4 : 0);
   if (cap > 0 && blocks > cap) blocks = cap;
   if (blocks > 2147483647LL) blocks = 2147483647LL;
