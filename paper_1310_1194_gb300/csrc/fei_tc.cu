@@ -14,10 +14,11 @@
 // Precision (FEI_TC_F16X3).  Each operand x is split into two fp16 numbers
 // hi = rn(x), lo = rn(x - hi); hi*hi + hi*lo + lo*hi is x*y to about 2^-21
 // relative.  To keep fp16 in range, G is scaled by 2^tau (per degree) and
-// H'_e by 2^sigma_e (per element), chosen from the exact bound
-// max |H'| <= max_{q,b} sum_a |Dt[a][b]| max |G|, so every operand value is
-// at most 2^14; the accumulator holds A_e 2^(sigma_e + tau) and the
-// epilogue scales back exactly.  The tensor core adds into its FP32 accumulator with truncation,
+// H'_e by 2^sigma_e (per element), chosen from the bound
+// max |H'| <= max_{q,b} sum_a |Dt[a][b]| max |G| (itself bounded from the
+// norms of the Jacobian columns, tc_bound), so every operand value is at
+// most 2^14; the accumulator holds A_e 2^(sigma_e + tau) and the epilogue
+// scales back exactly.  The tensor core adds into its FP32 accumulator with truncation,
 // so a long chain of MMAs drifts by about half an ulp of the accumulator per
 // instruction; to keep the error independent of K, each K chunk (and N half)
 // accumulates into a fresh partial buffer in tensor memory, and the epilogue
@@ -26,21 +27,25 @@
 // operators are formed as in the FEI_FP32 path (element vectors, node
 // columns and w det J in FP64).
 //
-// One thread block per SM walks 128-row tiles; nothing synchronises the
-// whole block between tiles.  Roles (warp = 32 threads):
+// One thread block per SM walks a contiguous range of 128-row tiles;
+// nothing synchronises the whole block between tiles.  Roles (warp = 32
+// threads):
 //   warp 0       TMEM owner; lane 0 streams the pre-swizzled B operand (the
-//                split G image) into shared memory with cp.async.bulk;
+//                split G image) and, for p <= 4, the chunk's rows of the
+//                FP32 table into shared memory with cp.async.bulk;
 //   warp 1       lane 0 issues tcgen05.mma (M = 128, N = N_pad or 2 halves);
-//   next warps   point operators: per tile, the touched elements' geometry
-//                (FP64 node columns, w det J at every point), their scales
-//                and the row data; per K chunk, the point operators of its
-//                points into a ring that runs ahead of the producers;
-//   producers    per K chunk, H' for the 128 rows from the FP32 table (read
-//                through L2, 16 bytes per row and point), split into hi/lo,
-//                written in the swizzled K-major operand layout, and the
-//                partial load vectors;
+//   next warps   point operators: per tile, the geometry of the elements
+//                not seen before (FP64 node columns, w det J at every point),
+//                their scales and the row data; per K chunk, the point
+//                operators of its points into a ring that runs ahead of the
+//                producers;
+//   producers    per K chunk, H' for the 128 rows from the FP32 table (from
+//                the stage for p <= 4, else through L2; 16 bytes per row and
+//                point), split into hi/lo, written in the swizzled K-major
+//                operand layout, and the partial load vectors;
 //   last 4 warps epilogue: promotion of every partial accumulator, then
-//                scaling and coalesced stores of A_e, b_e and the statuses.
+//                scaling and stores of A_e (bulk copies of staged rows for
+//                a contiguous layout at p <= 4), b_e and the statuses.
 // All hand-offs are mbarriers; every wait is bounded by a time limit after
 // which the block raises an abort flag, marks its remaining elements with
 // FEI_ERR_TIMEOUT, drains its MMAs, frees its TMEM and exits.
