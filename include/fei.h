@@ -247,6 +247,16 @@ fei_status fei_plan_tune(fei_plan_t plan, const fei_batch *batch, void *A_out,
 fei_status fei_plan_choice(fei_plan_t plan, int p, int *variant, int64_t *grid_cap,
                            float *tuned_ms);
 
+/* Batch-level summary of the per-element statuses (device int32
+ * [n_elem], as written by fei_integrate): summary (device int32 [2])
+ * receives the worst status (FEI_ERR_NONFINITE over
+ * FEI_ERR_NEGATIVE_JACOBIAN over any other nonzero code over FEI_OK) and the
+ * number of flagged elements.  Asynchronous on the stream; read summary
+ * after the stream has reached this point.  elem_status or summary NULL ->
+ * INVALID_ARG (summary may be NULL only when n_elem is 0). */
+fei_status fei_status_summary(const int32_t *elem_status, int64_t n_elem, int32_t *summary,
+                              fei_stream_t stream);
+
 /* Largest batch fei_integrate_noalloc accepts. */
 #define FEI_NOALLOC_MAX_ELEM 262144
 

@@ -82,6 +82,7 @@ def _load():
     lib.fei_integrate_backward_quadratic.argtypes = [ref_p, ctypes.c_int, ctypes.POINTER(fei_batch), ctypes.c_int,
                                                      vp, vp, ctypes.POINTER(fei_coef_grad), vp]
     lib.fei_plan_offsets.argtypes = [vp, i64, vp, vp, vp, vp, vp]
+    lib.fei_status_summary.argtypes = [vp, i64, vp, vp]
     lib.fei_integrate_noalloc.argtypes = [ref_p, ctypes.c_int, ctypes.POINTER(fei_batch), ctypes.c_int,
                                           vp, vp, vp, vp]
     lib.fei_plan_create.argtypes = [ref_p, ctypes.c_int, i64, ctypes.c_int, ref_p]
@@ -96,7 +97,7 @@ def _load():
                  "fei_reference_copy_table", "fei_integrate", "fei_integrate_backward",
                  "fei_integrate_backward_quadratic",
                  "fei_plan_offsets", "fei_integrate_noalloc", "fei_plan_create", "fei_plan_destroy",
-                 "fei_plan_execute", "fei_plan_tune", "fei_plan_choice"):
+                 "fei_plan_execute", "fei_plan_tune", "fei_plan_choice", "fei_status_summary"):
         getattr(lib, name).restype = i32
     return lib
 

@@ -108,6 +108,16 @@ def fei_plan_offsets(degree: torch.Tensor) -> Layout:
     return Layout(Ao, bo, qo, int(tail[0]), int(tail[1]), int(tail[2]))
 
 
+def fei_status_summary(status: torch.Tensor):
+    """(worst status, number of flagged elements) of a status array, reduced
+    on the device (one small copy back)."""
+    status = _need(status, "status", torch.int32)
+    out = torch.zeros(2, dtype=torch.int32, device=status.device)
+    check(lib.fei_status_summary(_ptr(status), status.numel(), _ptr(out), _stream()), "fei_status_summary")
+    worst, count = out.cpu().tolist()
+    return int(worst), int(count)
+
+
 def uniform_layout(n: int, p: int) -> Layout:
     s = nsh(p)
     return Layout(None, None, None, n * s * s, n * s, n * nq(p))

@@ -212,6 +212,62 @@ using namespace fei;
 
 extern "C" const char *fei_last_error_string(void) { return g_err; }
 
+namespace fei {
+namespace {
+
+// Rank of a status for the summary: NONFINITE > NEGATIVE_JACOBIAN > other
+// nonzero codes > OK.
+__device__ __forceinline__ int status_rank(int st) {
+  return st == FEI_ERR_NONFINITE ? 3 : st == FEI_ERR_NEGATIVE_JACOBIAN ? 2 : st != 0 ? 1 : 0;
+}
+
+// summary[0] = worst status, summary[1] = count of nonzero statuses; one
+// block, so no second pass and no host work.
+__global__ void __launch_bounds__(1024) status_summary_kernel(const int32_t *st, int64_t n, int32_t *summary) {
+  __shared__ int s_rank, s_code, s_count;
+  if (threadIdx.x == 0) {
+    s_rank = 0;
+    s_code = 0;
+    s_count = 0;
+  }
+  __syncthreads();
+  int best_rank = 0, best_code = 0, count = 0;
+  for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
+    const int v = st[e];
+    const int r = status_rank(v);
+    if (r > best_rank || (r == best_rank && v > best_code)) {
+      best_rank = r;
+      best_code = v;
+    }
+    count += v != 0;
+  }
+  atomicAdd(&s_count, count);
+  atomicMax(&s_rank, best_rank);
+  __syncthreads();
+  if (best_rank == s_rank) atomicMax(&s_code, best_code);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    summary[0] = s_code;
+    summary[1] = s_count;
+  }
+}
+
+}  // namespace
+}  // namespace fei
+
+extern "C" fei_status fei_status_summary(const int32_t *elem_status, int64_t n_elem, int32_t *summary,
+                                         fei_stream_t stream) {
+  if (n_elem < 0) return set_error(FEI_ERR_INVALID_ARG, "fei_status_summary: n_elem < 0");
+  if (!summary) {
+    if (n_elem == 0) return FEI_OK;
+    return set_error(FEI_ERR_INVALID_ARG, "fei_status_summary: summary is NULL");
+  }
+  if (!elem_status && n_elem > 0) return set_error(FEI_ERR_INVALID_ARG, "fei_status_summary: elem_status is NULL");
+  status_summary_kernel<<<1, 1024, 0, (cudaStream_t)stream>>>(elem_status, n_elem, summary);
+  FEI_CUDA_TRY(cudaGetLastError(), "status_summary_kernel launch");
+  return FEI_OK;
+}
+
 extern "C" fei_status fei_plan_offsets(const int32_t *degree, int64_t n_elem, int64_t *A_offset,
                                        int64_t *b_offset, int64_t *q_offset, int32_t *bad_count,
                                        fei_stream_t stream) {

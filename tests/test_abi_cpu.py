@@ -65,6 +65,10 @@ def test_argument_errors_before_any_cuda_call(lib):
     assert lib.fei_plan_destroy(None) == 0
     lib.fei_integrate_backward_quadratic.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int, vp, vp, vp, vp]
     assert lib.fei_integrate_backward_quadratic(None, 1, None, 0, None, None, None, None) == 1
+    lib.fei_status_summary.argtypes = [vp, ctypes.c_int64, vp, vp]
+    assert lib.fei_status_summary(None, 5, None, None) == 1
+    assert lib.fei_status_summary(None, 0, None, None) == 0
+    assert lib.fei_status_summary(None, -1, None, None) == 1
 
 
 def test_python_binding_loads():

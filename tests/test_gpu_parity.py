@@ -261,3 +261,14 @@ def test_quadratic_adjoint_mixed_degrees(api):
     for name, got, want in zip(("geom", "K", "b", "c", "f"), out, ref):
         got = got.cpu().numpy().reshape(want.shape)
         assert np.linalg.norm(got - want) / np.linalg.norm(want) < 1e-10, name
+
+
+def test_status_summary(api):
+    st = torch.tensor([0, 3, 0, 4, 3, 0, 7, 0], dtype=torch.int32, device="cuda")
+    assert api.fei_status_summary(st) == (4, 4)
+    st = torch.tensor([0, 3, 0, 0], dtype=torch.int32, device="cuda")
+    assert api.fei_status_summary(st) == (3, 1)
+    st = torch.zeros(100000, dtype=torch.int32, device="cuda")
+    assert api.fei_status_summary(st) == (0, 0)
+    st[77777] = 6
+    assert api.fei_status_summary(st) == (6, 1)
