@@ -11,7 +11,8 @@ Each function names the passage of the paper it follows:
 * ``gauss_legendre``   -- Gaussian quadrature (Sec. 2, the accuracy rule
   "products of shape functions integrated exactly"); Newton on P_n.
 * ``quadrature``       -- Duffy-collapsed Gauss-Legendre, (p+1)^3 points on the
-  reference prism (Sec. 2; the point count is this build's reading).
+  reference prism (Sec. 2; the paper names no rule, so the point count is a
+  reading: exact for products of shape functions on affine prisms).
 * ``basis``            -- prism shape functions: complete triangle basis times
   1D functions along the vertical direction (Table 1 and its text).
 * ``integrate``        -- Eq. (2) generalised to
