@@ -228,8 +228,8 @@ struct TcCfg {
   static constexpr int W_DW = 2, W_PW = W_DW + NDW, W_EW = W_PW + NPW;
   static constexpr int NTHREADS = (2 + NDW + NPW + NEW) * 32;
   static constexpr int QPG = PPC / (NPW / 4);  // points per producer thread per chunk
-  static constexpr int DRING = P <= 4 ? 8 : 4;  // chunks of point operators ahead
-  static constexpr int DB = 2;                  // chunks of point operators per round
+  static constexpr int DRING = 8;  // chunks of point operators ahead
+  static constexpr int DB = 4;     // chunks of point operators per round
   static constexpr int A_BYTES = 128 * ROWB;
   static constexpr int B_BYTES = NPAD * ROWB;
   // GS: the chunk's rows of the FP32 table (PPC points x N_sh x 16 bytes)
