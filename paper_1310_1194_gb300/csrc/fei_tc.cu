@@ -809,7 +809,8 @@ __global__ void __launch_bounds__(TcCfg<P, V>::NTHREADS, 1) tc_forward_kernel(Fw
         for (int pc = 0; pc < C::QPG / 2; ++pc) {
           const int chunk = grp * (C::QPG / 2) + pc;
           uint32_t hw[4], lw[4];
-          if (rvalid) {
+          // the last chunk may end past the final point (uniform per warp)
+          if (rvalid && c * PPC + chunk * 2 < NQ) {
 #pragma unroll
             for (int h2 = 0; h2 < 2; ++h2) {  // two points per 16-byte chunk
               const int qq = chunk * 2 + h2;  // point within the chunk
