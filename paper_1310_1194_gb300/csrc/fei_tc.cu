@@ -315,21 +315,26 @@ struct TcAux {
   alignas(16) float rows16[C::BS ? C::NEW : 1][C::BS ? 16 * C::NSH : 4];
 };
 
-__device__ __forceinline__ bool load_coef_tc(const FwdArgs &a, int64_t r, double *cd) {
-  bool ok = true;
+// finite test by the exponent bits (integer pipe; FP64 compares are slow here)
+__device__ __forceinline__ bool finite_d(double x) {
+  return ((__double_as_longlong(x) >> 52) & 0x7ff) != 0x7ff;
+}
+// Per-point coefficient record r (K 9, b 3, c, f) rounded to FP32; returns
+// whether all 14 values are finite (tested on the FP64 bits).
+__device__ __forceinline__ bool load_coef_tc(const FwdArgs &a, int64_t r, float *cf) {
+  double cd[14];
 #pragma unroll
-  for (int k = 0; k < 9; ++k) {
-    cd[k] = a.K[9 * r + k];
-    ok &= isfinite(cd[k]);
-  }
+  for (int k = 0; k < 9; ++k) cd[k] = a.K[9 * r + k];
 #pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    cd[9 + k] = a.b[3 * r + k];
-    ok &= isfinite(cd[9 + k]);
-  }
+  for (int k = 0; k < 3; ++k) cd[9 + k] = a.b[3 * r + k];
   cd[12] = a.c[r];
   cd[13] = a.f[r];
-  ok &= isfinite(cd[12]) && isfinite(cd[13]);
+  bool ok = true;
+#pragma unroll
+  for (int k = 0; k < 14; ++k) {
+    ok &= finite_d(cd[k]);
+    cf[k] = (float)cd[k];
+  }
   return ok;
 }
 
@@ -370,10 +375,6 @@ __device__ __forceinline__ float tc_bound(const TcElem<P> &E, const AX &ax, cons
   const float kn = sqrtf(r1 * ri), bn = norm3f(cf + 9);
   return fmaxf(sf * fabsf(cf[12]), w * amax * (bn + (w / sf) * kn * asum));
 }
-// finite test by the exponent bits (integer pipe; FP64 compares are slow here)
-__device__ __forceinline__ bool finite_bits(double x) {
-  return ((__double_as_longlong(x) >> 52) & 0x7ff) != 0x7ff;
-}
 // One component (j = vector * 3 + axis) of the element vectors, FP64:
 // A1, B1, A2, B2, C, D1, D2 from the bottom (P) and top (Q) vertices.
 __device__ __forceinline__ double elem_vector_component(const double *X, int j) {
@@ -388,10 +389,6 @@ __device__ __forceinline__ double elem_vector_component(const double *X, int j) 
     case 5: return 0.5 * ((q1 - p1) - (q0 - p0));
     default: return 0.5 * ((q2 - p2) - (q0 - p0));
   }
-}
-__device__ __forceinline__ void coef_to_float(const double *cd, float *cf) {
-#pragma unroll
-  for (int k = 0; k < 14; ++k) cf[k] = (float)cd[k];
 }
 
 // Shared-memory matrix descriptor of a K-major operand with ROWB-byte rows
@@ -522,12 +519,12 @@ __global__ void __launch_bounds__(TcCfg<P, V>::NTHREADS, 1) tc_forward_kernel(Fw
         if (lane < 18) {
           const double x = a.geom[18 * e + lane];
           E.X[lane] = x;
-          ok = finite_bits(x);
+          ok = finite_d(x);
         } else if (a.coef_mode == FEI_COEF_PER_ELEMENT) {
           const int k = lane - 18;
           const double x = k < 9 ? a.K[9 * e + k] : k < 12 ? a.b[3 * e + (k - 9)] : k == 12 ? a.c[e] : a.f[e];
           E.cf[k] = (float)x;
-          ok = finite_bits(x);
+          ok = finite_d(x);
         }
         if (lane == 0) {
           E.e = e;
@@ -631,13 +628,11 @@ __global__ void __launch_bounds__(TcCfg<P, V>::NTHREADS, 1) tc_forward_kernel(Fw
           const int iz = q / NT, t = q - iz * NT;
           const double s = ax.ttab[t][0] * E.zabg[iz][0] + ax.ttab[t][1] * E.zabg[iz][1] + ax.ttab[t][2] * E.zabg[iz][2];
           const float sf = (float)s;
-          int st = !finite_bits(s) ? FEI_ERR_NONFINITE : (!(sf > 0.f) ? FEI_ERR_NEGATIVE_JACOBIAN : 0);
+          int st = !finite_d(s) ? FEI_ERR_NONFINITE : (!(sf > 0.f) ? FEI_ERR_NEGATIVE_JACOBIAN : 0);
           float cq[14];
           const float *cp = E.cf;
           if (a.coef_mode == FEI_COEF_PER_POINT) {
-            double cdq[14];
-            if (!load_coef_tc(a, E.qoff + q, cdq)) st = FEI_ERR_NONFINITE;
-            coef_to_float(cdq, cq);
+            if (!load_coef_tc(a, E.qoff + q, cq)) st = FEI_ERR_NONFINITE;
             cp = cq;
           }
           ax.sp[sl][q] = sf;
@@ -725,9 +720,7 @@ __global__ void __launch_bounds__(TcCfg<P, V>::NTHREADS, 1) tc_forward_kernel(Fw
               float cq[14];
               const float *cp = E.cf;
               if (a.coef_mode == FEI_COEF_PER_POINT) {
-                double cdq[14];
-                load_coef_tc(a, E.qoff + q, cdq);
-                coef_to_float(cdq, cq);
+                (void)load_coef_tc(a, E.qoff + q, cq);  // finiteness was tested in the pre-pass
                 cp = cq;
               }
               float Dt[16];
