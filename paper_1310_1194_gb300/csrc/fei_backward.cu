@@ -66,16 +66,16 @@ __device__ __forceinline__ bool load_coef_b(const BwdArgs &a, int64_t r, double 
 #pragma unroll
   for (int k = 0; k < 9; ++k) {
     cd[k] = a.K[9 * r + k];
-    ok &= isfinite(cd[k]);
+    ok &= finite64(cd[k]);
   }
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     cd[9 + k] = a.b[3 * r + k];
-    ok &= isfinite(cd[9 + k]);
+    ok &= finite64(cd[9 + k]);
   }
   cd[12] = a.c[r];
   cd[13] = a.f[r];
-  ok &= isfinite(cd[12]) && isfinite(cd[13]);
+  ok &= finite64(cd[12]) && finite64(cd[13]);
   return ok;
 }
 
@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(256, 2) cc_backward_kernel(BwdArgs a) {
     bool ok = true;
     if (tid < 18) {
       sm.X[tid] = a.geom[18 * e + tid];
-      ok = isfinite(sm.X[tid]);
+      ok = finite64(sm.X[tid]);
     }
     if (a.coef_mode == FEI_COEF_PER_ELEMENT && tid == 32) ok = load_coef_b(a, e, sm.cd);
     if (!ok) sm.status = FEI_ERR_NONFINITE;

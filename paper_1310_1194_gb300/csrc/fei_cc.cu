@@ -44,16 +44,16 @@ __device__ __forceinline__ bool load_coef(const FwdArgs &a, int64_t r, double *c
 #pragma unroll
   for (int k = 0; k < 9; ++k) {
     cd[k] = a.K[9 * r + k];
-    ok &= isfinite(cd[k]);
+    ok &= finite64(cd[k]);
   }
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     cd[9 + k] = a.b[3 * r + k];
-    ok &= isfinite(cd[9 + k]);
+    ok &= finite64(cd[9 + k]);
   }
   cd[12] = a.c[r];
   cd[13] = a.f[r];
-  ok &= isfinite(cd[12]) && isfinite(cd[13]);
+  ok &= finite64(cd[12]) && finite64(cd[13]);
   return ok;
 }
 
@@ -99,11 +99,6 @@ __device__ __forceinline__ int point_direct(const double *ev, const double *pt, 
 // points, p = 2: one of 27), so that every lane takes a point in the FP64
 // Jacobian work; lanes then run over the entries of the A_e.
 // ---------------------------------------------------------------------------
-
-// finite test by the exponent bits (integer pipe; FP64 compares are slow here)
-__device__ __forceinline__ bool finite_d(double x) {
-  return ((__double_as_longlong(x) >> 52) & 0x7ff) != 0x7ff;
-}
 
 // One component (j = vector * 3 + axis) of the element vectors A1, B1, A2,
 // B2, C, D1, D2 from the bottom (P) and top (Q) vertices, FP64.
@@ -165,12 +160,12 @@ __global__ void __launch_bounds__(SmallCfg<T, P>::WPB * 32) cc_small_kernel(FwdA
       if (k < 18) {
         const double x = a.geom[18 * e + k];
         Xs(sl)[k] = x;
-        ok = finite_d(x);
+        ok = finite64(x);
       } else if (a.coef_mode == FEI_COEF_PER_ELEMENT) {
         const int c = k - 18;
         const double x = c < 9 ? a.K[9 * e + c] : c < 12 ? a.b[3 * e + (c - 9)] : c == 12 ? a.c[e] : a.f[e];
         cds(sl)[c] = x;
-        ok = finite_d(x);
+        ok = finite64(x);
       }
       // lanes of one element are one aligned group of 32: the whole warp
       const unsigned bad = __ballot_sync(0xffffffffu, !ok);
@@ -306,7 +301,7 @@ __global__ void __launch_bounds__(256) cc_tile_kernel(FwdArgs a) {
     bool ok = true;
     if (tid < 18) {
       sm.X[tid] = a.geom[18 * e + tid];
-      ok = isfinite(sm.X[tid]);
+      ok = finite64(sm.X[tid]);
     }
     if (a.coef_mode == FEI_COEF_PER_ELEMENT && tid == 32) ok = load_coef(a, e, sm.cd);
     if (!ok) sm.status = FEI_ERR_NONFINITE;

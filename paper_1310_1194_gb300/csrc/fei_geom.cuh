@@ -100,9 +100,15 @@ __device__ __forceinline__ void dt_from_adj(const T *a0, const T *a1, const T *a
   D[15] = T(0);
 }
 
+// Finite test on the exponent bits of an FP64 value (integer pipe: FP64
+// compares run at the FP64 rate, which is low on this part).
+__device__ __forceinline__ bool finite64(double x) {
+  return ((__double_as_longlong(x) >> 52) & 0x7ff) != 0x7ff;
+}
+
 // Status of one point from s = w det J: 0 ok, 3 det <= 0, 4 non-finite.
 __device__ __forceinline__ int point_status(double s) {
-  if (!isfinite(s)) return FEI_ERR_NONFINITE;
+  if (!finite64(s)) return FEI_ERR_NONFINITE;
   if (!(s > 0.0)) return FEI_ERR_NEGATIVE_JACOBIAN;
   return 0;
 }

@@ -315,10 +315,6 @@ struct TcAux {
   alignas(16) float rows16[C::BS ? C::NEW : 1][C::BS ? 16 * C::NSH : 4];
 };
 
-// finite test by the exponent bits (integer pipe; FP64 compares are slow here)
-__device__ __forceinline__ bool finite_d(double x) {
-  return ((__double_as_longlong(x) >> 52) & 0x7ff) != 0x7ff;
-}
 // Per-point coefficient record r (K 9, b 3, c, f) rounded to FP32; returns
 // whether all 14 values are finite (tested on the FP64 bits).
 __device__ __forceinline__ bool load_coef_tc(const FwdArgs &a, int64_t r, float *cf) {
@@ -332,7 +328,7 @@ __device__ __forceinline__ bool load_coef_tc(const FwdArgs &a, int64_t r, float 
   bool ok = true;
 #pragma unroll
   for (int k = 0; k < 14; ++k) {
-    ok &= finite_d(cd[k]);
+    ok &= finite64(cd[k]);
     cf[k] = (float)cd[k];
   }
   return ok;
@@ -519,12 +515,12 @@ __global__ void __launch_bounds__(TcCfg<P, V>::NTHREADS, 1) tc_forward_kernel(Fw
         if (lane < 18) {
           const double x = a.geom[18 * e + lane];
           E.X[lane] = x;
-          ok = finite_d(x);
+          ok = finite64(x);
         } else if (a.coef_mode == FEI_COEF_PER_ELEMENT) {
           const int k = lane - 18;
           const double x = k < 9 ? a.K[9 * e + k] : k < 12 ? a.b[3 * e + (k - 9)] : k == 12 ? a.c[e] : a.f[e];
           E.cf[k] = (float)x;
-          ok = finite_d(x);
+          ok = finite64(x);
         }
         if (lane == 0) {
           E.e = e;
@@ -628,7 +624,7 @@ __global__ void __launch_bounds__(TcCfg<P, V>::NTHREADS, 1) tc_forward_kernel(Fw
           const int iz = q / NT, t = q - iz * NT;
           const double s = ax.ttab[t][0] * E.zabg[iz][0] + ax.ttab[t][1] * E.zabg[iz][1] + ax.ttab[t][2] * E.zabg[iz][2];
           const float sf = (float)s;
-          int st = !finite_d(s) ? FEI_ERR_NONFINITE : (!(sf > 0.f) ? FEI_ERR_NEGATIVE_JACOBIAN : 0);
+          int st = !finite64(s) ? FEI_ERR_NONFINITE : (!(sf > 0.f) ? FEI_ERR_NEGATIVE_JACOBIAN : 0);
           float cq[14];
           const float *cp = E.cf;
           if (a.coef_mode == FEI_COEF_PER_POINT) {
