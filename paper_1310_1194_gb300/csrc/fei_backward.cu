@@ -47,7 +47,10 @@ struct BwdCfg {
   static constexpr size_t OFF_GD = OFF_W + (Q ? 0 : sizeof(T) * BI * KC);    // T [NQ][16]
   static constexpr size_t OFF_GSF = OFF_GD + sizeof(T) * NQ * 16;            // T [NQ]
   static constexpr size_t OFF_END = ((OFF_GSF + sizeof(T) * NQ + 15) / 16) * 16;
-  static constexpr size_t SMEM = OFF_END;
+  // the sums over points reuse the dynamic area: per warp 35 values x 32
+  // lanes (rows padded to 33) in FP64
+  static constexpr size_t RED_BYTES = sizeof(double) * 8 * 35 * 33;
+  static constexpr size_t SMEM = OFF_END > RED_BYTES ? OFF_END : RED_BYTES;
 };
 
 struct BwdStatic {
@@ -391,18 +394,24 @@ __global__ void __launch_bounds__(256, 2) cc_backward_kernel(BwdArgs a) {
       }
     }
     if (pst) atomicMax(&sm.status, pst);
+    // sums over the points: every lane stores its 35 partial sums, then lane
+    // k of the warp adds up value k over the 32 lanes (a 32-term FP64 sum per
+    // value, instead of a 5-level shuffle tree for each of the 35 values)
+    __syncthreads();  // every point's dL/dDt has been read: the area is free
+    {
+      const int lane = tid & 31;
+      double *red = reinterpret_cast<double *>(dsm) + (tid >> 5) * (35 * 33);
 #pragma unroll
-    for (int k = 0; k < 21; ++k) {
-      double v = gev[k];
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if ((tid & 31) == 0) atomicAdd(&sm.gev[k], v);
-    }
-    if (a.coef_mode == FEI_COEF_PER_ELEMENT) {
+      for (int k = 0; k < 21; ++k) red[k * 33 + lane] = gev[k];
 #pragma unroll
-      for (int k = 0; k < 14; ++k) {
-        double v = gco[k];
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if ((tid & 31) == 0) atomicAdd(&sm.gcoef[k], v);
+      for (int k = 0; k < 14; ++k) red[(21 + k) * 33 + lane] = gco[k];
+      __syncwarp();
+      for (int k = lane; k < 35; k += 32) {
+        if (k >= 21 && a.coef_mode != FEI_COEF_PER_ELEMENT) continue;
+        double v = 0.0;
+#pragma unroll 8
+        for (int l = 0; l < 32; ++l) v += red[k * 33 + l];
+        atomicAdd(k < 21 ? &sm.gev[k] : &sm.gcoef[k - 21], v);
       }
     }
     __syncthreads();
