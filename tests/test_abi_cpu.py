@@ -75,3 +75,19 @@ def test_python_binding_loads():
     from paper_1310_1194_gb300 import _lib
     assert _lib.lib is not None
     assert _lib.PRECISIONS["fp64"] == 0
+
+
+def test_binding_fails_loudly_without_the_library(tmp_path, monkeypatch):
+    """No CPU fallback: with libfei.so absent, importing the binding raises."""
+    import importlib.util
+    import os as _os
+    import sys as _sys
+    src = _os.path.join(ROOT, "paper_1310_1194_gb300", "_lib.py")
+    text = open(src).read().replace('LIB_PATH = os.path.join(HERE, "_build", "libfei.so")',
+                                    f'LIB_PATH = {str(tmp_path / "missing" / "libfei.so")!r}')
+    path = tmp_path / "lib_missing.py"
+    path.write_text(text)
+    spec = importlib.util.spec_from_file_location("lib_missing", str(path))
+    mod = importlib.util.module_from_spec(spec)
+    with pytest.raises(ImportError):
+        spec.loader.exec_module(mod)
