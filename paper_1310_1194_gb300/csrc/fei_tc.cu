@@ -773,10 +773,12 @@ __global__ void __launch_bounds__(TcCfg<P, V>::NTHREADS, 1) tc_forward_kernel(Fw
             gq[j] = (rvalid && q < NQ) ? __ldg(G4 + (size_t)q * NSH + ri) : make_float4(0.f, 0.f, 0.f, 0.f);
           }
         }
-        // A slot free, point operators ready (and the table chunk landed)
-        bool ok = mbar_wait(smem_u32(&ax.empty[s]), (u & 1u) ^ 1u, abort_flag);
-        ok = ok && mbar_wait(smem_u32(&ax.dfull[dr]), ud & 1u, abort_flag);
+        // A slot free, point operators ready (and the table chunk landed:
+        // the copy engine fills a stage only after its MMAs completed, so
+        // with the table in the stage that wait also frees the A slot)
+        bool ok = mbar_wait(smem_u32(&ax.dfull[dr]), ud & 1u, abort_flag);
         if constexpr (C::GS) ok = ok && mbar_wait(smem_u32(&ax.bfull[s]), u & 1u, abort_flag);
+        else ok = ok && mbar_wait(smem_u32(&ax.empty[s]), (u & 1u) ^ 1u, abort_flag);
         ok = __all_sync(0xffffffffu, ok);
         if (!ok) break;
         if constexpr (C::GS) {
@@ -832,12 +834,14 @@ __global__ void __launch_bounds__(TcCfg<P, V>::NTHREADS, 1) tc_forward_kernel(Fw
           *reinterpret_cast<uint4 *>(ahp + aoff) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
           *reinterpret_cast<uint4 *>(alp + aoff) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
         }
-        // the point operators of this chunk are consumed
-        __syncwarp();
-        if (lane == 0) mbar_arrive(smem_u32(&ax.dempty[dr]));
+        // the point operators of this chunk are consumed and the A slot is
+        // written (made visible to the tensor core's proxy)
         fence_proxy_async();
         __syncwarp();
-        if (lane == 0) mbar_arrive(smem_u32(&ax.full[s]));
+        if (lane == 0) {
+          mbar_arrive(smem_u32(&ax.dempty[dr]));
+          mbar_arrive(smem_u32(&ax.full[s]));
+        }
       }
       if (*abort_flag) break;
       // load-vector partials of this tile for the epilogue (the slot is free
