@@ -439,10 +439,17 @@ def main():
     precision_all = precision
     precision = dom["precision"]
     if low_p:
-        # p <= 2: a few kflops per element against 0.4-0.6 KB of traffic; the
-        # path streams geometry in and element matrices out
-        bound, peak, unit, achieved = "hbm", peaks["hbm_gbs"], "GB/s", Bts / (ms * 1e-3) / 1e9
-        peak_note = f"HBM copy bandwidth ({peak_src})"
+        # p <= 2: a few kflops per element against 0.4-0.6 KB of traffic, but
+        # the Jacobian work is FP64 (about 45 FP64 flops per point and 84 per
+        # element for the element vectors on the FP32 paths; everything on the
+        # FP64 path), and at GB300's FP64 rate that, not HBM, binds
+        f64 = (F if precision == "fp64" else
+               sum(int(counts[d]) * (45 * nq(d) + 84) for d in range(1, 3)))
+        peak = 152 * 2 * 2 * sm_max * 1e6 / 1e12
+        bound, unit, achieved = "alu", "TFLOP/s", f64 / (ms * 1e-3) / 1e12
+        peak_note = "FP64 FMA: 152 SMs x 2 DFMA/clk x 2 flops x max SM clock (FP64 Jacobian work)"
+        hw = {"hbm_gbs": Bts / (ms * 1e-3) / 1e9, "hbm_frac": Bts / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
+              "hbm_peak_gbs": peaks["hbm_gbs"]}
     elif precision == "tc_f16x3":
         # every algorithmic multiply-add is three fp16 tensor products (hi*hi,
         # hi*lo, lo*hi), so the peak for algorithmic flops is a third of the
