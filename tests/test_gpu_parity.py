@@ -272,3 +272,53 @@ def test_status_summary(api):
     assert api.fei_status_summary(st) == (0, 0)
     st[77777] = 6
     assert api.fei_status_summary(st) == (6, 1)
+
+
+@pytest.mark.parametrize("p", [3, 4, 5])
+def test_tc_output_not_16_byte_aligned(api, p):
+    """A_out starting 4 bytes past an aligned address (and b_out likewise):
+    the tensor-core path must fall back from its bulk stores and still match
+    the oracle element by element."""
+    w = inputs.workload("p4", n_max=41)
+    n = len(w["geom"])
+    s = api.nsh(p)
+    Abuf = torch.zeros(n * s * s + 1, dtype=torch.float32, device="cuda")
+    bbuf = torch.zeros(n * s + 1, dtype=torch.float32, device="cuda")
+    st = torch.empty(n, dtype=torch.int32, device="cuda")
+    A, bv = Abuf[1:], bbuf[1:]
+    api.fei_integrate(dev(w["geom"]), dev(w["K"]), dev(w["b"]), dev(w["c"]), dev(w["f"]), p=p,
+                      precision="tc_f16x3", out=(A, bv, st))
+    torch.cuda.synchronize()
+    assert float(Abuf[0]) == 0.0 and float(bbuf[0]) == 0.0
+    Ao, bo, so, _ = oracle.integrate(w["geom"], w["K"], w["b"], w["c"], w["f"], p=p)
+    Ah = A.double().cpu().numpy().reshape(n, -1)
+    Aor = Ao.reshape(n, -1)
+    for e in range(n):
+        assert np.linalg.norm(Ah[e] - Aor[e]) <= 1e-6 * np.linalg.norm(Aor[e]), e
+
+
+def test_plan_per_point_coefficients_mixed(api):
+    """A plan over a mixed batch with per-point coefficient records."""
+    w = inputs.workload("mixed", n_max=90)
+    deg = dev(w["degree"], torch.int32)
+    layout = api.fei_plan_offsets(deg)
+    q = (w["degree"].astype(np.int64) + 1) ** 3
+    rng = np.random.default_rng(3)
+    m = int(q.sum())
+    K = np.broadcast_to(np.eye(3), (m, 3, 3)).copy() * rng.uniform(0.5, 2.0, size=(m, 1, 1))
+    b = rng.uniform(-1, 1, size=(m, 3))
+    c = rng.uniform(0, 1, size=m)
+    f = rng.uniform(-1, 1, size=m)
+    plan = api.Plan(max_elem=len(w["geom"]), precision="tc_f16x3")
+    s_ = torch.cuda.Stream()
+    with torch.cuda.stream(s_):
+        A, bv, st, _ = plan.execute(dev(w["geom"]), dev(K), dev(b), dev(c), dev(f), degree=deg, per_qp=True,
+                                    layout=layout)
+    s_.synchronize()
+    Ao, bo, so, _ = oracle.integrate(w["geom"], K, b, c, f, degree=w["degree"], per_qp=True)
+    assert int(st.abs().max()) == 0 and int(np.abs(so).max()) == 0
+    Ah = A.double().cpu().numpy()
+    Aoff = layout.A_offset.cpu().numpy()
+    for e in range(len(w["geom"])):
+        sl = slice(int(Aoff[e]), int(Aoff[e + 1]))
+        assert np.linalg.norm(Ah[sl] - Ao[sl]) <= 1e-6 * np.linalg.norm(Ao[sl]), (e, int(w["degree"][e]))
