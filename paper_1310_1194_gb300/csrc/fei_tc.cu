@@ -40,9 +40,12 @@
 //                operators of its points into a ring that runs ahead of the
 //                producers;
 //   producers    per K chunk, H' for the 128 rows from the FP32 table (from
-//                the stage for p <= 4, else through L2; 16 bytes per row and
-//                point), split into hi/lo, written in the swizzled K-major
-//                operand layout, and the partial load vectors;
+//                the stage for p <= 4, else through L2), a thread working on
+//                a pair of consecutive points of a few rows with packed FP32
+//                FMAs (the pair's point operators held in registers); split
+//                into hi/lo (the residual by one mixed-precision FMA per
+//                value), written in the swizzled K-major operand layout,
+//                and the partial load vectors;
 //   last 4 warps epilogue: promotion of every partial accumulator, then
 //                scaling and stores of A_e (bulk copies of staged rows for
 //                a contiguous layout at p <= 4), b_e and the statuses.
@@ -60,6 +63,11 @@ namespace fei {
 
 struct TcImage {
   __half *img;  // [NCHUNK][2][NPAD][ROWB/2], each [NPAD][ROWB/2] block swizzled
+  // the FP32 table by chunk and point pair: [NCHUNK][2][PP][GST] float4,
+  // half h of pair (q, q+1) and shape i = (G_2h(q), G_2h(q+1), G_2h+1(q),
+  // G_2h+1(q+1)), G_b = phi, dphi/dxi1, dphi/dxi2, dphi/dzeta; zero past
+  // N_q and N_sh (GST >= N_sh is the row stride)
+  float *gp;
   int npad, nchunk, rowb, tau;
 };
 
@@ -222,22 +230,33 @@ struct TcCfg {
   static constexpr int RREG = NPAD - RT;
   static constexpr int EMAX = (128 + NSH - 1) / NSH + 1;  // elements a tile can touch
   static constexpr int NSLOT = EMAX + 1;  // element slots: a tile's elements plus the one it shares
-  static constexpr int NDW = P == 7 ? 2 : P == 6 ? 4 : 6;  // point-operator warps
+  static constexpr int NDW = P == 7 ? 2 : P == 6 ? 4 : P == 5 ? 2 : 6;  // point-operator warps
   static constexpr int NPW = V == 1 ? 16 : 8;  // producer warps
   static constexpr int NEW = 4;  // epilogue warps
   static constexpr int W_DW = 2, W_PW = W_DW + NDW, W_EW = W_PW + NPW;
   static constexpr int NTHREADS = (2 + NDW + NPW + NEW) * 32;
-  static constexpr int QPG = PPC / (NPW / 4);  // points per producer thread per chunk
-  static constexpr int DRING = 8;  // chunks of point operators ahead
-  static constexpr int DB = 4;     // chunks of point operators per round
-  static constexpr int A_BYTES = 128 * ROWB;
-  static constexpr int B_BYTES = NPAD * ROWB;
-  // GS: the chunk's rows of the FP32 table (PPC points x N_sh x 16 bytes)
+  // GS: the chunk's rows of the FP32 table (PPC points x GST x 16 bytes)
   // travel with the B operand into the stage (copy engine), so the
   // producers read them from shared memory instead of L2 (p <= 4, where
   // they fit beside two stages)
   static constexpr bool GS = P <= 4;
-  static constexpr int G_BYTES = GS ? PPC * NSH * 16 : 0;
+  // producer layout, PP = pairs of consecutive points per chunk (a pair is
+  // one 16-byte chunk of an operand row).  With the table chunk in shared
+  // memory (GS): lane = pp + PP rg, a warp covers RW consecutive rows in RG
+  // row groups.  Otherwise a warp works on one pair (WPP warps per pair) for
+  // RWP consecutive rows, lanes over consecutive rows, so that the table
+  // reads from L2 are contiguous.  RPT = rows per thread.
+  static constexpr int PP = PPC / 2, RG = 32 / PP, RW = 128 / NPW;
+  static constexpr int WPP = NPW / PP, RWP = 128 / WPP;
+  static constexpr int RPT = GS ? RW / RG : RWP / 32;
+  // row stride of the paired table: odd with GS, so that the 8 pairs of a
+  // row group fall into different 16-byte bank groups of shared memory
+  static constexpr int GST = GS ? (NSH | 1) : NSH;
+  static constexpr int DRING = 8;  // chunks of point operators ahead
+  static constexpr int DB = 4;     // chunks of point operators per round
+  static constexpr int A_BYTES = 128 * ROWB;
+  static constexpr int B_BYTES = NPAD * ROWB;
+  static constexpr int G_BYTES = GS ? PPC * GST * 16 : 0;
   static constexpr int G_AREA = (G_BYTES + 1023) / 1024 * 1024;
   static constexpr bool BS = P <= 4;  // bulk stores of staged rows (shared-memory budget)
   static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES + G_AREA;
@@ -246,7 +265,8 @@ struct TcCfg {
   static_assert(NMMA % 16 == 0 && NMMA <= 256, "MMA N");
   static_assert(RT % 16 == 0 && RREG % 16 == 0 && RT >= 0, "running-sum split");
   static_assert(2 * NMMA + RT <= TMEM_COLS, "tensor memory");
-  static_assert(QPG % 2 == 0, "two points per 16-byte chunk");
+  static_assert(PPC % 2 == 0 && (GS ? 32 % PP == 0 && RW % RG == 0 : NPW % PP == 0 && RWP % 32 == 0) && RPT >= 1,
+                "producer layout");
   static_assert(STAGES > UC, "a promotion unit must leave a stage for the producers");
   static_assert(DRING >= 2 * DB, "the operator ring holds two rounds");
   static_assert(NEW == 4, "four consecutive epilogue warps cover the four TMEM lane quarters");
@@ -303,12 +323,14 @@ struct TcAux {
   double ttab[C::NT][3];     // (w_t, w_t xi1, w_t xi2) per triangle node
   float ttabf[C::NT][3];     // (w_t, xi1, xi2) in FP32
   float ztabf[C::NZ][2];     // (zeta, w_z) in FP32
-  // point operators of a chunk: [tile-relative element][16-byte group][point],
-  // so that consecutive points are consecutive 16-byte words (conflict-free
-  // stores by the point-operator warps, broadcast loads by the producers)
-  float4 Dc[C::DRING][C::EMAX][4][C::PPC];
+  // point operators of a chunk, [tile-relative element][k'][point pair]:
+  // float4 k' of pair (q, q+1) is (c_2k'(q), c_2k'(q+1), c_2k'+1(q),
+  // c_2k'+1(q+1)) for the 14 values c_0..c_13 of a point (Dt by rows, then
+  // w det J f), i.e. the pairs the producers feed to packed FP32 FMAs;
+  // consecutive pairs are consecutive 16-byte words (broadcast loads)
+  float4 Dc[C::DRING][C::EMAX][7][C::PP];
   TcMeta meta[2];
-  float bsum[2][C::NPW * 32 / 128][128];
+  float bsum[2][C::PP][128];
   alignas(16) float stg[C::NEW][32][17];  // epilogue transpose staging
   // BS: for a contiguous output layout (p <= 4), each epilogue warp stages
   // 16 of its rows of A_e here and stores them with one bulk copy
@@ -407,13 +429,28 @@ __host__ __device__ __forceinline__ uint32_t sw_off(int r, int c) {
   const int x = ROWB == 128 ? (r & 7) : ((r >> 1) & 3);
   return (uint32_t)(r * ROWB + ((c ^ x) << 4));
 }
+// x - hi for the two values of a split: hi holds rn_f16(x0) (low half) and
+// rn_f16(x1) (high half).  One mixed-precision FMA per value, hi * (-1) + x
+// with the fp16 operand widened exactly; the difference is exact in FP32
+// (hi is x rounded to 11 significant bits).
+__device__ __forceinline__ float2 split_residual(__half2 hi, float x0, float x1) {
+  uint32_t h;
+  memcpy(&h, &hi, 4);
+  float r0, r1;
+  asm("{\n .reg .f16 a, b, m;\n mov.b32 {a, b}, %2;\n mov.b16 m, 0xBC00;\n"
+      " fma.rn.f32.f16 %0, a, m, %3;\n fma.rn.f32.f16 %1, b, m, %4;\n}"
+      : "=f"(r0), "=f"(r1)
+      : "r"(h), "f"(x0), "f"(x1));
+  return make_float2(r0, r1);
+}
 // Instruction descriptor, kind::f16: fp16 A and B (K-major), FP32 D.
 __host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
   return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
 template <int P, int V>
-__global__ void __launch_bounds__(TcCfg<P, V>::NTHREADS, 1) tc_forward_kernel(FwdArgs a, const __half *img, int tau) {
+__global__ void __launch_bounds__(TcCfg<P, V>::NTHREADS, 1)
+    tc_forward_kernel(FwdArgs a, const __half *img, const float4 *gp, int tau) {
   using C = TcCfg<P, V>;
   constexpr int NSH = C::NSH, NQ = C::NQ, NT = C::NT, NZ = C::NZ, S = C::STAGES, NCH = C::NCHUNK;
   constexpr int NP = C::NPW * 32, ND = C::NDW * 32, PPC = C::PPC, ROWB = C::ROWB, DR = C::DRING;
@@ -711,7 +748,10 @@ __global__ void __launch_bounds__(TcCfg<P, V>::NTHREADS, 1) tc_forward_kernel(Fw
             const int dr = (it * NCH + c0 + j) % DR;
             const int sl = slot_of(k0 + el);
             const TcElem<P> &E = ax.el[sl];
-            float4 *D4 = &ax.Dc[dr][el][0][qq];
+            // value k of this point: float4 k/2 of its pair, component
+            // 2 (k % 2) + (the point's position in the pair)
+            float *D1 = reinterpret_cast<float *>(&ax.Dc[dr][el][0][qq >> 1]) + (qq & 1);
+            float cv[14];
             if (q < NQ && E.status == 0) {
               float cq[14];
               const float *cp = E.cf;
@@ -722,17 +762,15 @@ __global__ void __launch_bounds__(TcCfg<P, V>::NTHREADS, 1) tc_forward_kernel(Fw
               float Dt[16];
               tc_point<P>(E, ax, cp, q, ax.sp[sl][q], Dt);
               const float up = E.up;
-              D4[0] = make_float4(Dt[0] * up, Dt[1] * up, Dt[2] * up, Dt[3] * up);
-              D4[PPC] = make_float4(Dt[4] * up, Dt[5] * up, Dt[6] * up, Dt[7] * up);
-              D4[2 * PPC] = make_float4(Dt[8] * up, Dt[9] * up, Dt[10] * up, Dt[11] * up);
-              D4[3 * PPC] = make_float4(Dt[12] * up, Dt[13], 0.f, 0.f);
+#pragma unroll
+              for (int k = 0; k < 13; ++k) cv[k] = Dt[k] * up;
+              cv[13] = Dt[13];
             } else {
-              const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-              D4[0] = z4;
-              D4[PPC] = z4;
-              D4[2 * PPC] = z4;
-              D4[3 * PPC] = z4;
+#pragma unroll
+              for (int k = 0; k < 14; ++k) cv[k] = 0.f;
             }
+#pragma unroll
+            for (int k = 0; k < 14; ++k) D1[(k >> 1) * 4 * C::PP + (k & 1) * 2] = cv[k];
           }
         }
         named_bar(2, ND);
@@ -741,36 +779,51 @@ __global__ void __launch_bounds__(TcCfg<P, V>::NTHREADS, 1) tc_forward_kernel(Fw
     }
   } else if (warp >= C::W_PW && warp < C::W_EW) {
     // ================================================================ producers
+    // The thread forms H' of one point pair pp of every chunk for its RPT
+    // rows rb + rs k, both points at once with packed FP32 instructions on
+    // (first point, second point) pairs.  The point operators of the pair
+    // stay in registers while consecutive rows belong to the same element.
     const int tp = tid - C::W_PW * 32;  // 0 .. NP-1
-    const int r = tp & 127, grp = tp >> 7;
+    const int pw = warp - C::W_PW;
+    const int pp = C::GS ? lane % C::PP : pw / C::WPP;
+    const int rb = C::GS ? pw * C::RW + lane / C::PP : (pw % C::WPP) * C::RWP + lane;
+    constexpr int RT = C::RPT, rs = C::GS ? C::RG : 32, GST = C::GST;
     int it = 0;
     int64_t tile = t_begin;
     for (; tile < t_end; ++tile, ++it) {
       if (*abort_flag) break;
       const int64_t r0 = tile * 128;
       const int64_t k0 = r0 / NSH;
-      const int64_t grow = r0 + r;
-      const bool rvalid = grow < rows_total;
-      int rel = 0, ri = 0;
-      if (rvalid) {
-        const int64_t k = grow / NSH;
-        ri = (int)(grow - k * NSH);
-        rel = (int)(k - k0);
+      // rows past the end compute finite values from element 0 of the
+      // tile; the epilogue drops them
+      int rowr[RT], rel[RT], ri[RT];
+#pragma unroll
+      for (int k = 0; k < RT; ++k) {
+        rowr[k] = rb + rs * k;
+        const int64_t grow = r0 + rowr[k];
+        rel[k] = 0;
+        ri[k] = 0;
+        if (grow < rows_total) {
+          const int64_t kk = grow / NSH;
+          ri[k] = (int)(grow - kk * NSH);
+          rel[k] = (int)(kk - k0);
+        }
       }
-      float bpart = 0.f;
-      const float4 *G4 = reinterpret_cast<const float4 *>(a.G32T);
+      float2 bp[RT];
+#pragma unroll
+      for (int k = 0; k < RT; ++k) bp[k] = make_float2(0.f, 0.f);
       for (int c = 0; c < NCH; ++c) {
         const int g = it * NCH + c, s = g % S, dr = g % DR;
         const uint32_t u = (uint32_t)(g / S), ud = (uint32_t)(g / DR);
-        // the FP32 table values of this row at this thread's points: from
-        // the stage (copied there with the B operand), or from L2, fetched
-        // before the waits so that their latency overlaps them
-        float4 gq[C::QPG];
+        // the paired FP32 table of this point pair at this thread's rows:
+        // from the stage (copied there with the B operand), or from L2,
+        // fetched before the waits so that their latency overlaps them
+        float4 ga[RT], gb[RT];
         if constexpr (!C::GS) {
 #pragma unroll
-          for (int j = 0; j < C::QPG; ++j) {
-            const int q = c * PPC + grp * C::QPG + j;
-            gq[j] = (rvalid && q < NQ) ? __ldg(G4 + (size_t)q * NSH + ri) : make_float4(0.f, 0.f, 0.f, 0.f);
+          for (int k = 0; k < RT; ++k) {
+            ga[k] = __ldg(gp + (size_t)((c * 2 + 0) * C::PP + pp) * GST + ri[k]);
+            gb[k] = __ldg(gp + (size_t)((c * 2 + 1) * C::PP + pp) * GST + ri[k]);
           }
         }
         // A slot free, point operators ready (and the table chunk landed:
@@ -784,55 +837,56 @@ __global__ void __launch_bounds__(TcCfg<P, V>::NTHREADS, 1) tc_forward_kernel(Fw
         if constexpr (C::GS) {
           const float4 *Gs = reinterpret_cast<const float4 *>(dsm_raw + (stageG(s) - smem_u32(dsm_raw)));
 #pragma unroll
-          for (int j = 0; j < C::QPG; ++j) {
-            const int qq = grp * C::QPG + j, q = c * PPC + qq;
-            gq[j] = (rvalid && q < NQ) ? Gs[qq * NSH + ri] : make_float4(0.f, 0.f, 0.f, 0.f);
+          for (int k = 0; k < RT; ++k) {
+            ga[k] = Gs[pp * GST + ri[k]];
+            gb[k] = Gs[(C::PP + pp) * GST + ri[k]];
           }
         }
         // generic pointers to the stage's hi and lo operand tiles
         unsigned char *const ahp = dsm_raw + (stageA(s, 0) - smem_u32(dsm_raw));
         unsigned char *const alp = ahp + C::A_BYTES;
-        // this thread: row r, points grp*QPG .. of the chunk = 16-byte chunks
-        // grp*QPG/2 .. of the operand row (two points each); each 16-byte
-        // chunk is stored as soon as it is formed (plain stores, so the
-        // compiler may overlap them with the next points' loads)
+        float2 pd[14];
+        int cur = -1;
 #pragma unroll
-        for (int pc = 0; pc < C::QPG / 2; ++pc) {
-          const int chunk = grp * (C::QPG / 2) + pc;
-          uint32_t hw[4], lw[4];
-          // the last chunk may end past the final point (uniform per warp)
-          if (rvalid && c * PPC + chunk * 2 < NQ) {
+        for (int k = 0; k < RT; ++k) {
+          if (rel[k] != cur) {
+            cur = rel[k];
+            const float4 *D4 = &ax.Dc[dr][cur][0][pp];
 #pragma unroll
-            for (int h2 = 0; h2 < 2; ++h2) {  // two points per 16-byte chunk
-              const int qq = chunk * 2 + h2;  // point within the chunk
-              const float4 *D4 = &ax.Dc[dr][rel][0][qq];
-              const float4 gg = gq[pc * 2 + h2];
-              const float gv[4] = {gg.x, gg.y, gg.z, gg.w};
-              // D carries 2^sigma; the operand is H' 2^sigma
-              const float4 d0 = D4[0], d1 = D4[PPC], d2 = D4[2 * PPC], d3 = D4[3 * PPC];
-              float hv[4];
-              hv[0] = d0.x * gv[0];
-              hv[1] = d0.y * gv[0] + d1.x * gv[1] + d1.w * gv[2] + d2.z * gv[3];
-              hv[2] = d0.z * gv[0] + d1.y * gv[1] + d2.x * gv[2] + d2.w * gv[3];
-              hv[3] = d0.w * gv[0] + d1.z * gv[1] + d2.y * gv[2] + d3.x * gv[3];
-              bpart += d3.y * gv[0];  // (w det J f) phi
-              const __half2 h01 = __floats2half2_rn(hv[0], hv[1]);
-              const __half2 h23 = __floats2half2_rn(hv[2], hv[3]);
-              const float2 f01 = __half22float2(h01), f23 = __half22float2(h23);
-              const __half2 l01 = __floats2half2_rn(hv[0] - f01.x, hv[1] - f01.y);
-              const __half2 l23 = __floats2half2_rn(hv[2] - f23.x, hv[3] - f23.y);
-              memcpy(&hw[2 * h2], &h01, 4);
-              memcpy(&hw[2 * h2 + 1], &h23, 4);
-              memcpy(&lw[2 * h2], &l01, 4);
-              memcpy(&lw[2 * h2 + 1], &l23, 4);
+            for (int j = 0; j < 7; ++j) {
+              const float4 d = D4[j * C::PP];
+              pd[2 * j] = make_float2(d.x, d.y);
+              pd[2 * j + 1] = make_float2(d.z, d.w);
             }
-          } else {
-#pragma unroll
-            for (int k = 0; k < 4; ++k) hw[k] = lw[k] = 0u;
           }
-          const uint32_t aoff = sw_off<ROWB>(r, chunk);
-          *reinterpret_cast<uint4 *>(ahp + aoff) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-          *reinterpret_cast<uint4 *>(alp + aoff) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+          const float2 g0 = make_float2(ga[k].x, ga[k].y), g1 = make_float2(ga[k].z, ga[k].w);
+          const float2 g2 = make_float2(gb[k].x, gb[k].y), g3 = make_float2(gb[k].z, gb[k].w);
+          // H' 2^sigma = Dt 2^sigma G at both points; (w det J f) phi
+          const float2 h0 = __fmul2_rn(pd[0], g0);
+          const float2 h1 = __ffma2_rn(pd[10], g3, __ffma2_rn(pd[7], g2, __ffma2_rn(pd[4], g1, __fmul2_rn(pd[1], g0))));
+          const float2 h2 = __ffma2_rn(pd[11], g3, __ffma2_rn(pd[8], g2, __ffma2_rn(pd[5], g1, __fmul2_rn(pd[2], g0))));
+          const float2 h3 = __ffma2_rn(pd[12], g3, __ffma2_rn(pd[9], g2, __ffma2_rn(pd[6], g1, __fmul2_rn(pd[3], g0))));
+          bp[k] = __ffma2_rn(pd[13], g0, bp[k]);
+          // the 16-byte operand chunk: 4 values of the first point, then 4
+          // of the second, as fp16 hi and lo = rn(x - hi)
+          const __half2 w0 = __floats2half2_rn(h0.x, h1.x), w1 = __floats2half2_rn(h2.x, h3.x);
+          const __half2 w2 = __floats2half2_rn(h0.y, h1.y), w3 = __floats2half2_rn(h2.y, h3.y);
+          const float2 e0 = split_residual(w0, h0.x, h1.x), e1 = split_residual(w1, h2.x, h3.x);
+          const float2 e2 = split_residual(w2, h0.y, h1.y), e3 = split_residual(w3, h2.y, h3.y);
+          const __half2 l0 = __floats2half2_rn(e0.x, e0.y), l1 = __floats2half2_rn(e1.x, e1.y);
+          const __half2 l2 = __floats2half2_rn(e2.x, e2.y), l3 = __floats2half2_rn(e3.x, e3.y);
+          uint4 hw, lw;
+          memcpy(&hw.x, &w0, 4);
+          memcpy(&hw.y, &w1, 4);
+          memcpy(&hw.z, &w2, 4);
+          memcpy(&hw.w, &w3, 4);
+          memcpy(&lw.x, &l0, 4);
+          memcpy(&lw.y, &l1, 4);
+          memcpy(&lw.z, &l2, 4);
+          memcpy(&lw.w, &l3, 4);
+          const uint32_t aoff = sw_off<ROWB>(rowr[k], pp);
+          *reinterpret_cast<uint4 *>(ahp + aoff) = hw;
+          *reinterpret_cast<uint4 *>(alp + aoff) = lw;
         }
         // the point operators of this chunk are consumed and the A slot is
         // written (made visible to the tensor core's proxy)
@@ -844,13 +898,14 @@ __global__ void __launch_bounds__(TcCfg<P, V>::NTHREADS, 1) tc_forward_kernel(Fw
         }
       }
       if (*abort_flag) break;
-      // load-vector partials of this tile for the epilogue (the slot is free
-      // once the epilogue finished the tile two before)
+      // load-vector partials of the tile's rows for this point pair (the
+      // slot is free once the epilogue finished the tile two before)
       const int slot = it & 1;
       const bool mok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&ax.meta_empty[slot]),
                                                          ((uint32_t)(it >> 1) & 1u) ^ 1u, abort_flag));
       if (!mok) break;
-      ax.bsum[slot][grp][r] = bpart;
+#pragma unroll
+      for (int k = 0; k < RT; ++k) ax.bsum[slot][pp][rowr[k]] = bp[k].x + bp[k].y;
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&ax.bsum_full[slot]));
     }
@@ -918,7 +973,12 @@ __global__ void __launch_bounds__(TcCfg<P, V>::NTHREADS, 1) tc_forward_kernel(Fw
                 if (ncol < C::RT) {
                   if (c > 0) {
 #pragma unroll
-                    for (int k2 = 0; k2 < 16; ++k2) v[k2] += __uint_as_float(rv[j][k2]);
+                    for (int k2 = 0; k2 < 16; k2 += 2) {
+                      const float2 t = __fadd2_rn(make_float2(v[k2], v[k2 + 1]),
+                                                  make_float2(__uint_as_float(rv[j][k2]), __uint_as_float(rv[j][k2 + 1])));
+                      v[k2] = t.x;
+                      v[k2 + 1] = t.y;
+                    }
                   }
                   tmem_st16(tmem + lane_base + 2 * C::NMMA + ncol, v);
                 } else if constexpr (C::RREG > 0) {
@@ -948,7 +1008,7 @@ __global__ void __launch_bounds__(TcCfg<P, V>::NTHREADS, 1) tc_forward_kernel(Fw
       if (M.row_boff[myrow] >= 0) {
         float bsum = 0.f;
 #pragma unroll
-        for (int gq = 0; gq < C::NPW * 32 / 128; ++gq) bsum += ax.bsum[slot][gq][myrow];
+        for (int j = 0; j < C::PP; ++j) bsum += ax.bsum[slot][j][myrow];
         const int st = M.row_status[myrow];
         reinterpret_cast<float *>(a.bv)[M.row_boff[myrow]] = st ? 0.f : bsum;
         if (M.row_eid[myrow] >= 0) a.status[M.row_eid[myrow]] = st;
@@ -1058,12 +1118,10 @@ __global__ void __launch_bounds__(TcCfg<P, V>::NTHREADS, 1) tc_forward_kernel(Fw
             break;
           }
           const uint32_t bar = smem_u32(&ax.bfull[s]);
-          // points of this chunk that exist (the last chunk may be short)
-          const int npts = NQ - c * PPC < PPC ? NQ - c * PPC : PPC;
-          const uint32_t gbytes = C::GS ? (uint32_t)(npts * NSH * 16) : 0u;
+          const uint32_t gbytes = C::GS ? (uint32_t)C::G_BYTES : 0u;
           mbar_expect_tx(bar, 2u * C::B_BYTES + gbytes);
           bulk_g2s(stageB(s), img + (size_t)c * 2 * C::NPAD * (ROWB / 2), 2u * C::B_BYTES, bar);
-          if (C::GS) bulk_g2s(stageG(s), a.G32T + (size_t)c * PPC * NSH * 4, gbytes, bar);
+          if (C::GS) bulk_g2s(stageG(s), gp + (size_t)c * 2 * C::PP * C::GST, gbytes, bar);
         }
         if (!ok) break;
       }
@@ -1168,6 +1226,19 @@ __global__ void image_kernel(const double *G, int nsh, int nq, int npad, int nch
   }
 }
 
+__global__ void pair_table_kernel(const double *G, int nsh, int nq, int gst, int nchunk, int pp, float *out) {
+  const int64_t total = (int64_t)nchunk * 2 * pp * gst * 4;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int m = (int)(idx % 4);
+    const int i = (int)((idx / 4) % gst);
+    const int64_t rest = idx / (4 * (int64_t)gst);
+    const int pr = (int)(rest % pp), h = (int)((rest / pp) % 2), c = (int)(rest / (2 * pp));
+    const int b = 2 * h + (m >> 1), q = c * 2 * pp + 2 * pr + (m & 1);
+    out[idx] = q < nq && i < nsh ? (float)G[(size_t)(4 * q + b) * nsh + i] : 0.f;
+  }
+}
+
 template <int P, int V>
 fei_status launch_tc(const fei_reference *ref, const FwdArgs &a, int64_t grid_work, cudaStream_t s) {
   using C = TcCfg<P, V>;
@@ -1181,16 +1252,18 @@ fei_status launch_tc(const fei_reference *ref, const FwdArgs &a, int64_t grid_wo
   const int64_t tiles = (grid_work * C::NSH + 127) / 128;
   int64_t blocks = tiles < sms ? tiles : sms;
   if (blocks < 1) blocks = 1;
-  tc_forward_kernel<P, V><<<(unsigned)blocks, C::NTHREADS, C::DYN_SMEM, s>>>(a, im->img, im->tau);
+  tc_forward_kernel<P, V><<<(unsigned)blocks, C::NTHREADS, C::DYN_SMEM, s>>>(
+      a, im->img, reinterpret_cast<const float4 *>(im->gp), im->tau);
   FEI_CUDA_TRY(cudaGetLastError(), "tc_forward_kernel launch");
   return FEI_OK;
 }
 
 template <int P>
-void tc_dims(int &npad, int &nchunk, int &rowb) {
+void tc_dims(int &npad, int &nchunk, int &rowb, int &gst) {
   npad = TcCfg<P>::NPAD;
   nchunk = TcCfg<P>::NCHUNK;
   rowb = TcCfg<P>::ROWB;
+  gst = TcCfg<P>::GST;
 }
 
 }  // namespace
@@ -1198,22 +1271,26 @@ void tc_dims(int &npad, int &nchunk, int &rowb) {
 fei_status build_tc_image(fei_reference *ref) {
   ref->tc = nullptr;
   if (ref->p < 3) return FEI_OK;
-  int npad = 0, nchunk = 0, rowb = 0;
+  int npad = 0, nchunk = 0, rowb = 0, gst = 0;
   switch (ref->p) {
-    case 3: tc_dims<3>(npad, nchunk, rowb); break;
-    case 4: tc_dims<4>(npad, nchunk, rowb); break;
-    case 5: tc_dims<5>(npad, nchunk, rowb); break;
-    case 6: tc_dims<6>(npad, nchunk, rowb); break;
-    case 7: tc_dims<7>(npad, nchunk, rowb); break;
+    case 3: tc_dims<3>(npad, nchunk, rowb, gst); break;
+    case 4: tc_dims<4>(npad, nchunk, rowb, gst); break;
+    case 5: tc_dims<5>(npad, nchunk, rowb, gst); break;
+    case 6: tc_dims<6>(npad, nchunk, rowb, gst); break;
+    case 7: tc_dims<7>(npad, nchunk, rowb, gst); break;
   }
   TcImage *im = new TcImage();
   im->npad = npad;
   im->nchunk = nchunk;
   im->rowb = rowb;
   im->img = nullptr;
+  im->gp = nullptr;
   unsigned long long *dmax = nullptr;
   const size_t halves = (size_t)nchunk * 2 * npad * (rowb / 2);
+  const int pp = rowb / 16;  // point pairs per chunk
+  const size_t gfloats = (size_t)nchunk * 2 * pp * gst * 4;
   cudaError_t e = cudaMalloc(&im->img, sizeof(__half) * halves);
+  if (e == cudaSuccess) e = cudaMalloc(&im->gp, sizeof(float) * gfloats);
   if (e == cudaSuccess) e = cudaMalloc(&dmax, sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMemset(dmax, 0, sizeof(unsigned long long));
   if (e == cudaSuccess) {
@@ -1231,11 +1308,16 @@ fei_status build_tc_image(fei_reference *ref) {
     im->tau = 14 - ex;
     image_kernel<<<256, 256>>>(ref->G64, ref->nsh, ref->nq, npad, nchunk, rowb, ldexp(1.0, im->tau), im->img);
     e = cudaGetLastError();
+    if (e == cudaSuccess) {
+      pair_table_kernel<<<256, 256>>>(ref->G64, ref->nsh, ref->nq, gst, nchunk, pp, im->gp);
+      e = cudaGetLastError();
+    }
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
   }
   if (dmax) cudaFree(dmax);
   if (e != cudaSuccess) {
     if (im->img) cudaFree(im->img);
+    if (im->gp) cudaFree(im->gp);
     delete im;
     return cuda_error(e, "tensor-core image");
   }
@@ -1246,6 +1328,7 @@ fei_status build_tc_image(fei_reference *ref) {
 void free_tc_image(fei_reference *ref) {
   if (ref->tc) {
     cudaFree(ref->tc->img);
+    cudaFree(ref->tc->gp);
     delete ref->tc;
     ref->tc = nullptr;
   }
