@@ -95,6 +95,9 @@ typedef struct fei_reference *fei_reference_t;
  *            element e's records start at q_offset[e], point order as above).
  *            K is used as given (row k, column l multiplies d/dx_l of the
  *            trial function in the k-th component); it need not be symmetric.
+ *            The library cannot see the arrays' lengths: the caller owns
+ *            them and must pass n_rec records (a shorter array is read past
+ *            its end; the Python binding refuses one).
  *  A_offset, b_offset, q_offset  int64 [n_elem + 1] start of element e in
  *            A_out (scalars), b_out, and the per-point records; NULL means
  *            the contiguous layout of a uniform degree (e*N_sh^2, e*N_sh,

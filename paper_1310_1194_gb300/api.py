@@ -161,6 +161,14 @@ def _inputs(geom, K, b, c, f, degree, p, per_qp, layout):
             raise ValueError("give p or degree")
         if layout is None:
             layout = uniform_layout(geom.shape[0], p)
+    # the kernels index the coefficient records by element (or by element
+    # and point) without knowing the arrays' lengths, so a short array would
+    # be read past its end: its size is checked here
+    m = layout.q_total if per_qp else geom.shape[0]
+    for t, name, width in ((K, "K", 9), (b, "b", 3), (c, "c", 1), (f, "f", 1)):
+        if t.numel() != width * m:
+            per = "quadrature point" if per_qp else "element"
+            raise ValueError(f"{name} must hold {width} values per {per} ({width * m} in all), got {t.numel()}")
     return geom, layout
 
 

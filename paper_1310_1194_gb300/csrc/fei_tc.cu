@@ -230,7 +230,7 @@ struct TcCfg {
   static constexpr int RREG = NPAD - RT;
   static constexpr int EMAX = (128 + NSH - 1) / NSH + 1;  // elements a tile can touch
   static constexpr int NSLOT = EMAX + 1;  // element slots: a tile's elements plus the one it shares
-  static constexpr int NDW = P == 7 ? 2 : P == 6 ? 4 : P == 5 ? 2 : 6;  // point-operator warps
+  static constexpr int NDW = P == 7 ? 2 : P == 6 || P == 5 ? 4 : 6;  // point-operator warps
   static constexpr int NPW = V == 1 ? 16 : 8;  // producer warps
   static constexpr int NEW = 4;  // epilogue warps
   static constexpr int W_DW = 2, W_PW = W_DW + NDW, W_EW = W_PW + NPW;

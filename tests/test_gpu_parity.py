@@ -322,3 +322,14 @@ def test_plan_per_point_coefficients_mixed(api):
     for e in range(len(w["geom"])):
         sl = slice(int(Aoff[e]), int(Aoff[e + 1]))
         assert np.linalg.norm(Ah[sl] - Ao[sl]) <= 1e-6 * np.linalg.norm(Ao[sl]), (e, int(w["degree"][e]))
+
+
+def test_coefficient_arrays_of_the_wrong_length_are_refused(api):
+    """Per-point records sized for p = 5 given with p = 6: refused before any
+    launch (the kernels cannot see the arrays' lengths)."""
+    w = inputs.workload("diff", n_max=4)
+    g = {k: dev(w[k]) for k in ("geom", "K", "b", "c", "f")}
+    with pytest.raises(ValueError, match="per quadrature point"):
+        api.fei_integrate(g["geom"], g["K"], g["b"], g["c"], g["f"], p=6, per_qp=True, precision="fp64")
+    with pytest.raises(ValueError, match="per element"):
+        api.fei_integrate(g["geom"], g["K"], g["b"], g["c"], g["f"], p=5, per_qp=False, precision="fp64")
