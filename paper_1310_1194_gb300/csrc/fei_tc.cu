@@ -680,8 +680,9 @@ __global__ void __launch_bounds__(TcCfg<P, V>::NTHREADS, 1)
           }
         }
         // one atomic per element per warp (the bound is a max of
-        // non-negative floats, so their bit patterns order as integers)
-        const int i0 = __shfl_sync(0xffffffffu, i, 0), i1 = __shfl_sync(0xffffffffu, i, 31);
+        // non-negative floats, so their bit patterns order as integers);
+        // lanes past the last point hold i = -1, lane 0 the smallest i
+        const int i0 = __shfl_sync(0xffffffffu, i, 0), i1 = __reduce_max_sync(0xffffffffu, i);
         for (int i2 = i0 < 0 ? 0 : i0; i2 <= i1 && i2 < nnew; ++i2) {
           const unsigned mb = __reduce_max_sync(0xffffffffu, i == i2 ? __float_as_uint(m) : 0u);
           if (lane == 0 && mb) atomicMax(&ax.el[slot_of(kn0 + i2)].mbits, (int)mb);

@@ -333,3 +333,29 @@ def test_coefficient_arrays_of_the_wrong_length_are_refused(api):
         api.fei_integrate(g["geom"], g["K"], g["b"], g["c"], g["f"], p=6, per_qp=True, precision="fp64")
     with pytest.raises(ValueError, match="per element"):
         api.fei_integrate(g["geom"], g["K"], g["b"], g["c"], g["f"], p=5, per_qp=False, precision="fp64")
+
+
+@pytest.mark.parametrize("p", [4, 5])
+def test_tc_operand_scale_covers_every_point(api, p):
+    """Per-point diffusion 10^4 times larger at the last quadrature point of
+    every element: each element's fp16 operand scale must come from the bound
+    of all its points (a scale that missed that point would overflow fp16)."""
+    n = 9
+    w = inputs.workload("pr1", n_max=n)
+    q = (p + 1) ** 3
+    K = np.broadcast_to(np.eye(3), (n, q, 3, 3)).copy()
+    K[:, -1] *= 1e4
+    K = K.reshape(n * q, 3, 3)
+    b = np.full((n * q, 3), 0.1)
+    c = np.full(n * q, 0.5)
+    f = np.ones(n * q)
+    A, bv, st, _ = api.fei_integrate(dev(w["geom"]), dev(K), dev(b), dev(c), dev(f), p=p, per_qp=True,
+                                     precision="tc_f16x3")
+    torch.cuda.synchronize()
+    Ao, bo, so, _ = oracle.integrate(w["geom"], K, b, c, f, p=p, per_qp=True)
+    assert int(st.abs().max()) == 0 and int(np.abs(so).max()) == 0
+    Ah = A.double().cpu().numpy().reshape(n, -1)
+    assert np.isfinite(Ah).all()
+    Aor = Ao.reshape(n, -1)
+    for e in range(n):
+        assert np.linalg.norm(Ah[e] - Aor[e]) <= 1e-6 * np.linalg.norm(Aor[e]), e
