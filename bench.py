@@ -314,7 +314,7 @@ def main():
         try:
             api.fei_integrate(g["geom"][:1], g["K"][: (nq(p) if per_qp else 1)], g["b"][: (nq(p) if per_qp else 1)],
                               g["c"][: (nq(p) if per_qp else 1)], g["f"][: (nq(p) if per_qp else 1)],
-                              p=p if p is not None else 3, precision=precision)
+                              p=p if p is not None else 3, per_qp=per_qp, precision=precision)
         except _lib.FeiError:
             precision = "fp32"
     layout = api.fei_plan_offsets(deg) if deg is not None else api.uniform_layout(n, p)
