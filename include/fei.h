@@ -285,6 +285,78 @@ fei_status fei_integrate_noalloc(const fei_reference_t *refs, int nrefs,
                                  void *A_out, void *b_out, int32_t *elem_status,
                                  fei_stream_t stream);
 
+/* ---- Assembly into a global CSR matrix (Sec. 2) -------------------------
+ * After integration, entry (r, c) of the global matrix is the sum of
+ * A_e[i][j] over the elements e whose local functions i and j carry the
+ * global numbers r = l2g_e[i] and c = l2g_e[j]; the global load vector
+ * gathers b_e[i] at l2g_e[i].  Elements that share a global function
+ * depend on each other; a colouring in which such elements never share a
+ * colour removes the dependency (Sec. 2), so each colour is added by one
+ * launch without atomics. */
+typedef struct fei_assembly *fei_assembly_t;
+
+/* fei_assembly_create flag: build the pattern and colouring on the host
+ * only (no device memory, no CUDA call); fei_assembly_info and
+ * fei_assembly_pattern work, the assemble calls refuse the handle. */
+#define FEI_ASSEMBLY_HOST_ONLY 1
+
+/* Builds, on the host, the CSR pattern, a greedy colouring of the elements
+ * and the scatter map, and copies them to the current device.
+ *  n_elem            number of elements (1..2^31-1).
+ *  degree            HOST int32 [n_elem] degrees, or NULL: every element has
+ *                    uniform_degree (1..7).
+ *  l2g               HOST int64, element e's N_sh(p_e) global numbers at
+ *                    the element's load-vector offset (the layout of b_out
+ *                    of fei_integrate: sum of N_sh over earlier elements).
+ *                    Values in 0..n_dof-1, distinct within an element.
+ *  n_dof             global functions (rows), 1..2^31-1.
+ *  flags             0 or FEI_ASSEMBLY_HOST_ONLY.
+ * The pattern holds, in row r, the sorted global numbers of every element
+ * that contains r; a row may hold at most 65535 entries.  Errors:
+ * INVALID_ARG (NULL pointers, sizes, l2g out of range or repeated within an
+ * element), INVALID_DEGREE, UNSUPPORTED (a row over 65535 entries), OOM,
+ * CUDA.  Synchronous; the handle owns all its memory. */
+fei_status fei_assembly_create(int64_t n_elem, const int32_t *degree, int32_t uniform_degree,
+                               const int64_t *l2g, int64_t n_dof, int32_t flags,
+                               fei_assembly_t *out);
+fei_status fei_assembly_destroy(fei_assembly_t as);
+
+/* Sizes (host pointers, any may be NULL): rows, stored entries, colours,
+ * and chunks of the fused path. */
+fei_status fei_assembly_info(fei_assembly_t as, int64_t *n_dof, int64_t *nnz, int32_t *n_colours,
+                             int32_t *n_chunks);
+
+/* Copies the pattern and the colouring to HOST arrays (any may be NULL):
+ * row_ptr int64 [n_dof + 1], col_idx int32 [nnz], colour int32 [n_elem].
+ * Synchronous. */
+fei_status fei_assembly_pattern(fei_assembly_t as, int64_t *row_ptr, int32_t *col_idx, int32_t *colour);
+
+/* values (device [nnz]) = the assembled matrix and rhs (device [n_dof]) =
+ * the assembled load vector, from element matrices and vectors in the
+ * layout fei_integrate writes for the batch the handle describes (A_offset
+ * and b_offset of fei_plan_offsets, or the contiguous uniform layout).
+ * Types follow prec: double for FEI_FP64, float otherwise.  Both outputs are
+ * overwritten.  One launch per colour, in colour order, so the sum of each
+ * entry runs in a fixed order.  Asynchronous on the stream. */
+fei_status fei_assemble(fei_assembly_t as, fei_precision prec, const void *A, const void *b,
+                        void *values, void *rhs, fei_stream_t stream);
+
+/* Integration and assembly fused: the handle's elements, grouped by colour
+ * and degree into chunks, are integrated chunk by chunk into a scratch
+ * buffer that the library allocates on first use (kept with the handle)
+ * and sized to stay in L2, and each chunk is assembled from there at once,
+ * so no element matrix goes to HBM.  batch: as for fei_integrate, with the
+ * handle's element count and degrees (a degree array if and only if the
+ * handle was created with one, holding the same degrees); its A_offset and
+ * b_offset are not used (no element output).  values, rhs: as for
+ * fei_assemble; elem_status: as for
+ * fei_integrate (device int32 [n_elem]).  Calls on one handle must not
+ * overlap on the GPU (they share the scratch).  Asynchronous on the stream
+ * (the first call allocates). */
+fei_status fei_integrate_assemble(fei_assembly_t as, const fei_reference_t *refs, int nrefs,
+                                  const fei_batch *batch, fei_precision prec, void *values,
+                                  void *rhs, int32_t *elem_status, fei_stream_t stream);
+
 /* Thread-local description of the last failure of the calling thread. */
 const char *fei_last_error_string(void);
 

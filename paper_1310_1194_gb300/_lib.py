@@ -91,13 +91,23 @@ def _load():
     lib.fei_plan_tune.argtypes = [vp, ctypes.POINTER(fei_batch), vp, vp, vp, vp]
     lib.fei_plan_choice.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(i64),
                                     ctypes.POINTER(ctypes.c_float)]
+    lib.fei_assembly_create.argtypes = [i64, vp, i32, vp, i64, i32, ref_p]
+    lib.fei_assembly_destroy.argtypes = [vp]
+    lib.fei_assembly_info.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i32),
+                                      ctypes.POINTER(i32)]
+    lib.fei_assembly_pattern.argtypes = [vp, vp, vp, vp]
+    lib.fei_assemble.argtypes = [vp, ctypes.c_int, vp, vp, vp, vp, vp]
+    lib.fei_integrate_assemble.argtypes = [vp, ref_p, ctypes.c_int, ctypes.POINTER(fei_batch), ctypes.c_int,
+                                           vp, vp, vp, vp]
     lib.fei_last_error_string.argtypes = []
     lib.fei_last_error_string.restype = ctypes.c_char_p
     for name in ("fei_reference_create", "fei_reference_destroy", "fei_reference_info",
                  "fei_reference_copy_table", "fei_integrate", "fei_integrate_backward",
                  "fei_integrate_backward_quadratic",
                  "fei_plan_offsets", "fei_integrate_noalloc", "fei_plan_create", "fei_plan_destroy",
-                 "fei_plan_execute", "fei_plan_tune", "fei_plan_choice", "fei_status_summary"):
+                 "fei_plan_execute", "fei_plan_tune", "fei_plan_choice", "fei_status_summary",
+                 "fei_assembly_create", "fei_assembly_destroy", "fei_assembly_info", "fei_assembly_pattern",
+                 "fei_assemble", "fei_integrate_assemble"):
         getattr(lib, name).restype = i32
     return lib
 

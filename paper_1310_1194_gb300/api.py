@@ -9,6 +9,7 @@ from __future__ import annotations
 import ctypes
 from dataclasses import dataclass
 
+import numpy as np
 import torch
 
 from . import _lib
@@ -297,6 +298,98 @@ class Plan:
         h = getattr(self, "handle", None)
         if h is not None and h.value:
             lib.fei_plan_destroy(h)
+            self.handle = None
+
+
+class Assembly:
+    """Assembly of element matrices into a global CSR matrix (Sec. 2).
+
+    ``l2g``: host int64 array, element e's N_sh(p_e) global numbers at the
+    element's load-vector offset; ``n_dof``: number of global functions.
+    The pattern, a colouring of the elements (elements that share a global
+    function get different colours) and the scatter map are built on the
+    host; ``assemble`` then adds the element matrices colour by colour
+    without atomics, and ``integrate_assemble`` integrates and assembles
+    chunk by chunk through an L2-sized scratch.  ``host_only`` builds the
+    pattern and colouring without touching a GPU."""
+
+    def __init__(self, l2g, n_dof, p=None, degree=None, host_only=False):
+        l2g = np.ascontiguousarray(l2g, dtype=np.int64)
+        if degree is not None:
+            self.degree = np.ascontiguousarray(degree, dtype=np.int32)
+            n = len(self.degree)
+            deg_ptr = self.degree.ctypes.data
+        else:
+            if p is None:
+                raise ValueError("give p or degree")
+            self.degree = None
+            n = len(l2g) // nsh(p)
+            deg_ptr = None
+        self.p, self.n_elem, self.host_only = p, n, host_only
+        self._l2g = l2g
+        h = ctypes.c_void_p()
+        check(lib.fei_assembly_create(n, deg_ptr, int(p or 0), l2g.ctypes.data, int(n_dof),
+                                      1 if host_only else 0, ctypes.byref(h)), "fei_assembly_create")
+        self.handle = h
+        self.n_dof, self.nnz, self.n_colours, self.n_chunks = self.info()
+
+    def info(self):
+        """(n_dof, nnz, colours, chunks of the fused path)."""
+        a, b, c, d = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32()
+        check(lib.fei_assembly_info(self.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
+                                    ctypes.byref(d)), "fei_assembly_info")
+        return a.value, b.value, c.value, d.value
+
+    def pattern(self):
+        """Host copies: row_ptr int64 [n_dof + 1], col_idx int32 [nnz],
+        colour int32 [n_elem]."""
+        rp = np.empty(self.n_dof + 1, dtype=np.int64)
+        ci = np.empty(max(self.nnz, 1), dtype=np.int32)
+        co = np.empty(self.n_elem, dtype=np.int32)
+        check(lib.fei_assembly_pattern(self.handle, rp.ctypes.data, ci.ctypes.data, co.ctypes.data),
+              "fei_assembly_pattern")
+        return rp, ci[: self.nnz], co
+
+    def _outputs(self, precision, device, out):
+        dtype = torch.float64 if precision == "fp64" else torch.float32
+        if out is not None:
+            return out
+        return (torch.empty(self.nnz, dtype=dtype, device=device),
+                torch.empty(self.n_dof, dtype=dtype, device=device))
+
+    def assemble(self, A, bvec, precision="fp32", out=None):
+        """values [nnz], rhs [n_dof] from A, b in fei_integrate's layout."""
+        dtype = torch.float64 if precision == "fp64" else torch.float32
+        for t, name in ((A, "A"), (bvec, "b")):
+            if not t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+                raise ValueError(f"{name} must be a contiguous CUDA {dtype} tensor")
+        values, rhs = self._outputs(precision, A.device, out)
+        check(lib.fei_assemble(self.handle, _lib.PRECISIONS[precision], _ptr(A), _ptr(bvec), _ptr(values),
+                               _ptr(rhs), _stream()), "fei_assemble")
+        return values, rhs
+
+    def integrate_assemble(self, geom, K, b, c, f, precision="fp32", per_qp=False, degree=None, refs=None,
+                           out=None):
+        """Fused integration and assembly; returns (values, rhs, status).
+        ``degree``: device int32 tensor of the handle's degrees (a mixed
+        batch), else the handle's uniform degree is used."""
+        p = None if degree is not None else self.p
+        geom, layout = _inputs(geom, K, b, c, f, degree, p, per_qp, None)
+        if refs is None:
+            degs = [int(p)] if degree is None else sorted(set(int(x) for x in self.degree))
+            refs = [fei_reference_create(d) for d in degs]
+        values, rhs = self._outputs(precision, geom.device, None if out is None else out[:2])
+        st = torch.empty(geom.shape[0], dtype=torch.int32, device=geom.device) if out is None else out[2]
+        bt = _batch(geom, K, b, c, f, degree, p, per_qp, layout)
+        check(lib.fei_integrate_assemble(self.handle, _refs_array(refs), len(refs), ctypes.byref(bt),
+                                         _lib.PRECISIONS[precision], _ptr(values), _ptr(rhs), _ptr(st),
+                                         _stream()), "fei_integrate_assemble")
+        return values, rhs, st
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            lib.fei_assembly_destroy(h)
             self.handle = None
 
 

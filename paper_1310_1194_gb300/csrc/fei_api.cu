@@ -145,6 +145,10 @@ __global__ void __launch_bounds__(1024) offsets_kernel(const int32_t *degree, in
   if (t == 0 && bad) *bad = sbad;
 }
 
+}  // namespace
+
+// Argument checks and the per-degree forward launch, shared with the
+// assembly entry points (fei_assembly.cu).
 fei_status check_refs(const fei_reference_t *refs, int nrefs, int dev, const fei_reference **by_p) {
   if (!refs || nrefs < 1) return set_error(FEI_ERR_INVALID_ARG, "refs is NULL or nrefs < 1");
   for (int p = 0; p <= kPMax; ++p) by_p[p] = nullptr;
@@ -205,7 +209,6 @@ fei_status launch_forward(int p, fei_precision prec, const fei_reference *r, con
   return launch_cc_forward(p, prec == FEI_FP64, a, grid_work, s);
 }
 
-}  // namespace
 }  // namespace fei
 
 using namespace fei;

@@ -88,6 +88,15 @@ struct BwdArgs {
 fei_status set_error(fei_status st, const char *fmt, ...);
 fei_status cuda_error(cudaError_t e, const char *what);
 
+// Argument checks and forward dispatch (fei_api.cu).  check_refs fills
+// by_p[p] with the handle of degree p (or null); fill_fwd sets the
+// arguments of a forward launch over the whole batch (no list).
+fei_status check_refs(const fei_reference_t *refs, int nrefs, int dev, const fei_reference **by_p);
+fei_status check_batch(const fei_batch *b);
+void fill_fwd(FwdArgs &a, const fei_batch *b, const fei_reference *r, void *A, void *bv, int32_t *st);
+fei_status launch_forward(int p, fei_precision prec, const fei_reference *r, const FwdArgs &a, int64_t grid_work,
+                          cudaStream_t s);
+
 // Kernel launchers (each returns FEI_OK or an error already recorded).
 // grid_cap: largest grid (blocks) of the grid-stride kernels, 0 = default
 // (all work items for a known count, 152 x 4 or 152 x 8 for a device count)

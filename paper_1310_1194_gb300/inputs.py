@@ -244,6 +244,41 @@ def workload(name: str, n_max: int | None = None) -> dict:
     return out
 
 
+def dof_map(w: dict, shared: str = "vertex") -> tuple[np.ndarray, int]:
+    """Element-to-global numbering for assembly of workload ``w``: int64
+    l2g in the load-vector layout (element e's N_sh(p_e) numbers follow
+    those of the elements before it) and the number of global functions.
+
+    ``shared="vertex"``: the first 6 local functions of an element take the
+    numbers of its 6 mesh vertices (numbered compactly over the vertices the
+    elements use), the others are private, numbered after all vertices in
+    element order.  The modal basis has no vertex functions, so this is a
+    synthetic sharing pattern; it gives assembly the neighbourhood structure
+    of the prism mesh (a vertex is shared by up to 12 prisms).
+    ``shared="none"``: every function private (block-diagonal matrix)."""
+    cfg = WORKLOADS[w["name"]]
+    degree = np.asarray(w["degree"], dtype=np.int64)
+    n = len(degree)
+    s = (degree + 1) ** 2 * (degree + 2) // 2
+    if shared == "none":
+        return np.arange(int(s.sum()), dtype=np.int64), int(s.sum())
+    if shared != "vertex":
+        raise ValueError(shared)
+    pv = _prism_vertices(*cfg["grid"])[:n]
+    used, vert = np.unique(pv.reshape(-1), return_inverse=True)
+    vert = vert.reshape(n, 6)
+    n_vert = len(used)
+    priv = s - 6
+    pstart = n_vert + np.concatenate([[0], np.cumsum(priv)[:-1]])
+    l2g = np.empty(int(s.sum()), dtype=np.int64)
+    off = np.concatenate([[0], np.cumsum(s)[:-1]])
+    for e in range(n):
+        o = off[e]
+        l2g[o:o + 6] = vert[e]
+        l2g[o + 6:o + s[e]] = pstart[e] + np.arange(priv[e])
+    return l2g, int(n_vert + priv.sum())
+
+
 def loss_weights(n_total: int, seed: int) -> np.ndarray:
     """u ~ N(0, 1) FP64 for the loss L = sum_e u_e^T A_e u_e - u_e^T b_e."""
     return _rng(seed, 4).standard_normal(n_total)
