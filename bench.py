@@ -257,6 +257,70 @@ def metric_name(args):
     return METRIC
 
 
+def assembly_measure(api, w, g, deg, refs, precision, flush, steps):
+    """Assembly of the workload into CSR with the vertex-sharing DOF map:
+    host build time, the fused integrate-and-assemble step, and the
+    assembly of precomputed element matrices with its algorithmic bytes."""
+    import torch
+    t0 = time.perf_counter()
+    l2g, nd = inputs.dof_map(w)
+    t1 = time.perf_counter()
+    asm = api.Assembly(l2g, nd, p=w["p"], degree=w["degree"] if w["p"] is None else None)
+    t2 = time.perf_counter()
+    per_qp = bool(w["per_qp"])
+    vt = torch.float64 if precision == "fp64" else torch.float32
+    vsize = 8 if precision == "fp64" else 4
+    values = torch.empty(asm.nnz, dtype=vt, device="cuda")
+    rhs = torch.empty(asm.n_dof, dtype=vt, device="cuda")
+    st = torch.empty(len(w["degree"]), dtype=torch.int32, device="cuda")
+    A, bv, st3, layout = api.fei_integrate(*g, p=w["p"], degree=deg, per_qp=per_qp, precision=precision,
+                                           refs=refs)
+    values2 = torch.empty_like(values)
+    rhs2 = torch.empty_like(rhs)
+
+    def fused():
+        asm.integrate_assemble(*g, precision=precision, per_qp=per_qp, degree=deg, refs=refs, out=(values, rhs, st))
+
+    def standalone():
+        asm.assemble(A, bv, precision=precision, out=(values2, rhs2))
+
+    def integrate():
+        api.fei_integrate(*g, p=w["p"], degree=deg, per_qp=per_qp, precision=precision, refs=refs, layout=layout,
+                          out=(A, bv, st3))
+
+    def timed(fn):
+        for _ in range(2):
+            fn()
+        ts = []
+        for k in range(steps):
+            flush.fill_(float(k))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    fused_ms = timed(fused)
+    integrate_ms = timed(integrate)
+    asm_ms = timed(standalone)
+    torch.cuda.synchronize()
+    # algorithmic bytes of the standalone assembly: what any assembly must
+    # move, the element matrices and vectors read once and the CSR values and
+    # right-hand side written once
+    bytes_asm = (int(A.numel()) + int(bv.numel()) + asm.nnz + asm.n_dof) * vsize
+    return {
+        "dof_map": "vertex-sharing: 6 local functions on the prism's mesh vertices, the rest private (synthetic)",
+        "n_dof": asm.n_dof, "nnz": asm.nnz, "colours": asm.n_colours, "chunks": asm.n_chunks,
+        "host_build_s": round(t2 - t1, 3), "dof_map_s": round(t1 - t0, 3),
+        "fused_ms": fused_ms, "fused_elements_per_s": len(w["degree"]) / (fused_ms * 1e-3),
+        "integrate_ms": integrate_ms, "assemble_ms": asm_ms, "unfused_ms": integrate_ms + asm_ms,
+        "assemble_bytes": bytes_asm, "assemble_gbs": bytes_asm / (asm_ms * 1e-3) / 1e9,
+        "fused_equals_unfused": bool(torch.equal(values, values2) and torch.equal(rhs, rhs2)),
+    }
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -273,6 +337,9 @@ def main():
     ap.add_argument("--adjoint", default="quadratic", choices=["quadratic", "general"],
                     help="differentiation workload: the adjoint of the quadratic loss (gA never formed) or the "
                          "general adjoint given gA = u u^T, gb = -u")
+    ap.add_argument("--assemble", action="store_true",
+                    help="also measure colour-by-colour assembly into CSR (vertex-sharing DOF map): the fused "
+                         "integrate-and-assemble step and the assembly of given element matrices")
     ap.add_argument("--elements", type=int, default=0,
                     help="integrate only the first N elements of the workload (small profiling cases); "
                          "0 = the whole workload")
@@ -606,6 +673,12 @@ def main():
         cpu = {"value": rate, "unit": "elements/s", "cores": cores, "kind": "oracle",
                "sample": f"first {ns} elements of the workload ({dt:.1f} s on the host cores)"}
 
+    assembly = None
+    if args.assemble and rank == 0 and world == 1:
+        assembly = assembly_measure(api, w, [g[k] for k in ("geom", "K", "b", "c", "f")], deg, refs, precision,
+                                    flush, max(3, min(args.steps, 10)))
+        assembly["assemble_hbm_frac"] = assembly["assemble_gbs"] / peaks["hbm_gbs"]
+
     if rank == 0:
         line = {
             "metric": metric_name(args), "value": value, "unit": "elements/s", "n_gpus": world,
@@ -624,6 +697,8 @@ def main():
             "fp32_path": fp32_path,
             "plan": plan_choices,
         }
+        if assembly is not None:
+            line["assembly"] = assembly
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.barrier()

@@ -336,16 +336,19 @@ fei_status fei_assembly_pattern(fei_assembly_t as, int64_t *row_ptr, int32_t *co
  * layout fei_integrate writes for the batch the handle describes (A_offset
  * and b_offset of fei_plan_offsets, or the contiguous uniform layout).
  * Types follow prec: double for FEI_FP64, float otherwise.  Both outputs are
- * overwritten.  One launch per colour, in colour order, so the sum of each
- * entry runs in a fixed order.  Asynchronous on the stream. */
+ * overwritten.  One launch per run of elements of equal (degree, colour),
+ * in that order, so the sum of each entry runs in a fixed order (the same
+ * as in fei_integrate_assemble).  Asynchronous on the stream. */
 fei_status fei_assemble(fei_assembly_t as, fei_precision prec, const void *A, const void *b,
                         void *values, void *rhs, fei_stream_t stream);
 
-/* Integration and assembly fused: the handle's elements, grouped by colour
- * and degree into chunks, are integrated chunk by chunk into a scratch
- * buffer that the library allocates on first use (kept with the handle)
- * and sized to stay in L2, and each chunk is assembled from there at once,
- * so no element matrix goes to HBM.  batch: as for fei_integrate, with the
+/* Integration and assembly fused: the handle's elements, grouped by degree
+ * into chunks (all elements of a degree unless their FP32 element matrices
+ * pass 256 MB), are integrated chunk by chunk into a scratch buffer that
+ * the library allocates on first use (kept with the handle), and each
+ * chunk is assembled from there, run by (degree, colour) run, before the
+ * next, so a batch never needs memory for all of its element matrices.
+ * batch: as for fei_integrate, with the
  * handle's element count and degrees (a degree array if and only if the
  * handle was created with one, holding the same degrees); its A_offset and
  * b_offset are not used (no element output).  values, rhs: as for

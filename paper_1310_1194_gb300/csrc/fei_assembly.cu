@@ -14,16 +14,24 @@
 //      held by an earlier element that shares a global function with it;
 //   3. CSR pattern: row r lists, sorted, the global functions of all the
 //      elements that contain r;
-//   4. scatter map: for entry (i, j) of element e, the place of l2g_e[j] in
-//      row l2g_e[i], counted from the row's start (uint16);
-//   5. chunks for the fused path: elements sorted by (colour, degree) and
-//      split so that a chunk's element matrices fit in a scratch buffer
-//      that stays in the L2 (129 MB).
-// Device part: a block per element adds its N_sh^2 entries at
-// row_ptr[l2g_i] + off and its load vector at rhs[l2g_i].
-// fei_integrate_assemble integrates one chunk into the scratch and
-// assembles it right away, so the element matrices are read back from L2
-// instead of making a round trip through HBM.
+//   4. scatter map.  A row that only one element touches ("private") holds
+//      exactly that element's functions, sorted, so entry (i, j) goes to the
+//      rank of l2g_e[j] among them, the same for every private row of the
+//      element: one uint16 rank per local function.  A shared row needs its
+//      own offsets: for each shared local row i, the place of every l2g_e[j]
+//      in row l2g_e[i] (uint16), reached through a per-row slot;
+//   5. elements sorted by (degree, colour): the runs of equal (degree,
+//      colour) are the assembly launches, in that order, for both entry
+//      points (so both add the contributions of a shared entry in the same
+//      order); for the fused path, the elements of one degree split into
+//      chunks where a chunk's element matrices would pass a size cap.
+// Device part (fei_assemble): the shared rows are cleared, then a block
+// per element stores its entries of private rows (the only contribution
+// they get) and adds those of shared rows, one launch per (degree, colour)
+// run.  fei_integrate_assemble integrates the batch chunk by chunk into one
+// scratch buffer (one forward launch per chunk, all colours of a degree
+// together) and assembles each chunk from it run by run, so that a batch
+// never needs memory for all of its element matrices at once.
 #include <stdint.h>
 #include <string.h>
 
@@ -43,7 +51,8 @@ struct fei_assembly {
   std::vector<int32_t> colour_h;
   std::vector<int64_t> row_ptr_h;  // kept only in host-only mode
   std::vector<int32_t> col_idx_h;
-  std::vector<int64_t> colour_start;  // [n_colours + 1] into elems (sorted by colour, degree)
+  std::vector<int64_t> run_start;  // runs of equal (degree, colour) in elems: [runs + 1]
+  std::vector<int32_t> run_degree;  // [runs]
   struct Chunk {
     int32_t colour, degree;
     int64_t start, n, a_len, b_len;
@@ -55,12 +64,21 @@ struct fei_assembly {
   int32_t *col_idx;
   int64_t *l2g;
   int64_t *loff;  // start of element e in l2g and in b (sum of N_sh before e)
-  int64_t *moff;  // start of element e in A and in the scatter map (sum of N_sh^2)
-  uint16_t *off;
-  int32_t *degree;
+  int64_t *moff;     // start of element e in A (sum of N_sh^2)
+  uint16_t *rank;    // [loff layout] rank of l2g_e[j] among the element's functions
+  int16_t *slot;     // [loff layout] shared-row slot of local row i, -1 = private
+  int64_t *shptr;    // [n_elem] start of element e's shared-row offsets in shoff
+  uint16_t *shoff;   // per shared row: the N_sh places of the element's columns
+  int32_t *shrows;   // global rows touched by several elements (cleared first)
+  int64_t n_shrows;
   int32_t *elems;        // elements sorted by (colour, degree)
   int32_t *chunk_count;  // [chunks] element count of each chunk (the forward's device count)
   int64_t *scr_aoff, *scr_boff;  // start of element e in its chunk's scratch
+  // fused path: two scratch buffers (chunk k uses buffer k % 2), the stream
+  // that assembles while the caller's stream integrates the next chunk, and
+  // the events that order the two
+  // fused path: the chunk scratch (element matrices and vectors), allocated
+  // on first use
   void *scratch_A, *scratch_b;
   size_t scratch_A_bytes, scratch_b_bytes;
 };
@@ -68,43 +86,92 @@ struct fei_assembly {
 namespace fei {
 namespace {
 
-constexpr int64_t kChunkBytes = 48ll << 20;  // FP32 element matrices of one chunk
+constexpr int64_t kChunkBytes = 256ll << 20;  // cap of one chunk's FP32 element matrices
 
 template <typename T>
-__global__ void assemble_kernel(const int32_t *elems, int64_t n, const int32_t *degree, const T *A,
-                                const int64_t *aoff, const T *bv, const int64_t *boff, const int64_t *l2g,
-                                const int64_t *loff, const int64_t *moff, const uint16_t *off,
-                                const int64_t *row_ptr, T *values, T *rhs) {
-  __shared__ int64_t rstart[nsh_of(kPMax)];
+__global__ void clear_rows_kernel(const int32_t *rows, int64_t n, const int64_t *row_ptr, T *values) {
   for (int64_t k = blockIdx.x; k < n; k += gridDim.x) {
+    const int64_t r0 = row_ptr[rows[k]], r1 = row_ptr[rows[k] + 1];
+    for (int64_t t = r0 + threadIdx.x; t < r1; t += blockDim.x) values[t] = T(0);
+  }
+}
+
+// One run of elements of a single degree (s functions each) that share no
+// global function: work unit u is rows [rb part, rb part + rb) of element
+// k = u / units_per_element (a warp per row, lanes over columns), so that a
+// run of few large elements still fills the GPU.
+template <typename T>
+__global__ void assemble_kernel(const int32_t *elems, int64_t n, int s, int rb, const T *A, const int64_t *aoff,
+                                const T *bv, const int64_t *boff, const int64_t *l2g, const int64_t *loff,
+                                const uint16_t *rank, const int16_t *slot, const int64_t *shptr,
+                                const uint16_t *shoff, const int64_t *row_ptr, T *values, T *rhs) {
+  __shared__ int64_t rstart[nsh_of(kPMax)];
+  __shared__ int16_t sl[nsh_of(kPMax)];
+  __shared__ uint16_t rk[nsh_of(kPMax)];
+  const int upe = (s + rb - 1) / rb;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int64_t u = blockIdx.x; u < n * upe; u += gridDim.x) {
+    const int64_t k = u / upe;
+    const int i0 = (int)(u - k * upe) * rb;
+    const int nr = s - i0 < rb ? s - i0 : rb;
     const int e = elems[k];
-    const int s = nsh_of(degree[e]);
-    const int64_t *g = l2g + loff[e];
-    __syncthreads();  // the previous element's row starts are no longer read
-    for (int i = threadIdx.x; i < s; i += blockDim.x) {
-      rstart[i] = row_ptr[g[i]];
-      rhs[g[i]] += bv[boff[e] + i];
+    const int64_t lo = loff[e];
+    __syncthreads();  // the previous unit's row data are no longer read
+    for (int j = threadIdx.x; j < s; j += blockDim.x) rk[j] = rank[lo + j];
+    for (int t = threadIdx.x; t < nr; t += blockDim.x) {
+      const int64_t g = l2g[lo + i0 + t];
+      rstart[t] = row_ptr[g];
+      sl[t] = slot[lo + i0 + t];
+      rhs[g] += bv[boff[e] + i0 + t];
     }
     __syncthreads();
     const T *Ae = A + aoff[e];
-    const uint16_t *oe = off + moff[e];
-    for (int idx = threadIdx.x; idx < s * s; idx += blockDim.x) {
-      const int i = idx / s;
-      values[rstart[i] + oe[idx]] += Ae[idx];
+    const uint16_t *so = shoff + shptr[e];
+    for (int t = warp; t < nr; t += nw) {
+      const int i = i0 + t, q = sl[t];
+      const int64_t base = rstart[t];
+      const T *Ai = Ae + (int64_t)i * s;
+      if (q < 0) {
+        for (int j = lane; j < s; j += 32) values[base + rk[j]] = Ai[j];  // a private row: its only contribution
+      } else {
+        const uint16_t *o = so + q * s;
+        for (int j = lane; j < s; j += 32) values[base + o[j]] += Ai[j];
+      }
     }
   }
 }
 
+// elems[0 .. n): one run (one degree p)
 template <typename T>
-fei_status launch_assemble(const fei_assembly *as, const int32_t *elems, int64_t n, const void *A,
+fei_status launch_assemble(const fei_assembly *as, int p, const int32_t *elems, int64_t n, const void *A,
                            const int64_t *aoff, const void *bv, const int64_t *boff, void *values, void *rhs,
                            cudaStream_t s) {
   if (n <= 0) return FEI_OK;
-  const int64_t blocks = n < 152 * 16 ? n : 152 * 16;
-  assemble_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(elems, n, as->degree, (const T *)A, aoff, (const T *)bv,
-                                                      boff, as->l2g, as->loff, as->moff, as->off, as->row_ptr,
-                                                      (T *)values, (T *)rhs);
+  const int sh = nsh_of(p);
+  // rows per work unit: whole elements when the run has enough of them,
+  // else split so that the run gives about 8 units per SM (at least 32 rows)
+  int64_t rb = (n * sh + 152 * 8 - 1) / (152 * 8);
+  rb = rb < 32 ? 32 : (rb > sh ? sh : rb);
+  const int64_t units = n * ((sh + rb - 1) / rb);
+  const int64_t blocks = units < 152 * 16 ? units : 152 * 16;
+  assemble_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(elems, n, sh, (int)rb, (const T *)A, aoff, (const T *)bv, boff,
+                                                      as->l2g, as->loff, as->rank, as->slot, as->shptr, as->shoff,
+                                                      as->row_ptr, (T *)values, (T *)rhs);
   FEI_CUDA_TRY(cudaGetLastError(), "assemble_kernel launch");
+  return FEI_OK;
+}
+
+// values of the shared rows and the whole rhs set to zero (private rows are
+// stored, not added, by the assembly)
+fei_status clear_outputs(const fei_assembly *as, size_t vb, void *values, void *rhs, cudaStream_t s) {
+  FEI_CUDA_TRY(cudaMemsetAsync(rhs, 0, vb * as->n_dof, s), "cudaMemsetAsync(rhs)");
+  if (as->n_shrows == 0) return FEI_OK;
+  const int64_t blocks = as->n_shrows < 152 * 16 ? as->n_shrows : 152 * 16;
+  if (vb == 8)
+    clear_rows_kernel<double><<<(unsigned)blocks, 256, 0, s>>>(as->shrows, as->n_shrows, as->row_ptr, (double *)values);
+  else
+    clear_rows_kernel<float><<<(unsigned)blocks, 256, 0, s>>>(as->shrows, as->n_shrows, as->row_ptr, (float *)values);
+  FEI_CUDA_TRY(cudaGetLastError(), "clear_rows_kernel launch");
   return FEI_OK;
 }
 
@@ -114,8 +181,11 @@ void free_device(fei_assembly *as) {
   cudaFree(as->l2g);
   cudaFree(as->loff);
   cudaFree(as->moff);
-  cudaFree(as->off);
-  cudaFree(as->degree);
+  cudaFree(as->rank);
+  cudaFree(as->slot);
+  cudaFree(as->shptr);
+  cudaFree(as->shoff);
+  cudaFree(as->shrows);
   cudaFree(as->elems);
   cudaFree(as->chunk_count);
   cudaFree(as->scr_aoff);
@@ -246,49 +316,63 @@ fei_status build(fei_assembly *as, const int64_t *l2g) {
       for (const int64_t c : tmp) *dst++ = (int32_t)c;
     }
   }
-  // 4. scatter map
-  std::vector<uint16_t> off;
-  try {
-    off.resize(moff[n]);
-  } catch (const std::bad_alloc &) {
-    return set_error(FEI_ERR_OOM, "fei_assembly_create: host scatter map of %lld entries", (long long)moff[n]);
+  // 4. scatter map: ranks (computed above), slots of shared rows and
+  // their offsets, and the list of shared rows
+  std::vector<int16_t> slot(loff[n], -1);
+  std::vector<int64_t> shptr(n + 1, 0);
+  for (int64_t e = 0; e < n; ++e) {
+    const int64_t s = loff[e + 1] - loff[e];
+    int64_t q = 0;
+    for (int64_t i = 0; i < s; ++i) {
+      const int64_t r = l2g[loff[e] + i];
+      if (inc_ptr[r + 1] - inc_ptr[r] > 1) slot[loff[e] + i] = (int16_t)q++;
+    }
+    shptr[e + 1] = shptr[e] + q * s;
   }
+  std::vector<uint16_t> shoff(shptr[n]);
   for (int64_t e = 0; e < n; ++e) {
     const int64_t s = loff[e + 1] - loff[e];
     for (int64_t i = 0; i < s; ++i) {
+      const int16_t q = slot[loff[e] + i];
+      if (q < 0) continue;
       const int64_t r = l2g[loff[e] + i];
-      uint16_t *o = off.data() + moff[e] + i * s;
-      if (inc_ptr[r + 1] - inc_ptr[r] == 1) {
-        for (int64_t j = 0; j < s; ++j) o[j] = rank[loff[e] + j];
-      } else {
-        const int32_t *b = col_idx.data() + row_ptr[r], *end = col_idx.data() + row_ptr[r + 1];
-        for (int64_t j = 0; j < s; ++j) o[j] = (uint16_t)(std::lower_bound(b, end, (int32_t)l2g[loff[e] + j]) - b);
-      }
+      const int32_t *b = col_idx.data() + row_ptr[r], *end = col_idx.data() + row_ptr[r + 1];
+      uint16_t *o = shoff.data() + shptr[e] + q * s;
+      for (int64_t j = 0; j < s; ++j) o[j] = (uint16_t)(std::lower_bound(b, end, (int32_t)l2g[loff[e] + j]) - b);
     }
   }
-  // 5. elements by (colour, degree), colour ranges, chunks
+  std::vector<int32_t> shrows;
+  for (int64_t d = 0; d < nd; ++d)
+    if (inc_ptr[d + 1] - inc_ptr[d] > 1) shrows.push_back((int32_t)d);
+  as->n_shrows = (int64_t)shrows.size();
+  // 5. elements by (degree, colour), runs, chunks
   std::vector<int32_t> elems(n);
   for (int64_t e = 0; e < n; ++e) elems[e] = (int32_t)e;
   std::stable_sort(elems.begin(), elems.end(), [&](int32_t x, int32_t y) {
-    return as->colour_h[x] != as->colour_h[y] ? as->colour_h[x] < as->colour_h[y]
-                                              : as->degree_h[x] < as->degree_h[y];
+    return as->degree_h[x] != as->degree_h[y] ? as->degree_h[x] < as->degree_h[y]
+                                              : as->colour_h[x] < as->colour_h[y];
   });
-  as->colour_start.assign(as->n_colours + 1, 0);
-  for (int64_t e = 0; e < n; ++e) ++as->colour_start[as->colour_h[e] + 1];
-  for (int32_t c = 0; c < as->n_colours; ++c) as->colour_start[c + 1] += as->colour_start[c];
+  as->run_start.assign(1, 0);
+  as->run_degree.clear();
+  for (int64_t k = 1; k <= n; ++k)
+    if (k == n || as->degree_h[elems[k]] != as->degree_h[elems[k - 1]] ||
+        as->colour_h[elems[k]] != as->colour_h[elems[k - 1]]) {
+      as->run_degree.push_back(as->degree_h[elems[k - 1]]);
+      as->run_start.push_back(k);
+    }
   std::vector<int64_t> scr_aoff(n), scr_boff(n);
   as->chunks.clear();
   as->max_chunk_a = as->max_chunk_b = 0;
   for (int64_t k = 0; k < n;) {
     const int32_t e0 = elems[k], c = as->colour_h[e0], p = as->degree_h[e0];
     const int64_t s = nsh_of(p);
-    // enough elements for a few tiles per SM, and no more than the L2 budget
-    // allows beyond that
+    // all elements of a degree unless their matrices pass the cap (the
+    // forward kernels want large launches), and at least a few tiles per SM
     int64_t cap = kChunkBytes / (4 * s * s);
     const int64_t tiles_min = 8ll * 152 * 128 / s;
     if (cap < tiles_min) cap = tiles_min;
     fei_assembly::Chunk ch{c, p, k, 0, 0, 0};
-    while (k < n && ch.n < cap && as->colour_h[elems[k]] == c && as->degree_h[elems[k]] == p) {
+    while (k < n && ch.n < cap && as->degree_h[elems[k]] == p) {
       scr_aoff[elems[k]] = ch.a_len;
       scr_boff[elems[k]] = ch.b_len;
       ch.a_len += s * s;
@@ -313,10 +397,14 @@ fei_status build(fei_assembly *as, const int64_t *l2g) {
   if ((st = upload(&as->l2g, l2g, (size_t)loff[n]))) return st;
   if ((st = upload(&as->loff, loff.data(), loff.size()))) return st;
   if ((st = upload(&as->moff, moff.data(), moff.size()))) return st;
-  if ((st = upload(&as->off, off.data(), off.size()))) return st;
-  if ((st = upload(&as->degree, as->degree_h.data(), as->degree_h.size()))) return st;
+  if ((st = upload(&as->rank, rank.data(), rank.size()))) return st;
+  if ((st = upload(&as->slot, slot.data(), slot.size()))) return st;
+  if ((st = upload(&as->shptr, shptr.data(), shptr.size()))) return st;
+  if ((st = upload(&as->shoff, shoff.data(), shoff.size()))) return st;
+  if ((st = upload(&as->shrows, shrows.data(), shrows.size()))) return st;
   if ((st = upload(&as->elems, elems.data(), elems.size()))) return st;
   if ((st = upload(&as->chunk_count, ccount.data(), ccount.size()))) return st;
+
   if ((st = upload(&as->scr_aoff, scr_aoff.data(), scr_aoff.size()))) return st;
   if ((st = upload(&as->scr_boff, scr_boff.data(), scr_boff.size()))) return st;
   return FEI_OK;
@@ -442,12 +530,12 @@ extern "C" fei_status fei_assemble(fei_assembly_t as, fei_precision prec, const 
   if ((st = value_type(prec, &vb))) return st;
   if (!A || !b || !values || !rhs) return set_error(FEI_ERR_INVALID_ARG, "A, b, values and rhs are required");
   cudaStream_t s = (cudaStream_t)stream;
-  FEI_CUDA_TRY(cudaMemsetAsync(values, 0, vb * as->nnz, s), "cudaMemsetAsync(values)");
-  FEI_CUDA_TRY(cudaMemsetAsync(rhs, 0, vb * as->n_dof, s), "cudaMemsetAsync(rhs)");
-  for (int32_t c = 0; c < as->n_colours; ++c) {
-    const int64_t k0 = as->colour_start[c], k1 = as->colour_start[c + 1];
-    st = vb == 8 ? launch_assemble<double>(as, as->elems + k0, k1 - k0, A, as->moff, b, as->loff, values, rhs, s)
-                 : launch_assemble<float>(as, as->elems + k0, k1 - k0, A, as->moff, b, as->loff, values, rhs, s);
+  if ((st = clear_outputs(as, vb, values, rhs, s))) return st;
+  for (size_t r = 0; r + 1 < as->run_start.size(); ++r) {
+    const int64_t k0 = as->run_start[r], k1 = as->run_start[r + 1];
+    const int p = as->run_degree[r];
+    st = vb == 8 ? launch_assemble<double>(as, p, as->elems + k0, k1 - k0, A, as->moff, b, as->loff, values, rhs, s)
+                 : launch_assemble<float>(as, p, as->elems + k0, k1 - k0, A, as->moff, b, as->loff, values, rhs, s);
     if (st) return st;
   }
   return FEI_OK;
@@ -479,27 +567,26 @@ extern "C" fei_status fei_integrate_assemble(fei_assembly_t as, const fei_refere
   if ((st = check_refs(refs, nrefs, as->device, by_p))) return st;
   for (const auto &ch : as->chunks)
     if (!by_p[ch.degree]) return set_error(FEI_ERR_INVALID_DEGREE, "no reference for degree %d", ch.degree);
-  // scratch for the largest chunk (FP64 size, so that any precision fits)
+  // the chunk scratch (FP64 size, so that any precision fits), on first use
   const size_t need_a = 8 * (size_t)as->max_chunk_a, need_b = 8 * (size_t)as->max_chunk_b;
-  if (as->scratch_A_bytes < need_a) {
+  if (as->scratch_A_bytes < need_a || as->scratch_b_bytes < need_b) {
     cudaFree(as->scratch_A);
-    as->scratch_A = nullptr;
-    as->scratch_A_bytes = 0;
-    cudaError_t e = cudaMalloc(&as->scratch_A, need_a);
-    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? set_error(FEI_ERR_OOM, "assembly scratch") : cuda_error(e, "cudaMalloc");
-    as->scratch_A_bytes = need_a;
-  }
-  if (as->scratch_b_bytes < need_b) {
     cudaFree(as->scratch_b);
-    as->scratch_b = nullptr;
-    as->scratch_b_bytes = 0;
-    cudaError_t e = cudaMalloc(&as->scratch_b, need_b);
-    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? set_error(FEI_ERR_OOM, "assembly scratch") : cuda_error(e, "cudaMalloc");
+    as->scratch_A = as->scratch_b = nullptr;
+    as->scratch_A_bytes = as->scratch_b_bytes = 0;
+    cudaError_t e = cudaMalloc(&as->scratch_A, need_a);
+    if (e == cudaSuccess) e = cudaMalloc(&as->scratch_b, need_b);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return e == cudaErrorMemoryAllocation ? set_error(FEI_ERR_OOM, "assembly scratch") : cuda_error(e, "cudaMalloc");
+    }
+    as->scratch_A_bytes = need_a;
     as->scratch_b_bytes = need_b;
   }
   cudaStream_t s = (cudaStream_t)stream;
-  FEI_CUDA_TRY(cudaMemsetAsync(values, 0, vb * as->nnz, s), "cudaMemsetAsync(values)");
-  FEI_CUDA_TRY(cudaMemsetAsync(rhs, 0, vb * as->n_dof, s), "cudaMemsetAsync(rhs)");
+  if ((st = clear_outputs(as, vb, values, rhs, s))) return st;
+  // chunk by chunk, in (colour, degree) order: integrate into the scratch,
+  // then assemble from it (the next chunk's forward follows on the stream)
   for (size_t ci = 0; ci < as->chunks.size(); ++ci) {
     const auto &ch = as->chunks[ci];
     const fei_reference *r = by_p[ch.degree];
@@ -508,14 +595,21 @@ extern "C" fei_status fei_integrate_assemble(fei_assembly_t as, const fei_refere
     a.n_work = ch.n;
     a.count = as->chunk_count + ci;
     a.list = as->elems + ch.start;
-    a.A_off = as->scr_aoff;
-    a.b_off = as->scr_boff;
+    a.A_off = nullptr;
+    a.b_off = nullptr;
+    a.out_by_item = 1;  // the chunk's matrices in list order: scr_aoff / scr_boff
     if ((st = launch_forward(ch.degree, prec, r, a, ch.n, s))) return st;
-    st = vb == 8 ? launch_assemble<double>(as, a.list, ch.n, as->scratch_A, as->scr_aoff, as->scratch_b, as->scr_boff,
-                                           values, rhs, s)
-                 : launch_assemble<float>(as, a.list, ch.n, as->scratch_A, as->scr_aoff, as->scratch_b, as->scr_boff,
-                                          values, rhs, s);
-    if (st) return st;
+    // the chunk's part of each (degree, colour) run, one launch each
+    const int64_t c0 = ch.start, c1 = ch.start + ch.n;
+    const size_t r0 = std::upper_bound(as->run_start.begin(), as->run_start.end(), c0) - as->run_start.begin() - 1;
+    for (size_t rr = r0; rr + 1 < as->run_start.size() && as->run_start[rr] < c1; ++rr) {
+      const int64_t k0 = std::max(as->run_start[rr], c0), k1 = std::min(as->run_start[rr + 1], c1);
+      st = vb == 8 ? launch_assemble<double>(as, ch.degree, as->elems + k0, k1 - k0, as->scratch_A, as->scr_aoff,
+                                             as->scratch_b, as->scr_boff, values, rhs, s)
+                   : launch_assemble<float>(as, ch.degree, as->elems + k0, k1 - k0, as->scratch_A, as->scr_aoff,
+                                            as->scratch_b, as->scr_boff, values, rhs, s);
+      if (st) return st;
+    }
   }
   return FEI_OK;
 }

@@ -220,7 +220,7 @@ __global__ void __launch_bounds__(SmallCfg<T, P>::WPB * 32) cc_small_kernel(FwdA
       const int sl = idx / (NSH * NSH), ij = idx - sl * (NSH * NSH);
       const int i = ij / NSH, j = ij - i * NSH;
       const int64_t e = a.list ? (int64_t)a.list[item0 + sl] : item0 + sl;
-      const int64_t aoff = a.A_off ? a.A_off[e] : e * (int64_t)(NSH * NSH);
+      const int64_t aoff = out_a(a, item0 + sl, e, NSH);
       const T *H = Hs(sl);
       T acc = T(0);
 #pragma unroll 4
@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(SmallCfg<T, P>::WPB * 32) cc_small_kernel(FwdA
     for (int idx = lane; idx < nel * NSH; idx += 32) {
       const int sl = idx / NSH, i = idx - sl * NSH;
       const int64_t e = a.list ? (int64_t)a.list[item0 + sl] : item0 + sl;
-      const int64_t boff = a.b_off ? a.b_off[e] : e * (int64_t)NSH;
+      const int64_t boff = out_b(a, item0 + sl, e, NSH);
       const T *D = Ds(sl);
       T acc = T(0);
       for (int qq = 0; qq < NQ; ++qq) acc += D[16 * qq + 13] * Gs[(4 * qq) * NSH + i];
@@ -436,7 +436,7 @@ __global__ void __launch_bounds__(256) cc_tile_kernel(FwdArgs a) {
       __syncthreads();
     }
     const int st = sm.status;
-    const int64_t aoff = a.A_off ? a.A_off[e] : e * (int64_t)(NSH * NSH);
+    const int64_t aoff = out_a(a, item, e, NSH);
     T *A = reinterpret_cast<T *>(a.A) + aoff;
 #pragma unroll
     for (int r = 0; r < RM; ++r) {
@@ -448,7 +448,7 @@ __global__ void __launch_bounds__(256) cc_tile_kernel(FwdArgs a) {
       }
     }
     if (cb == 0 && tid < BM && brow < NSH) {
-      const int64_t boff = a.b_off ? a.b_off[e] : e * (int64_t)NSH;
+      const int64_t boff = out_b(a, item, e, NSH);
       reinterpret_cast<T *>(a.bv)[boff + brow] = st ? T(0) : bacc;
     }
     if (tid == 0 && rb == 0 && cb == 0) a.status[e] = st;

@@ -55,6 +55,10 @@ struct FwdArgs {
   int coef_mode;
   const double *K, *b, *c, *f;
   const int64_t *A_off, *b_off, *q_off;
+  // with A_off and b_off null: 1 = work item k's outputs at k N_sh^2 and
+  // k N_sh (a list written contiguously in list order), 0 = at e N_sh^2 and
+  // e N_sh for element e
+  int out_by_item;
   void *A;
   void *bv;
   int32_t *status;
@@ -64,6 +68,14 @@ struct FwdArgs {
   const double *tnode;
   const float *G32T;
 };
+
+// Start of work item k (element e) in A and in b (s = N_sh).
+__device__ __forceinline__ int64_t out_a(const FwdArgs &a, int64_t k, int64_t e, int64_t s) {
+  return a.A_off ? a.A_off[e] : (a.out_by_item ? k : e) * s * s;
+}
+__device__ __forceinline__ int64_t out_b(const FwdArgs &a, int64_t k, int64_t e, int64_t s) {
+  return a.b_off ? a.b_off[e] : (a.out_by_item ? k : e) * s;
+}
 
 struct BwdArgs {
   int64_t n_work;

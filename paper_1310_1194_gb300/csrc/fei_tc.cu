@@ -561,8 +561,8 @@ __global__ void __launch_bounds__(TcCfg<P, V>::NTHREADS, 1)
         }
         if (lane == 0) {
           E.e = e;
-          E.aoff = a.A_off ? a.A_off[e] : e * (int64_t)(NSH * NSH);
-          E.boff = a.b_off ? a.b_off[e] : e * (int64_t)NSH;
+          E.aoff = out_a(a, kn0 + i, e, NSH);
+          E.boff = out_b(a, kn0 + i, e, NSH);
           E.qoff = a.q_off ? a.q_off[e] : e * (int64_t)NQ;
           E.mbits = 0;
         }
@@ -930,7 +930,7 @@ __global__ void __launch_bounds__(TcCfg<P, V>::NTHREADS, 1)
     const int myrow = quarter * 32 + lane;
     // a contiguous output (uniform degree, no element list, 16-byte aligned):
     // the tile's rows of A_e are one range of A
-    const bool contiguous = a.A_off == nullptr && a.list == nullptr &&
+    const bool contiguous = a.A_off == nullptr && (a.list == nullptr || a.out_by_item) &&
                             (reinterpret_cast<uintptr_t>(a.A) & 15u) == 0u;
     float rreg[C::RREG > 0 ? C::RREG : 1];
     int it = 0;
