@@ -360,6 +360,15 @@ fei_status fei_integrate_assemble(fei_assembly_t as, const fei_reference_t *refs
                                   const fei_batch *batch, fei_precision prec, void *values,
                                   void *rhs, int32_t *elem_status, fei_stream_t stream);
 
+/* Fault injection for tests: the time limit of the tensor-core forward's
+ * pipeline waits on the current device, in nanoseconds (0 restores the
+ * default, 2 s).  A block whose wait runs out raises an abort flag, marks
+ * the elements of its remaining tiles FEI_ERR_TIMEOUT, lets its in-flight
+ * tensor-core work and copies finish, frees its tensor memory and returns:
+ * nothing traps and the context stays usable.  A tiny limit makes a launch
+ * report FEI_ERR_TIMEOUT without any fault.  Synchronous. */
+fei_status fei_debug_set_wait_limit(uint64_t ns);
+
 /* Thread-local description of the last failure of the calling thread. */
 const char *fei_last_error_string(void);
 

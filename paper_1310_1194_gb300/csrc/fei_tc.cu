@@ -74,6 +74,11 @@ struct TcImage {
 namespace {
 
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s per wait
+// The limit of the pipeline waits (mbar_wait), per device: kWaitLimitNs,
+// or what fei_debug_set_wait_limit set for fault-injection tests.  The
+// drain of in-flight MMAs before an aborted block frees its tensor memory
+// always uses kWaitLimitNs.
+__device__ uint64_t g_wait_limit_ns = kWaitLimitNs;
 
 // ---------------------------------------------------------------------------
 // PTX wrappers
@@ -116,15 +121,15 @@ __device__ __forceinline__ bool mbar_try_wait_sleep(uint32_t a, uint32_t parity)
       : "memory");
   return ok != 0;
 }
-// Bounded wait: false (and the abort flag raised) after kWaitLimitNs, or as
-// soon as another role raised the flag (checked between sleeps).
+// Bounded wait: false (and the abort flag raised) after g_wait_limit_ns, or
+// as soon as another role raised the flag (checked between sleeps).
 __device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int *abort_flag) {
   if (mbar_try_wait(a, parity)) return true;
   const uint64_t t0 = global_ns();
   for (;;) {
     if (mbar_try_wait_sleep(a, parity)) return true;
     if (*abort_flag) return false;
-    if (global_ns() - t0 > kWaitLimitNs) {
+    if (global_ns() - t0 > g_wait_limit_ns) {
       *abort_flag = 1;
       return false;
     }
@@ -1356,3 +1361,9 @@ fei_status launch_tc_forward(int p, const fei_reference *ref, const FwdArgs &a, 
 }
 
 }  // namespace fei
+
+extern "C" fei_status fei_debug_set_wait_limit(uint64_t ns) {
+  const uint64_t v = ns ? ns : fei::kWaitLimitNs;
+  FEI_CUDA_TRY(cudaMemcpyToSymbol(fei::g_wait_limit_ns, &v, sizeof(v)), "cudaMemcpyToSymbol(wait limit)");
+  return FEI_OK;
+}

@@ -359,3 +359,37 @@ def test_tc_operand_scale_covers_every_point(api, p):
     Aor = Ao.reshape(n, -1)
     for e in range(n):
         assert np.linalg.norm(Ah[e] - Aor[e]) <= 1e-6 * np.linalg.norm(Aor[e]), e
+
+
+def test_tc_wait_timeout_reports_status_and_context_survives(api):
+    """Fault injection: with a 1 us limit on the tensor-core forward's
+    pipeline waits, blocks give up, flag their remaining elements
+    FEI_ERR_TIMEOUT and return without any fault; elements of tiles that
+    finished keep exact results, and the next launch with the default limit
+    is whole and correct."""
+    from paper_1310_1194_gb300 import _lib
+    w = inputs.workload("p4", n_max=3000)
+    g = [dev(w[k]) for k in ("geom", "K", "b", "c", "f")]
+    _lib.check(_lib.lib.fei_debug_set_wait_limit(1000), "fei_debug_set_wait_limit")
+    try:
+        A, bv, st, _ = api.fei_integrate(*g, p=4, precision="tc_f16x3")
+        torch.cuda.synchronize()
+    finally:
+        _lib.check(_lib.lib.fei_debug_set_wait_limit(0), "fei_debug_set_wait_limit")
+    stc = st.cpu().numpy()
+    assert (stc == _lib.FEI_ERR_TIMEOUT).sum() > 0
+    assert set(np.unique(stc).tolist()) <= {0, _lib.FEI_ERR_TIMEOUT}
+    A2, b2, st2, _ = api.fei_integrate(*g, p=4, precision="tc_f16x3")
+    torch.cuda.synchronize()
+    assert int(st2.abs().max()) == 0
+    s = api.nsh(4)
+    done = np.flatnonzero(stc == 0)
+    if len(done):
+        Ad = A.view(-1, s * s)[torch.from_numpy(done).cuda()]
+        assert torch.equal(Ad, A2.view(-1, s * s)[torch.from_numpy(done).cuda()])
+    idx = np.array([0, 1500, 2999])
+    Ao, bo, so, _ = oracle.integrate(w["geom"][idx], w["K"][idx], w["b"][idx], w["c"][idx], w["f"][idx], p=4)
+    Ah = A2.view(-1, s * s)[torch.from_numpy(idx).cuda()].double().cpu().numpy()
+    for j in range(len(idx)):
+        ao = Ao[j * s * s:(j + 1) * s * s]
+        assert np.linalg.norm(Ah[j] - ao) <= 1e-6 * np.linalg.norm(ao)
