@@ -250,6 +250,14 @@ fei_status fei_plan_tune(fei_plan_t plan, const fei_batch *batch, void *A_out,
 fei_status fei_plan_choice(fei_plan_t plan, int p, int *variant, int64_t *grid_cap,
                            float *tuned_ms);
 
+/* Sets the choice for degree p, e.g. one that fei_plan_tune measured in an
+ * earlier process on the same GPU model (the tuning cache persisted by the
+ * caller).  variant: a warp-role variant of the tensor-core kernel (0 ..
+ * count - 1 under FEI_TC_F16X3 at p >= 3, else 0); grid_cap: blocks, 0 =
+ * the kernel's default.  The plan's graph is recaptured on the next
+ * fei_plan_execute.  Errors: INVALID_ARG, INVALID_DEGREE. */
+fei_status fei_plan_set_choice(fei_plan_t plan, int p, int variant, int64_t grid_cap);
+
 /* Batch-level summary of the per-element statuses (device int32
  * [n_elem], as written by fei_integrate): summary (device int32 [2])
  * receives the worst status (FEI_ERR_NONFINITE over

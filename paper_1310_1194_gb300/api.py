@@ -294,6 +294,31 @@ class Plan:
               "fei_plan_choice")
         return v.value, g.value, t.value
 
+    def set_choice(self, p: int, variant: int, grid_cap: int):
+        check(lib.fei_plan_set_choice(self.handle, int(p), int(variant), int(grid_cap)), "fei_plan_set_choice")
+
+    def save_choices(self, path: str):
+        """The tuning cache: this plan's per-degree choices as JSON, keyed by
+        the GPU model and the precision."""
+        import json
+        data = {"gpu": torch.cuda.get_device_name(), "precision": self.precision,
+                "degrees": {str(p): dict(zip(("variant", "grid_cap", "tuned_ms"), self.choice(p)))
+                            for p in range(1, 8)}}
+        with open(path, "w") as fh:
+            json.dump(data, fh, indent=1)
+
+    def load_choices(self, path: str) -> bool:
+        """Applies a cache written by save_choices on the same GPU model and
+        precision; returns False (and changes nothing) otherwise."""
+        import json
+        with open(path) as fh:
+            data = json.load(fh)
+        if data.get("gpu") != torch.cuda.get_device_name() or data.get("precision") != self.precision:
+            return False
+        for p, c in data["degrees"].items():
+            self.set_choice(int(p), c["variant"], c["grid_cap"])
+        return True
+
     def __del__(self):
         h = getattr(self, "handle", None)
         if h is not None and h.value:

@@ -337,3 +337,19 @@ extern "C" fei_status fei_plan_choice(fei_plan_t plan, int p, int *variant, int6
   if (tuned_ms) *tuned_ms = plan->tuned_ms[p];
   return FEI_OK;
 }
+
+extern "C" fei_status fei_plan_set_choice(fei_plan_t plan, int p, int variant, int64_t grid_cap) {
+  if (!plan) return set_error(FEI_ERR_INVALID_ARG, "fei_plan_set_choice: plan is NULL");
+  if (p < 1 || p > kPMax) return set_error(FEI_ERR_INVALID_DEGREE, "fei_plan_set_choice: degree %d", p);
+  const int nv = tc_path(plan->prec, p) ? tc_variant_count(p) : 1;
+  if (variant < 0 || variant >= nv)
+    return set_error(FEI_ERR_INVALID_ARG, "fei_plan_set_choice: variant %d for degree %d", variant, p);
+  if (grid_cap < 0 || grid_cap > 2147483647LL)
+    return set_error(FEI_ERR_INVALID_ARG, "fei_plan_set_choice: grid cap %lld", (long long)grid_cap);
+  plan->variant[p] = variant;
+  plan->grid_cap[p] = grid_cap;
+  plan->tuned_ms[p] = -1.f;
+  drop_graph(plan);  // the next execute captures with the new choice
+  return FEI_OK;
+}
+

@@ -62,6 +62,8 @@ def test_argument_errors_before_any_cuda_call(lib):
     assert lib.fei_plan_tune(None, None, None, None, None, None) == 1
     lib.fei_plan_choice.argtypes = [vp, ctypes.c_int, vp, vp, vp]
     assert lib.fei_plan_choice(None, 3, None, None, None) == 1
+    lib.fei_plan_set_choice.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int64]
+    assert lib.fei_plan_set_choice(None, 3, 0, 0) == 1
     assert lib.fei_plan_destroy(None) == 0
     lib.fei_integrate_backward_quadratic.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int, vp, vp, vp, vp]
     assert lib.fei_integrate_backward_quadratic(None, 1, None, 0, None, None, None, None) == 1

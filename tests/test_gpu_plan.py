@@ -95,3 +95,36 @@ def test_plan_rejects_oversized_batch():
     with pytest.raises(_lib.FeiError) as ei:
         plan.execute(g["geom"], g["K"], g["b"], g["c"], g["f"], degree=deg, layout=layout)
     assert ei.value.status == _lib.FEI_ERR_INVALID_ARG
+
+
+def test_plan_tuning_cache_round_trip(tmp_path):
+    """Choices saved by one plan and loaded into another give the same
+    kernel shapes and the same results; a cache for another precision is
+    not applied."""
+    from paper_1310_1194_gb300 import api, _lib
+    w, g, deg = _mixed(500)
+    n = g["geom"].shape[0]
+    layout = api.fei_plan_offsets(deg)
+    args = (g["geom"], g["K"], g["b"], g["c"], g["f"])
+    tuned = api.Plan(max_elem=n, precision="tc_f16x3")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        tuned.tune(*args, degree=deg, layout=layout)
+        A1, b1, _, _ = tuned.execute(*args, degree=deg, layout=layout)
+    s.synchronize()
+    path = str(tmp_path / "plan_cache.json")
+    tuned.save_choices(path)
+    loaded = api.Plan(max_elem=n, precision="tc_f16x3")
+    assert loaded.load_choices(path)
+    with torch.cuda.stream(s):
+        A2, b2, st2, _ = loaded.execute(*args, degree=deg, layout=layout)
+    s.synchronize()
+    for p in range(1, 8):
+        assert tuned.choice(p)[:2] == loaded.choice(p)[:2]
+    assert torch.equal(A1, A2) and torch.equal(b1, b2) and int(st2.abs().max()) == 0
+    other = api.Plan(max_elem=n, precision="fp32")
+    before = [other.choice(p) for p in range(1, 8)]
+    assert not other.load_choices(path)
+    assert [other.choice(p) for p in range(1, 8)] == before
+    with pytest.raises(_lib.FeiError):
+        loaded.set_choice(4, 10 ** 6, 0)
