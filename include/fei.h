@@ -368,6 +368,54 @@ fei_status fei_integrate_assemble(fei_assembly_t as, const fei_reference_t *refs
                                   const fei_batch *batch, fei_precision prec, void *values,
                                   void *rhs, int32_t *elem_status, fei_stream_t stream);
 
+/* ---- Host-memory batches --------------------------------------------
+ * Integration of a batch whose inputs and outputs live in host memory.
+ * The batch is cut into chunks of consecutive elements that fit one device
+ * slot; each chunk is uploaded on the pipeline's upload stream, integrated
+ * with fei_integrate on the caller's stream and downloaded on the
+ * pipeline's download stream.  Two input and two output slots let the
+ * download of one chunk overlap the integration of the next and the upload
+ * of the one after.  Element matrices and vectors are those of
+ * fei_integrate (same kernels, same values, bit for bit).
+ *
+ * fei_pipeline_create: refs / nrefs as for fei_integrate (the handles must
+ * outlive the pipeline); prec as for fei_integrate; slot_bytes = the size
+ * of one slot's A_e output (0: 256 MiB; 1 MiB .. 1 TiB, else
+ * FEI_ERR_INVALID_ARG).  Allocates two input slots (geometry for
+ * slot_bytes / 144 elements, coefficient records for slot_bytes / 112
+ * records, degrees and offsets) and two output slots (A_e, b_e, status) on
+ * the current device, about 7 x slot_bytes in all, and two streams.
+ * Allocation failure -> FEI_ERR_OOM.  The handle belongs to the caller and
+ * is used by one host thread at a time. */
+typedef struct fei_pipeline *fei_pipeline_t;
+fei_status fei_pipeline_create(const fei_reference_t *refs, int nrefs, fei_precision prec,
+                               int64_t slot_bytes, fei_pipeline_t *out);
+/* Waits for the pipeline's outstanding copies, then frees it.  NULL is a
+ * no-op. */
+fei_status fei_pipeline_destroy(fei_pipeline_t pipeline);
+/* Slot size in bytes and the largest number of elements of one chunk. */
+fei_status fei_pipeline_info(fei_pipeline_t pipeline, int64_t *slot_bytes, int64_t *max_elem);
+
+/* batch: a fei_batch whose pointers (geom, degree, K, b, c, f) are HOST
+ * pointers, with the same layouts as for fei_integrate; A_offset, b_offset
+ * and q_offset must be NULL (FEI_ERR_INVALID_ARG otherwise): the outputs
+ * are packed in element order, element e's A_e at the sum of N_sh^2 over
+ * the elements before it (its b_e likewise, the per-point records at the
+ * sum of N_q), degrees outside 1..7 taking no room -- the layout of
+ * fei_plan_offsets.  A_host, b_host: host arrays of that total size (FP64
+ * for FEI_FP64, FP32 otherwise); status_host: int32 [n_elem], the
+ * per-element status of fei_integrate.  *n_chunks (may be NULL) receives
+ * the number of chunks.  Asynchronous: the call returns once every copy
+ * and launch is enqueued; the outputs are complete when the work enqueued
+ * on `stream` so far has completed, and work enqueued on `stream` before
+ * the call runs first.  The host arrays must stay valid until then.  Page-
+ * locked host memory (cudaHostAlloc, cudaHostRegister) lets the copies
+ * overlap; pageable memory works, with copies that block the calling
+ * thread.  An element larger than a slot -> FEI_ERR_INVALID_ARG. */
+fei_status fei_integrate_host(fei_pipeline_t pipeline, const fei_batch *batch, void *A_host,
+                              void *b_host, int32_t *status_host, int64_t *n_chunks,
+                              fei_stream_t stream);
+
 /* Fault injection for tests: the time limit of the tensor-core forward's
  * pipeline waits on the current device, in nanoseconds (0 restores the
  * default, 2 s).  A block whose wait runs out raises an abort flag, marks

@@ -12,7 +12,7 @@ from . import inputs  # noqa: F401
 
 _API_NAMES = ("fei_integrate", "fei_integrate_backward", "fei_reference_create",
               "fei_plan_offsets", "integrate", "Reference", "Layout", "uniform_layout", "nsh", "nq", "Plan",
-              "fei_integrate_backward_quadratic", "fei_status_summary", "Assembly")
+              "fei_integrate_backward_quadratic", "fei_status_summary", "Assembly", "Pipeline")
 
 
 def __getattr__(name):

@@ -101,6 +101,10 @@ def _load():
                                            vp, vp, vp, vp]
     lib.fei_debug_set_wait_limit.argtypes = [ctypes.c_uint64]
     lib.fei_plan_set_choice.argtypes = [vp, ctypes.c_int, ctypes.c_int, i64]
+    lib.fei_pipeline_create.argtypes = [ref_p, ctypes.c_int, ctypes.c_int, i64, ref_p]
+    lib.fei_pipeline_destroy.argtypes = [vp]
+    lib.fei_pipeline_info.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]
+    lib.fei_integrate_host.argtypes = [vp, ctypes.POINTER(fei_batch), vp, vp, vp, ctypes.POINTER(i64), vp]
     lib.fei_last_error_string.argtypes = []
     lib.fei_last_error_string.restype = ctypes.c_char_p
     for name in ("fei_reference_create", "fei_reference_destroy", "fei_reference_info",
@@ -109,7 +113,8 @@ def _load():
                  "fei_plan_offsets", "fei_integrate_noalloc", "fei_plan_create", "fei_plan_destroy",
                  "fei_plan_execute", "fei_plan_tune", "fei_plan_choice", "fei_status_summary",
                  "fei_assembly_create", "fei_assembly_destroy", "fei_assembly_info", "fei_assembly_pattern",
-                 "fei_assemble", "fei_integrate_assemble", "fei_debug_set_wait_limit", "fei_plan_set_choice"):
+                 "fei_assemble", "fei_integrate_assemble", "fei_debug_set_wait_limit", "fei_plan_set_choice",
+                 "fei_pipeline_create", "fei_pipeline_destroy", "fei_pipeline_info", "fei_integrate_host"):
         getattr(lib, name).restype = i32
     return lib
 

@@ -326,6 +326,93 @@ class Plan:
             self.handle = None
 
 
+def _host_f64(t, name, dtype=torch.float64):
+    if t is None:
+        raise ValueError(f"{name} is required")
+    if t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous host {dtype} tensor")
+    return t
+
+
+class Pipeline:
+    """Owning wrapper of a fei_pipeline_t: integration of a batch held in
+    host memory, chunk by chunk through two device slots, the copies of one
+    chunk overlapping the integration of the next (include/fei.h).
+
+    ``integrate_host`` takes host tensors (page-locked ones let the copies
+    overlap) and returns host tensors (A, b_vec, status) packed in element
+    order, complete once the current stream has reached them."""
+
+    def __init__(self, degrees=range(1, 8), precision: str = "tc_f16x3", slot_bytes: int = 0, refs=None):
+        self.precision = precision
+        self.refs = list(refs) if refs is not None else [fei_reference_create(d) for d in degrees]
+        h = ctypes.c_void_p()
+        check(lib.fei_pipeline_create(_refs_array(self.refs), len(self.refs), _lib.PRECISIONS[precision],
+                                      int(slot_bytes), ctypes.byref(h)), "fei_pipeline_create")
+        self.handle = h
+        sb, me = ctypes.c_int64(), ctypes.c_int64()
+        check(lib.fei_pipeline_info(h, ctypes.byref(sb), ctypes.byref(me)), "fei_pipeline_info")
+        self.slot_bytes, self.max_elem = sb.value, me.value
+        self.n_chunks = 0
+
+    def totals(self, n, p=None, degree=None, per_qp=False):
+        """(A_total, b_total, record count) of the packed layout."""
+        if degree is None:
+            s, q = (p + 1) ** 2 * (p + 2) // 2, (p + 1) ** 3
+            return n * s * s, n * s, n * q if per_qp else n
+        d = degree.numpy().astype(np.int64)
+        ok = (d >= 1) & (d <= 7)
+        s = np.where(ok, (d + 1) ** 2 * (d + 2) // 2, 0)
+        q = np.where(ok, (d + 1) ** 3, 0)
+        return int((s * s).sum()), int(s.sum()), int(q.sum()) if per_qp else n
+
+    def integrate_host(self, geom, K, b, c, f, p=None, degree=None, per_qp=False, out=None):
+        geom = _host_f64(geom, "geom")
+        if geom.dim() != 3 or geom.shape[1:] != (6, 3):
+            raise ValueError("geom must be [n, 6, 3]")
+        if degree is not None:
+            _host_f64(degree, "degree", torch.int32)
+        elif p is None:
+            raise ValueError("give p or degree")
+        n = geom.shape[0]
+        A_total, b_total, m = self.totals(n, p, degree, per_qp)
+        for t, name, width in ((K, "K", 9), (b, "b", 3), (c, "c", 1), (f, "f", 1)):
+            _host_f64(t, name)
+            if t.numel() != width * m:
+                per = "quadrature point" if per_qp else "element"
+                raise ValueError(f"{name} must hold {width} values per {per} ({width * m} in all), got {t.numel()}")
+        dtype = torch.float64 if self.precision == "fp64" else torch.float32
+        if out is None:
+            A = torch.empty(A_total, dtype=dtype, pin_memory=True)
+            bv = torch.empty(b_total, dtype=dtype, pin_memory=True)
+            st = torch.empty(n, dtype=torch.int32, pin_memory=True)
+        else:
+            A, bv, st = out
+            for t, name, size, dt in ((A, "A", A_total, dtype), (bv, "b_vec", b_total, dtype),
+                                      (st, "status", n, torch.int32)):
+                _host_f64(t, name, dt)
+                if t.numel() != size:
+                    raise ValueError(f"{name} must hold {size} values, got {t.numel()}")
+        bt = _lib.fei_batch()
+        bt.n_elem = n
+        bt.geom = geom.data_ptr()
+        bt.degree = degree.data_ptr() if degree is not None else None
+        bt.uniform_degree = int(p) if p is not None else 0
+        bt.coef_mode = _lib.FEI_COEF_PER_POINT if per_qp else _lib.FEI_COEF_PER_ELEMENT
+        bt.K, bt.b, bt.c, bt.f = K.data_ptr(), b.data_ptr(), c.data_ptr(), f.data_ptr()
+        nc = ctypes.c_int64()
+        check(lib.fei_integrate_host(self.handle, ctypes.byref(bt), _ptr(A), _ptr(bv), _ptr(st),
+                                     ctypes.byref(nc), _stream()), "fei_integrate_host")
+        self.n_chunks = nc.value
+        return A, bv, st
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            lib.fei_pipeline_destroy(h)
+            self.handle = None
+
+
 class Assembly:
     """Assembly of element matrices into a global CSR matrix (Sec. 2).
 

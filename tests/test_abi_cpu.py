@@ -64,6 +64,16 @@ def test_argument_errors_before_any_cuda_call(lib):
     assert lib.fei_plan_choice(None, 3, None, None, None) == 1
     lib.fei_plan_set_choice.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int64]
     assert lib.fei_plan_set_choice(None, 3, 0, 0) == 1
+    lib.fei_pipeline_create.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int64, vp]
+    out = vp()
+    assert lib.fei_pipeline_create(None, 1, 0, 0, ctypes.byref(out)) == 1 and out.value is None
+    assert lib.fei_pipeline_create(None, 1, 0, 0, None) == 1
+    lib.fei_integrate_host.argtypes = [vp] * 7
+    assert lib.fei_integrate_host(None, None, None, None, None, None, None) == 1
+    lib.fei_pipeline_info.argtypes = [vp] * 3
+    assert lib.fei_pipeline_info(None, None, None) == 1
+    lib.fei_pipeline_destroy.argtypes = [vp]
+    assert lib.fei_pipeline_destroy(None) == 0
     assert lib.fei_plan_destroy(None) == 0
     lib.fei_integrate_backward_quadratic.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int, vp, vp, vp, vp]
     assert lib.fei_integrate_backward_quadratic(None, 1, None, 0, None, None, None, None) == 1
