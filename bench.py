@@ -451,12 +451,14 @@ def main():
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
+    torch.cuda.nvtx.range_push("timed steps")
     for k in range(args.steps):
         flush.fill_(float(k))  # evict L2 between steps (outside the events)
         evs[k][0].record(stream)
         step(mid=mids[k] if mids else None)
         evs[k][1].record(stream)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     if world > 1:
         torch.distributed.barrier()
     clk = clocks.stop()
@@ -652,9 +654,11 @@ def main():
         e2e_step()  # untimed: first-use allocations
         torch.cuda.synchronize()
         t0 = time.perf_counter()
+        torch.cuda.nvtx.range_push("end-to-end steps")
         for _ in range(e2e_steps):
             e2e_step()
             torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
         dt = (time.perf_counter() - t0) / e2e_steps
         e2e = {"value": world * n / dt, "unit": "elements/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "ms_per_step": dt * 1e3,

@@ -7,6 +7,7 @@ the current device; inputs are FP64 and contiguous.
 from __future__ import annotations
 
 import ctypes
+import os
 from dataclasses import dataclass
 
 import numpy as np
@@ -283,9 +284,21 @@ class Plan:
         return self._call(lib.fei_plan_execute, "fei_plan_execute", geom, K, b, c, f, p, degree, per_qp,
                           layout, out)
 
-    def tune(self, geom, K, b, c, f, p=None, degree=None, per_qp=False, layout=None, out=None):
-        return self._call(lib.fei_plan_tune, "fei_plan_tune", geom, K, b, c, f, p, degree, per_qp,
-                          layout, out)
+    def tune(self, geom, K, b, c, f, p=None, degree=None, per_qp=False, layout=None, out=None, cache=None):
+        """Times the candidate kernel shapes of every degree on this batch
+        and keeps the fastest.  With a cache file (``cache``, else the
+        environment variable FEI_AUTOTUNE_CACHE) holding choices for this GPU
+        model and precision, those are applied instead of timing; otherwise
+        the tuned choices are added to it."""
+        path = cache if cache is not None else os.environ.get("FEI_AUTOTUNE_CACHE")
+        if path and os.path.exists(path) and self.load_choices(path):
+            return self.execute(geom, K, b, c, f, p, degree, per_qp, layout, out)
+        result = self._call(lib.fei_plan_tune, "fei_plan_tune", geom, K, b, c, f, p, degree, per_qp,
+                            layout, out)
+        if path:
+            torch.cuda.current_stream().synchronize()
+            self.save_choices(path)
+        return result
 
     def choice(self, p: int):
         """(variant, grid cap in blocks, tuned ms) chosen for degree p."""
@@ -297,25 +310,34 @@ class Plan:
     def set_choice(self, p: int, variant: int, grid_cap: int):
         check(lib.fei_plan_set_choice(self.handle, int(p), int(variant), int(grid_cap)), "fei_plan_set_choice")
 
+    def _cache_key(self):
+        return f"{torch.cuda.get_device_name()}|{self.precision}"
+
     def save_choices(self, path: str):
-        """The tuning cache: this plan's per-degree choices as JSON, keyed by
-        the GPU model and the precision."""
+        """The tuning cache: this plan's per-degree choices, added to the
+        JSON file under the key "<GPU model>|<precision>" (other keys kept)."""
         import json
-        data = {"gpu": torch.cuda.get_device_name(), "precision": self.precision,
-                "degrees": {str(p): dict(zip(("variant", "grid_cap", "tuned_ms"), self.choice(p)))
-                            for p in range(1, 8)}}
-        with open(path, "w") as fh:
+        data = {}
+        if os.path.exists(path):
+            with open(path) as fh:
+                data = json.load(fh)
+        data[self._cache_key()] = {str(p): dict(zip(("variant", "grid_cap", "tuned_ms"), self.choice(p)))
+                                   for p in range(1, 8)}
+        tmp = path + ".tmp"
+        with open(tmp, "w") as fh:
             json.dump(data, fh, indent=1)
+        os.replace(tmp, path)
 
     def load_choices(self, path: str) -> bool:
-        """Applies a cache written by save_choices on the same GPU model and
-        precision; returns False (and changes nothing) otherwise."""
+        """Applies the choices stored for this GPU model and precision;
+        returns False (and changes nothing) if the file has none."""
         import json
         with open(path) as fh:
             data = json.load(fh)
-        if data.get("gpu") != torch.cuda.get_device_name() or data.get("precision") != self.precision:
+        entry = data.get(self._cache_key())
+        if entry is None:
             return False
-        for p, c in data["degrees"].items():
+        for p, c in entry.items():
             self.set_choice(int(p), c["variant"], c["grid_cap"])
         return True
 

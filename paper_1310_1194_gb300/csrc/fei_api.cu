@@ -285,6 +285,7 @@ extern "C" fei_status fei_plan_offsets(const int32_t *degree, int64_t n_elem, in
 extern "C" fei_status fei_integrate(const fei_reference_t *refs, int nrefs, const fei_batch *batch,
                                     fei_precision prec, void *A_out, void *b_out, int32_t *elem_status,
                                     fei_stream_t stream) {
+  const Range range_("fei_integrate");
   fei_status st = check_batch(batch);
   if (st) return st;
   if (prec != FEI_FP64 && prec != FEI_FP32 && prec != FEI_TC_F16X3)
@@ -337,6 +338,7 @@ namespace {
 fei_status backward_impl(const char *who, const fei_reference_t *refs, int nrefs, const fei_batch *batch,
                          fei_precision prec, const void *gA, const void *gb, const double *u, double *g_geom,
                          const fei_coef_grad *g_coef, fei_stream_t stream) {
+  const Range range_(who);
   const bool quad = u != nullptr;
   fei_status st = check_batch(batch);
   if (st) return st;

@@ -524,6 +524,7 @@ extern "C" fei_status fei_assembly_pattern(fei_assembly_t as, int64_t *row_ptr, 
 
 extern "C" fei_status fei_assemble(fei_assembly_t as, fei_precision prec, const void *A, const void *b,
                                    void *values, void *rhs, fei_stream_t stream) {
+  const Range range_("fei_assemble");
   fei_status st = check_device(as);
   if (st) return st;
   size_t vb;
@@ -544,6 +545,7 @@ extern "C" fei_status fei_assemble(fei_assembly_t as, fei_precision prec, const 
 extern "C" fei_status fei_integrate_assemble(fei_assembly_t as, const fei_reference_t *refs, int nrefs,
                                              const fei_batch *batch, fei_precision prec, void *values, void *rhs,
                                              int32_t *elem_status, fei_stream_t stream) {
+  const Range range_("fei_integrate_assemble");
   fei_status st = check_device(as);
   if (st) return st;
   if (!batch) return set_error(FEI_ERR_INVALID_ARG, "batch is NULL");

@@ -14,6 +14,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include "../../include/fei.h"
@@ -124,6 +125,19 @@ fei_status launch_tc_forward(int p, const fei_reference *ref, const FwdArgs &a, 
 int tc_variant_count(int p);
 fei_status build_tc_image(fei_reference *ref);
 void free_tc_image(fei_reference *ref);
+
+}  // namespace fei
+
+namespace fei {
+
+// NVTX range over a host entry point: visible in a profiler's timeline,
+// a no-op when no tool is attached (NVTX v3, header only).
+struct Range {
+  explicit Range(const char *name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+  Range(const Range &) = delete;
+  Range &operator=(const Range &) = delete;
+};
 
 }  // namespace fei
 

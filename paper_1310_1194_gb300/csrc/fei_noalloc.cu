@@ -88,6 +88,7 @@ using namespace fei;
 extern "C" fei_status fei_integrate_noalloc(const fei_reference_t *refs, int nrefs, const fei_batch *batch,
                                             fei_precision prec, void *A_out, void *b_out, int32_t *elem_status,
                                             fei_stream_t stream) {
+  const Range range_("fei_integrate_noalloc");
   if (!batch) return set_error(FEI_ERR_INVALID_ARG, "fei_integrate_noalloc: batch is NULL");
   if (batch->n_elem < 0) return set_error(FEI_ERR_INVALID_ARG, "fei_integrate_noalloc: n_elem < 0");
   if (batch->n_elem > kNoAllocMax)

@@ -256,6 +256,7 @@ extern "C" fei_status fei_pipeline_info(fei_pipeline_t pl, int64_t *slot_bytes, 
 
 extern "C" fei_status fei_integrate_host(fei_pipeline_t pl, const fei_batch *hb, void *A_host, void *b_host,
                                          int32_t *status_host, int64_t *n_chunks, fei_stream_t stream) {
+  const Range range_("fei_integrate_host");
   if (!pl) return set_error(FEI_ERR_INVALID_ARG, "fei_integrate_host: pipeline is NULL");
   if (!hb) return set_error(FEI_ERR_INVALID_ARG, "fei_integrate_host: batch is NULL");
   if (hb->A_offset || hb->b_offset || hb->q_offset)

@@ -225,6 +225,7 @@ extern "C" fei_status fei_plan_destroy(fei_plan_t plan) {
 
 extern "C" fei_status fei_plan_tune(fei_plan_t plan, const fei_batch *batch, void *A_out, void *b_out,
                                     int32_t *elem_status, fei_stream_t stream) {
+  const Range range_("fei_plan_tune");
   fei_status st = check_call(plan, batch, A_out, b_out, elem_status);
   if (st || batch->n_elem == 0) return st;
   cudaStream_t s = (cudaStream_t)stream;
@@ -285,6 +286,7 @@ extern "C" fei_status fei_plan_tune(fei_plan_t plan, const fei_batch *batch, voi
 
 extern "C" fei_status fei_plan_execute(fei_plan_t plan, const fei_batch *batch, void *A_out, void *b_out,
                                        int32_t *elem_status, fei_stream_t stream) {
+  const Range range_("fei_plan_execute");
   fei_status st = check_call(plan, batch, A_out, b_out, elem_status);
   if (st || batch->n_elem == 0) return st;
   cudaStream_t s = (cudaStream_t)stream;

@@ -182,6 +182,7 @@ __global__ void tabulate_kernel(int p, const double *znode, const double *tnode,
 using namespace fei;
 
 extern "C" fei_status fei_reference_create(int p, fei_reference_t *out) {
+  const Range range_("fei_reference_create");
   if (!out) return set_error(FEI_ERR_INVALID_ARG, "fei_reference_create: out is NULL");
   *out = nullptr;
   if (p < 1 || p > kPMax)

@@ -128,3 +128,16 @@ def test_plan_tuning_cache_round_trip(tmp_path):
     assert [other.choice(p) for p in range(1, 8)] == before
     with pytest.raises(_lib.FeiError):
         loaded.set_choice(4, 10 ** 6, 0)
+    # tune() with a cache file applies the stored choices instead of timing,
+    # and a plan of another precision adds its own entry
+    third = api.Plan(max_elem=n, precision="tc_f16x3")
+    with torch.cuda.stream(s):
+        A3, b3, _, _ = third.tune(*args, degree=deg, layout=layout, cache=path)
+        other.tune(*args, degree=deg, layout=layout, cache=path)
+    s.synchronize()
+    for p in range(1, 8):
+        assert third.choice(p)[:2] == tuned.choice(p)[:2]
+    assert torch.equal(A3, A1) and torch.equal(b3, b1)
+    import json
+    with open(path) as fh:
+        assert len(json.load(fh)) == 2
