@@ -634,7 +634,8 @@ def main():
         pipe = None
         if grads is None:
             pipe = api.Pipeline(precision=precision, refs=refs)
-            hdeg = torch.from_numpy(np.ascontiguousarray(w["degree"])).to(torch.int32) if deg is not None else None
+            hdeg = (torch.from_numpy(np.ascontiguousarray(w["degree"])).to(torch.int32).pin_memory()
+                    if deg is not None else None)
             hst = torch.empty(n, dtype=torch.int32).pin_memory()
             d2h += hst.numel() * 4
             if hdeg is not None:

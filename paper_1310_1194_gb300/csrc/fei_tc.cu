@@ -824,10 +824,14 @@ __global__ void __launch_bounds__(TcCfg<P, V>::NTHREADS, 1)
         // the paired FP32 table of this point pair at this thread's rows:
         // from the stage (copied there with the B operand), or from L2,
         // fetched before the waits so that their latency overlaps them
+        // (at p = 5, 6 only the first half of the rows is fetched early:
+        // holding all of them across the waits exceeded the register budget
+        // and was slower; p = 7 has the registers)
+        constexpr int RPRE = P == 7 ? RT : RT / 2;
         float4 ga[RT], gb[RT];
         if constexpr (!C::GS) {
 #pragma unroll
-          for (int k = 0; k < RT; ++k) {
+          for (int k = 0; k < RPRE; ++k) {
             ga[k] = __ldg(gp + (size_t)((c * 2 + 0) * C::PP + pp) * GST + ri[k]);
             gb[k] = __ldg(gp + (size_t)((c * 2 + 1) * C::PP + pp) * GST + ri[k]);
           }
@@ -840,6 +844,13 @@ __global__ void __launch_bounds__(TcCfg<P, V>::NTHREADS, 1)
         else ok = ok && mbar_wait(smem_u32(&ax.empty[s]), (u & 1u) ^ 1u, abort_flag);
         ok = __all_sync(0xffffffffu, ok);
         if (!ok) break;
+        if constexpr (!C::GS) {
+#pragma unroll
+          for (int k = RPRE; k < RT; ++k) {
+            ga[k] = __ldg(gp + (size_t)((c * 2 + 0) * C::PP + pp) * GST + ri[k]);
+            gb[k] = __ldg(gp + (size_t)((c * 2 + 1) * C::PP + pp) * GST + ri[k]);
+          }
+        }
         if constexpr (C::GS) {
           const float4 *Gs = reinterpret_cast<const float4 *>(dsm_raw + (stageG(s) - smem_u32(dsm_raw)));
 #pragma unroll
@@ -953,13 +964,15 @@ __global__ void __launch_bounds__(TcCfg<P, V>::NTHREADS, 1)
             break;
           }
           tc_fence_after();
-          // groups of two 16-column blocks: issue the loads of the partial
-          // (and of the running sum), wait once, add, store
+          // one 16-column block at a time: load the partial (and the running
+          // sum), wait, add, store.  Loading two blocks before one wait
+          // raised the register peak of the whole kernel above its budget
+          // (spills at every degree) and was slower.
 #pragma unroll
-          for (int b0 = 0; b0 < C::NMMA / 16; b0 += 2) {
-            uint32_t pv[2][16], rv[2][16];
+          for (int b0 = 0; b0 < C::NMMA / 16; b0 += 1) {
+            uint32_t pv[1][16], rv[1][16];
 #pragma unroll
-            for (int j = 0; j < 2; ++j) {
+            for (int j = 0; j < 1; ++j) {
               const int b = b0 + j;
               if (b < C::NMMA / 16) {
                 const int ncol = nh * C::NMMA + b * 16;
@@ -969,7 +982,7 @@ __global__ void __launch_bounds__(TcCfg<P, V>::NTHREADS, 1)
             }
             tmem_wait_ld();
 #pragma unroll
-            for (int j = 0; j < 2; ++j) {
+            for (int j = 0; j < 1; ++j) {
               const int b = b0 + j;
               if (b < C::NMMA / 16) {
                 const int ncol = nh * C::NMMA + b * 16;
