@@ -157,7 +157,11 @@ fei_status fei_reference_copy_table(fei_reference_t ref, double *pts, double *G)
  *              whose outputs are then zero (NONFINITE takes precedence).
  * Uniform-degree batches use no scratch memory.  A batch with a degree
  * array needs a bucketing workspace, which this call allocates on first
- * use per device and keeps; use a plan (below) to allocate up front. */
+ * use per device and keeps; use a plan (below) to allocate up front.
+ * Every call with a degree array on one device uses that one workspace:
+ * issue such calls on one stream (calls on different streams may overlap
+ * on the GPU and race on it), or use plans or pipelines, which own their
+ * scratch. */
 fei_status fei_integrate(const fei_reference_t *refs, int nrefs,
                          const fei_batch *batch, fei_precision prec,
                          void *A_out, void *b_out, int32_t *elem_status,

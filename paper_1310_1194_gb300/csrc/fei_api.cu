@@ -282,6 +282,41 @@ extern "C" fei_status fei_plan_offsets(const int32_t *degree, int64_t n_elem, in
   return FEI_OK;
 }
 
+namespace fei {
+
+fei_status integrate_scratch(const fei_reference *const *by_p, const fei_batch *batch, fei_precision prec,
+                             void *A_out, void *b_out, int32_t *elem_status, int32_t *counts, int32_t *lists,
+                             int64_t cap, cudaStream_t s) {
+  if (!batch->degree) {
+    const int p = batch->uniform_degree;
+    if (!by_p[p]) return set_error(FEI_ERR_INVALID_DEGREE, "no reference for degree %d", p);
+    FwdArgs a;
+    fill_fwd(a, batch, by_p[p], A_out, b_out, elem_status);
+    return launch_forward(p, prec, by_p[p], a, batch->n_elem, s);
+  }
+  unsigned avail = 0;
+  for (int p = 1; p <= kPMax; ++p)
+    if (by_p[p]) avail |= 1u << p;
+  FEI_CUDA_TRY(cudaMemsetAsync(counts, 0, sizeof(int32_t) * 8, s), "cudaMemsetAsync(bucket counts)");
+  int64_t blocks = (batch->n_elem + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  bucket_kernel<<<(unsigned)blocks, 256, 0, s>>>(batch->degree, batch->n_elem, avail, counts, lists, cap,
+                                                  elem_status);
+  FEI_CUDA_TRY(cudaGetLastError(), "bucket_kernel launch");
+  for (int p = 1; p <= kPMax; ++p) {
+    if (!by_p[p]) continue;
+    FwdArgs a;
+    fill_fwd(a, batch, by_p[p], A_out, b_out, elem_status);
+    a.count = counts + p;
+    a.list = lists + (int64_t)(p - 1) * cap;
+    const fei_status st = launch_forward(p, prec, by_p[p], a, batch->n_elem, s);
+    if (st) return st;
+  }
+  return FEI_OK;
+}
+
+}  // namespace fei
+
 extern "C" fei_status fei_integrate(const fei_reference_t *refs, int nrefs, const fei_batch *batch,
                                     fei_precision prec, void *A_out, void *b_out, int32_t *elem_status,
                                     fei_stream_t stream) {
@@ -297,37 +332,13 @@ extern "C" fei_status fei_integrate(const fei_reference_t *refs, int nrefs, cons
   const fei_reference *by_p[kPMax + 1];
   st = check_refs(refs, nrefs, dev, by_p);
   if (st) return st;
-  if (batch->n_elem == 0) return FEI_OK;
-  cudaStream_t s = (cudaStream_t)stream;
-  if (!batch->degree) {
-    const int p = batch->uniform_degree;
-    if (!by_p[p]) return set_error(FEI_ERR_INVALID_DEGREE, "no reference for degree %d", p);
-    FwdArgs a;
-    fill_fwd(a, batch, by_p[p], A_out, b_out, elem_status);
-    return launch_forward(p, prec, by_p[p], a, batch->n_elem, s);
-  }
-  Workspace *ws;
-  st = workspace_for(dev, batch->n_elem, &ws);
-  if (st) return st;
-  unsigned avail = 0;
-  for (int p = 1; p <= kPMax; ++p)
-    if (by_p[p]) avail |= 1u << p;
-  FEI_CUDA_TRY(cudaMemsetAsync(ws->counts, 0, sizeof(int32_t) * 8, s), "cudaMemsetAsync(bucket counts)");
-  int64_t blocks = (batch->n_elem + 255) / 256;
-  if (blocks > 152 * 16) blocks = 152 * 16;
-  bucket_kernel<<<(unsigned)blocks, 256, 0, s>>>(batch->degree, batch->n_elem, avail, ws->counts, ws->lists,
-                                                  ws->capacity, elem_status);
-  FEI_CUDA_TRY(cudaGetLastError(), "bucket_kernel launch");
-  for (int p = 1; p <= kPMax; ++p) {
-    if (!by_p[p]) continue;
-    FwdArgs a;
-    fill_fwd(a, batch, by_p[p], A_out, b_out, elem_status);
-    a.count = ws->counts + p;
-    a.list = ws->lists + (int64_t)(p - 1) * ws->capacity;
-    st = launch_forward(p, prec, by_p[p], a, batch->n_elem, s);
+  Workspace *ws = nullptr;
+  if (batch->degree) {
+    st = workspace_for(dev, batch->n_elem, &ws);
     if (st) return st;
   }
-  return FEI_OK;
+  return integrate_scratch(by_p, batch, prec, A_out, b_out, elem_status, ws ? ws->counts : nullptr,
+                           ws ? ws->lists : nullptr, ws ? ws->capacity : 0, (cudaStream_t)stream);
 }
 
 namespace fei {

@@ -109,6 +109,12 @@ fei_status check_batch(const fei_batch *b);
 void fill_fwd(FwdArgs &a, const fei_batch *b, const fei_reference *r, void *A, void *bv, int32_t *st);
 fei_status launch_forward(int p, fei_precision prec, const fei_reference *r, const FwdArgs &a, int64_t grid_work,
                           cudaStream_t s);
+// The forward of fei_integrate on checked arguments (by_p from check_refs),
+// with the bucketing scratch given: counts int32 [8] and lists int32
+// [7][cap], cap >= n_elem (both unused for a uniform degree).
+fei_status integrate_scratch(const fei_reference *const *by_p, const fei_batch *batch, fei_precision prec,
+                             void *A_out, void *b_out, int32_t *elem_status, int32_t *counts, int32_t *lists,
+                             int64_t cap, cudaStream_t s);
 
 // Kernel launchers (each returns FEI_OK or an error already recorded).
 // grid_cap: largest grid (blocks) of the grid-stride kernels, 0 = default

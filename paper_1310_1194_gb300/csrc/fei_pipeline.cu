@@ -2,7 +2,8 @@
 //
 // The batch is cut into chunks of consecutive elements whose inputs and
 // outputs fit one device slot.  Each chunk is copied in on an upload
-// stream, integrated (fei_integrate) on the caller's stream and copied out
+// stream, integrated (the kernels of fei_integrate, with the bucketing
+// scratch of the slot) on the caller's stream and copied out
 // on a download stream, with two input slots and two output slots, so that
 // the download of chunk k overlaps the integration of chunk k + 1 and the
 // upload of chunk k + 2.  Outputs are packed in element order (the layout
@@ -28,6 +29,7 @@ struct InSlot {
   int32_t *degree = nullptr;
   int64_t *A_off = nullptr, *b_off = nullptr, *q_off = nullptr;
   int32_t *bad = nullptr;
+  int32_t *counts = nullptr, *lists = nullptr;  // the chunk's degree buckets (own scratch)
   cudaEvent_t ready = nullptr;     // inputs of the slot's chunk uploaded
   cudaEvent_t consumed = nullptr;  // the chunk's integration has run
 };
@@ -50,7 +52,7 @@ struct Chunk {
 struct fei_pipeline {
   int device = -1;
   fei_precision prec = FEI_FP32;
-  std::vector<fei_reference_t> refs;
+  const fei_reference *by_p[kPMax + 1] = {};
   int64_t slot_bytes = 0;
   int64_t max_elem = 0, max_rec = 0, max_a = 0, max_b = 0;  // per chunk
   InSlot in[kSlots];
@@ -68,7 +70,8 @@ void release(fei_pipeline *pl) {
   for (int k = 0; k < kSlots; ++k) {
     InSlot &i = pl->in[k];
     for (void *ptr : {(void *)i.geom, (void *)i.K, (void *)i.b, (void *)i.c, (void *)i.f, (void *)i.degree,
-                      (void *)i.A_off, (void *)i.b_off, (void *)i.q_off, (void *)i.bad})
+                      (void *)i.A_off, (void *)i.b_off, (void *)i.q_off, (void *)i.bad, (void *)i.counts,
+                      (void *)i.lists})
       if (ptr) cudaFree(ptr);
     if (i.ready) cudaEventDestroy(i.ready);
     if (i.consumed) cudaEventDestroy(i.consumed);
@@ -114,6 +117,8 @@ fei_status allocate(fei_pipeline *pl) {
     if ((st = dmalloc((void **)&i.b_off, (ne + 1) * 8, "pipeline b offsets"))) return st;
     if ((st = dmalloc((void **)&i.q_off, (ne + 1) * 8, "pipeline point offsets"))) return st;
     if ((st = dmalloc((void **)&i.bad, 4, "pipeline bad count"))) return st;
+    if ((st = dmalloc((void **)&i.counts, 8 * 4, "pipeline bucket counts"))) return st;
+    if ((st = dmalloc((void **)&i.lists, 7 * ne * 4, "pipeline bucket lists"))) return st;
     FEI_CUDA_TRY(cudaEventCreateWithFlags(&i.ready, cudaEventDisableTiming), "cudaEventCreate");
     FEI_CUDA_TRY(cudaEventCreateWithFlags(&i.consumed, cudaEventDisableTiming), "cudaEventCreate");
     OutSlot &o = pl->out[k];
@@ -221,7 +226,7 @@ extern "C" fei_status fei_pipeline_create(const fei_reference_t *refs, int nrefs
   fei_pipeline *pl = new fei_pipeline;
   pl->device = dev;
   pl->prec = prec;
-  pl->refs.assign(refs, refs + nrefs);
+  for (int p = 0; p <= kPMax; ++p) pl->by_p[p] = by_p[p];
   pl->slot_bytes = slot_bytes;
   st = allocate(pl);
   if (st) {
@@ -325,8 +330,8 @@ extern "C" fei_status fei_integrate_host(fei_pipeline_t pl, const fei_batch *hb,
       db.b_offset = in.b_off;
       db.q_offset = per_point ? in.q_off : nullptr;
     }
-    st = fei_integrate(pl->refs.data(), (int)pl->refs.size(), &db, pl->prec, out.A, out.bv, out.status,
-                       (fei_stream_t)s);
+    st = integrate_scratch(pl->by_p, &db, pl->prec, out.A, out.bv, out.status, in.counts, in.lists,
+                           pl->max_elem, s);
     if (st) return st;
     FEI_CUDA_TRY(cudaEventRecord(in.consumed, s), "cudaEventRecord");
     // download

@@ -155,3 +155,33 @@ def test_refused_arguments(api):
     A, bv, st = pl.integrate_host(h["geom"], h["K"], h["b"], h["c"], h["f"], degree=deg)
     torch.cuda.current_stream().synchronize()
     assert int(st[3]) == 2 and int(st.abs().sum()) == 2
+
+
+def test_pipeline_scratch_is_its_own(api):
+    """A mixed batch through the pipeline on one stream while fei_integrate
+    integrates another mixed batch on a second stream: both results are
+    right (the pipeline buckets degrees in its own scratch, not in the
+    workspace that fei_integrate keeps per device)."""
+    w1 = inputs.workload("mixed", n_max=700)
+    w2 = dict(inputs.workload("mixed", n_max=900))
+    w2["geom"] = w2["geom"] * 1.5  # a different batch
+    refs = [api.fei_reference_create(d) for d in range(1, 8)]
+    A1r, b1r, _ = device_reference(api, w1, "fp32", refs, degree=w1["degree"])
+    A2r, b2r, _ = device_reference(api, w2, "fp32", refs, degree=w2["degree"])
+    pl = api.Pipeline(precision="fp32", slot_bytes=MIB, refs=refs)
+    h = host(w1)
+    hdeg = torch.from_numpy(np.ascontiguousarray(w1["degree"])).to(torch.int32).pin_memory()
+    g2 = {k: torch.from_numpy(np.ascontiguousarray(w2[k])).cuda() for k in ("geom", "K", "b", "c", "f")}
+    d2 = torch.from_numpy(np.ascontiguousarray(w2["degree"])).to(torch.int32).cuda()
+    torch.cuda.synchronize()
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    with torch.cuda.stream(s1):
+        A1, b1, st1 = pl.integrate_host(h["geom"], h["K"], h["b"], h["c"], h["f"], degree=hdeg)
+    with torch.cuda.stream(s2):
+        for _ in range(3):
+            A2, b2, st2, _ = api.fei_integrate(g2["geom"], g2["K"], g2["b"], g2["c"], g2["f"], degree=d2,
+                                               precision="fp32", refs=refs)
+    torch.cuda.synchronize()
+    assert pl.n_chunks > 2
+    assert torch.equal(A1, A1r) and torch.equal(b1, b1r)
+    assert torch.equal(A2.cpu(), A2r) and torch.equal(b2.cpu(), b2r)
