@@ -58,7 +58,7 @@ struct fei_pipeline {
   InSlot in[kSlots];
   OutSlot out[kSlots];
   cudaStream_t up = nullptr, down = nullptr;
-  cudaEvent_t start = nullptr, done = nullptr;
+  cudaEvent_t start = nullptr, up_done = nullptr, done = nullptr;
   int next = 0;  // slot of the next chunk (carried across calls)
   std::vector<int64_t> aoff, boff, qoff;
   std::vector<Chunk> chunks;
@@ -84,6 +84,7 @@ void release(fei_pipeline *pl) {
   if (pl->down) cudaStreamDestroy(pl->down);
   if (pl->start) cudaEventDestroy(pl->start);
   if (pl->done) cudaEventDestroy(pl->done);
+  if (pl->up_done) cudaEventDestroy(pl->up_done);
   delete pl;
 }
 
@@ -131,6 +132,7 @@ fei_status allocate(fei_pipeline *pl) {
   FEI_CUDA_TRY(cudaStreamCreateWithFlags(&pl->down, cudaStreamNonBlocking), "cudaStreamCreate(download)");
   FEI_CUDA_TRY(cudaEventCreateWithFlags(&pl->start, cudaEventDisableTiming), "cudaEventCreate");
   FEI_CUDA_TRY(cudaEventCreateWithFlags(&pl->done, cudaEventDisableTiming), "cudaEventCreate");
+  FEI_CUDA_TRY(cudaEventCreateWithFlags(&pl->up_done, cudaEventDisableTiming), "cudaEventCreate");
   return FEI_OK;
 }
 
@@ -259,40 +261,15 @@ extern "C" fei_status fei_pipeline_info(fei_pipeline_t pl, int64_t *slot_bytes, 
   return FEI_OK;
 }
 
-extern "C" fei_status fei_integrate_host(fei_pipeline_t pl, const fei_batch *hb, void *A_host, void *b_host,
-                                         int32_t *status_host, int64_t *n_chunks, fei_stream_t stream) {
-  const Range range_("fei_integrate_host");
-  if (!pl) return set_error(FEI_ERR_INVALID_ARG, "fei_integrate_host: pipeline is NULL");
-  if (!hb) return set_error(FEI_ERR_INVALID_ARG, "fei_integrate_host: batch is NULL");
-  if (hb->A_offset || hb->b_offset || hb->q_offset)
-    return set_error(FEI_ERR_INVALID_ARG, "fei_integrate_host: outputs are packed in element order; "
-                                          "A_offset, b_offset and q_offset must be NULL");
-  // the checks of fei_integrate, with the offsets the pipeline makes itself
-  fei_batch probe = *hb;
-  if (hb->degree) {
-    static const int64_t dummy = 0;
-    probe.A_offset = probe.b_offset = probe.q_offset = &dummy;
-  }
-  fei_status st = check_batch(&probe);
-  if (st) return st;
-  if (n_chunks) *n_chunks = 0;
-  if (hb->n_elem == 0) return FEI_OK;
-  if (!A_host || !b_host || !status_host)
-    return set_error(FEI_ERR_INVALID_ARG, "fei_integrate_host: A_host, b_host and status_host are required");
-  int dev;
-  FEI_CUDA_TRY(cudaGetDevice(&dev), "cudaGetDevice");
-  if (dev != pl->device)
-    return set_error(FEI_ERR_INVALID_ARG, "fei_integrate_host: pipeline was created on device %d, current is %d",
-                     pl->device, dev);
-  st = plan_chunks(pl, hb);
-  if (st) return st;
-  cudaStream_t s = (cudaStream_t)stream;
+namespace {
+
+// Enqueues the chunks of pl->chunks (see fei_integrate_host).
+fei_status enqueue_chunks(fei_pipeline *pl, const fei_batch *hb, void *A_host, void *b_host, int32_t *status_host,
+                          cudaStream_t s) {
   const int64_t dt = pl->prec == FEI_FP64 ? 8 : 4;
   const bool mixed = hb->degree != nullptr;
   const bool per_point = hb->coef_mode == FEI_COEF_PER_POINT;
-  // work enqueued on the caller's stream before this call comes first
-  FEI_CUDA_TRY(cudaEventRecord(pl->start, s), "cudaEventRecord");
-  FEI_CUDA_TRY(cudaStreamWaitEvent(pl->up, pl->start, 0), "cudaStreamWaitEvent");
+  fei_status st;
   for (const Chunk &ch : pl->chunks) {
     const int k = pl->next;
     pl->next = (pl->next + 1) % kSlots;
@@ -341,9 +318,51 @@ extern "C" fei_status fei_integrate_host(fei_pipeline_t pl, const fei_batch *hb,
     if ((st = copy_out(status_host + ch.e0, out.status, ne * 4, pl->down))) return st;
     FEI_CUDA_TRY(cudaEventRecord(out.drained, pl->down), "cudaEventRecord");
   }
-  // the caller's stream completes after the last download
-  FEI_CUDA_TRY(cudaEventRecord(pl->done, pl->down), "cudaEventRecord");
-  FEI_CUDA_TRY(cudaStreamWaitEvent(s, pl->done, 0), "cudaStreamWaitEvent");
+  return FEI_OK;
+}
+
+}  // namespace
+
+extern "C" fei_status fei_integrate_host(fei_pipeline_t pl, const fei_batch *hb, void *A_host, void *b_host,
+                                         int32_t *status_host, int64_t *n_chunks, fei_stream_t stream) {
+  const Range range_("fei_integrate_host");
+  if (!pl) return set_error(FEI_ERR_INVALID_ARG, "fei_integrate_host: pipeline is NULL");
+  if (!hb) return set_error(FEI_ERR_INVALID_ARG, "fei_integrate_host: batch is NULL");
+  if (hb->A_offset || hb->b_offset || hb->q_offset)
+    return set_error(FEI_ERR_INVALID_ARG, "fei_integrate_host: outputs are packed in element order; "
+                                          "A_offset, b_offset and q_offset must be NULL");
+  // the checks of fei_integrate, with the offsets the pipeline makes itself
+  fei_batch probe = *hb;
+  if (hb->degree) {
+    static const int64_t dummy = 0;
+    probe.A_offset = probe.b_offset = probe.q_offset = &dummy;
+  }
+  fei_status st = check_batch(&probe);
+  if (st) return st;
+  if (n_chunks) *n_chunks = 0;
+  if (hb->n_elem == 0) return FEI_OK;
+  if (!A_host || !b_host || !status_host)
+    return set_error(FEI_ERR_INVALID_ARG, "fei_integrate_host: A_host, b_host and status_host are required");
+  int dev;
+  FEI_CUDA_TRY(cudaGetDevice(&dev), "cudaGetDevice");
+  if (dev != pl->device)
+    return set_error(FEI_ERR_INVALID_ARG, "fei_integrate_host: pipeline was created on device %d, current is %d",
+                     pl->device, dev);
+  st = plan_chunks(pl, hb);
+  if (st) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  // work enqueued on the caller's stream before this call comes first
+  FEI_CUDA_TRY(cudaEventRecord(pl->start, s), "cudaEventRecord");
+  FEI_CUDA_TRY(cudaStreamWaitEvent(pl->up, pl->start, 0), "cudaStreamWaitEvent");
+  st = enqueue_chunks(pl, hb, A_host, b_host, status_host, s);
+  // the caller's stream completes after the last upload and download, also
+  // when enqueueing failed part-way (what was enqueued still runs)
+  cudaError_t e = cudaEventRecord(pl->up_done, pl->up);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, pl->up_done, 0);
+  if (e == cudaSuccess) e = cudaEventRecord(pl->done, pl->down);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, pl->done, 0);
+  if (st) return st;
+  if (e != cudaSuccess) return cuda_error(e, "fei_integrate_host: joining the copy streams");
   if (n_chunks) *n_chunks = (int64_t)pl->chunks.size();
   return FEI_OK;
 }
