@@ -10,6 +10,7 @@
 // processing order does not change any output bit.
 #include <stdarg.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <mutex>
@@ -205,8 +206,27 @@ void fill_fwd(FwdArgs &a, const fei_batch *b, const fei_reference *r, void *A, v
 
 fei_status launch_forward(int p, fei_precision prec, const fei_reference *r, const FwdArgs &a,
                           int64_t grid_work, cudaStream_t s) {
-  if (prec == FEI_TC_F16X3 && p >= 3) return launch_tc_forward(p, r, a, grid_work, s);
-  return launch_cc_forward(p, prec == FEI_FP64, a, grid_work, s);
+  const fei_status st = (prec == FEI_TC_F16X3 && p >= 3) ? launch_tc_forward(p, r, a, grid_work, s)
+                                                          : launch_cc_forward(p, prec == FEI_FP64, a, grid_work, s);
+  return st ? st : debug_check(s, "forward kernel");
+}
+
+bool debug_enabled() {
+  static const bool on = [] {
+    const char *v = getenv("FEI_DEBUG");
+    return v != nullptr && *v != '\0' && strcmp(v, "0") != 0;
+  }();
+  return on;
+}
+
+fei_status debug_check(cudaStream_t s, const char *what) {
+  if (!debug_enabled()) return FEI_OK;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  FEI_CUDA_TRY(cudaStreamIsCapturing(s, &cs), "cudaStreamIsCapturing");
+  if (cs != cudaStreamCaptureStatusNone) return FEI_OK;
+  FEI_CUDA_TRY(cudaGetLastError(), what);
+  FEI_CUDA_TRY(cudaStreamSynchronize(s), what);
+  return FEI_OK;
 }
 
 }  // namespace fei
@@ -303,6 +323,8 @@ fei_status integrate_scratch(const fei_reference *const *by_p, const fei_batch *
   bucket_kernel<<<(unsigned)blocks, 256, 0, s>>>(batch->degree, batch->n_elem, avail, counts, lists, cap,
                                                   elem_status);
   FEI_CUDA_TRY(cudaGetLastError(), "bucket_kernel launch");
+  fei_status st0 = debug_check(s, "bucket_kernel");
+  if (st0) return st0;
   for (int p = 1; p <= kPMax; ++p) {
     if (!by_p[p]) continue;
     FwdArgs a;
@@ -392,7 +414,8 @@ fei_status backward_impl(const char *who, const fei_reference_t *refs, int nrefs
     a.G32 = r->G32;
     a.znode = r->znode;
     a.tnode = r->tnode;
-    return launch_cc_backward(p, prec == FEI_FP64, a, batch->n_elem, s, quad);
+    st = launch_cc_backward(p, prec == FEI_FP64, a, batch->n_elem, s, quad);
+    return st ? st : debug_check(s, "backward kernel");
   }
   Workspace *ws;
   st = workspace_for(dev, batch->n_elem, &ws);
@@ -419,6 +442,7 @@ fei_status backward_impl(const char *who, const fei_reference_t *refs, int nrefs
     ap.count = ws->counts + p;
     ap.list = ws->lists + (int64_t)(p - 1) * ws->capacity;
     st = launch_cc_backward(p, prec == FEI_FP64, ap, batch->n_elem, s, quad);
+    if (!st) st = debug_check(s, "backward kernel");
     if (st) return st;
   }
   return FEI_OK;

@@ -158,7 +158,7 @@ fei_status launch_assemble(const fei_assembly *as, int p, const int32_t *elems, 
                                                       as->l2g, as->loff, as->rank, as->slot, as->shptr, as->shoff,
                                                       as->row_ptr, (T *)values, (T *)rhs);
   FEI_CUDA_TRY(cudaGetLastError(), "assemble_kernel launch");
-  return FEI_OK;
+  return debug_check(s, "assemble_kernel");
 }
 
 // values of the shared rows and the whole rhs set to zero (private rows are
@@ -172,7 +172,7 @@ fei_status clear_outputs(const fei_assembly *as, size_t vb, void *values, void *
   else
     clear_rows_kernel<float><<<(unsigned)blocks, 256, 0, s>>>(as->shrows, as->n_shrows, as->row_ptr, (float *)values);
   FEI_CUDA_TRY(cudaGetLastError(), "clear_rows_kernel launch");
-  return FEI_OK;
+  return debug_check(s, "clear_rows_kernel");
 }
 
 void free_device(fei_assembly *as) {

@@ -411,8 +411,19 @@ __global__ void __launch_bounds__(256, 2) cc_backward_kernel(BwdArgs a) {
         double v = 0.0;
 #pragma unroll 8
         for (int l = 0; l < 32; ++l) v += red[k * 33 + l];
-        atomicAdd(k < 21 ? &sm.gev[k] : &sm.gcoef[k - 21], v);
+        red[k * 33 + 32] = v;  // this warp's sum, in the row's spare slot
       }
+    }
+    __syncthreads();
+    // the warps' sums added in warp order: a fixed order, so the gradients
+    // are the same bit for bit from run to run
+    if (tid < 35 && (tid < 21 || a.coef_mode == FEI_COEF_PER_ELEMENT)) {
+      const double *red0 = reinterpret_cast<const double *>(dsm);
+      double v = 0.0;
+#pragma unroll
+      for (int w = 0; w < 256 / 32; ++w) v += red0[w * (35 * 33) + tid * 33 + 32];
+      if (tid < 21) sm.gev[tid] = v;
+      else sm.gcoef[tid - 21] = v;
     }
     __syncthreads();
     const int st = sm.status;

@@ -109,6 +109,13 @@ fei_status check_batch(const fei_batch *b);
 void fill_fwd(FwdArgs &a, const fei_batch *b, const fei_reference *r, void *A, void *bv, int32_t *st);
 fei_status launch_forward(int p, fei_precision prec, const fei_reference *r, const FwdArgs &a, int64_t grid_work,
                           cudaStream_t s);
+// FEI_DEBUG set (and not "0") in the environment: every launch is followed
+// by a wait on its stream and an error check, so that a failing kernel is
+// reported by the call that launched it, under its name.  Skipped while the
+// stream is being captured into a CUDA graph.  Off: returns FEI_OK at once.
+bool debug_enabled();
+fei_status debug_check(cudaStream_t s, const char *what);
+
 // The forward of fei_integrate on checked arguments (by_p from check_refs),
 // with the bucketing scratch given: counts int32 [8] and lists int32
 // [7][cap], cap >= n_elem (both unused for a uniform degree).

@@ -76,8 +76,9 @@ __global__ void noalloc_clear_counts(int32_t *counts) {
 
 fei_status launch_one(int p, fei_precision prec, const fei_reference *r, const FwdArgs &a, int64_t grid_work,
                       cudaStream_t s) {
-  if (prec == FEI_TC_F16X3 && p >= 3) return launch_tc_forward(p, r, a, grid_work, s);
-  return launch_cc_forward(p, prec == FEI_FP64, a, grid_work, s);
+  const fei_status st = (prec == FEI_TC_F16X3 && p >= 3) ? launch_tc_forward(p, r, a, grid_work, s)
+                                                          : launch_cc_forward(p, prec == FEI_FP64, a, grid_work, s);
+  return st ? st : debug_check(s, "forward kernel");
 }
 
 }  // namespace

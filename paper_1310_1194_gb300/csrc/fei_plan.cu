@@ -93,8 +93,9 @@ fei_status launch_degree(const fei_plan *pl, int p, int variant, int64_t grid_ca
     a.count = pl->counts + p;
     a.list = pl->lists + (int64_t)(p - 1) * pl->max_elem;
   }
-  if (tc_path(pl->prec, p)) return launch_tc_forward(p, r, a, b->n_elem, s, variant);
-  return launch_cc_forward(p, pl->prec == FEI_FP64, a, b->n_elem, s, grid_cap);
+  const fei_status ls = tc_path(pl->prec, p) ? launch_tc_forward(p, r, a, b->n_elem, s, variant)
+                                             : launch_cc_forward(p, pl->prec == FEI_FP64, a, b->n_elem, s, grid_cap);
+  return ls ? ls : debug_check(s, "forward kernel");
 }
 
 __global__ void plan_bucket_kernel(const int32_t *degree, int64_t n, unsigned avail, int32_t *counts,
