@@ -272,6 +272,20 @@ fei_status fei_plan_set_choice(fei_plan_t plan, int p, int variant, int64_t grid
 fei_status fei_status_summary(const int32_t *elem_status, int64_t n_elem, int32_t *summary,
                               fei_stream_t stream);
 
+/* Host-side read of the status summary (the boundary's per-batch error
+ * report; Sec. 2 leaves failures unspecified, this library flags them per
+ * element): reduces elem_status (device int32 [n_elem], as written by
+ * fei_integrate or a plan) on `stream` to the worst status (same order as
+ * fei_status_summary) and the number of flagged elements, waits for the
+ * stream (so every call enqueued on it before has finished) and writes both
+ * to the HOST pointers worst and count.  n_elem == 0 waits for the stream and
+ * reports (0, 0).  The reduction goes through a summary word inside libfei
+ * (no allocation); calls on one device are serialised.  Errors: INVALID_ARG
+ * (NULL pointers, n_elem < 0), CUDA (including a failed kernel earlier on
+ * the stream, reported by the wait).  Synchronous. */
+fei_status fei_sync_status(const int32_t *elem_status, int64_t n_elem, int32_t *worst, int64_t *count,
+                           fei_stream_t stream);
+
 /* Largest batch fei_integrate_noalloc accepts. */
 #define FEI_NOALLOC_MAX_ELEM 262144
 
@@ -279,19 +293,20 @@ fei_status fei_status_summary(const int32_t *elem_status, int64_t n_elem, int32_
  * counterpart; this serves callers that cannot allocate).  fei_integrate
  * allocates scratch with cudaMalloc for a batch with a degree array (the
  * per-degree element lists).  Callers that cannot have a library allocate
- * -- code running while a stream is captured into a CUDA graph, code that
- * must never block the device, applications whose device memory belongs to
- * a pool or budget the library must not bypass -- call this instead.  Same
- * arguments, layout, outputs and statuses as fei_integrate; the scratch is
- * a fixed device array inside libfei (4 * (8 + 7 * FEI_NOALLOC_MAX_ELEM)
- * bytes, about 7.3 MB, reserved on every GPU that loads the library until
- * the process exits); no cudaMalloc, cudaFree or allocating routine is
- * called.  n_elem > FEI_NOALLOC_MAX_ELEM -> FEI_ERR_INVALID_ARG.  Every
- * call on a device shares that array and leaves its contents behind (the
- * call clears the counts it needs); calls whose work overlaps on the GPU
- * race on it, so order them on one stream.  The first call on a device
- * looks the array's address up (cudaGetSymbolAddress): make it before any
- * stream capture starts. */
+ * -- code that must never block the device (cudaMalloc can synchronise
+ * it), applications whose device memory belongs to a pool or budget the
+ * library must not bypass -- call this instead.  Same arguments, layout,
+ * outputs and statuses as fei_integrate, and the same values bit for bit;
+ * the scratch is a fixed device array inside libfei (4 * (8 + 7 *
+ * FEI_NOALLOC_MAX_ELEM) bytes, about 7.3 MB, reserved on every GPU that
+ * loads the library until the process exits); no cudaMalloc, cudaFree or
+ * allocating routine is called.  n_elem > FEI_NOALLOC_MAX_ELEM ->
+ * FEI_ERR_INVALID_ARG.  Every call on a device shares that array and
+ * leaves its contents behind (the call clears the counts it needs); calls
+ * whose work overlaps on the GPU race on it, so order them on one stream.
+ * The first call on a device with a degree array looks the array's address
+ * up (cudaGetSymbolAddress) and keeps it: make that call before any stream
+ * capture starts; the kept address does not survive cudaDeviceReset. */
 fei_status fei_integrate_noalloc(const fei_reference_t *refs, int nrefs,
                                  const fei_batch *batch, fei_precision prec,
                                  void *A_out, void *b_out, int32_t *elem_status,

@@ -83,6 +83,7 @@ def _load():
                                                      vp, vp, ctypes.POINTER(fei_coef_grad), vp]
     lib.fei_plan_offsets.argtypes = [vp, i64, vp, vp, vp, vp, vp]
     lib.fei_status_summary.argtypes = [vp, i64, vp, vp]
+    lib.fei_sync_status.argtypes = [vp, i64, ctypes.POINTER(i32), ctypes.POINTER(i64), vp]
     lib.fei_integrate_noalloc.argtypes = [ref_p, ctypes.c_int, ctypes.POINTER(fei_batch), ctypes.c_int,
                                           vp, vp, vp, vp]
     lib.fei_plan_create.argtypes = [ref_p, ctypes.c_int, i64, ctypes.c_int, ref_p]
@@ -111,7 +112,7 @@ def _load():
                  "fei_reference_copy_table", "fei_integrate", "fei_integrate_backward",
                  "fei_integrate_backward_quadratic",
                  "fei_plan_offsets", "fei_integrate_noalloc", "fei_plan_create", "fei_plan_destroy",
-                 "fei_plan_execute", "fei_plan_tune", "fei_plan_choice", "fei_status_summary",
+                 "fei_plan_execute", "fei_plan_tune", "fei_plan_choice", "fei_status_summary", "fei_sync_status",
                  "fei_assembly_create", "fei_assembly_destroy", "fei_assembly_info", "fei_assembly_pattern",
                  "fei_assemble", "fei_integrate_assemble", "fei_debug_set_wait_limit", "fei_plan_set_choice",
                  "fei_pipeline_create", "fei_pipeline_destroy", "fei_pipeline_info", "fei_integrate_host"):

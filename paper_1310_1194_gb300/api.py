@@ -120,6 +120,17 @@ def fei_status_summary(status: torch.Tensor):
     return int(worst), int(count)
 
 
+def fei_sync_status(status: torch.Tensor):
+    """(worst status, number of flagged elements) of a status array: the
+    library reduces it on the current stream, waits for the stream and
+    returns host values (fei_sync_status of the C ABI)."""
+    status = _need(status, "status", torch.int32)
+    worst, count = ctypes.c_int32(), ctypes.c_int64()
+    check(lib.fei_sync_status(_ptr(status), status.numel(), ctypes.byref(worst), ctypes.byref(count), _stream()),
+          "fei_sync_status")
+    return int(worst.value), int(count.value)
+
+
 def uniform_layout(n: int, p: int) -> Layout:
     s = nsh(p)
     return Layout(None, None, None, n * s * s, n * s, n * nq(p))

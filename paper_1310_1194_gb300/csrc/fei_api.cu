@@ -291,6 +291,51 @@ extern "C" fei_status fei_status_summary(const int32_t *elem_status, int64_t n_e
   return FEI_OK;
 }
 
+namespace fei {
+namespace {
+
+// The summary word fei_sync_status reads back: [worst, count] per device
+// (a __device__ array exists once on every device), written by the summary
+// kernel; calls on one device are serialised by the mutex.
+static __device__ int32_t g_sync_summary[2];
+std::mutex g_sync_mutex[64];
+int32_t *g_sync_ptr[64];
+
+}  // namespace
+}  // namespace fei
+
+extern "C" fei_status fei_sync_status(const int32_t *elem_status, int64_t n_elem, int32_t *worst, int64_t *count,
+                                      fei_stream_t stream) {
+  const Range range_("fei_sync_status");
+  if (n_elem < 0) return set_error(FEI_ERR_INVALID_ARG, "fei_sync_status: n_elem < 0");
+  if (!worst || !count) return set_error(FEI_ERR_INVALID_ARG, "fei_sync_status: worst and count are required");
+  if (!elem_status && n_elem > 0) return set_error(FEI_ERR_INVALID_ARG, "fei_sync_status: elem_status is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n_elem == 0) {
+    FEI_CUDA_TRY(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    *worst = 0;
+    *count = 0;
+    return FEI_OK;
+  }
+  int dev;
+  FEI_CUDA_TRY(cudaGetDevice(&dev), "cudaGetDevice");
+  if (dev < 0 || dev >= 64) return set_error(FEI_ERR_UNSUPPORTED, "device ordinal %d", dev);
+  std::lock_guard<std::mutex> lock(g_sync_mutex[dev]);
+  if (!g_sync_ptr[dev]) {
+    void *ptr = nullptr;
+    FEI_CUDA_TRY(cudaGetSymbolAddress(&ptr, g_sync_summary), "cudaGetSymbolAddress(status summary)");
+    g_sync_ptr[dev] = static_cast<int32_t *>(ptr);
+  }
+  status_summary_kernel<<<1, 1024, 0, s>>>(elem_status, n_elem, g_sync_ptr[dev]);
+  FEI_CUDA_TRY(cudaGetLastError(), "status_summary_kernel launch");
+  int32_t h[2] = {0, 0};
+  FEI_CUDA_TRY(cudaMemcpyAsync(h, g_sync_ptr[dev], sizeof(h), cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync(summary)");
+  FEI_CUDA_TRY(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+  *worst = h[0];
+  *count = h[1];
+  return FEI_OK;
+}
+
 extern "C" fei_status fei_plan_offsets(const int32_t *degree, int64_t n_elem, int64_t *A_offset,
                                        int64_t *b_offset, int64_t *q_offset, int32_t *bad_count,
                                        fei_stream_t stream) {

@@ -49,6 +49,10 @@ def test_argument_errors_before_any_cuda_call(lib):
     lib.fei_plan_offsets.argtypes = [ctypes.c_void_p, ctypes.c_int64] + [ctypes.c_void_p] * 5
     assert lib.fei_plan_offsets(None, 5, None, None, None, None, None) == 1
     assert lib.fei_reference_destroy(None) == 0
+    lib.fei_sync_status.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                                    ctypes.c_void_p]
+    assert lib.fei_sync_status(None, 4, None, None, None) == 1
+    assert lib.fei_sync_status(None, -1, None, None, None) == 1
     # plans: argument errors are reported before any CUDA call
     vp = ctypes.c_void_p
     lib.fei_plan_create.argtypes = [vp, ctypes.c_int, ctypes.c_int64, ctypes.c_int, vp]
