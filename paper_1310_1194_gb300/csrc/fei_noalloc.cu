@@ -6,13 +6,14 @@
 // lists before it launches one kernel per degree; those lists and their
 // counts are scratch memory, which fei_integrate allocates (once per device,
 // grown on demand) with cudaMalloc.  Some callers cannot let a library call
-// cudaMalloc: code that runs while a stream is being captured into a CUDA
-// graph (an allocation there is not allowed), code that must never block
-// the device (cudaMalloc can synchronise), and applications whose device
-// memory is owned by a pool or budget the library must not bypass.  This
-// entry point serves them: its scratch is the file-scope array below,
-// reserved on every GPU that loads the library until the process exits, and
-// it calls no allocating routine at all.
+// cudaMalloc: code that must never block the device (cudaMalloc can
+// synchronise it), and applications whose device memory is owned by a pool
+// or a budget that the library must not bypass.  This entry point serves
+// them: its scratch is the file-scope array below, reserved on every GPU
+// that loads the library until the process exits, and it calls no
+// allocating routine at all.  After the bucketing it runs the same code as
+// fei_integrate (integrate_scratch), so its outputs are those of
+// fei_integrate bit for bit.
 //
 // Limits and sharing:
 //  - at most FEI_NOALLOC_MAX_ELEM elements per call (larger batches are
@@ -22,13 +23,12 @@
 //    but two calls whose work overlaps on the GPU (different streams without
 //    ordering between them) race on the array and give wrong results;
 //  - the first call on a device looks up the array's device address
-//    (cudaGetSymbolAddress) -- make that first call before any stream
-//    capture begins.
-#include <string.h>
+//    (cudaGetSymbolAddress) and keeps it for the life of the process --
+//    make that first call before any stream capture begins.  The kept
+//    address is not valid after cudaDeviceReset on that device.
+#include "fei_internal.cuh"
 
 #include <mutex>
-
-#include "fei_internal.cuh"
 
 namespace fei {
 namespace {
@@ -55,32 +55,6 @@ fei_status scratch_ptr(int dev, int32_t **out) {
   return FEI_OK;
 }
 
-// Same bucketing as the allocating path: one atomic per element into the
-// list of its degree; degrees without a reference are marked.
-__global__ void noalloc_bucket_kernel(const int32_t *degree, int64_t n, unsigned avail, int32_t *counts,
-                                      int32_t *lists, int64_t cap, int32_t *status) {
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-    const int p = degree[e];
-    if (p >= 1 && p <= kPMax && ((avail >> p) & 1u)) {
-      const int pos = atomicAdd(&counts[p], 1);
-      lists[(int64_t)(p - 1) * cap + pos] = (int32_t)e;
-    } else {
-      status[e] = FEI_ERR_INVALID_DEGREE;
-    }
-  }
-}
-
-__global__ void noalloc_clear_counts(int32_t *counts) {
-  if (threadIdx.x < 8) counts[threadIdx.x] = 0;
-}
-
-fei_status launch_one(int p, fei_precision prec, const fei_reference *r, const FwdArgs &a, int64_t grid_work,
-                      cudaStream_t s) {
-  const fei_status st = (prec == FEI_TC_F16X3 && p >= 3) ? launch_tc_forward(p, r, a, grid_work, s)
-                                                          : launch_cc_forward(p, prec == FEI_FP64, a, grid_work, s);
-  return st ? st : debug_check(s, "forward kernel");
-}
-
 }  // namespace
 }  // namespace fei
 
@@ -91,76 +65,31 @@ extern "C" fei_status fei_integrate_noalloc(const fei_reference_t *refs, int nre
                                             fei_stream_t stream) {
   const Range range_("fei_integrate_noalloc");
   if (!batch) return set_error(FEI_ERR_INVALID_ARG, "fei_integrate_noalloc: batch is NULL");
-  if (batch->n_elem < 0) return set_error(FEI_ERR_INVALID_ARG, "fei_integrate_noalloc: n_elem < 0");
   if (batch->n_elem > kNoAllocMax)
     return set_error(FEI_ERR_INVALID_ARG,
                      "fei_integrate_noalloc: %lld elements exceed the fixed scratch capacity of %lld "
                      "(FEI_NOALLOC_MAX_ELEM); split the batch or use fei_integrate",
                      (long long)batch->n_elem, (long long)kNoAllocMax);
+  fei_status st = check_batch(batch);
+  if (st) return st;
   if (prec != FEI_FP64 && prec != FEI_FP32 && prec != FEI_TC_F16X3)
     return set_error(FEI_ERR_INVALID_ARG, "fei_integrate_noalloc: precision %d", (int)prec);
   if (batch->n_elem == 0) return FEI_OK;
-  if (!batch->geom || !batch->K || !batch->b || !batch->c || !batch->f || !A_out || !b_out || !elem_status)
-    return set_error(FEI_ERR_INVALID_ARG, "fei_integrate_noalloc: NULL input or output pointer");
-  if (batch->coef_mode != FEI_COEF_PER_ELEMENT && batch->coef_mode != FEI_COEF_PER_POINT)
-    return set_error(FEI_ERR_INVALID_ARG, "fei_integrate_noalloc: coef_mode %d", batch->coef_mode);
-  if (!batch->degree)  // a uniform-degree batch needs no scratch at all
-    return fei_integrate(refs, nrefs, batch, prec, A_out, b_out, elem_status, stream);
-  if (!batch->A_offset || !batch->b_offset || (batch->coef_mode == FEI_COEF_PER_POINT && !batch->q_offset))
-    return set_error(FEI_ERR_INVALID_ARG, "fei_integrate_noalloc: a degree array needs A_offset, b_offset (and q_offset per point)");
-  if (!refs || nrefs < 1) return set_error(FEI_ERR_INVALID_ARG, "fei_integrate_noalloc: refs is NULL or nrefs < 1");
+  if (!A_out || !b_out || !elem_status)
+    return set_error(FEI_ERR_INVALID_ARG, "fei_integrate_noalloc: A_out, b_out and elem_status are required");
   int dev;
   FEI_CUDA_TRY(cudaGetDevice(&dev), "cudaGetDevice");
-  const fei_reference *by_p[kPMax + 1] = {nullptr};
-  for (int k = 0; k < nrefs; ++k) {
-    if (!refs[k]) return set_error(FEI_ERR_INVALID_ARG, "fei_integrate_noalloc: refs[%d] is NULL", k);
-    if (refs[k]->device != dev)
-      return set_error(FEI_ERR_INVALID_ARG, "fei_integrate_noalloc: refs[%d] belongs to device %d", k, refs[k]->device);
-    by_p[refs[k]->p] = refs[k];
-  }
-  int32_t *scratch;
-  fei_status st = scratch_ptr(dev, &scratch);
+  const fei_reference *by_p[kPMax + 1];
+  st = check_refs(refs, nrefs, dev, by_p);
   if (st) return st;
-  int32_t *counts = scratch, *lists = scratch + 8;
-  cudaStream_t s = (cudaStream_t)stream;
-  unsigned avail = 0;
-  for (int p = 1; p <= kPMax; ++p)
-    if (by_p[p]) avail |= 1u << p;
-  // the array keeps the previous call's counts: clear them first
-  noalloc_clear_counts<<<1, 32, 0, s>>>(counts);
-  FEI_CUDA_TRY(cudaGetLastError(), "noalloc_clear_counts launch");
-  int64_t blocks = (batch->n_elem + 255) / 256;
-  if (blocks > 152 * 16) blocks = 152 * 16;
-  noalloc_bucket_kernel<<<(unsigned)blocks, 256, 0, s>>>(batch->degree, batch->n_elem, avail, counts, lists,
-                                                          kNoAllocMax, elem_status);
-  FEI_CUDA_TRY(cudaGetLastError(), "noalloc_bucket_kernel launch");
-  for (int p = 1; p <= kPMax; ++p) {
-    const fei_reference *r = by_p[p];
-    if (!r) continue;
-    FwdArgs a;
-    memset(&a, 0, sizeof(a));
-    a.n_work = batch->n_elem;
-    a.count = counts + p;
-    a.list = lists + (int64_t)(p - 1) * kNoAllocMax;
-    a.geom = batch->geom;
-    a.coef_mode = batch->coef_mode;
-    a.K = batch->K;
-    a.b = batch->b;
-    a.c = batch->c;
-    a.f = batch->f;
-    a.A_off = batch->A_offset;
-    a.b_off = batch->b_offset;
-    a.q_off = batch->q_offset;
-    a.A = A_out;
-    a.bv = b_out;
-    a.status = elem_status;
-    a.G64 = r->G64;
-    a.G32 = r->G32;
-    a.znode = r->znode;
-    a.tnode = r->tnode;
-    a.G32T = r->G32T;
-    st = launch_one(p, prec, r, a, batch->n_elem, s);
+  int32_t *counts = nullptr, *lists = nullptr;
+  if (batch->degree) {  // a uniform-degree batch needs no scratch at all
+    int32_t *scratch;
+    st = scratch_ptr(dev, &scratch);
     if (st) return st;
+    counts = scratch;
+    lists = scratch + 8;
   }
-  return FEI_OK;
+  return integrate_scratch(by_p, batch, prec, A_out, b_out, elem_status, counts, lists, kNoAllocMax,
+                           (cudaStream_t)stream);
 }
