@@ -200,12 +200,13 @@ def cpu_sample_size(w, per_qp, target_s):
     """Elements the oracle integrates in about target_s seconds on all host
     cores (calibrated on a small prefix)."""
     n0 = 64 if (w["p"] or 7) >= 6 else 256
-    rate, _, _, _ = cpu_oracle_rate(w, None, n0, per_qp)
-    return int(max(n0, min(len(w["geom"]), rate * target_s)))
+    rate, _, _, _, _ = cpu_oracle_run(w, n0, per_qp)
+    return int(max(min(n0, len(w["geom"])), min(len(w["geom"]), rate * target_s)))
 
 
-def cpu_oracle_rate(w, p_or_degree, n_sample, per_qp):
-    """Oracle (FP64 C, all host cores) on the first n_sample elements."""
+def cpu_oracle_run(w, n_sample, per_qp):
+    """Oracle (FP64 C, all host cores) on the first n_sample elements:
+    (elements/s, cores, elements, seconds, (A, b, status, offsets))."""
     import oracle
     n = min(n_sample, len(w["geom"]))
     sl = slice(0, n)
@@ -219,9 +220,449 @@ def cpu_oracle_rate(w, p_or_degree, n_sample, per_qp):
     oracle.build()
     cores = len(os.sched_getaffinity(0))
     t0 = time.perf_counter()
-    oracle.integrate(w["geom"][sl], K, b, c, f, p=p, degree=degree, per_qp=per_qp, nthreads=cores)
+    out = oracle.integrate(w["geom"][sl], K, b, c, f, p=p, degree=degree, per_qp=per_qp, nthreads=cores)
     dt = time.perf_counter() - t0
-    return n / dt, cores, n, dt
+    return n / dt, cores, n, dt, out
+
+
+def errors_vs_oracle(A, bv, st, ref, n_s):
+    """Per-element relative Frobenius error of A_e (2-norm of b_e) of the
+    first n_s elements of a device result against the oracle's, which uses
+    the same prefix layout.  Returns max, p99 and mean of A's errors, the
+    max of b's, and whether the statuses agree."""
+    Ao, bo, so, (oA, ob, _) = ref
+    offs = np.asarray(oA[: n_s + 1], dtype=np.int64)
+    boffs = np.asarray(ob[: n_s + 1], dtype=np.int64)
+    ea = np.empty(n_s)
+    eb = np.empty(n_s)
+    # element chunks of about 32 M values, compared on the host in FP64
+    e0 = 0
+    while e0 < n_s:
+        e1 = int(np.searchsorted(offs, offs[e0] + (1 << 25), side="right")) - 1
+        e1 = min(max(e1, e0 + 1), n_s)
+        a = A[int(offs[e0]):int(offs[e1])].double().cpu().numpy()
+        r = Ao[int(offs[e0]):int(offs[e1])]
+        seg = offs[e0:e1] - offs[e0]
+        num = np.add.reduceat((a - r) ** 2, seg)
+        den = np.add.reduceat(r * r, seg)
+        ea[e0:e1] = np.sqrt(num / np.maximum(den, 1e-300))
+        e0 = e1
+    bg = bv[: int(boffs[n_s])].double().cpu().numpy()
+    segb = boffs[:n_s]
+    num = np.add.reduceat((bg - bo[: int(boffs[n_s])]) ** 2, segb)
+    den = np.add.reduceat(bo[: int(boffs[n_s])] ** 2, segb)
+    eb[:] = np.sqrt(num / np.maximum(den, 1e-300))
+    so = np.asarray(so[:n_s])
+    ok = so == 0
+    return {"elements": int(n_s), "max": float(ea[ok].max()) if ok.any() else None,
+            "p99": float(np.percentile(ea[ok], 99)) if ok.any() else None,
+            "mean": float(ea[ok].mean()) if ok.any() else None,
+            "b_max": float(eb[ok].max()) if ok.any() else None,
+            "status_equal": bool(np.array_equal(st[:n_s].cpu().numpy(), so))}
+
+
+def shard_workload(w, rank, world, mode):
+    """The part of the job that this rank integrates.  strong: the workload
+    is the whole job, split by shard.partition (contiguous ranges balanced
+    by F(p)).  weak: the job is `world` copies of the workload, each copy's
+    mesh translated by its index along x, split the same way, so a rank
+    holds about one workload's worth of work (exactly one copy for a
+    uniform degree)."""
+    from paper_1310_1194_gb300 import shard
+    if world == 1:
+        return w
+    if mode == "strong":
+        return shard.shard(w, rank, world)
+    n = len(w["geom"])
+    deg1 = w["degree"] if w.get("degree") is not None else np.full(n, w["p"], dtype=np.int32)
+    lo, hi = shard.partition(np.tile(deg1, world), world)[rank]
+    idx = np.arange(lo, hi)
+    copy, e = idx // n, idx % n
+    out = dict(w)
+    geom = w["geom"][e].copy()
+    geom[:, :, 0] += copy[:, None].astype(np.float64)
+    out["geom"] = np.ascontiguousarray(geom)
+    out["degree"] = np.ascontiguousarray(deg1[e])
+    if w.get("per_qp"):
+        q = (np.asarray(deg1, dtype=np.int64) + 1) ** 3
+        qo = np.concatenate([[0], np.cumsum(q)])
+        rows = np.concatenate([np.arange(qo[k], qo[k + 1]) for k in e]) if len(e) else np.zeros(0, np.int64)
+    else:
+        rows = e
+    for k in ("K", "b", "c", "f"):
+        out[k] = np.ascontiguousarray(w[k][rows])
+    out["start"], out["end"] = lo, hi
+    return out
+
+
+def roofline_of(dom, counts, precision, peaks, peak_src, live, Bts, ms_all, p, n, per_qp):
+    """The roofline object of the dominant kernel `dom` (its algorithmic
+    flops over its own duration, against the pipe that bounds it)."""
+    F, ms = dom["F"], dom["ms"]
+    counts = dom["counts"]
+    precision = dom["precision"]
+    hw = None
+    low_p = p is not None and p <= 2 and dom["kernel"] == "forward"
+    f64_peak = live.get("fp64_fma_tflops") if live else None
+    f32_peak = live.get("fp32_fma_tflops") if live else None
+    f64_note = "FP64 FMA, measured (csrc_peaks, best of 5)" if f64_peak else "FP64 FMA derived: 152 x 2 x 2 x clock"
+    f32_note = "FP32 FMA, measured (csrc_peaks, best of 5)" if f32_peak else "FP32 FMA derived: 152 x 128 x 2 x clock"
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    if not f64_peak:
+        f64_peak = 152 * 2 * 2 * sm_max * 1e6 / 1e12
+    if not f32_peak:
+        f32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12
+    if low_p:
+        # p <= 2: a few kflops per element against 0.4-0.6 KB of traffic, but
+        # the Jacobian work is FP64 (about 45 FP64 flops per point and 84 per
+        # element for the element vectors on the FP32 paths; everything on
+        # the FP64 path), and at GB300's FP64 rate that, not HBM, binds
+        f64 = (F if precision == "fp64" else sum(int(counts[d]) * (45 * nq(d) + 84) for d in range(1, 3)))
+        bound, peak, unit, achieved = "alu", f64_peak, "TFLOP/s", f64 / (ms * 1e-3) / 1e12
+        peak_note = f64_note + " (the FP64 Jacobian work binds before HBM)"
+        hw = {"hbm_gbs": Bts / (ms * 1e-3) / 1e9, "hbm_frac": Bts / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
+              "hbm_peak_gbs": peaks["hbm_gbs"]}
+    elif precision == "tc_f16x3":
+        # every algorithmic multiply-add is three fp16 tensor products (hi*hi,
+        # hi*lo, lo*hi), so the peak for algorithmic flops is a third of the
+        # fp16 (= bf16) dense peak
+        bound, peak, unit, achieved = "tensor", peaks["bf16_tflops"] / 3, "TFLOP/s", F / (ms * 1e-3) / 1e12
+        peak_note = f"bf16/fp16 dense peak / 3 ({peak_src})"
+        hwF = sum(int(counts[d]) * tc_hw_flops(d) for d in range(3, 8))
+        hw = {"tensor_tflops": hwF / (ms * 1e-3) / 1e12,
+              "frac_of_fp16_peak": hwF / (ms * 1e-3) / 1e12 / peaks["bf16_tflops"],
+              "note": "issued tcgen05 flops: 3 products x 2 x 128-row tiles x N_pad x 4 N_q"}
+    elif precision == "fp32":
+        bound, peak, unit, achieved = "alu", f32_peak, "TFLOP/s", F / (ms * 1e-3) / 1e12
+        peak_note = f32_note
+    else:
+        bound, peak, unit, achieved = "alu", f64_peak, "TFLOP/s", F / (ms * 1e-3) / 1e12
+        peak_note = f64_note
+    traffic = None
+    if precision == "tc_f16x3" and dom["kernel"] == "forward" and p is not None and p >= 3:
+        traffic = measured_traffic("tc_forward_kernel", p, n)
+    r = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
+         "traffic": traffic, "peak_source": peak_note, "kernel": dom["kernel"], "kernel_ms": ms,
+         "step_hbm_gbs": Bts / (ms_all * 1e-3) / 1e9, "step_hbm_frac": Bts / (ms_all * 1e-3) / 1e9 / peaks["hbm_gbs"],
+         "hardware": hw}
+    if "fwd_ms" in dom:
+        r["forward_ms"] = dom["fwd_ms"]
+    if "adjoint_ms" in dom:
+        r["adjoint_ms"] = dom["adjoint_ms"]
+        r["adjoint"] = "quadratic loss (gA never formed)"
+    return r
+
+
+def run_workload(name, args, ctx, headline):
+    """One workload: the timed steps of the fastest path that meets 1e-6,
+    its dominant kernel's roofline, the plain FP64 GPU path on the same
+    batch, and errors against the FP64 oracle on the prefix the oracle
+    integrates.  The headline adds the FP32 CUDA-core path, end to end
+    through the host-memory entry, and the CPU baseline."""
+    import torch
+    from paper_1310_1194_gb300 import api, _lib
+    world, rank, dev, stream, flush, peaks, peak_src, live = (ctx[k] for k in (
+        "world", "rank", "dev", "stream", "flush", "peaks", "peak_src", "live"))
+    steps = args.steps if headline else max(2, min(args.steps, args.per_workload_steps))
+    w0 = inputs.workload(name, n_max=(args.elements or None) if headline else None)
+    w = shard_workload(w0, rank, world, args.scaling)
+    per_qp = bool(w["per_qp"])
+    p = w["p"]
+    n = len(w["geom"])
+    # the whole job's elements (every rank's share)
+    n_job = n if world == 1 else len(w0["geom"]) * (world if args.scaling == "weak" else 1)
+    g = {k: torch.from_numpy(np.ascontiguousarray(w[k])).to(dev) for k in ("geom", "K", "b", "c", "f")}
+    deg = None if p is not None else torch.from_numpy(np.ascontiguousarray(w["degree"])).to(dev)
+
+    # the oracle on a prefix of this rank's batch (N = 1 only): the CPU
+    # baseline, and the reference every path's error is measured against
+    ref = None
+    n_s = 0
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        secs = args.cpu_seconds if headline else args.per_workload_cpu_seconds
+        n_s = args.cpu_sample if (args.cpu_sample and headline) else cpu_sample_size(w, per_qp, secs)
+        rate, cores, n_s, dt, ref = cpu_oracle_run(w, n_s, per_qp)
+        cpu = {"value": rate, "unit": "elements/s", "cores": cores, "kind": "oracle",
+               "sample": f"first {n_s} elements of the workload ({dt:.1f} s on the host cores)"}
+
+    precision = args.precision if headline else None
+    if precision is None:
+        precision = "tc_f16x3" if (p is None or p >= 3) else "fp32"
+    layout = api.fei_plan_offsets(deg) if deg is not None else api.uniform_layout(n, p)
+    refs = [api.fei_reference_create(d) for d in ([p] if p is not None else range(1, 8))]
+    out_dtype = torch.float64 if precision == "fp64" else torch.float32
+    A = torch.empty(layout.A_total, dtype=out_dtype, device=dev)
+    bv = torch.empty(layout.b_total, dtype=out_dtype, device=dev)
+    st = torch.empty(n, dtype=torch.int32, device=dev)
+
+    # mixed degree: a plan (bucketing + one kernel per degree in one CUDA
+    # graph), its per-degree kernel shapes tuned once before timing
+    plan = None
+    plan_choices = None
+    if deg is not None:
+        plan = api.Plan(degrees=range(1, 8), max_elem=n, precision=precision)
+        plan.tune(g["geom"], g["K"], g["b"], g["c"], g["f"], degree=deg, per_qp=per_qp, layout=layout,
+                  out=(A, bv, st))
+        plan_choices = {f"p{d}": dict(zip(("variant", "grid_cap", "tuned_ms"), plan.choice(d)))
+                        for d in range(1, 8) if (w["degree"] == d).any()}
+
+    # differentiation: the step is the forward and the adjoint of
+    # L = sum_e u_e^T A_e u_e - u_e^T b_e (gA_e = u_e u_e^T, gb_e = -u_e)
+    grads = None
+    if name == "diff":
+        u = torch.from_numpy(inputs.loss_weights(layout.b_total, 4)).to(dev)
+        if args.adjoint == "general" and headline:
+            s_ = nsh(p)
+            uu = u.view(n, s_)
+            grads = ((uu[:, :, None] * uu[:, None, :]).reshape(-1).to(torch.float32), (-u).to(torch.float32))
+        else:
+            grads = (u,)
+
+    def step(prec=precision, outs=(A, bv, st), mid=None):
+        if plan is not None and prec == precision:
+            plan.execute(g["geom"], g["K"], g["b"], g["c"], g["f"], degree=deg, per_qp=per_qp, layout=layout,
+                         out=outs)
+        else:
+            api.fei_integrate(g["geom"], g["K"], g["b"], g["c"], g["f"], p=p, degree=deg, per_qp=per_qp,
+                              precision=prec, refs=refs, layout=layout, out=outs)
+        if grads is not None and prec == precision:
+            if mid is not None:
+                mid.record(stream)
+            if len(grads) == 2:
+                api.fei_integrate_backward(g["geom"], g["K"], g["b"], g["c"], g["f"], grads[0], grads[1], p=p,
+                                           degree=deg, per_qp=per_qp, precision="fp32", refs=refs, layout=layout)
+            else:
+                api.fei_integrate_backward_quadratic(g["geom"], g["K"], g["b"], g["c"], g["f"], grads[0], p=p,
+                                                     degree=deg, per_qp=per_qp, precision="fp32", refs=refs,
+                                                     layout=layout)
+
+    # kernels of one step: bucketing + one per degree (a plan), or one
+    launches_per_step = (1 + len(refs)) if deg is not None else 1
+    if grads is not None:
+        launches_per_step += 1
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(ctx["local"])
+    clocks.start()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    mids = [torch.cuda.Event(enable_timing=True) for _ in range(steps)] if grads is not None else None
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.nvtx.range_push(f"timed steps {name}")
+    for k in range(steps):
+        flush.fill_(float(k))  # evict L2 between steps (outside the events)
+        evs[k][0].record(stream)
+        step(mid=mids[k] if mids else None)
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    ms = sum(step_ms) / len(step_ms)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = n_job / (ms * 1e-3)
+
+    # errors of the timed path's outputs (the last step) against the oracle
+    err = errors_vs_oracle(A, bv, st, ref, n_s) if ref is not None else None
+
+    # algorithmic flops / bytes of one step
+    degs = np.full(n, p) if p is not None else np.asarray(w["degree"])
+    counts = np.bincount(degs, minlength=8)
+    out_b = 8 if precision == "fp64" else 4
+    F = sum(int(counts[d]) * flops_per_element(d) for d in range(1, 8))
+    Bts = sum(int(counts[d]) * bytes_per_element(d, out_b, per_qp) for d in range(1, 8))
+    # the dominant kernel and its own duration (CUDA events on its stream):
+    # the one kernel of a uniform forward step; the slowest degree of a
+    # plan (timed per degree by the plan's tuner above); the adjoint kernel
+    # of a differentiation step (events around it)
+    dom = {"kernel": "forward", "ms": ms, "F": F, "precision": precision, "counts": counts}
+    plan_buckets = None
+    if plan is not None:
+        per_deg = {d: plan.choice(d)[2] for d in range(1, 8) if counts[d]}
+        d_star = max(per_deg, key=per_deg.get)
+        c1 = np.zeros(8, dtype=np.int64)
+        c1[d_star] = counts[d_star]
+        dom = {"kernel": f"forward, p={d_star} bucket", "ms": per_deg[d_star],
+               "F": int(counts[d_star]) * flops_per_element(d_star),
+               "precision": precision if (precision != "tc_f16x3" or d_star >= 3) else "fp32", "counts": c1}
+        # every bucket against its own roofline (its tuned time, CUDA events)
+        plan_buckets = {}
+        for d, tms in per_deg.items():
+            cd = np.zeros(8, dtype=np.int64)
+            cd[d] = counts[d]
+            prec_d = precision if (precision != "tc_f16x3" or d >= 3) else "fp32"
+            dd = {"kernel": "forward", "ms": tms, "F": int(counts[d]) * flops_per_element(d), "precision": prec_d,
+                  "counts": cd}
+            Bd = int(counts[d]) * bytes_per_element(d, out_b, per_qp)
+            rd = roofline_of(dd, cd, prec_d, peaks, peak_src, live, Bd, tms, d, int(counts[d]), per_qp)
+            plan_buckets[f"p{d}"] = {"elements": int(counts[d]), "ms": tms, "bound": rd["bound"],
+                                     "achieved": rd["achieved"], "peak": rd["peak"], "frac": rd["frac"]}
+    elif grads is not None:
+        bwd_ms = statistics.median([mids[k].elapsed_time(evs[k][1]) for k in range(steps)])
+        fwd_ms = statistics.median([evs[k][0].elapsed_time(mids[k]) for k in range(steps)])
+        if len(grads) == 2:
+            dom = {"kernel": "adjoint (fp32 contraction, fp64 chain)", "ms": bwd_ms,
+                   "F": n * bwd_flops_per_element(p), "precision": "fp32", "counts": counts, "fwd_ms": fwd_ms}
+        elif bwd_ms > fwd_ms:
+            dom = {"kernel": "quadratic-loss adjoint (fp32 G u, fp64 chain)", "ms": bwd_ms,
+                   "F": n * quad_bwd_flops_per_element(p), "precision": "fp32", "counts": counts, "fwd_ms": fwd_ms}
+        else:
+            dom = {"kernel": "forward", "ms": fwd_ms, "F": F, "precision": precision, "counts": counts,
+                   "adjoint_ms": bwd_ms}
+    roofline = roofline_of(dom, counts, precision, peaks, peak_src, live, Bts, ms, p, n, per_qp)
+
+    # the plain FP64 GPU path on the same batch (the comparison the metric
+    # asks for), its error against the oracle, and for the headline the
+    # FP32 CUDA-core path
+    fp64 = None
+    fp32_path = None
+    if precision != "fp64" and rank == 0:
+        A64 = torch.empty(layout.A_total, dtype=torch.float64, device=dev)
+        b64 = torch.empty(layout.b_total, dtype=torch.float64, device=dev)
+        st64 = torch.empty(n, dtype=torch.int32, device=dev)
+        step("fp64", (A64, b64, st64))
+        torch.cuda.synchronize()
+        t64 = []
+        for _ in range(args.fp64_steps if headline else 1):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            flush.fill_(1.0)
+            e0.record(stream)
+            step("fp64", (A64, b64, st64))
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t64.append(e0.elapsed_time(e1))
+        fp64 = {"elements_per_s": n / (statistics.median(t64) * 1e-3), "ms_per_step": statistics.median(t64),
+                "steps": len(t64), "forward_only": grads is not None}
+        if ref is not None:
+            fp64["rel_err_vs_oracle"] = errors_vs_oracle(A64, b64, st64, ref, n_s)
+        del A64, b64, st64
+        if precision == "tc_f16x3" and headline:
+            A32 = torch.empty(layout.A_total, dtype=torch.float32, device=dev)
+            b32 = torch.empty(layout.b_total, dtype=torch.float32, device=dev)
+            st32 = torch.empty(n, dtype=torch.int32, device=dev)
+            step("fp32", (A32, b32, st32))
+            torch.cuda.synchronize()
+            t32 = []
+            for _ in range(max(1, args.fp64_steps)):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                flush.fill_(2.0)
+                e0.record(stream)
+                step("fp32", (A32, b32, st32))
+                e1.record(stream)
+                torch.cuda.synchronize()
+                t32.append(e0.elapsed_time(e1))
+            fp32_path = {"elements_per_s": n / (statistics.median(t32) * 1e-3),
+                         "ms_per_step": statistics.median(t32)}
+            if ref is not None:
+                fp32_path["rel_err_vs_oracle"] = errors_vs_oracle(A32, b32, st32, ref, n_s)
+            del A32, b32, st32
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if headline and not args.no_e2e:
+        e2e = end_to_end(args, ctx, w, g, deg, p, per_qp, layout, refs, precision, out_dtype, grads, step, A, bv,
+                         n_job)
+
+    assembly = None
+    if headline and args.assemble and rank == 0 and world == 1:
+        assembly = assembly_measure(api, w, [g[k] for k in ("geom", "K", "b", "c", "f")], deg, refs, precision,
+                                    flush, max(3, min(steps, 10)))
+        assembly["assemble_hbm_frac"] = assembly["assemble_gbs"] / peaks["hbm_gbs"]
+
+    res = {"workload": WORKLOAD_TEXT[name], "elements": n_job, "elements_per_s": value, "ms_per_step": ms,
+           "steps": steps, "precision": precision, "gflops_algorithmic": F / (ms * 1e-3) / 1e9 * (n_job / n),
+           "roofline": roofline, "rel_err_vs_oracle": err, "fp64_path": fp64, "clocks": clk,
+           "launches_per_step": launches_per_step}
+    if fp64 is not None:
+        res["speedup_vs_fp64_path"] = fp64["ms_per_step"] / ms if not fp64["forward_only"] else None
+    if fp32_path is not None:
+        res["fp32_path"] = fp32_path
+    if plan_choices is not None:
+        res["plan"] = plan_choices
+        res["plan_buckets"] = plan_buckets
+    if cpu is not None:
+        res["cpu_baseline"] = cpu
+    if e2e is not None:
+        res["e2e"] = e2e
+    if assembly is not None:
+        res["assembly"] = assembly
+    del A, bv, st, g, plan
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    return res
+
+
+def end_to_end(args, ctx, w, g, deg, p, per_qp, layout, refs, precision, out_dtype, grads, step, A, bv, n_job):
+    """The same workload through the library's public entry with host
+    buffers: pinned inputs, the uploads and downloads inside the timed
+    region (fei_integrate_host for a forward batch; copy in, forward +
+    adjoint, copy back for the differentiation step)."""
+    import torch
+    from paper_1310_1194_gb300 import api
+    n = len(w["geom"])
+    hin = {k: torch.from_numpy(np.ascontiguousarray(w[k])).pin_memory() for k in ("geom", "K", "b", "c", "f")}
+    hA = torch.empty(layout.A_total, dtype=out_dtype).pin_memory()
+    hb = torch.empty(layout.b_total, dtype=out_dtype).pin_memory()
+    h2d = sum(t.numel() * t.element_size() for t in hin.values())
+    d2h = hA.numel() * hA.element_size() + hb.numel() * hb.element_size()
+    e2e_steps = max(2, min(args.steps, 5))
+    pipe = None
+    hdeg = None
+    hst = None
+    if grads is None:
+        pipe = api.Pipeline(precision=precision, refs=refs)
+        hdeg = (torch.from_numpy(np.ascontiguousarray(w["degree"])).to(torch.int32).pin_memory()
+                if deg is not None else None)
+        hst = torch.empty(n, dtype=torch.int32).pin_memory()
+        d2h += hst.numel() * 4
+        if hdeg is not None:
+            h2d += hdeg.numel() * 4
+
+    def e2e_step():
+        if pipe is not None:
+            pipe.integrate_host(hin["geom"], hin["K"], hin["b"], hin["c"], hin["f"], p=p, degree=hdeg,
+                                per_qp=per_qp, out=(hA, hb, hst))
+            return
+        for k in hin:
+            g[k].copy_(hin[k], non_blocking=True)
+        step()
+        hA.copy_(A, non_blocking=True)
+        hb.copy_(bv, non_blocking=True)
+
+    e2e_step()  # untimed: first-use allocations
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("end-to-end steps")
+    e2e_ms = []
+    for _ in range(e2e_steps):
+        if ctx["world"] > 1:
+            torch.distributed.barrier()
+        t1 = time.perf_counter()
+        e2e_step()
+        torch.cuda.synchronize()
+        e2e_ms.append((time.perf_counter() - t1) * 1e3)
+    torch.cuda.nvtx.range_pop()
+    # the median step: the host link is shared with the machine's other
+    # tenants, and a burst of their traffic can slow single steps
+    dt = statistics.median(e2e_ms) * 1e-3
+    if ctx["world"] > 1:
+        t = torch.tensor([dt], device=ctx["dev"])
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        dt = float(t.item())
+    return {"value": n_job / dt, "unit": "elements/s", "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "ms_per_step": dt * 1e3, "step_ms": [round(x, 3) for x in e2e_ms],
+            "pipeline": (f"fei_integrate_host: {pipe.n_chunks} chunks of <= {pipe.slot_bytes >> 20} MiB of A_e "
+                         "through two device slots, downloads overlapped with integration")
+            if pipe is not None else "copy in, forward + adjoint, copy back"}
 
 
 def run_reference(args, world, rank):
@@ -233,18 +674,18 @@ def run_reference(args, world, rank):
     per_qp = bool(w["per_qp"])
     n_sample = args.cpu_sample or cpu_sample_size(w, per_qp, max(1.0, 60.0 / max(1, args.steps + args.warmup)))
     for _ in range(args.warmup):
-        cpu_oracle_rate(w, None, max(64, n_sample // 8), per_qp)
+        cpu_oracle_run(w, max(64, n_sample // 8), per_qp)
     rates, times = [], []
     cores = None
     for _ in range(args.steps):
-        r, cores, n, dt = cpu_oracle_rate(w, None, n_sample, per_qp)
+        r, cores, n, dt, _ = cpu_oracle_run(w, n_sample, per_qp)
         rates.append(r)
         times.append(dt)
     value = statistics.median(rates)
     line = {
         "impl": "reference", "metric": metric_name(args), "value": value, "unit": "elements/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1e3 * statistics.median(times), "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": 1e3 * statistics.median(times), "higher_is_better": True, "scaling": args.scaling,
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD_TEXT[args.workload], "precision": "fp64 CPU oracle"},
         "cpu_baseline": {"value": value, "unit": "elements/s", "cores": cores, "kind": "oracle",
@@ -254,7 +695,7 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
-METRIC = "elements/s & GFLOP/s per degree p vs plain FP64 GPU path at rel err \u22641e-6"
+METRIC = "elements/s & GFLOP/s per degree p vs plain FP64 GPU path at rel err ≤1e-6"
 
 
 def metric_name(args):
@@ -327,6 +768,9 @@ def assembly_measure(api, w, g, deg, refs, precision, flush, steps):
     }
 
 
+PER_WORKLOAD_ORDER = ("pr1", "p1m", "p4", "mixed", "diff", "p7")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -335,11 +779,19 @@ def main():
     ap.add_argument("--workload", default="p4", choices=sorted(WORKLOAD_TEXT))
     ap.add_argument("--precision", default=None)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--scaling", default="weak", choices=["weak", "strong"],
+                    help="N > 1: weak = N translated copies of the workload, strong = the workload itself; either "
+                         "way the job is split into contiguous element ranges balanced by F(p) (shard.partition)")
     ap.add_argument("--cpu-sample", type=int, default=0, help="elements; 0 = about --cpu-seconds of work")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-per-workload", action="store_true",
+                    help="skip the other workloads (by default every workload is measured after the headline, "
+                         "at N = 1)")
+    ap.add_argument("--per-workload-steps", type=int, default=5)
+    ap.add_argument("--per-workload-cpu-seconds", type=float, default=4.0)
     ap.add_argument("--adjoint", default="quadratic", choices=["quadratic", "general"],
                     help="differentiation workload: the adjoint of the quadratic loss (gA never formed) or the "
                          "general adjoint given gA = u u^T, gb = -u")
@@ -367,350 +819,65 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
-    from paper_1310_1194_gb300 import api, _lib
+    from paper_1310_1194_gb300 import peaks as peak_probe
 
-    w = inputs.workload(args.workload, n_max=args.elements or None)
-    per_qp = bool(w["per_qp"])
     dev = torch.device("cuda", local)
     # a non-default stream for everything (a plan captures its launches into
     # a CUDA graph, which the legacy default stream does not allow)
     stream = torch.cuda.Stream(device=dev)
     torch.cuda.set_stream(stream)
-    g = {k: torch.from_numpy(np.ascontiguousarray(w[k])).to(dev) for k in ("geom", "K", "b", "c", "f")}
-    deg = None if w["p"] is not None else torch.from_numpy(w["degree"]).to(dev)
-    p = w["p"]
-    n = g["geom"].shape[0]
-
-    precision = args.precision
-    if precision is None:
-        precision = "tc_f16x3"
-        try:
-            api.fei_integrate(g["geom"][:1], g["K"][: (nq(p) if per_qp else 1)], g["b"][: (nq(p) if per_qp else 1)],
-                              g["c"][: (nq(p) if per_qp else 1)], g["f"][: (nq(p) if per_qp else 1)],
-                              p=p if p is not None else 3, per_qp=per_qp, precision=precision)
-        except _lib.FeiError:
-            precision = "fp32"
-    layout = api.fei_plan_offsets(deg) if deg is not None else api.uniform_layout(n, p)
-    refs = [api.fei_reference_create(d) for d in ([p] if p is not None else range(1, 8))]
-    out_dtype = torch.float64 if precision == "fp64" else torch.float32
-    A = torch.empty(layout.A_total, dtype=out_dtype, device=dev)
-    bv = torch.empty(layout.b_total, dtype=out_dtype, device=dev)
-    st = torch.empty(n, dtype=torch.int32, device=dev)
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > L2
-
-    # mixed degree: a plan (bucketing + one kernel per degree in one CUDA
-    # graph), its per-degree kernel shapes tuned once before timing
-    plan = None
-    plan_choices = None
-    if deg is not None:
-        plan = api.Plan(degrees=range(1, 8), max_elem=n, precision=precision)
-        plan.tune(g["geom"], g["K"], g["b"], g["c"], g["f"], degree=deg, per_qp=per_qp, layout=layout,
-                  out=(A, bv, st))
-        plan_choices = {f"p{d}": dict(zip(("variant", "grid_cap", "tuned_ms"), plan.choice(d)))
-                        for d in range(1, 8) if (w["degree"] == d).any()}
-
-    # differentiation: the step is the forward and the adjoint of
-    # L = sum_e u_e^T A_e u_e - u_e^T b_e (gA_e = u_e u_e^T, gb_e = -u_e)
-    grads = None
-    if args.workload == "diff":
-        u = torch.from_numpy(inputs.loss_weights(layout.b_total, 4)).to(dev)
-        if args.adjoint == "general":
-            s_ = nsh(p)
-            uu = u.view(n, s_)
-            gA = (uu[:, :, None] * uu[:, None, :]).reshape(-1).to(torch.float32)
-            gb = (-u).to(torch.float32)
-            grads = (gA, gb)
-        else:
-            grads = (u,)
-
-    def step(prec=precision, outs=(A, bv, st), mid=None):
-        if plan is not None and prec == precision:
-            plan.execute(g["geom"], g["K"], g["b"], g["c"], g["f"], degree=deg, per_qp=per_qp, layout=layout,
-                         out=outs)
-        else:
-            api.fei_integrate(g["geom"], g["K"], g["b"], g["c"], g["f"], p=p, degree=deg, per_qp=per_qp,
-                              precision=prec, refs=refs, layout=layout, out=outs)
-        if grads is not None and prec == precision:
-            if mid is not None:
-                mid.record(stream)
-            if len(grads) == 2:
-                api.fei_integrate_backward(g["geom"], g["K"], g["b"], g["c"], g["f"], grads[0], grads[1], p=p,
-                                           degree=deg, per_qp=per_qp, precision="fp32", refs=refs, layout=layout)
-            else:
-                api.fei_integrate_backward_quadratic(g["geom"], g["K"], g["b"], g["c"], g["f"], grads[0], p=p,
-                                                     degree=deg, per_qp=per_qp, precision="fp32", refs=refs,
-                                                     layout=layout)
-
-    # kernels of one step: bucketing + one per degree (a plan), or one
-    launches_per_step = (1 + len(refs)) if deg is not None else 1
-    if grads is not None:
-        launches_per_step += 1
-    for _ in range(max(3, args.warmup)):
-        step()
-    torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
-    clocks = ClockSampler(local)
-    clocks.start()
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    mids = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)] if grads is not None else None
-    torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.nvtx.range_push("timed steps")
-    for k in range(args.steps):
-        flush.fill_(float(k))  # evict L2 between steps (outside the events)
-        evs[k][0].record(stream)
-        step(mid=mids[k] if mids else None)
-        evs[k][1].record(stream)
-    torch.cuda.synchronize()
-    torch.cuda.nvtx.range_pop()
-    if world > 1:
-        torch.distributed.barrier()
-    clk = clocks.stop()
-    step_ms = [a.elapsed_time(b) for a, b in evs]
-    ms = sum(step_ms) / len(step_ms)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * n / (ms * 1e-3)
-
-    # algorithmic flops / bytes of one step
-    degs = np.full(n, p) if p is not None else w["degree"]
-    counts = np.bincount(degs, minlength=8)
-    out_b = 8 if precision == "fp64" else 4
-    F = sum(int(counts[d]) * flops_per_element(d) for d in range(1, 8))
-    Bts = sum(int(counts[d]) * bytes_per_element(d, out_b, per_qp) for d in range(1, 8))
     peaks, peak_src = load_peaks()
-    sm_max = peaks.get("sm_max_mhz", 2070.0)
-    # the dominant kernel and its own duration (CUDA events on its stream):
-    # the one kernel of a uniform forward step; the slowest degree of a
-    # plan (timed per degree by the plan's tuner above); the adjoint kernel
-    # of a differentiation step (events around it)
-    dom = {"kernel": "forward", "ms": ms, "F": F, "precision": precision, "counts": counts}
-    if plan is not None:
-        per_deg = {d: plan.choice(d)[2] for d in range(1, 8) if counts[d]}
-        d_star = max(per_deg, key=per_deg.get)
-        c1 = np.zeros(8, dtype=np.int64)
-        c1[d_star] = counts[d_star]
-        dom = {"kernel": f"forward, p={d_star} bucket", "ms": per_deg[d_star],
-               "F": int(counts[d_star]) * flops_per_element(d_star),
-               "precision": precision if (precision != "tc_f16x3" or d_star >= 3) else "fp32", "counts": c1}
-    elif grads is not None:
-        bwd_ms = statistics.median([mids[k].elapsed_time(evs[k][1]) for k in range(args.steps)])
-        fwd_ms = statistics.median([evs[k][0].elapsed_time(mids[k]) for k in range(args.steps)])
-        if len(grads) == 2:
-            dom = {"kernel": "adjoint (fp32 contraction, fp64 chain)", "ms": bwd_ms,
-                   "F": n * bwd_flops_per_element(p), "precision": "fp32", "counts": counts, "fwd_ms": fwd_ms}
-        elif bwd_ms > fwd_ms:
-            dom = {"kernel": "quadratic-loss adjoint (fp32 G u, fp64 chain)", "ms": bwd_ms,
-                   "F": n * quad_bwd_flops_per_element(p), "precision": "fp32", "counts": counts, "fwd_ms": fwd_ms}
-        else:
-            # the forward contraction dominates; the adjoint's time is
-            # reported beside it
-            dom = {"kernel": "forward", "ms": fwd_ms, "F": F, "precision": precision, "counts": counts,
-                   "adjoint_ms": bwd_ms}
-    hw = None
-    low_p = p is not None and p <= 2 and grads is None
-    F, ms_all = dom["F"], ms
-    ms = dom["ms"]
-    counts = dom["counts"]
-    precision_all = precision
-    precision = dom["precision"]
-    if low_p:
-        # p <= 2: a few kflops per element against 0.4-0.6 KB of traffic, but
-        # the Jacobian work is FP64 (about 45 FP64 flops per point and 84 per
-        # element for the element vectors on the FP32 paths; everything on the
-        # FP64 path), and at GB300's FP64 rate that, not HBM, binds
-        f64 = (F if precision == "fp64" else
-               sum(int(counts[d]) * (45 * nq(d) + 84) for d in range(1, 3)))
-        peak = 152 * 2 * 2 * sm_max * 1e6 / 1e12
-        bound, unit, achieved = "alu", "TFLOP/s", f64 / (ms * 1e-3) / 1e12
-        peak_note = "FP64 FMA: 152 SMs x 2 DFMA/clk x 2 flops x max SM clock (FP64 Jacobian work)"
-        hw = {"hbm_gbs": Bts / (ms * 1e-3) / 1e9, "hbm_frac": Bts / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
-              "hbm_peak_gbs": peaks["hbm_gbs"]}
-    elif precision == "tc_f16x3":
-        # every algorithmic multiply-add is three fp16 tensor products (hi*hi,
-        # hi*lo, lo*hi), so the peak for algorithmic flops is a third of the
-        # fp16 (= bf16) dense peak
-        bound, peak, unit, achieved = "tensor", peaks["bf16_tflops"] / 3, "TFLOP/s", F / (ms * 1e-3) / 1e12
-        peak_note = f"bf16/fp16 dense peak / 3 ({peak_src})"
-        hwF = sum(int(counts[d]) * tc_hw_flops(d) for d in range(3, 8))
-        hw = {"tensor_tflops": hwF / (ms * 1e-3) / 1e12,
-              "frac_of_fp16_peak": hwF / (ms * 1e-3) / 1e12 / peaks["bf16_tflops"],
-              "note": "issued tcgen05 flops: 3 products x 2 x 128-row tiles x N_pad x 4 N_q"}
-    elif precision == "fp32":
-        peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12
-        bound, unit, achieved = "alu", "TFLOP/s", F / (ms * 1e-3) / 1e12
-        peak_note = "FP32 FMA: 152 SMs x 128 lanes x 2 flops x max SM clock"
-    else:
-        peak = 152 * 2 * 2 * sm_max * 1e6 / 1e12
-        bound, unit, achieved = "alu", "TFLOP/s", F / (ms * 1e-3) / 1e12
-        peak_note = "FP64 FMA: 152 SMs x 2 DFMA/clk x 2 flops x max SM clock"
-    traffic = None
-    if precision == "tc_f16x3" and dom["kernel"] == "forward" and p is not None and p >= 3:
-        traffic = measured_traffic("tc_forward_kernel", p, n)
-    roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
-                "traffic": traffic, "peak_source": peak_note, "kernel": dom["kernel"], "kernel_ms": ms,
-                "step_hbm_gbs": Bts / (ms_all * 1e-3) / 1e9,
-                "step_hbm_frac": Bts / (ms_all * 1e-3) / 1e9 / peaks["hbm_gbs"],
-                "hardware": hw}
-    if "fwd_ms" in dom:
-        roofline["forward_ms"] = dom["fwd_ms"]
-    if "adjoint_ms" in dom:
-        roofline["adjoint_ms"] = dom["adjoint_ms"]
-        roofline["adjoint"] = "quadratic loss (gA never formed)"
-    precision, ms = precision_all, ms_all
+    try:
+        live = peak_probe.measure()
+    except Exception as exc:  # the probe is a measurement aid: report, derive instead
+        live = {"error": str(exc)}
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > L2
+    ctx = {"world": world, "rank": rank, "local": local, "dev": dev, "stream": stream, "flush": flush,
+           "peaks": peaks, "peak_src": peak_src, "live": live if "error" not in live else None}
 
-    # accuracy of this path against the FP64 GPU path on sampled elements,
-    # and the FP64 GPU path's own throughput (the comparison the metric asks for)
-    fp64 = None
-    fp32_path = None
-    rel_err = None
-    if precision != "fp64" and rank == 0:
-        A64 = torch.empty(layout.A_total, dtype=torch.float64, device=dev)
-        b64 = torch.empty(layout.b_total, dtype=torch.float64, device=dev)
-        st64 = torch.empty(n, dtype=torch.int32, device=dev)
-        step("fp64", (A64, b64, st64))
-        torch.cuda.synchronize()
-        t64 = []
-        for _ in range(args.fp64_steps):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            flush.fill_(1.0)
-            e0.record(stream)
-            step("fp64", (A64, b64, st64))
-            e1.record(stream)
-            torch.cuda.synchronize()
-            t64.append(e0.elapsed_time(e1))
-        fp64 = {"elements_per_s": n / (statistics.median(t64) * 1e-3), "ms_per_step": statistics.median(t64)}
-        step()
-        torch.cuda.synchronize()
-        Aoff = layout.A_offset.cpu().numpy() if layout.A_offset is not None else None
-        errs = []
-        for e in np.linspace(0, n - 1, 64).astype(np.int64):
-            d = int(degs[e])
-            s2 = nsh(d) ** 2
-            o = int(Aoff[e]) if Aoff is not None else int(e) * s2
-            x = A[o:o + s2].double()
-            y = A64[o:o + s2]
-            errs.append(float(torch.linalg.norm(x - y) / torch.linalg.norm(y)))
-        rel_err = max(errs)
-        # the FP32 CUDA-core path on the same batch, timed and checked the same way
-        if precision == "tc_f16x3":
-            A32 = torch.empty(layout.A_total, dtype=torch.float32, device=dev)
-            b32 = torch.empty(layout.b_total, dtype=torch.float32, device=dev)
-            st32 = torch.empty(n, dtype=torch.int32, device=dev)
-            step("fp32", (A32, b32, st32))
-            torch.cuda.synchronize()
-            t32 = []
-            for _ in range(max(1, args.fp64_steps)):
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                flush.fill_(2.0)
-                e0.record(stream)
-                step("fp32", (A32, b32, st32))
-                e1.record(stream)
+    head = run_workload(args.workload, args, ctx, headline=True)
+    per = None
+    if rank == 0 and world == 1 and not args.no_per_workload and not args.elements:
+        per = {}
+        for name in PER_WORKLOAD_ORDER:
+            if name == args.workload:
+                continue
+            try:
+                per[name] = run_workload(name, args, ctx, headline=False)
+            except Exception as exc:  # one workload's failure must not hide the headline
+                per[name] = {"error": f"{type(exc).__name__}: {exc}"}
                 torch.cuda.synchronize()
-                t32.append(e0.elapsed_time(e1))
-            errs32 = []
-            for e in np.linspace(0, n - 1, 64).astype(np.int64):
-                d = int(degs[e])
-                s2 = nsh(d) ** 2
-                o = int(Aoff[e]) if Aoff is not None else int(e) * s2
-                errs32.append(float(torch.linalg.norm(A32[o:o + s2].double() - A64[o:o + s2]) /
-                                    torch.linalg.norm(A64[o:o + s2])))
-            fp32_path = {"elements_per_s": n / (statistics.median(t32) * 1e-3), "ms_per_step": statistics.median(t32),
-                         "rel_err_vs_fp64_path_max_of_64_sampled": max(errs32)}
-            del A32, b32, st32
-        del A64, b64, st64
-
-    # end to end through the public API with host buffers
-    e2e = None
-    if not args.no_e2e:
-        hin = {k: torch.from_numpy(np.ascontiguousarray(w[k])).pin_memory() for k in ("geom", "K", "b", "c", "f")}
-        hA = torch.empty(layout.A_total, dtype=out_dtype).pin_memory()
-        hb = torch.empty(layout.b_total, dtype=out_dtype).pin_memory()
-        h2d = sum(t.numel() * t.element_size() for t in hin.values())
-        d2h = hA.numel() * hA.element_size() + hb.numel() * hb.element_size()
-        e2e_steps = max(2, min(args.steps, 5))
-        # a forward batch goes through the library's host-memory entry
-        # (fei_integrate_host): chunks of consecutive elements through two
-        # device slots, each chunk's download overlapping the next chunk's
-        # integration; the differentiation step copies, runs, copies back
-        pipe = None
-        if grads is None:
-            pipe = api.Pipeline(precision=precision, refs=refs)
-            hdeg = (torch.from_numpy(np.ascontiguousarray(w["degree"])).to(torch.int32).pin_memory()
-                    if deg is not None else None)
-            hst = torch.empty(n, dtype=torch.int32).pin_memory()
-            d2h += hst.numel() * 4
-            if hdeg is not None:
-                h2d += hdeg.numel() * 4
-
-        def e2e_step():
-            if pipe is not None:
-                pipe.integrate_host(hin["geom"], hin["K"], hin["b"], hin["c"], hin["f"], p=p, degree=hdeg,
-                                    per_qp=per_qp, out=(hA, hb, hst))
-                return
-            for k in hin:
-                g[k].copy_(hin[k], non_blocking=True)
-            step()
-            hA.copy_(A, non_blocking=True)
-            hb.copy_(bv, non_blocking=True)
-
-        e2e_step()  # untimed: first-use allocations
-        torch.cuda.synchronize()
-        torch.cuda.nvtx.range_push("end-to-end steps")
-        e2e_ms = []
-        for _ in range(e2e_steps):
-            t1 = time.perf_counter()
-            e2e_step()
-            torch.cuda.synchronize()
-            e2e_ms.append((time.perf_counter() - t1) * 1e3)
-        torch.cuda.nvtx.range_pop()
-        # the median step: the host link is shared with the machine's other
-        # tenants, and a burst of their traffic can slow single steps
-        dt = statistics.median(e2e_ms) * 1e-3
-        e2e = {"value": world * n / dt, "unit": "elements/s", "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(d2h), "ms_per_step": dt * 1e3,
-               "step_ms": [round(x, 3) for x in e2e_ms],
-               "pipeline": (f"fei_integrate_host: {pipe.n_chunks} chunks of <= {pipe.slot_bytes >> 20} MiB of A_e "
-                            "through two device slots, downloads overlapped with integration")
-               if pipe is not None else "copy in, forward + adjoint, copy back"}
-
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        n_sample = args.cpu_sample or cpu_sample_size(w, per_qp, args.cpu_seconds)
-        rate, cores, ns, dt = cpu_oracle_rate(w, None, n_sample, per_qp)
-        cpu = {"value": rate, "unit": "elements/s", "cores": cores, "kind": "oracle",
-               "sample": f"first {ns} elements of the workload ({dt:.1f} s on the host cores)"}
-
-    assembly = None
-    if args.assemble and rank == 0 and world == 1:
-        assembly = assembly_measure(api, w, [g[k] for k in ("geom", "K", "b", "c", "f")], deg, refs, precision,
-                                    flush, max(3, min(args.steps, 10)))
-        assembly["assemble_hbm_frac"] = assembly["assemble_gbs"] / peaks["hbm_gbs"]
+                torch.cuda.empty_cache()
 
     if rank == 0:
+        precision = head["precision"]
+        err = head["rel_err_vs_oracle"]
         line = {
-            "metric": metric_name(args), "value": value, "unit": "elements/s", "n_gpus": world,
-            "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None,
+            "metric": metric_name(args), "value": head["elements_per_s"], "unit": "elements/s", "n_gpus": world,
+            "steps": head["steps"], "warmup": max(3, args.warmup), "ms_per_step": head["ms_per_step"],
+            "higher_is_better": True, "scaling": args.scaling, "vs_baseline": None,
             "dtype": {"fp64": "f64", "fp32": "f32", "tc_f16x3": "f16x3->f32"}[precision],
             "data": "synthetic",
-            "config": {"workload": WORKLOAD_TEXT[args.workload], "precision": precision,
+            "config": {"workload": head["workload"], "precision": precision, "elements": head["elements"],
                        "l2": "256 MB buffer written between timed steps (outside the events); "
                              "each step also writes its outputs (> L2)",
-                       "gflops_algorithmic": F / (ms * 1e-3) / 1e9,
-                       "rel_err_vs_fp64_path_max_of_64_sampled": rel_err},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": launches_per_step * args.steps, "clocks": clk,
-            "fp64_path": fp64,
-            "fp32_path": fp32_path,
-            "plan": plan_choices,
+                       "gflops_algorithmic": head["gflops_algorithmic"],
+                       "rel_err_vs_oracle_max": err["max"] if err else None,
+                       "rel_err_vs_oracle_elements": err["elements"] if err else None,
+                       "sharding": (f"{args.scaling}: contiguous element ranges balanced by F(p) "
+                                    "(shard.partition), no data-path collective") if world > 1 else None},
+            "roofline": head["roofline"], "cpu_baseline": head.get("cpu_baseline"), "e2e": head.get("e2e"),
+            "gpu_launches": head["launches_per_step"] * head["steps"], "clocks": head["clocks"],
+            "rel_err_vs_oracle": err,
+            "fp64_path": head["fp64_path"], "fp32_path": head.get("fp32_path"),
+            "speedup_vs_fp64_path": head.get("speedup_vs_fp64_path"),
+            "plan": head.get("plan"), "plan_buckets": head.get("plan_buckets"),
+            "peaks_measured": live,
         }
-        if assembly is not None:
-            line["assembly"] = assembly
+        if "assembly" in head:
+            line["assembly"] = head["assembly"]
+        if per is not None:
+            line["per_workload"] = per
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.barrier()

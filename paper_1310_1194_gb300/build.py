@@ -62,6 +62,7 @@ def up_to_date() -> bool:
 
 def build(force: bool = False, verbose_ptxas: bool = False) -> str:
     if not force and up_to_date():
+        build_peaks()
         return LIB
     os.makedirs(OUT, exist_ok=True)
     with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 4)) as ex:
@@ -73,7 +74,28 @@ def build(force: bool = False, verbose_ptxas: bool = False) -> str:
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
+    build_peaks()
     return LIB
+
+
+PEAKS_SRC = os.path.join(HERE, "csrc_peaks", "fei_peaks.cu")
+PEAKS_LIB = os.path.join(OUT, "libfei_peaks.so")
+
+
+def build_peaks() -> str:
+    """The pipe-peak probes (csrc_peaks/), a library of their own: they are
+    measurement tools, not part of the integration ABI."""
+    if os.path.exists(PEAKS_LIB) and os.path.getmtime(PEAKS_LIB) >= os.path.getmtime(PEAKS_SRC):
+        return PEAKS_LIB
+    os.makedirs(OUT, exist_ok=True)
+    tmp = PEAKS_LIB + f".tmp{os.getpid()}"
+    cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-shared", "-cudart", "shared",
+           "-o", tmp, PEAKS_SRC, "-Xlinker", f"-rpath,{cuda_lib_dir()}"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc failed for {PEAKS_SRC}:\n{r.stdout}\n{r.stderr}")
+    os.replace(tmp, PEAKS_LIB)
+    return PEAKS_LIB
 
 
 if __name__ == "__main__":
