@@ -23,9 +23,20 @@
 // instruction; to keep the error independent of K, each K chunk (and N half)
 // accumulates into a fresh partial buffer in tensor memory, and the epilogue
 // warps add the partial into a running FP32 sum with round-to-nearest
-// ("promotion") while the MMAs fill the other partial buffer.  The point
-// operators are formed as in the FEI_FP32 path (element vectors, node
-// columns and w det J in FP64).
+// ("promotion") while the MMAs fill the next partial buffer.  The point
+// operators are formed as in the FEI_FP32 path: element vectors, the
+// vertical-node cross products and the node sums of det J in FP64; w det J
+// at each point from those FP64 sums in double-FP32 arithmetic (error-free
+// to about 2^-44 before its single rounding to FP32), which needs no FP64
+// instruction per point (FP64 is slow per instruction on this part).
+//
+// Operand A in tensor memory (p <= 5).  The producers write H' hi/lo with
+// tcgen05.st into tensor-memory columns and the MMAs read A from there
+// (tcgen05.mma [d], [a], b-desc), so that shared memory carries only the B
+// operand to the tensor core and no A tile is stored to it: at p = 4 the
+// A tiles were about 40 % of the shared-memory traffic, which bound the
+// kernel.  At p = 6, 7 the accumulators fill tensor memory and A stays in
+// shared memory.
 //
 // One thread block per SM walks a contiguous range of 128-row tiles;
 // nothing synchronises the whole block between tiles.  Roles (warp = 32
@@ -34,18 +45,20 @@
 //                split G image) and, for p <= 4, the chunk's rows of the
 //                FP32 table into shared memory with cp.async.bulk;
 //   warp 1       lane 0 issues tcgen05.mma (M = 128, N = N_pad or 2 halves);
-//   next warps   point operators: per tile, the geometry of the elements
-//                not seen before (FP64 node columns, w det J at every point),
-//                their scales and the row data; per K chunk, the point
-//                operators of its points into a ring that runs ahead of the
-//                producers;
+//   next warps   point operators: per tile, the elements not seen before
+//                (one warp per element for its FP64 node data, its inputs
+//                fetched during the previous tile; then w det J, status and
+//                operand bound at every point over all these warps), their
+//                scales and the row data; per K chunk, the point operators
+//                of its points into a ring that runs ahead of the producers;
 //   producers    per K chunk, H' for the 128 rows from the FP32 table (from
-//                the stage for p <= 4, else through L2), a thread working on
-//                a pair of consecutive points of a few rows with packed FP32
-//                FMAs (the pair's point operators held in registers); split
-//                into hi/lo (the residual by one mixed-precision FMA per
-//                value), written in the swizzled K-major operand layout,
-//                and the partial load vectors;
+//                the stage for p <= 4, else through L2) with packed FP32
+//                FMAs on pairs of consecutive points; split into hi/lo (the
+//                residual by one mixed-precision FMA per value), written to
+//                tensor memory (a thread per row and a few point pairs,
+//                p <= 5) or in the swizzled K-major shared-memory layout (a
+//                thread per point pair and a few rows, p = 6, 7); and the
+//                partial load vectors;
 //   last 4 warps epilogue: promotion of every partial accumulator, then
 //                scaling and stores of A_e (bulk copies of staged rows for
 //                a contiguous layout at p <= 4), b_e and the statuses.
@@ -163,6 +176,21 @@ __device__ __forceinline__ void tc_mma_f16(uint32_t d, uint64_t a, uint64_t b, u
       "l"(a), "l"(b), "r"(idesc), "r"(acc)
       : "memory");
 }
+// A from tensor memory (a = TMEM address of the 128 x 16 fp16 A slice:
+// lane = row, two consecutive K values per 32-bit column), B from shared
+// memory by descriptor.
+__device__ __forceinline__ void tc_mma_f16_ts(uint32_t d, uint32_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d),
+      "r"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+// 32 lanes x 8 columns of 32-bit values from registers (thread t = lane t)
+__device__ __forceinline__ void tmem_st8u(uint32_t taddr, const uint32_t *v) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr), "r"(v[0]),
+               "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+               : "memory");
+}
 __device__ __forceinline__ void named_bar(int id, int count) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
@@ -201,6 +229,30 @@ __device__ __forceinline__ void tmem_ld16_nw(uint32_t taddr, uint32_t *r) {
       : "r"(taddr));
 }
 
+// An FP64 value as an unevaluated sum of two FP32 values, hi = rn(x) and
+// lo = rn(x - hi): 48 significant bits, enough for products and sums whose
+// FP32 rounding is taken once at the end.
+__device__ __forceinline__ float2 split_f64(double x) {
+  const float hi = (float)x;
+  return make_float2(hi, (float)(x - (double)hi));
+}
+// a.x b.x + a.y b.x + a.x b.y (the lo * lo term is below 2^-46 relative)
+// as (product, error) with the error of the leading product exact (FMA)
+__device__ __forceinline__ float2 mul_ff(float2 a, float2 b) {
+  const float p = a.x * b.x;
+  float e = fmaf(a.x, b.x, -p);
+  e = fmaf(a.x, b.y, e);
+  e = fmaf(a.y, b.x, e);
+  return make_float2(p, e);
+}
+// sum of two (value, error) pairs, the rounding error of the leading sum
+// kept exactly (Knuth's two-sum)
+__device__ __forceinline__ float2 add_ff(float2 a, float2 b) {
+  const float s = a.x + b.x;
+  const float bb = s - a.x;
+  const float err = (a.x - (s - bb)) + (b.x - bb);
+  return make_float2(s, err + a.y + b.y);
+}
 __device__ __forceinline__ float exp2i(int k) {  // exact 2^k for |k| < 126
   return __int_as_float((127 + k) << 23);
 }
@@ -228,11 +280,25 @@ struct TcCfg {
   // chunks per promotion unit: a partial accumulator collects 4 K slices
   // (12 MMAs) before the epilogue adds it into the running sum
   static constexpr int UC = KSL == 2 ? 2 : 1;
-  static constexpr int TMEM_COLS = 3 * NPAD <= 256 ? 256 : 512;
-  // running sum: columns [0, RT) in TMEM after the two partial buffers, the
+  // partial accumulators the MMAs fill in turn while the epilogue promotes
+  // the previous ones: three where tensor memory leaves room (p <= 4), so
+  // that the MMAs do not wait for the promotion of the one before
+  static constexpr int NPART = (P <= 4) ? 3 : 2;
+  // running sum: columns [0, RT) in TMEM after the partial buffers, the
   // rest (RREG columns) in registers of the epilogue threads
-  static constexpr int RT = (512 - 2 * NMMA) < NPAD ? (512 - 2 * NMMA) : NPAD;
+  static constexpr int RT = (512 - NPART * NMMA) < NPAD ? (512 - NPART * NMMA) : NPAD;
   static constexpr int RREG = NPAD - RT;
+  // TS: the A operand (H' split into hi/lo) lives in tensor memory, written
+  // by the producers with tcgen05.st and read by the MMA from there, so the
+  // MMA reads only B from shared memory and the producers store nothing to
+  // it (p <= 5, where the accumulators leave room).  Per stage KCH columns:
+  // KCH/2 of hi (two fp16 per column) then KCH/2 of lo, from column ABASE.
+  static constexpr bool TS = P <= 5;
+  static constexpr int ACC_COLS = NPART * NMMA + RT;
+  static constexpr int RSUM = NPART * NMMA;  // first column of the running sum
+  static constexpr int ABASE = TS ? (ACC_COLS + 31) / 32 * 32 : 0;
+  static constexpr int ACOLS = KCH;
+  static constexpr int TMEM_COLS = TS ? 512 : (3 * NPAD <= 256 ? 256 : 512);
   static constexpr int EMAX = (128 + NSH - 1) / NSH + 1;  // elements a tile can touch
   static constexpr int NSLOT = EMAX + 1;  // element slots: a tile's elements plus the one it shares
   static constexpr int NDW = P == 7 ? 2 : P == 6 || P == 5 ? 4 : 6;  // point-operator warps
@@ -264,15 +330,24 @@ struct TcCfg {
   static constexpr int G_BYTES = GS ? PPC * GST * 16 : 0;
   static constexpr int G_AREA = (G_BYTES + 1023) / 1024 * 1024;
   static constexpr bool BS = P <= 4;  // bulk stores of staged rows (shared-memory budget)
-  static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES + G_AREA;
-  static constexpr int STAGES = P == 7 ? 3 : 2;
+  static constexpr int STAGE_BYTES = (TS ? 0 : 2 * A_BYTES) + 2 * B_BYTES + G_AREA;
+  static constexpr int STAGES = P == 7 ? 3 : (TS && ABASE + 3 * ACOLS <= 512 ? 3 : 2);
+  // TS producer layout: PQ warps per TMEM lane quarter, each thread one row
+  // (its lane) and PPW consecutive point pairs of the chunk
+  static constexpr int PQ = NPW / 4, PPW = PP / PQ;
+  // load-vector partials per row (one per producer thread that covers it)
+  static constexpr int BSN = TS ? PQ : PP;
   static constexpr int DYN_SMEM = STAGES * STAGE_BYTES + 1024;
   static_assert(NMMA % 16 == 0 && NMMA <= 256, "MMA N");
   static_assert(RT % 16 == 0 && RREG % 16 == 0 && RT >= 0, "running-sum split");
-  static_assert(2 * NMMA + RT <= TMEM_COLS, "tensor memory");
+  static_assert(NPART * NMMA + RT <= TMEM_COLS, "tensor memory");
+  static_assert(!TS || (ABASE + STAGES * ACOLS <= TMEM_COLS && PP % PQ == 0 && (PPW * 4) % 8 == 0 &&
+                        STAGE_BYTES % 1024 == 0),
+                "tensor-memory A operand");
   static_assert(PPC % 2 == 0 && (GS ? 32 % PP == 0 && RW % RG == 0 : NPW % PP == 0 && RWP % 32 == 0) && RPT >= 1,
                 "producer layout");
   static_assert(STAGES > UC, "a promotion unit must leave a stage for the producers");
+  static_assert(BSN <= PP, "load-vector partials");
   static_assert(DRING >= 2 * DB, "the operator ring holds two rounds");
   static_assert(NEW == 4, "four consecutive epilogue warps cover the four TMEM lane quarters");
 };
@@ -283,8 +358,9 @@ struct TcElem {
   double X[18];
   double ev[21];          // element vectors A1, B1, A2, B2, C, D1, D2 (FP64)
   float evf[21];          // the same rounded once to FP32
-  float cf[14];           // the per-element coefficients rounded once to FP32
-  double zabg[C::NZ][3];  // w_z (n3.C, n3.D1, n3.D2) per vertical node (FP64)
+  alignas(16) float cf[16];  // the per-element coefficients rounded once to FP32 (14 used)
+  float cn[3];            // their norms in the scale bound: sqrt(||K||_1 ||K||_inf), |b|, |c|
+  float2 zabg[C::NZ][3];  // w_z (n3.C, n3.D1, n3.D2) per vertical node: FP64 as FP32 hi + lo
   float zc1f[C::NZ][3], zc2f[C::NZ][3], zn3f[C::NZ][3];
   float tc3f[C::NT][3];
   float zn[C::NZ][3];  // |c1|, |c2|, |c1 x c2| per vertical node (FP32)
@@ -314,8 +390,8 @@ struct TcAux {
   uint64_t empty[C::STAGES];  // MMAs of the stage completed
   uint64_t dfull[C::DRING];   // point operators of a chunk ready
   uint64_t dempty[C::DRING];  // producers done with them
-  uint64_t part_full[2];      // partial accumulator ready for promotion
-  uint64_t promo_done[2];     // partial accumulator promoted (free again)
+  uint64_t part_full[3];      // partial accumulator ready for promotion
+  uint64_t promo_done[3];     // partial accumulator promoted (free again)
   uint64_t meta_full[2];
   uint64_t meta_empty[2];
   uint64_t bsum_full[2];      // producers' load-vector partials of a tile
@@ -325,7 +401,7 @@ struct TcAux {
   int dsnap;
   TcElem<P> el[C::NSLOT];    // element k lives in slot k % NSLOT
   float sp[C::NSLOT][C::NQ];  // w det J per point (FP32, from FP64)
-  double ttab[C::NT][3];     // (w_t, w_t xi1, w_t xi2) per triangle node
+  float2 ttab[C::NT][3];     // (w_t, w_t xi1, w_t xi2) per triangle node: FP64 as FP32 hi + lo
   float ttabf[C::NT][3];     // (w_t, xi1, xi2) in FP32
   float ztabf[C::NZ][2];     // (zeta, w_z) in FP32
   // point operators of a chunk, [tile-relative element][k'][point pair]:
@@ -383,37 +459,29 @@ __device__ __forceinline__ float norm3f(const float *v) { return sqrtf(v[0] * v[
 // the element's power-of-two operand scale, which only has to keep the fp16
 // operands in range; an over-estimate costs at most a few bits of headroom.
 template <int P, class AX>
-__device__ __forceinline__ float tc_bound(const TcElem<P> &E, const AX &ax, const float *cf, int iz, int t,
+__device__ __forceinline__ float tc_bound(const TcElem<P> &E, const AX &ax, const float *cn, int iz, int t,
                                           float sf) {
   const float w = ax.ztabf[iz][1] * ax.ttabf[t][0];
   const float n3 = E.tn[t];
   const float a0 = E.zn[iz][1] * n3, a1 = n3 * E.zn[iz][0], a2 = E.zn[iz][2];
   const float amax = fmaxf(fmaxf(a0, a1), a2), asum = a0 + a1 + a2;
+  // cn: the coefficient norms (coef_norms).  w / sf only sets a power-of-two scale with two bits of headroom in fp16
+  // range, so the fast division (error of a few ulp) is enough
+  return fmaxf(sf * cn[2], w * amax * (cn[1] + __fdividef(w, sf) * cn[0] * asum));
+}
+// The coefficient norms of the bound: sqrt(||K||_1 ||K||_inf) >= ||K||_2,
+// |b| and |c|, from the 14 FP32 coefficient values.
+__device__ __forceinline__ void coef_norms(const float *cf, float *cn) {
   float r1 = 0.f, ri = 0.f;
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     r1 = fmaxf(r1, fabsf(cf[k]) + fabsf(cf[3 + k]) + fabsf(cf[6 + k]));
     ri = fmaxf(ri, fabsf(cf[3 * k]) + fabsf(cf[3 * k + 1]) + fabsf(cf[3 * k + 2]));
   }
-  const float kn = sqrtf(r1 * ri), bn = norm3f(cf + 9);
-  return fmaxf(sf * fabsf(cf[12]), w * amax * (bn + (w / sf) * kn * asum));
+  cn[0] = sqrtf(r1 * ri);
+  cn[1] = norm3f(cf + 9);
+  cn[2] = fabsf(cf[12]);
 }
-// One component (j = vector * 3 + axis) of the element vectors, FP64:
-// A1, B1, A2, B2, C, D1, D2 from the bottom (P) and top (Q) vertices.
-__device__ __forceinline__ double elem_vector_component(const double *X, int j) {
-  const int v = j / 3, k = j - 3 * v;
-  const double p0 = X[k], p1 = X[3 + k], p2 = X[6 + k], q0 = X[9 + k], q1 = X[12 + k], q2 = X[15 + k];
-  switch (v) {
-    case 0: return 0.5 * ((p1 - p0) + (q1 - q0));
-    case 1: return 0.5 * ((q1 - q0) - (p1 - p0));
-    case 2: return 0.5 * ((p2 - p0) + (q2 - q0));
-    case 3: return 0.5 * ((q2 - q0) - (p2 - p0));
-    case 4: return 0.5 * (q0 - p0);
-    case 5: return 0.5 * ((q1 - p1) - (q0 - p0));
-    default: return 0.5 * ((q2 - p2) - (q0 - p0));
-  }
-}
-
 // Shared-memory matrix descriptor of a K-major operand with ROWB-byte rows
 // in the ROWB-byte swizzle layout; 8-row groups 8 * ROWB bytes apart.
 template <int ROWB>
@@ -464,8 +532,9 @@ __global__ void __launch_bounds__(TcCfg<P, V>::NTHREADS, 1)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t dbase = (smem_u32(dsm_raw) + 1023u) & ~1023u;
   auto stageA = [&](int s, int piece) { return dbase + s * C::STAGE_BYTES + piece * C::A_BYTES; };
-  auto stageB = [&](int s) { return dbase + s * C::STAGE_BYTES + 2 * C::A_BYTES; };
-  auto stageG = [&](int s) { return dbase + s * C::STAGE_BYTES + 2 * C::A_BYTES + 2 * C::B_BYTES; };
+  constexpr int AST = C::TS ? 0 : 2 * C::A_BYTES;  // A tiles of a stage in shared memory (SS only)
+  auto stageB = [&](int s) { return dbase + s * C::STAGE_BYTES + AST; };
+  auto stageG = [&](int s) { return dbase + s * C::STAGE_BYTES + AST + 2 * C::B_BYTES; };
   volatile int *abort_flag = &ax.abort_flag;
 
   if (tid == 0) {
@@ -478,9 +547,11 @@ __global__ void __launch_bounds__(TcCfg<P, V>::NTHREADS, 1)
       mbar_init(smem_u32(&ax.dfull[k]), 1);
       mbar_init(smem_u32(&ax.dempty[k]), C::NPW);
     }
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < C::NPART; ++k) {
       mbar_init(smem_u32(&ax.part_full[k]), 1);
       mbar_init(smem_u32(&ax.promo_done[k]), C::NEW);
+    }
+    for (int k = 0; k < 2; ++k) {
       mbar_init(smem_u32(&ax.meta_full[k]), 1);
       mbar_init(smem_u32(&ax.meta_empty[k]), C::NEW);
       mbar_init(smem_u32(&ax.bsum_full[k]), C::NPW);
@@ -498,9 +569,9 @@ __global__ void __launch_bounds__(TcCfg<P, V>::NTHREADS, 1)
   // quadrature node tables of this degree, once per block
   for (int t = tid; t < NT; t += blockDim.x) {
     const double x1 = a.tnode[4 * t], x2 = a.tnode[4 * t + 1], wt = a.tnode[4 * t + 2];
-    ax.ttab[t][0] = wt;
-    ax.ttab[t][1] = wt * x1;
-    ax.ttab[t][2] = wt * x2;
+    ax.ttab[t][0] = split_f64(wt);
+    ax.ttab[t][1] = split_f64(wt * x1);
+    ax.ttab[t][2] = split_f64(wt * x2);
     ax.ttabf[t][0] = (float)wt;
     ax.ttabf[t][1] = (float)x1;
     ax.ttabf[t][2] = (float)x2;
@@ -532,6 +603,22 @@ __global__ void __launch_bounds__(TcCfg<P, V>::NTHREADS, 1)
     const int td = tid - C::W_DW * 32;  // 0 .. ND-1
     int it = 0;
     int64_t kdone = -1;  // elements 0 .. kdone of this block are set up
+    // the inputs of the element this warp sets up first in the next tile,
+    // loaded while the current tile's point operators are formed (lanes
+    // 0-17 a vertex coordinate, 18-31 a per-element coefficient)
+    int64_t pf_k = -1;
+    double pf_x = 0.0;
+    auto fetch_input = [&](int64_t k) {
+      const int64_t e = a.list ? (int64_t)a.list[k] : k;
+      double x = 0.0;
+      if (lane < 18) {
+        x = a.geom[18 * e + lane];
+      } else if (a.coef_mode == FEI_COEF_PER_ELEMENT) {
+        const int j = lane - 18;
+        x = j < 9 ? a.K[9 * e + j] : j < 12 ? a.b[3 * e + (j - 9)] : j == 12 ? a.c[e] : a.f[e];
+      }
+      return x;
+    };
     for (int64_t tile = t_begin; tile < t_end; ++tile, ++it) {
       // the point-operator warps leave together (they share named barriers)
       if (td == 0) ax.dsnap = *abort_flag;
@@ -546,100 +633,99 @@ __global__ void __launch_bounds__(TcCfg<P, V>::NTHREADS, 1)
       const int nnew = (int)(k1 - kn0 + 1);
       kdone = k1;
       auto slot_of = [&](int64_t k) { return (int)(k % C::NSLOT); };
-      // geometry and coefficients of the new elements (one warp per
-      // element: lanes 0-17 the vertices, 18-31 the coefficients).  FP64 is
-      // slow per instruction on this part, so every FP64 step below runs
-      // across lanes rather than in one thread.
+      // Set-up of the new elements, one warp per element with lanes in
+      // parallel and only warp-level synchronisation between its steps, so
+      // that the elements of a tile are set up at the same time and no step
+      // waits for the whole group (FP64 is slow per instruction on this
+      // part, and a step of a few FP64 operations per element is mostly
+      // latency).
       for (int i = warp - C::W_DW; i < nnew; i += C::NDW) {
-        TcElem<P> &E = ax.el[slot_of(kn0 + i)];
+        const int sl = slot_of(kn0 + i);
+        TcElem<P> &E = ax.el[sl];
         const int64_t e = a.list ? (int64_t)a.list[kn0 + i] : kn0 + i;
-        bool ok = true;
-        if (lane < 18) {
-          const double x = a.geom[18 * e + lane];
-          E.X[lane] = x;
-          ok = finite64(x);
-        } else if (a.coef_mode == FEI_COEF_PER_ELEMENT) {
-          const int k = lane - 18;
-          const double x = k < 9 ? a.K[9 * e + k] : k < 12 ? a.b[3 * e + (k - 9)] : k == 12 ? a.c[e] : a.f[e];
-          E.cf[k] = (float)x;
-          ok = finite64(x);
-        }
+        // geometry (lanes 0-17) and per-element coefficients (lanes 18-31),
+        // prefetched during the previous tile when this warp knew the element
+        const double x = pf_k == kn0 + i ? pf_x : fetch_input(kn0 + i);
+        const bool ok = __all_sync(0xffffffffu, finite64(x));
+        if (lane >= 18 && a.coef_mode == FEI_COEF_PER_ELEMENT) E.cf[lane - 18] = (float)x;
         if (lane == 0) {
           E.e = e;
           E.aoff = out_a(a, kn0 + i, e, NSH);
           E.boff = out_b(a, kn0 + i, e, NSH);
           E.qoff = a.q_off ? a.q_off[e] : e * (int64_t)NQ;
+          E.status = ok ? 0 : FEI_ERR_NONFINITE;
           E.mbits = 0;
         }
-        ok = __all_sync(0xffffffffu, ok);
-        if (lane == 0) E.status = ok ? 0 : FEI_ERR_NONFINITE;
-      }
-      named_bar(2, ND);
-      // element vectors, one component per thread (FP64, and rounded once)
-      for (int idx = td; idx < nnew * 21; idx += ND) {
-        const int i = idx / 21, j = idx - i * 21;
-        TcElem<P> &E = ax.el[slot_of(kn0 + i)];
-        const double v = elem_vector_component(E.X, j);
-        E.ev[j] = v;
-        E.evf[j] = (float)v;
-      }
-      named_bar(2, ND);
-      // vertical nodes: c1, c2, n3 = c1 x c2 and w_z (n3.C, n3.D1, n3.D2) in
-      // FP64 (so that w det J = w_t (..) below is FP64), one lane per vector
-      // component and node (shuffles give the cross product); the columns
-      // for the FP32 adjugate from the FP32 element vectors.
-      {
-        constexpr int ZPW = 30;  // 10 nodes x 3 components per warp
-        const int ntask = nnew * NZ;
-        for (int base = (warp - C::W_DW) * 10; base < ntask; base += C::NDW * 10) {
-          const int node = base + lane / 3, k = lane % 3;
-          const bool act = lane < ZPW && node < ntask;
-          const int i = act ? node / NZ : 0, iz = act ? node - (node / NZ) * NZ : 0;
-          TcElem<P> &E = ax.el[slot_of(kn0 + i)];
+        // element vectors A1, B1, A2, B2, C, D1, D2 (FP64): lane j < 21 forms
+        // component k = j % 3 of vector j / 3 as (X_a - X_b) +- (X_c - X_d)
+        // over vertices a, b, c, d, halved, from the lanes holding them
+        double ev;
+        {
+          const int v = lane < 21 ? lane / 3 : 0, k = lane < 21 ? lane % 3 : 0;
+          // vertices (a, b, c, d) of vector v, 3 bits each, 12 bits per
+          // vector, in an immediate (a table in memory would be a local load)
+          //   A1 (1,0,4,3)  B1 (4,3,1,0)  A2 (2,0,5,3)  B2 (5,3,2,0)
+          //   C  (3,0,0,0)  D1 (4,1,3,0)  D2 (5,2,3,0)
+          constexpr unsigned long long kTab =
+              (0x223ull << 0) | (0x8C8ull << 12) | (0x42Bull << 24) | (0xAD0ull << 36) | (0x600ull << 48);
+          constexpr unsigned long long kTab2 = (0x858ull << 0) | (0xA98ull << 12);  // D1, D2
+          constexpr unsigned kNeg = 0x6Au;  // B1, B2, D1, D2 subtract
+          const unsigned tv = (unsigned)((v < 5 ? kTab >> (12 * v) : kTab2 >> (12 * (v - 5))) & 0xFFFu);
+          const double xa = __shfl_sync(0xffffffffu, x, 3 * ((tv >> 9) & 7u) + k);
+          const double xb = __shfl_sync(0xffffffffu, x, 3 * ((tv >> 6) & 7u) + k);
+          const double xc = __shfl_sync(0xffffffffu, x, 3 * ((tv >> 3) & 7u) + k);
+          const double xd = __shfl_sync(0xffffffffu, x, 3 * (tv & 7u) + k);
+          const double t1 = xa - xb, t2 = xc - xd;
+          ev = 0.5 * (((kNeg >> v) & 1u) ? t1 - t2 : t1 + t2);
+          if (lane < 21) E.evf[lane] = (float)ev;
+        }
+        // vertical nodes (lanes 3 iz + k): c1, c2 and n3 = c1 x c2 in FP64 and
+        // w_z (n3.C, n3.D1, n3.D2), so that w det J = w_t (..) is FP64; the
+        // FP32 columns and their norms from the FP32 element vectors
+        {
+          const bool act = lane < 3 * NZ;
+          const int iz = act ? lane / 3 : 0, k = act ? lane % 3 : 0;
           const double z = a.znode[2 * iz], wz = a.znode[2 * iz + 1];
-          const double c1 = fma(z, E.ev[3 + k], E.ev[0 + k]);
-          const double c2 = fma(z, E.ev[9 + k], E.ev[6 + k]);
-          // components k+1, k+2 (mod 3) from the neighbouring lanes of the node
+          const double c1 = fma(z, __shfl_sync(0xffffffffu, ev, 3 + k), __shfl_sync(0xffffffffu, ev, k));
+          const double c2 = fma(z, __shfl_sync(0xffffffffu, ev, 9 + k), __shfl_sync(0xffffffffu, ev, 6 + k));
           const int g0 = lane - k, l1 = g0 + (k + 1) % 3, l2 = g0 + (k + 2) % 3;
           const double c1a = __shfl_sync(0xffffffffu, c1, l1), c1b = __shfl_sync(0xffffffffu, c1, l2);
           const double c2a = __shfl_sync(0xffffffffu, c2, l1), c2b = __shfl_sync(0xffffffffu, c2, l2);
           const double n3 = c1a * c2b - c1b * c2a;  // (c1 x c2)_k
-          double ab = n3 * E.ev[12 + k], bb = n3 * E.ev[15 + k], gb = n3 * E.ev[18 + k];
+          double ab = n3 * __shfl_sync(0xffffffffu, ev, 12 + k);
+          double bb = n3 * __shfl_sync(0xffffffffu, ev, 15 + k);
+          double gb = n3 * __shfl_sync(0xffffffffu, ev, 18 + k);
           ab += __shfl_sync(0xffffffffu, ab, l1) + __shfl_sync(0xffffffffu, ab, l2);
           bb += __shfl_sync(0xffffffffu, bb, l1) + __shfl_sync(0xffffffffu, bb, l2);
           gb += __shfl_sync(0xffffffffu, gb, l1) + __shfl_sync(0xffffffffu, gb, l2);
-          if (act && k == 0) {
-            E.zabg[iz][0] = wz * ab;
-            E.zabg[iz][1] = wz * bb;
-            E.zabg[iz][2] = wz * gb;
+          // lane k of the node stores value k, split into FP32 hi + lo
+          if (act) E.zabg[iz][k] = split_f64(wz * (k == 0 ? ab : k == 1 ? bb : gb));
+          const float evf = (float)ev;
+          const float zf = ax.ztabf[iz][0];
+          const float f1 = fmaf(zf, __shfl_sync(0xffffffffu, evf, 3 + k), __shfl_sync(0xffffffffu, evf, k));
+          const float f2 = fmaf(zf, __shfl_sync(0xffffffffu, evf, 9 + k), __shfl_sync(0xffffffffu, evf, 6 + k));
+          const float f1a = __shfl_sync(0xffffffffu, f1, l1), f1b = __shfl_sync(0xffffffffu, f1, l2);
+          const float f2a = __shfl_sync(0xffffffffu, f2, l1), f2b = __shfl_sync(0xffffffffu, f2, l2);
+          const float fn = f1a * f2b - f1b * f2a;
+          float s1 = f1 * f1, s2 = f2 * f2, s3 = fn * fn;
+          s1 += __shfl_sync(0xffffffffu, s1, l1) + __shfl_sync(0xffffffffu, s1, l2);
+          s2 += __shfl_sync(0xffffffffu, s2, l1) + __shfl_sync(0xffffffffu, s2, l2);
+          s3 += __shfl_sync(0xffffffffu, s3, l1) + __shfl_sync(0xffffffffu, s3, l2);
+          if (act) {
+            E.zc1f[iz][k] = f1;
+            E.zc2f[iz][k] = f2;
+            E.zn3f[iz][k] = fn;
+            if (k == 0) {
+              E.zn[iz][0] = sqrtf(s1);
+              E.zn[iz][1] = sqrtf(s2);
+              E.zn[iz][2] = sqrtf(s3);
+            }
           }
         }
-      }
-      // FP32 columns and their norms: vertical nodes (c1, c2, n3) and
-      // triangle nodes (c3)
-      for (int idx = td; idx < nnew * (NZ + NT); idx += ND) {
-        const int i = idx / (NZ + NT), nd = idx - i * (NZ + NT);
-        TcElem<P> &E = ax.el[slot_of(kn0 + i)];
-        if (nd < NZ) {
-          const float zf = ax.ztabf[nd][0];
-          float f1[3], f2[3], fn[3];
-#pragma unroll
-          for (int k = 0; k < 3; ++k) {
-            f1[k] = fmaf(zf, E.evf[3 + k], E.evf[0 + k]);
-            f2[k] = fmaf(zf, E.evf[9 + k], E.evf[6 + k]);
-          }
-          cross3(f1, f2, fn);
-#pragma unroll
-          for (int k = 0; k < 3; ++k) {
-            E.zc1f[nd][k] = f1[k];
-            E.zc2f[nd][k] = f2[k];
-            E.zn3f[nd][k] = fn[k];
-          }
-          E.zn[nd][0] = norm3f(f1);
-          E.zn[nd][1] = norm3f(f2);
-          E.zn[nd][2] = norm3f(fn);
-        } else {
-          const int t = nd - NZ;
+        __syncwarp();
+        if (lane == 0 && a.coef_mode == FEI_COEF_PER_ELEMENT) coef_norms(E.cf, E.cn);
+        // triangle nodes: c3 = C + xi1 D1 + xi2 D2 (FP32) and |c3|
+        for (int t = lane; t < NT; t += 32) {
           const float x1 = ax.ttabf[t][1], x2 = ax.ttabf[t][2];
           float c3[3];
 #pragma unroll
@@ -649,10 +735,15 @@ __global__ void __launch_bounds__(TcCfg<P, V>::NTHREADS, 1)
           }
           E.tn[t] = norm3f(c3);
         }
+        __syncwarp();
       }
       named_bar(2, ND);
-      // pre-pass over the points of the new elements: w det J = w_t (a +
-      // xi1 b + xi2 g) in FP64 (rounded once), status, and the bound of
+      // every point of the new elements, spread over all point-operator
+      // threads (one warp's serial pass over an element's points took ten
+      // times longer): w det J = w_t (a + xi1 b + xi2 g) from the FP64 node
+      // sums in double-FP32 arithmetic (each factor an FP32 hi + lo pair,
+      // products and sum error-free to about 2^-44), rounded once -- no FP64
+      // instruction per point; the status; and the bound of
       // max_{q,b} sum_a |Dt[a][b]| that sets the element's scale
       for (int base = 0; base < nnew * NQ; base += ND) {
         const int idx = base + td;
@@ -664,20 +755,24 @@ __global__ void __launch_bounds__(TcCfg<P, V>::NTHREADS, 1)
           const int sl = slot_of(kn0 + i);
           TcElem<P> &E = ax.el[sl];
           const int iz = q / NT, t = q - iz * NT;
-          const double s = ax.ttab[t][0] * E.zabg[iz][0] + ax.ttab[t][1] * E.zabg[iz][1] + ax.ttab[t][2] * E.zabg[iz][2];
-          const float sf = (float)s;
-          int st = !finite64(s) ? FEI_ERR_NONFINITE : (!(sf > 0.f) ? FEI_ERR_NEGATIVE_JACOBIAN : 0);
-          float cq[14];
-          const float *cp = E.cf;
+          const float2 sd = add_ff(add_ff(mul_ff(ax.ttab[t][0], E.zabg[iz][0]), mul_ff(ax.ttab[t][1], E.zabg[iz][1])),
+                                   mul_ff(ax.ttab[t][2], E.zabg[iz][2]));
+          const float sf = sd.x + sd.y;
+          int st = !(fabsf(sf) <= 3.402823466e38f) ? FEI_ERR_NONFINITE : (!(sf > 0.f) ? FEI_ERR_NEGATIVE_JACOBIAN : 0);
+          // the bound reads the coefficient norms after the 16 values
+          float cq[19];
           if (a.coef_mode == FEI_COEF_PER_POINT) {
             if (!load_coef_tc(a, E.qoff + q, cq)) st = FEI_ERR_NONFINITE;
-            cp = cq;
+            coef_norms(cq, cq + 16);
+          } else {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) cq[16 + k] = E.cn[k];
           }
           ax.sp[sl][q] = sf;
           if (st) {
             atomicMax(&E.status, st);
           } else {
-            m = tc_bound<P>(E, ax, cp, iz, t, sf);
+            m = tc_bound<P>(E, ax, cq + 16, iz, t, sf);
             if (!(m <= 3.0e38f)) {
               atomicMax(&E.status, FEI_ERR_NONFINITE);
               m = 0.f;
@@ -710,6 +805,18 @@ __global__ void __launch_bounds__(TcCfg<P, V>::NTHREADS, 1)
         E.down = dn >= -126 && dn <= 126 ? exp2i(dn) : ldexpf(1.0f, dn);
       }
       named_bar(2, ND);
+      // prefetch for the next tile: its new elements start after k1
+      pf_k = -1;
+      if (tile + 1 < t_end) {
+        const int64_t r0n = r0 + 128;
+        int64_t k1n = (r0n + 127) / NSH;
+        if (k1n > items - 1) k1n = items - 1;
+        const int64_t kf = k1 + 1 + (warp - C::W_DW);
+        if (kf <= k1n) {
+          pf_k = kf;
+          pf_x = fetch_input(kf);
+        }
+      }
       // row data of this tile (double-buffered by tile parity)
       const int slot = it & 1;
       const bool mok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&ax.meta_empty[slot]), ((uint32_t)(it >> 1) & 1u) ^ 1u, abort_flag));
@@ -759,14 +866,23 @@ __global__ void __launch_bounds__(TcCfg<P, V>::NTHREADS, 1)
             float *D1 = reinterpret_cast<float *>(&ax.Dc[dr][el][0][qq >> 1]) + (qq & 1);
             float cv[14];
             if (q < NQ && E.status == 0) {
-              float cq[14];
-              const float *cp = E.cf;
+              float cq[16];
               if (a.coef_mode == FEI_COEF_PER_POINT) {
                 (void)load_coef_tc(a, E.qoff + q, cq);  // finiteness was tested in the pre-pass
-                cp = cq;
+              } else {
+                // four 16-byte loads (the values are the same for the points of an element)
+                const float4 *c4 = reinterpret_cast<const float4 *>(E.cf);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                  const float4 v = c4[k];
+                  cq[4 * k] = v.x;
+                  cq[4 * k + 1] = v.y;
+                  cq[4 * k + 2] = v.z;
+                  cq[4 * k + 3] = v.w;
+                }
               }
               float Dt[16];
-              tc_point<P>(E, ax, cp, q, ax.sp[sl][q], Dt);
+              tc_point<P>(E, ax, cq, q, ax.sp[sl][q], Dt);
               const float up = E.up;
 #pragma unroll
               for (int k = 0; k < 13; ++k) cv[k] = Dt[k] * up;
@@ -782,6 +898,153 @@ __global__ void __launch_bounds__(TcCfg<P, V>::NTHREADS, 1)
         named_bar(2, ND);
         if (td < cn && ok) mbar_arrive(smem_u32(&ax.dfull[(it * NCH + c0 + td) % DR]));
       }
+    }
+  } else if (warp >= C::W_PW && warp < C::W_EW && C::TS) {
+    // ========================================================= producers (TS)
+    // A thread owns one row of the tile (its tensor-memory lane: warp w
+    // reaches lanes 32 (w % 4) ..) and PPW consecutive point pairs of every
+    // chunk; it forms H' for both points of a pair with packed FP32 FMAs,
+    // splits into fp16 hi/lo and writes its pairs' hi and lo values into the
+    // stage's A columns with one tcgen05.st each.  The point operators of a
+    // pair are broadcast loads (the warp's rows belong to one or two
+    // elements).
+    const int tp = tid - C::W_PW * 32;  // 0 .. NP-1
+    const int pw = warp - C::W_PW;
+    const int quarter = warp & 3;
+    const int part = pw >> 2;  // the PQ warps of a lane quarter split the pairs
+    const int pp0 = part * C::PPW;
+    const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
+    const int row = quarter * 32 + lane;
+    constexpr int GST = C::GST, PPW = C::PPW;
+    int it = 0;
+    int64_t tile = t_begin;
+    for (; tile < t_end; ++tile, ++it) {
+      if (*abort_flag) break;
+      const int64_t r0 = tile * 128;
+      const int64_t k0 = r0 / NSH;
+      // a row past the end computes finite values from element 0 of the
+      // tile; the epilogue drops it
+      int rel = 0, ri = 0;
+      {
+        const int64_t grow = r0 + row;
+        if (grow < rows_total) {
+          const int64_t kk = grow / NSH;
+          ri = (int)(grow - kk * NSH);
+          rel = (int)(kk - k0);
+        }
+      }
+      float2 bp = make_float2(0.f, 0.f);
+      for (int c = 0; c < NCH; ++c) {
+        const int g = it * NCH + c, s = g % S, dr = g % DR;
+        const uint32_t u = (uint32_t)(g / S), ud = (uint32_t)(g / DR);
+        float4 ga[PPW], gb[PPW];
+        // from L2 (the table is not in the stage): the first two pairs are
+        // fetched before the waits, so that their latency overlaps them
+        constexpr int PRE = 0;
+        if constexpr (!C::GS) {
+#pragma unroll
+          for (int j = 0; j < PRE; ++j) {
+            ga[j] = __ldg(gp + (size_t)((c * 2 + 0) * C::PP + pp0 + j) * GST + ri);
+            gb[j] = __ldg(gp + (size_t)((c * 2 + 1) * C::PP + pp0 + j) * GST + ri);
+          }
+        }
+        // A columns free (the stage's MMAs completed: with the table in the
+        // stage, its copy landing implies that), point operators ready
+        bool ok = mbar_wait(smem_u32(&ax.dfull[dr]), ud & 1u, abort_flag);
+        if constexpr (C::GS) ok = ok && mbar_wait(smem_u32(&ax.bfull[s]), u & 1u, abort_flag);
+        else ok = ok && mbar_wait(smem_u32(&ax.empty[s]), (u & 1u) ^ 1u, abort_flag);
+        ok = __all_sync(0xffffffffu, ok);
+        if (!ok) break;
+        tc_fence_after();
+        const float4 *Gs = reinterpret_cast<const float4 *>(dsm_raw + (stageG(s) - smem_u32(dsm_raw)));
+        const uint32_t acol = tmem + lane_base + (uint32_t)(C::ABASE + s * C::ACOLS + pp0 * 4);
+        const float4 *D4 = &ax.Dc[dr][rel][0][pp0];
+        // two pairs at a time: 8 columns of hi and 8 of lo per tcgen05.st
+        // (holding all pairs' values until one wider store raised the
+        // register peak above the budget)
+        // (with the table prefetched from L2 into registers the loop is
+        // unrolled, so that the prefetched values stay in registers)
+#pragma unroll(PRE == 0 ? 1 : PPW / 2)
+        for (int j2 = 0; j2 < PPW; j2 += 2) {
+        uint32_t hv[8], lv[8];
+#pragma unroll
+        for (int j1 = 0; j1 < 2; ++j1) {
+          const int j = j2 + j1;
+          if constexpr (C::GS) {  // the table chunk in the stage, read pair by pair
+            ga[j] = Gs[(pp0 + j) * GST + ri];
+            gb[j] = Gs[(C::PP + pp0 + j) * GST + ri];
+          } else if (j >= PRE) {
+            ga[j] = __ldg(gp + (size_t)((c * 2 + 0) * C::PP + pp0 + j) * GST + ri);
+            gb[j] = __ldg(gp + (size_t)((c * 2 + 1) * C::PP + pp0 + j) * GST + ri);
+          }
+          float2 pd[14];
+#pragma unroll
+          for (int k = 0; k < 7; ++k) {
+            const float4 d = D4[k * C::PP + j];
+            pd[2 * k] = make_float2(d.x, d.y);
+            pd[2 * k + 1] = make_float2(d.z, d.w);
+          }
+          const float2 g0 = make_float2(ga[j].x, ga[j].y), g1 = make_float2(ga[j].z, ga[j].w);
+          const float2 g2 = make_float2(gb[j].x, gb[j].y), g3 = make_float2(gb[j].z, gb[j].w);
+          // H' 2^sigma = Dt 2^sigma G at both points; (w det J f) phi
+          const float2 h0 = __fmul2_rn(pd[0], g0);
+          const float2 h1 = __ffma2_rn(pd[10], g3, __ffma2_rn(pd[7], g2, __ffma2_rn(pd[4], g1, __fmul2_rn(pd[1], g0))));
+          const float2 h2 = __ffma2_rn(pd[11], g3, __ffma2_rn(pd[8], g2, __ffma2_rn(pd[5], g1, __fmul2_rn(pd[2], g0))));
+          const float2 h3 = __ffma2_rn(pd[12], g3, __ffma2_rn(pd[9], g2, __ffma2_rn(pd[6], g1, __fmul2_rn(pd[3], g0))));
+          bp = __ffma2_rn(pd[13], g0, bp);
+          // two consecutive K values per column: 4 values of the first
+          // point, then 4 of the second, as fp16 hi and lo = rn(x - hi)
+          const __half2 w0 = __floats2half2_rn(h0.x, h1.x), w1 = __floats2half2_rn(h2.x, h3.x);
+          const __half2 w2 = __floats2half2_rn(h0.y, h1.y), w3 = __floats2half2_rn(h2.y, h3.y);
+          const float2 e0 = split_residual(w0, h0.x, h1.x), e1 = split_residual(w1, h2.x, h3.x);
+          const float2 e2 = split_residual(w2, h0.y, h1.y), e3 = split_residual(w3, h2.y, h3.y);
+          const __half2 l0 = __floats2half2_rn(e0.x, e0.y), l1 = __floats2half2_rn(e1.x, e1.y);
+          const __half2 l2 = __floats2half2_rn(e2.x, e2.y), l3 = __floats2half2_rn(e3.x, e3.y);
+          const int h4 = 4 * j1;
+          memcpy(&hv[h4 + 0], &w0, 4);
+          memcpy(&hv[h4 + 1], &w1, 4);
+          memcpy(&hv[h4 + 2], &w2, 4);
+          memcpy(&hv[h4 + 3], &w3, 4);
+          memcpy(&lv[h4 + 0], &l0, 4);
+          memcpy(&lv[h4 + 1], &l1, 4);
+          memcpy(&lv[h4 + 2], &l2, 4);
+          memcpy(&lv[h4 + 3], &l3, 4);
+        }
+        tmem_st8u(acol + 4 * j2, hv);
+        tmem_st8u(acol + C::KCH / 2 + 4 * j2, lv);
+        }
+        // the point operators of this chunk are consumed and the A columns
+        // written (visible to the tensor core after the wait and the fence)
+        tmem_wait_st();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) {
+          mbar_arrive(smem_u32(&ax.dempty[dr]));
+          mbar_arrive(smem_u32(&ax.full[s]));
+        }
+      }
+      if (*abort_flag) break;
+      // load-vector partial of this thread's row (the slot is free once the
+      // epilogue finished the tile two before)
+      const int slot = it & 1;
+      const bool mok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&ax.meta_empty[slot]),
+                                                         ((uint32_t)(it >> 1) & 1u) ^ 1u, abort_flag));
+      if (!mok) break;
+      ax.bsum[slot][part][row] = bp.x + bp.y;
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&ax.bsum_full[slot]));
+    }
+    // an aborted block marks every element of its remaining tiles
+    if (*abort_flag) {
+      for (int64_t t2 = tile; t2 < t_end; ++t2)
+        for (int rr = tp; rr < 128; rr += NP) {
+          const int64_t grow = t2 * 128 + rr;
+          if (grow >= rows_total) continue;
+          const int64_t k = grow / NSH;
+          if (grow - k * NSH != 0 && rr != 0) continue;
+          const int64_t e = a.list ? (int64_t)a.list[k] : k;
+          a.status[e] = FEI_ERR_TIMEOUT;
+        }
     }
   } else if (warp >= C::W_PW && warp < C::W_EW) {
     // ================================================================ producers
@@ -956,7 +1219,7 @@ __global__ void __launch_bounds__(TcCfg<P, V>::NTHREADS, 1)
       for (int c = 0; c < NCH && !dead; c += C::UC) {
 #pragma unroll
         for (int nh = 0; nh < C::NHALF; ++nh) {
-          const uint32_t pb = unit & 1u, k = unit >> 1;
+          const uint32_t pb = unit % C::NPART, k = unit / C::NPART;
           ++unit;
           const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&ax.part_full[pb]), k & 1u, abort_flag));
           if (!ok) {
@@ -977,7 +1240,7 @@ __global__ void __launch_bounds__(TcCfg<P, V>::NTHREADS, 1)
               if (b < C::NMMA / 16) {
                 const int ncol = nh * C::NMMA + b * 16;
                 tmem_ld16_nw(tmem + lane_base + pb * C::NMMA + b * 16, pv[j]);
-                if (ncol < C::RT && c > 0) tmem_ld16_nw(tmem + lane_base + 2 * C::NMMA + ncol, rv[j]);
+                if (ncol < C::RT && c > 0) tmem_ld16_nw(tmem + lane_base + C::RSUM + ncol, rv[j]);
               }
             }
             tmem_wait_ld();
@@ -999,7 +1262,7 @@ __global__ void __launch_bounds__(TcCfg<P, V>::NTHREADS, 1)
                       v[k2 + 1] = t.y;
                     }
                   }
-                  tmem_st16(tmem + lane_base + 2 * C::NMMA + ncol, v);
+                  tmem_st16(tmem + lane_base + C::RSUM + ncol, v);
                 } else if constexpr (C::RREG > 0) {
                   const int ro = ncol - C::RT;
 #pragma unroll
@@ -1027,7 +1290,7 @@ __global__ void __launch_bounds__(TcCfg<P, V>::NTHREADS, 1)
       if (M.row_boff[myrow] >= 0) {
         float bsum = 0.f;
 #pragma unroll
-        for (int j = 0; j < C::PP; ++j) bsum += ax.bsum[slot][j][myrow];
+        for (int j = 0; j < C::BSN; ++j) bsum += ax.bsum[slot][j][myrow];
         const int st = M.row_status[myrow];
         reinterpret_cast<float *>(a.bv)[M.row_boff[myrow]] = st ? 0.f : bsum;
         if (M.row_eid[myrow] >= 0) a.status[M.row_eid[myrow]] = st;
@@ -1051,7 +1314,7 @@ __global__ void __launch_bounds__(TcCfg<P, V>::NTHREADS, 1)
             if (ncol < NSH) {
               float v[16];
               if (ncol < C::RT) {
-                tmem_ld16(tmem + lane_base + 2 * C::NMMA + ncol, v);
+                tmem_ld16(tmem + lane_base + C::RSUM + ncol, v);
               } else if constexpr (C::RREG > 0) {
 #pragma unroll
                 for (int k2 = 0; k2 < 16; ++k2) v[k2] = rreg[ncol - C::RT + k2];
@@ -1085,7 +1348,7 @@ __global__ void __launch_bounds__(TcCfg<P, V>::NTHREADS, 1)
           if (ncol < NSH) {
             float v[16];
             if (ncol < C::RT) {
-              tmem_ld16(tmem + lane_base + 2 * C::NMMA + ncol, v);
+              tmem_ld16(tmem + lane_base + C::RSUM + ncol, v);
             } else if constexpr (C::RREG > 0) {
   #pragma unroll
               for (int k2 = 0; k2 < 16; ++k2) v[k2] = rreg[ncol - C::RT + k2];
@@ -1167,23 +1430,36 @@ __global__ void __launch_bounds__(TcCfg<P, V>::NTHREADS, 1)
           tc_fence_after();
 #pragma unroll
           for (int nh = 0; nh < C::NHALF; ++nh) {
-            const uint32_t pb = unit & 1u, k = unit >> 1;
+            const uint32_t pb = unit % C::NPART, k = unit / C::NPART;
             ++unit;
             ok = mbar_wait(smem_u32(&ax.promo_done[pb]), (k & 1u) ^ 1u, abort_flag);
             if (!ok) break;
             tc_fence_after();
             const uint32_t d = tmem + pb * C::NMMA;
             for (int j = 0; j < cn; ++j) {
-              const uint32_t ah = stageA(st[j], 0), alo = stageA(st[j], 1);
               const uint32_t bh = stageB(st[j]), bl = bh + C::B_BYTES;
+              if constexpr (C::TS) {
+                // A hi / lo from the stage's tensor-memory columns
+                const uint32_t ah = tmem + (uint32_t)(C::ABASE + st[j] * C::ACOLS), alo = ah + C::KCH / 2;
 #pragma unroll
-              for (int kk = 0; kk < C::KSL; ++kk) {
-                const uint32_t boff = (uint32_t)(nh * C::NMMA * ROWB + kk * 32);
-                const uint64_t Ah = sw_desc<ROWB>(ah + kk * 32), Al = sw_desc<ROWB>(alo + kk * 32);
-                const uint64_t Bh = sw_desc<ROWB>(bh + boff), Bl = sw_desc<ROWB>(bl + boff);
-                tc_mma_f16(d, Ah, Bh, IDESC, (j | kk) != 0);
-                tc_mma_f16(d, Ah, Bl, IDESC, 1u);
-                tc_mma_f16(d, Al, Bh, IDESC, 1u);
+                for (int kk = 0; kk < C::KSL; ++kk) {
+                  const uint32_t boff = (uint32_t)(nh * C::NMMA * ROWB + kk * 32);
+                  const uint64_t Bh = sw_desc<ROWB>(bh + boff), Bl = sw_desc<ROWB>(bl + boff);
+                  tc_mma_f16_ts(d, ah + kk * 8, Bh, IDESC, (j | kk) != 0);
+                  tc_mma_f16_ts(d, ah + kk * 8, Bl, IDESC, 1u);
+                  tc_mma_f16_ts(d, alo + kk * 8, Bh, IDESC, 1u);
+                }
+              } else {
+                const uint32_t ah = stageA(st[j], 0), alo = stageA(st[j], 1);
+#pragma unroll
+                for (int kk = 0; kk < C::KSL; ++kk) {
+                  const uint32_t boff = (uint32_t)(nh * C::NMMA * ROWB + kk * 32);
+                  const uint64_t Ah = sw_desc<ROWB>(ah + kk * 32), Al = sw_desc<ROWB>(alo + kk * 32);
+                  const uint64_t Bh = sw_desc<ROWB>(bh + boff), Bl = sw_desc<ROWB>(bl + boff);
+                  tc_mma_f16(d, Ah, Bh, IDESC, (j | kk) != 0);
+                  tc_mma_f16(d, Ah, Bl, IDESC, 1u);
+                  tc_mma_f16(d, Al, Bh, IDESC, 1u);
+                }
               }
             }
             tc_commit(smem_u32(&ax.part_full[pb]));
