@@ -56,12 +56,15 @@ def flops_per_element(p):
     return 8 * s * s * q + 2 * s * q + 220 * q
 
 
-def tc_hw_flops(p):
-    """Tensor-core flops issued per element by the split-fp16 contraction:
-    3 products x 2 x (N_sh rows, stacked in 128-row tiles) x N_pad x 4 N_q."""
+def tc_hw_flops(p, precision="tc_f16x3"):
+    """Tensor-core flops issued per element by the split contraction: 3
+    products x 2 x (N_sh rows, stacked in 128-row tiles) x N_pad x 4 N_q
+    (N_q padded to the kernel's points per chunk: 128-byte operand rows of
+    fp16 or TF32 values, 64-byte rows at p = 7)."""
     s, q = nsh(p), nq(p)
     npad = 224 if p == 6 else (s + 15) // 16 * 16
-    ppc = 8 if p == 7 else 16
+    row_values = (64 if p == 7 else 128) // (4 if precision == "tc_3xtf32" else 2)
+    ppc = row_values // 4
     kpad = ((q + ppc - 1) // ppc) * ppc * 4
     return 3 * 2 * s * npad * kpad
 
@@ -322,15 +325,23 @@ def roofline_of(dom, counts, precision, peaks, peak_src, live, Bts, ms_all, p, n
         peak_note = f64_note + " (the FP64 Jacobian work binds before HBM)"
         hw = {"hbm_gbs": Bts / (ms * 1e-3) / 1e9, "hbm_frac": Bts / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
               "hbm_peak_gbs": peaks["hbm_gbs"]}
-    elif precision == "tc_f16x3":
-        # every algorithmic multiply-add is three fp16 tensor products (hi*hi,
+    elif precision in ("tc_f16x3", "tc_3xtf32"):
+        # every algorithmic multiply-add is three tensor products (hi*hi,
         # hi*lo, lo*hi), so the peak for algorithmic flops is a third of the
-        # fp16 (= bf16) dense peak
-        bound, peak, unit, achieved = "tensor", peaks["bf16_tflops"] / 3, "TFLOP/s", F / (ms * 1e-3) / 1e12
-        peak_note = f"bf16/fp16 dense peak / 3 ({peak_src})"
-        hwF = sum(int(counts[d]) * tc_hw_flops(d) for d in range(3, 8))
+        # dense peak of the operand type: fp16 (= bf16, the driver's
+        # measurement) or TF32 (measured here with a library GEMM, else the
+        # bf16 figure times the nominal ratio 1.1 / 2.25)
+        if precision == "tc_f16x3":
+            tpeak, tnote = peaks["bf16_tflops"], f"bf16/fp16 dense peak ({peak_src})"
+        elif live and live.get("tf32_tensor_tflops"):
+            tpeak, tnote = live["tf32_tensor_tflops"], "TF32 dense peak (measured: torch.matmul, TF32 allowed)"
+        else:
+            tpeak, tnote = peaks["bf16_tflops"] * 1.1 / 2.25, f"TF32: bf16 peak ({peak_src}) x nominal 1.1/2.25"
+        bound, peak, unit, achieved = "tensor", tpeak / 3, "TFLOP/s", F / (ms * 1e-3) / 1e12
+        peak_note = tnote + " / 3"
+        hwF = sum(int(counts[d]) * tc_hw_flops(d, precision) for d in range(3, 8))
         hw = {"tensor_tflops": hwF / (ms * 1e-3) / 1e12,
-              "frac_of_fp16_peak": hwF / (ms * 1e-3) / 1e12 / peaks["bf16_tflops"],
+              "frac_of_tensor_peak": hwF / (ms * 1e-3) / 1e12 / tpeak,
               "note": "issued tcgen05 flops: 3 products x 2 x 128-row tiles x N_pad x 4 N_q"}
     elif precision == "fp32":
         bound, peak, unit, achieved = "alu", f32_peak, "TFLOP/s", F / (ms * 1e-3) / 1e12
@@ -546,7 +557,7 @@ def run_workload(name, args, ctx, headline):
         if ref is not None:
             fp64["rel_err_vs_oracle"] = errors_vs_oracle(A64, b64, st64, ref, n_s)
         del A64, b64, st64
-        if precision == "tc_f16x3" and headline:
+        if precision in ("tc_f16x3", "tc_3xtf32") and headline:
             A32 = torch.empty(layout.A_total, dtype=torch.float32, device=dev)
             b32 = torch.empty(layout.b_total, dtype=torch.float32, device=dev)
             st32 = torch.empty(n, dtype=torch.int32, device=dev)
@@ -566,6 +577,35 @@ def run_workload(name, args, ctx, headline):
             if ref is not None:
                 fp32_path["rel_err_vs_oracle"] = errors_vs_oracle(A32, b32, st32, ref, n_s)
             del A32, b32, st32
+
+    # the other split of the tensor-core contraction on the same batch (the
+    # trade-off between fp16 and TF32 operands: time and error), for the
+    # headline and the p = 7 workload
+    alt_tc = None
+    if (rank == 0 and precision in ("tc_f16x3", "tc_3xtf32") and p is not None and p >= 3 and grads is None
+            and (headline or name == "p7")):
+        alt = "tc_3xtf32" if precision == "tc_f16x3" else "tc_f16x3"
+        Aa = torch.empty(layout.A_total, dtype=torch.float32, device=dev)
+        ba = torch.empty(layout.b_total, dtype=torch.float32, device=dev)
+        sa = torch.empty(n, dtype=torch.int32, device=dev)
+        step(alt, (Aa, ba, sa))
+        torch.cuda.synchronize()
+        ta = []
+        for _ in range(max(2, min(steps, 5))):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            flush.fill_(3.0)
+            e0.record(stream)
+            step(alt, (Aa, ba, sa))
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ta.append(e0.elapsed_time(e1))
+        ma = statistics.median(ta)
+        da = {"kernel": "forward", "ms": ma, "F": F, "precision": alt, "counts": counts}
+        alt_tc = {"precision": alt, "elements_per_s": n / (ma * 1e-3), "ms_per_step": ma,
+                  "roofline": roofline_of(da, counts, alt, peaks, peak_src, live, Bts, ma, p, n, per_qp)}
+        if ref is not None:
+            alt_tc["rel_err_vs_oracle"] = errors_vs_oracle(Aa, ba, sa, ref, n_s)
+        del Aa, ba, sa
 
     # end to end through the public API with host buffers
     e2e = None
@@ -587,6 +627,8 @@ def run_workload(name, args, ctx, headline):
         res["speedup_vs_fp64_path"] = fp64["ms_per_step"] / ms if not fp64["forward_only"] else None
     if fp32_path is not None:
         res["fp32_path"] = fp32_path
+    if alt_tc is not None:
+        res["other_tc_split"] = alt_tc
     if plan_choices is not None:
         res["plan"] = plan_choices
         res["plan_buckets"] = plan_buckets
@@ -856,7 +898,7 @@ def main():
             "metric": metric_name(args), "value": head["elements_per_s"], "unit": "elements/s", "n_gpus": world,
             "steps": head["steps"], "warmup": max(3, args.warmup), "ms_per_step": head["ms_per_step"],
             "higher_is_better": True, "scaling": args.scaling, "vs_baseline": None,
-            "dtype": {"fp64": "f64", "fp32": "f32", "tc_f16x3": "f16x3->f32"}[precision],
+            "dtype": {"fp64": "f64", "fp32": "f32", "tc_f16x3": "f16x3->f32", "tc_3xtf32": "tf32x3->f32"}[precision],
             "data": "synthetic",
             "config": {"workload": head["workload"], "precision": precision, "elements": head["elements"],
                        "l2": "256 MB buffer written between timed steps (outside the events); "
@@ -870,6 +912,7 @@ def main():
             "gpu_launches": head["launches_per_step"] * head["steps"], "clocks": head["clocks"],
             "rel_err_vs_oracle": err,
             "fp64_path": head["fp64_path"], "fp32_path": head.get("fp32_path"),
+            "other_tc_split": head.get("other_tc_split"),
             "speedup_vs_fp64_path": head.get("speedup_vs_fp64_path"),
             "plan": head.get("plan"), "plan_buckets": head.get("plan_buckets"),
             "peaks_measured": live,

@@ -71,9 +71,17 @@ typedef enum {
   FEI_FP32 = 1,
   /* As FEI_FP32 for the geometry and point operator; the contraction runs
    * on the tcgen05 tensor cores with each operand split into fp16 hi + lo
-   * (3 products: hi*hi + hi*lo + lo*hi) and FP32 accumulation in TMEM.
-   * Degrees 1 and 2 fall back to the FEI_FP32 kernels.  Output FP32. */
-  FEI_TC_F16X3 = 2
+   * (3 products: hi*hi + hi*lo + lo*hi) and FP32 accumulation in TMEM
+   * (operands scaled by powers of two into fp16 range).  Degrees 1 and 2
+   * fall back to the FEI_FP32 kernels.  Output FP32. */
+  FEI_TC_F16X3 = 2,
+  /* As FEI_TC_F16X3 with each operand split into TF32 hi + lo
+   * (tcgen05.mma kind::tf32, 3 products, FP32 accumulation): the FP32
+   * exponent range needs no scaling, at half the fp16 tensor rate.  The
+   * paper computes in single precision (Sec. 4); split bf16 is not offered:
+   * bf16's 8 significant bits need three pieces and six products for the
+   * same accuracy.  Degrees 1 and 2 fall back to FEI_FP32.  Output FP32. */
+  FEI_TC_3XTF32 = 3
 } fei_precision;
 
 typedef enum {

@@ -206,8 +206,8 @@ void fill_fwd(FwdArgs &a, const fei_batch *b, const fei_reference *r, void *A, v
 
 fei_status launch_forward(int p, fei_precision prec, const fei_reference *r, const FwdArgs &a,
                           int64_t grid_work, cudaStream_t s) {
-  const fei_status st = (prec == FEI_TC_F16X3 && p >= 3) ? launch_tc_forward(p, r, a, grid_work, s)
-                                                          : launch_cc_forward(p, prec == FEI_FP64, a, grid_work, s);
+  const fei_status st = (tc_precision(prec) && p >= 3) ? launch_tc_forward(p, r, a, grid_work, s, 0, prec)
+                                                        : launch_cc_forward(p, prec == FEI_FP64, a, grid_work, s);
   return st ? st : debug_check(s, "forward kernel");
 }
 
@@ -390,7 +390,7 @@ extern "C" fei_status fei_integrate(const fei_reference_t *refs, int nrefs, cons
   const Range range_("fei_integrate");
   fei_status st = check_batch(batch);
   if (st) return st;
-  if (prec != FEI_FP64 && prec != FEI_FP32 && prec != FEI_TC_F16X3)
+  if (!valid_precision(prec))
     return set_error(FEI_ERR_INVALID_ARG, "precision %d", (int)prec);
   if (batch->n_elem == 0) return FEI_OK;
   if (!A_out || !b_out || !elem_status) return set_error(FEI_ERR_INVALID_ARG, "A_out, b_out and elem_status are required");

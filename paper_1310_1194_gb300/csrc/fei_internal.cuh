@@ -10,7 +10,7 @@
 //   znode double [p+1][2]        (zeta, w_zeta)        vertical Gauss nodes
 //   tnode double [(p+1)^2][4]    (xi1, xi2, w_tri, 0)  collapsed triangle nodes
 //   point q = iz * (p+1)^2 + t, t = iv * (p+1) + iu, w_q = w_tri[t] w_zeta[iz].
-//   tcB   uint16 image of the tensor-core B operand (see fei_tc.cu).
+//   tc    the tensor-core B operand images and paired tables (fei_tc.cu).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -132,10 +132,16 @@ fei_status launch_cc_forward(int p, bool fp64, const FwdArgs &a, int64_t grid_wo
 // (gA_e = u_e u_e^T and gb_e = -u_e never formed; a.u holds u)
 fei_status launch_cc_backward(int p, bool fp64, const BwdArgs &a, int64_t grid_work, cudaStream_t s,
                               bool quadratic = false);
-// variant: 0 .. tc_variant_count(p) - 1 (warp-role variants of one kernel)
+// The tensor-core precisions (split fp16 or split TF32 operands).
+inline bool tc_precision(fei_precision prec) { return prec == FEI_TC_F16X3 || prec == FEI_TC_3XTF32; }
+inline bool valid_precision(fei_precision prec) {
+  return prec == FEI_FP64 || prec == FEI_FP32 || tc_precision(prec);
+}
+// variant: 0 .. tc_variant_count(p, prec) - 1 (warp-role variants of one
+// kernel); prec: FEI_TC_F16X3 or FEI_TC_3XTF32
 fei_status launch_tc_forward(int p, const fei_reference *ref, const FwdArgs &a, int64_t grid_work,
-                             cudaStream_t s, int variant = 0);
-int tc_variant_count(int p);
+                             cudaStream_t s, int variant, fei_precision prec);
+int tc_variant_count(int p, fei_precision prec);
 fei_status build_tc_image(fei_reference *ref);
 void free_tc_image(fei_reference *ref);
 

@@ -72,7 +72,7 @@ extern "C" fei_status fei_integrate_noalloc(const fei_reference_t *refs, int nre
                      (long long)batch->n_elem, (long long)kNoAllocMax);
   fei_status st = check_batch(batch);
   if (st) return st;
-  if (prec != FEI_FP64 && prec != FEI_FP32 && prec != FEI_TC_F16X3)
+  if (!valid_precision(prec))
     return set_error(FEI_ERR_INVALID_ARG, "fei_integrate_noalloc: precision %d", (int)prec);
   if (batch->n_elem == 0) return FEI_OK;
   if (!A_out || !b_out || !elem_status)

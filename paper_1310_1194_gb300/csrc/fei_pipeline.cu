@@ -213,7 +213,7 @@ extern "C" fei_status fei_pipeline_create(const fei_reference_t *refs, int nrefs
                                           int64_t slot_bytes, fei_pipeline_t *out) {
   if (!out) return set_error(FEI_ERR_INVALID_ARG, "fei_pipeline_create: out is NULL");
   *out = nullptr;
-  if (prec != FEI_FP64 && prec != FEI_FP32 && prec != FEI_TC_F16X3)
+  if (!valid_precision(prec))
     return set_error(FEI_ERR_INVALID_ARG, "fei_pipeline_create: precision %d", (int)prec);
   if (!refs || nrefs < 1) return set_error(FEI_ERR_INVALID_ARG, "fei_pipeline_create: refs is NULL or nrefs < 1");
   if (slot_bytes == 0) slot_bytes = kDefaultSlotBytes;

@@ -13,9 +13,9 @@
 // launch and no host work per degree.
 //
 // Candidates per degree (what fei_plan_tune times):
-//   tensor-core path (p >= 3, FEI_TC_F16X3): the warp-role variants of the
+//   tensor-core paths (p >= 3, FEI_TC_F16X3, FEI_TC_3XTF32): the warp-role variants of the
 //     tcgen05 kernel (8 or 16 producer warps), one CTA per SM;
-//   CUDA-core paths (FEI_FP64, FEI_FP32, and p <= 2 under FEI_TC_F16X3): the
+//   CUDA-core paths (FEI_FP64, FEI_FP32, and p <= 2 under the tensor-core precisions): the
 //     grid of the grid-stride kernel, 2, 4, 8 or 16 blocks per SM.
 // Every candidate computes the same quantities; variants differ only in the
 // order of a few FP32 additions (load-vector partial sums), so results stay
@@ -46,9 +46,9 @@ struct fei_plan {
 namespace fei {
 namespace {
 
-bool tc_path(fei_precision prec, int p) { return prec == FEI_TC_F16X3 && p >= 3; }
+bool tc_path(fei_precision prec, int p) { return tc_precision(prec) && p >= 3; }
 
-int n_candidates(fei_precision prec, int p) { return tc_path(prec, p) ? tc_variant_count(p) : 4; }
+int n_candidates(fei_precision prec, int p) { return tc_path(prec, p) ? tc_variant_count(p, prec) : 4; }
 
 // Candidate c of degree p as (variant, grid cap).
 void candidate(fei_precision prec, int p, int c, int *variant, int64_t *grid_cap) {
@@ -93,7 +93,7 @@ fei_status launch_degree(const fei_plan *pl, int p, int variant, int64_t grid_ca
     a.count = pl->counts + p;
     a.list = pl->lists + (int64_t)(p - 1) * pl->max_elem;
   }
-  const fei_status ls = tc_path(pl->prec, p) ? launch_tc_forward(p, r, a, b->n_elem, s, variant)
+  const fei_status ls = tc_path(pl->prec, p) ? launch_tc_forward(p, r, a, b->n_elem, s, variant, pl->prec)
                                              : launch_cc_forward(p, pl->prec == FEI_FP64, a, b->n_elem, s, grid_cap);
   return ls ? ls : debug_check(s, "forward kernel");
 }
@@ -180,7 +180,7 @@ extern "C" fei_status fei_plan_create(const fei_reference_t *refs, int nrefs, in
   if (!refs || nrefs < 1) return set_error(FEI_ERR_INVALID_ARG, "fei_plan_create: refs is NULL or nrefs < 1");
   if (max_elem < 0 || max_elem > 2147483647LL)
     return set_error(FEI_ERR_INVALID_ARG, "fei_plan_create: max_elem %lld outside 0..2^31-1", (long long)max_elem);
-  if (prec != FEI_FP64 && prec != FEI_FP32 && prec != FEI_TC_F16X3)
+  if (!valid_precision(prec))
     return set_error(FEI_ERR_INVALID_ARG, "fei_plan_create: precision %d", (int)prec);
   for (int k = 0; k < nrefs; ++k)
     if (!refs[k]) return set_error(FEI_ERR_INVALID_ARG, "fei_plan_create: refs[%d] is NULL", k);
@@ -344,7 +344,7 @@ extern "C" fei_status fei_plan_choice(fei_plan_t plan, int p, int *variant, int6
 extern "C" fei_status fei_plan_set_choice(fei_plan_t plan, int p, int variant, int64_t grid_cap) {
   if (!plan) return set_error(FEI_ERR_INVALID_ARG, "fei_plan_set_choice: plan is NULL");
   if (p < 1 || p > kPMax) return set_error(FEI_ERR_INVALID_DEGREE, "fei_plan_set_choice: degree %d", p);
-  const int nv = tc_path(plan->prec, p) ? tc_variant_count(p) : 1;
+  const int nv = tc_path(plan->prec, p) ? tc_variant_count(p, plan->prec) : 1;
   if (variant < 0 || variant >= nv)
     return set_error(FEI_ERR_INVALID_ARG, "fei_plan_set_choice: variant %d for degree %d", variant, p);
   if (grid_cap < 0 || grid_cap > 2147483647LL)

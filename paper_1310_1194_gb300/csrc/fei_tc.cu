@@ -74,14 +74,22 @@
 
 namespace fei {
 
-struct TcImage {
-  __half *img;  // [NCHUNK][2][NPAD][ROWB/2], each [NPAD][ROWB/2] block swizzled
+// The operands of one split kind (0: fp16 hi/lo of G 2^tau, 1: TF32 hi/lo
+// of G), chunked by that kind's points per chunk.
+struct TcOperands {
+  // B image [NCHUNK][2 (hi, lo)][NPAD][ROWB bytes], each [NPAD][ROWB] block
+  // in the ROWB-byte swizzled K-major layout
+  unsigned char *img;
   // the FP32 table by chunk and point pair: [NCHUNK][2][PP][GST] float4,
   // half h of pair (q, q+1) and shape i = (G_2h(q), G_2h(q+1), G_2h+1(q),
   // G_2h+1(q+1)), G_b = phi, dphi/dxi1, dphi/dxi2, dphi/dzeta; zero past
   // N_q and N_sh (GST >= N_sh is the row stride)
   float *gp;
-  int npad, nchunk, rowb, tau;
+  int nchunk;
+};
+struct TcImage {
+  TcOperands k[2];
+  int npad, rowb, tau;
 };
 
 namespace {
@@ -170,20 +178,41 @@ __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::
 __device__ __forceinline__ void tc_commit(uint32_t mbar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
 }
-__device__ __forceinline__ void tc_mma_f16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc)
-      : "memory");
+// KD = 0: kind::f16 (fp16 A and B), KD = 1: kind::tf32.
+template <int KD>
+__device__ __forceinline__ void tc_mma_ss(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  if constexpr (KD == 0)
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+  else
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
 }
-// A from tensor memory (a = TMEM address of the 128 x 16 fp16 A slice:
-// lane = row, two consecutive K values per 32-bit column), B from shared
-// memory by descriptor.
-__device__ __forceinline__ void tc_mma_f16_ts(uint32_t d, uint32_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d),
-      "r"(a), "l"(b), "r"(idesc), "r"(acc)
-      : "memory");
+// x rounded to TF32 (10 fraction bits, nearest, ties away), as FP32 bits
+__device__ __forceinline__ uint32_t tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+// A from tensor memory (a = TMEM address of the 128-row A slice: lane =
+// row; two consecutive fp16 K values, or one TF32 value, per 32-bit column),
+// B from shared memory by descriptor.
+template <int KD>
+__device__ __forceinline__ void tc_mma_ts(uint32_t d, uint32_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  if constexpr (KD == 0)
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d),
+        "r"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+  else
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d),
+        "r"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
 }
 // 32 lanes x 8 columns of 32-bit values from registers (thread t = lane t)
 __device__ __forceinline__ void tmem_st8u(uint32_t taddr, const uint32_t *v) {
@@ -266,16 +295,20 @@ __device__ __forceinline__ float exp2i(int k) {  // exact 2^k for |k| < 126
 // V selects a variant of the warp roles (the autotuner of a plan times
 // them): 0 = 8 producer warps, 1 = 16 producer warps with half the points
 // each (more warps in flight, fewer registers per thread).
-template <int P, int V = 0>
+template <int P, int V = 0, int KD = 0>
 struct TcCfg {
   static constexpr int NSH = nsh_of(P), NQ = nq_of(P), NZ = P + 1, NT = (P + 1) * (P + 1);
   static constexpr int NPAD = P == 6 ? 224 : (NSH + 15) / 16 * 16;
   static constexpr int NHALF = P >= 6 ? 2 : 1;
   static constexpr int NMMA = NPAD / NHALF;  // N of one MMA = one partial buffer
   static constexpr int ROWB = P == 7 ? 64 : 128;
-  static constexpr int KCH = ROWB / 2;        // K values per chunk
+  // KD = 0: split fp16 operands (2 bytes, K = 16 per MMA); KD = 1: split
+  // TF32 operands (4 bytes, K = 8 per MMA)
+  static constexpr int EB = KD ? 4 : 2;
+  static constexpr int KMMA = KD ? 8 : 16;
+  static constexpr int KCH = ROWB / EB;       // K values per chunk
   static constexpr int PPC = KCH / 4;         // points per chunk
-  static constexpr int KSL = KCH / 16;        // 16-wide K slices per chunk
+  static constexpr int KSL = KCH / KMMA;      // MMA K slices per chunk
   static constexpr int NCHUNK = (NQ + PPC - 1) / PPC;
   // chunks per promotion unit: a partial accumulator collects 4 K slices
   // (12 MMAs) before the epilogue adds it into the running sum
@@ -297,7 +330,9 @@ struct TcCfg {
   static constexpr int ACC_COLS = NPART * NMMA + RT;
   static constexpr int RSUM = NPART * NMMA;  // first column of the running sum
   static constexpr int ABASE = TS ? (ACC_COLS + 31) / 32 * 32 : 0;
-  static constexpr int ACOLS = KCH;
+  static constexpr int ACOLS = KCH * EB / 2;  // hi then lo, 32-bit columns
+  static constexpr int AHALF = ACOLS / 2;
+  static constexpr int VPC = 4 / EB;  // operand values per 32-bit column
   static constexpr int TMEM_COLS = TS ? 512 : (3 * NPAD <= 256 ? 256 : 512);
   static constexpr int EMAX = (128 + NSH - 1) / NSH + 1;  // elements a tile can touch
   static constexpr int NSLOT = EMAX + 1;  // element slots: a tile's elements plus the one it shares
@@ -382,9 +417,9 @@ struct TcMeta {
   int row_status[128];    // status of the row's element (nonzero: write zeros)
 };
 
-template <int P, int V>
+template <int P, int V, int KD>
 struct TcAux {
-  using C = TcCfg<P, V>;
+  using C = TcCfg<P, V, KD>;
   uint64_t full[C::STAGES];   // producers wrote A of the stage
   uint64_t bfull[C::STAGES];  // B of the stage landed
   uint64_t empty[C::STAGES];  // MMAs of the stage completed
@@ -516,19 +551,21 @@ __device__ __forceinline__ float2 split_residual(__half2 hi, float x0, float x1)
       : "r"(h), "f"(x0), "f"(x1));
   return make_float2(r0, r1);
 }
-// Instruction descriptor, kind::f16: fp16 A and B (K-major), FP32 D.
-__host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
-  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+// Instruction descriptor: FP32 D; A and B K-major, both fp16 (kind::f16,
+// type code 0) or both TF32 (kind::tf32, type code 2); N and M.
+__host__ __device__ constexpr uint32_t idesc_mma(int M, int N, int KD) {
+  return (1u << 4) | ((KD ? 2u : 0u) << 7) | ((KD ? 2u : 0u) << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
 }
 
-template <int P, int V>
-__global__ void __launch_bounds__(TcCfg<P, V>::NTHREADS, 1)
-    tc_forward_kernel(FwdArgs a, const __half *img, const float4 *gp, int tau) {
-  using C = TcCfg<P, V>;
+template <int P, int V, int KD>
+__global__ void __launch_bounds__(TcCfg<P, V, KD>::NTHREADS, 1)
+    tc_forward_kernel(FwdArgs a, const unsigned char *img, const float4 *gp, int tau) {
+  using C = TcCfg<P, V, KD>;
   constexpr int NSH = C::NSH, NQ = C::NQ, NT = C::NT, NZ = C::NZ, S = C::STAGES, NCH = C::NCHUNK;
   constexpr int NP = C::NPW * 32, ND = C::NDW * 32, PPC = C::PPC, ROWB = C::ROWB, DR = C::DRING;
   extern __shared__ __align__(1024) unsigned char dsm_raw[];
-  __shared__ TcAux<P, V> ax;
+  __shared__ TcAux<P, V, KD> ax;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t dbase = (smem_u32(dsm_raw) + 1023u) & ~1023u;
   auto stageA = [&](int s, int piece) { return dbase + s * C::STAGE_BYTES + piece * C::A_BYTES; };
@@ -789,7 +826,11 @@ __global__ void __launch_bounds__(TcCfg<P, V>::NTHREADS, 1)
         }
       }
       named_bar(2, ND);
-      if (td < nnew) {
+      if (td < nnew && KD == 1) {  // TF32 operands have the FP32 range: no scale
+        TcElem<P> &E = ax.el[slot_of(kn0 + td)];
+        E.up = 1.f;
+        E.down = 1.f;
+      } else if (td < nnew) {
         TcElem<P> &E = ax.el[slot_of(kn0 + td)];
         // The A operand is H' 2^sigma and max|G| <= 2^(14 - tau), so
         // |A| <= M 2^sigma 2^(14 - tau): sigma = tau - ex with M <= 2^ex
@@ -957,7 +998,8 @@ __global__ void __launch_bounds__(TcCfg<P, V>::NTHREADS, 1)
         if (!ok) break;
         tc_fence_after();
         const float4 *Gs = reinterpret_cast<const float4 *>(dsm_raw + (stageG(s) - smem_u32(dsm_raw)));
-        const uint32_t acol = tmem + lane_base + (uint32_t)(C::ABASE + s * C::ACOLS + pp0 * 4);
+        // a point pair is 8 K values: 4 columns of fp16 pairs, or 8 of TF32
+        const uint32_t acol = tmem + lane_base + (uint32_t)(C::ABASE + s * C::ACOLS + pp0 * 8 / C::VPC);
         const float4 *D4 = &ax.Dc[dr][rel][0][pp0];
         // two pairs at a time: 8 columns of hi and 8 of lo per tcgen05.st
         // (holding all pairs' values until one wider store raised the
@@ -992,6 +1034,21 @@ __global__ void __launch_bounds__(TcCfg<P, V>::NTHREADS, 1)
           const float2 h2 = __ffma2_rn(pd[11], g3, __ffma2_rn(pd[8], g2, __ffma2_rn(pd[5], g1, __fmul2_rn(pd[2], g0))));
           const float2 h3 = __ffma2_rn(pd[12], g3, __ffma2_rn(pd[9], g2, __ffma2_rn(pd[6], g1, __fmul2_rn(pd[3], g0))));
           bp = __ffma2_rn(pd[13], g0, bp);
+          if constexpr (KD == 1) {
+            // one K value per column: 4 values of the first point, then 4 of
+            // the second, as TF32 hi = rn(x) and lo = rn(x - hi) (x - hi is
+            // exact in FP32)
+            const float xv[8] = {h0.x, h1.x, h2.x, h3.x, h0.y, h1.y, h2.y, h3.y};
+            uint32_t th[8], tl[8];
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+              th[m] = tf32_rna(xv[m]);
+              tl[m] = tf32_rna(xv[m] - __uint_as_float(th[m]));
+            }
+            tmem_st8u(acol + 8 * j, th);
+            tmem_st8u(acol + C::AHALF + 8 * j, tl);
+            continue;
+          }
           // two consecutive K values per column: 4 values of the first
           // point, then 4 of the second, as fp16 hi and lo = rn(x - hi)
           const __half2 w0 = __floats2half2_rn(h0.x, h1.x), w1 = __floats2half2_rn(h2.x, h3.x);
@@ -1010,8 +1067,10 @@ __global__ void __launch_bounds__(TcCfg<P, V>::NTHREADS, 1)
           memcpy(&lv[h4 + 2], &l2, 4);
           memcpy(&lv[h4 + 3], &l3, 4);
         }
-        tmem_st8u(acol + 4 * j2, hv);
-        tmem_st8u(acol + C::KCH / 2 + 4 * j2, lv);
+        if constexpr (KD == 0) {
+          tmem_st8u(acol + 4 * j2, hv);
+          tmem_st8u(acol + C::AHALF + 4 * j2, lv);
+        }
         }
         // the point operators of this chunk are consumed and the A columns
         // written (visible to the tensor core after the wait and the fence)
@@ -1147,6 +1206,24 @@ __global__ void __launch_bounds__(TcCfg<P, V>::NTHREADS, 1)
           const float2 h2 = __ffma2_rn(pd[11], g3, __ffma2_rn(pd[8], g2, __ffma2_rn(pd[5], g1, __fmul2_rn(pd[2], g0))));
           const float2 h3 = __ffma2_rn(pd[12], g3, __ffma2_rn(pd[9], g2, __ffma2_rn(pd[6], g1, __fmul2_rn(pd[3], g0))));
           bp[k] = __ffma2_rn(pd[13], g0, bp[k]);
+          if constexpr (KD == 1) {
+            // two 16-byte operand chunks: the 4 values of the first point,
+            // then the 4 of the second, as TF32 hi = rn(x), lo = rn(x - hi)
+            const float xv[8] = {h0.x, h1.x, h2.x, h3.x, h0.y, h1.y, h2.y, h3.y};
+            uint32_t th[8], tl[8];
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+              th[m] = tf32_rna(xv[m]);
+              tl[m] = tf32_rna(xv[m] - __uint_as_float(th[m]));
+            }
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+              const uint32_t aoff = sw_off<ROWB>(rowr[k], 2 * pp + hh);
+              *reinterpret_cast<uint4 *>(ahp + aoff) = make_uint4(th[4 * hh], th[4 * hh + 1], th[4 * hh + 2], th[4 * hh + 3]);
+              *reinterpret_cast<uint4 *>(alp + aoff) = make_uint4(tl[4 * hh], tl[4 * hh + 1], tl[4 * hh + 2], tl[4 * hh + 3]);
+            }
+            continue;
+          }
           // the 16-byte operand chunk: 4 values of the first point, then 4
           // of the second, as fp16 hi and lo = rn(x - hi)
           const __half2 w0 = __floats2half2_rn(h0.x, h1.x), w1 = __floats2half2_rn(h2.x, h3.x);
@@ -1402,7 +1479,7 @@ __global__ void __launch_bounds__(TcCfg<P, V>::NTHREADS, 1)
           const uint32_t bar = smem_u32(&ax.bfull[s]);
           const uint32_t gbytes = C::GS ? (uint32_t)C::G_BYTES : 0u;
           mbar_expect_tx(bar, 2u * C::B_BYTES + gbytes);
-          bulk_g2s(stageB(s), img + (size_t)c * 2 * C::NPAD * (ROWB / 2), 2u * C::B_BYTES, bar);
+          bulk_g2s(stageB(s), img + (size_t)c * 2 * C::B_BYTES, 2u * C::B_BYTES, bar);
           if (C::GS) bulk_g2s(stageG(s), gp + (size_t)c * 2 * C::PP * C::GST, gbytes, bar);
         }
         if (!ok) break;
@@ -1411,7 +1488,7 @@ __global__ void __launch_bounds__(TcCfg<P, V>::NTHREADS, 1)
   } else {
     // ================================================================ MMA issue
     if (lane == 0) {
-      constexpr uint32_t IDESC = idesc_f16(128, C::NMMA);
+      constexpr uint32_t IDESC = idesc_mma(128, C::NMMA, KD);
       bool ok = true;
       uint32_t unit = 0;
       int it = 0;
@@ -1440,14 +1517,15 @@ __global__ void __launch_bounds__(TcCfg<P, V>::NTHREADS, 1)
               const uint32_t bh = stageB(st[j]), bl = bh + C::B_BYTES;
               if constexpr (C::TS) {
                 // A hi / lo from the stage's tensor-memory columns
-                const uint32_t ah = tmem + (uint32_t)(C::ABASE + st[j] * C::ACOLS), alo = ah + C::KCH / 2;
+                // one K slice (32 bytes of a row) is 8 columns in both kinds
+                const uint32_t ah = tmem + (uint32_t)(C::ABASE + st[j] * C::ACOLS), alo = ah + C::AHALF;
 #pragma unroll
                 for (int kk = 0; kk < C::KSL; ++kk) {
                   const uint32_t boff = (uint32_t)(nh * C::NMMA * ROWB + kk * 32);
                   const uint64_t Bh = sw_desc<ROWB>(bh + boff), Bl = sw_desc<ROWB>(bl + boff);
-                  tc_mma_f16_ts(d, ah + kk * 8, Bh, IDESC, (j | kk) != 0);
-                  tc_mma_f16_ts(d, ah + kk * 8, Bl, IDESC, 1u);
-                  tc_mma_f16_ts(d, alo + kk * 8, Bh, IDESC, 1u);
+                  tc_mma_ts<KD>(d, ah + kk * 8, Bh, IDESC, (j | kk) != 0);
+                  tc_mma_ts<KD>(d, ah + kk * 8, Bl, IDESC, 1u);
+                  tc_mma_ts<KD>(d, alo + kk * 8, Bh, IDESC, 1u);
                 }
               } else {
                 const uint32_t ah = stageA(st[j], 0), alo = stageA(st[j], 1);
@@ -1456,9 +1534,9 @@ __global__ void __launch_bounds__(TcCfg<P, V>::NTHREADS, 1)
                   const uint32_t boff = (uint32_t)(nh * C::NMMA * ROWB + kk * 32);
                   const uint64_t Ah = sw_desc<ROWB>(ah + kk * 32), Al = sw_desc<ROWB>(alo + kk * 32);
                   const uint64_t Bh = sw_desc<ROWB>(bh + boff), Bl = sw_desc<ROWB>(bl + boff);
-                  tc_mma_f16(d, Ah, Bh, IDESC, (j | kk) != 0);
-                  tc_mma_f16(d, Ah, Bl, IDESC, 1u);
-                  tc_mma_f16(d, Al, Bh, IDESC, 1u);
+                  tc_mma_ss<KD>(d, Ah, Bh, IDESC, (j | kk) != 0);
+                  tc_mma_ss<KD>(d, Ah, Bl, IDESC, 1u);
+                  tc_mma_ss<KD>(d, Al, Bh, IDESC, 1u);
                 }
               }
             }
@@ -1501,9 +1579,14 @@ __global__ void gmax_kernel(const double *G, int n, unsigned long long *out) {
   if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
 }
 
+// B image of a split kind: x = G 2^tau (FP64) as hi + lo, fp16 (KD = 0) or
+// TF32 (KD = 1, tau = 0), at the K-major swizzled position of K value k
+// (point q = chunk * PPC + k / 4, component k % 4) in row n.
+template <int KD>
 __global__ void image_kernel(const double *G, int nsh, int nq, int npad, int nchunk, int rowb, double scale,
-                             __half *img) {
-  const int kch = rowb / 2, ppc = kch / 4;
+                             unsigned char *img) {
+  constexpr int EB = KD ? 4 : 2;
+  const int kch = rowb / EB, ppc = kch / 4;
   const int64_t total = (int64_t)nchunk * npad * kch;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
@@ -1512,12 +1595,21 @@ __global__ void image_kernel(const double *G, int nsh, int nq, int npad, int nch
     const int c = (int)(idx / (kch * (int64_t)npad));
     const int q = c * ppc + k / 4, b = k % 4;
     const double x = (q < nq && n < nsh) ? G[(size_t)(4 * q + b) * nsh + n] * scale : 0.0;
-    const __half hi = __double2half(x);
-    const __half lo = __double2half(x - (double)__half2float(hi));
-    const uint32_t byte = rowb == 128 ? sw_off<128>(n, k >> 3) : sw_off<64>(n, k >> 3);
-    const size_t pos = byte / 2 + (k & 7);  // halves from the start of the block
-    img[(size_t)(c * 2 + 0) * npad * kch + pos] = hi;
-    img[(size_t)(c * 2 + 1) * npad * kch + pos] = lo;
+    // 16-byte chunk k * EB / 16 of the row, byte (k * EB) % 16 in it
+    const uint32_t byte = (rowb == 128 ? sw_off<128>(n, (k * EB) >> 4) : sw_off<64>(n, (k * EB) >> 4)) + ((k * EB) & 15);
+    unsigned char *hi = img + (size_t)(c * 2 + 0) * npad * rowb + byte;
+    unsigned char *lo = img + (size_t)(c * 2 + 1) * npad * rowb + byte;
+    if constexpr (KD == 0) {
+      const __half h = __double2half(x);
+      const __half l = __double2half(x - (double)__half2float(h));
+      *reinterpret_cast<__half *>(hi) = h;
+      *reinterpret_cast<__half *>(lo) = l;
+    } else {
+      const uint32_t h = tf32_rna((float)x);
+      const uint32_t l = tf32_rna((float)(x - (double)__uint_as_float(h)));
+      *reinterpret_cast<uint32_t *>(hi) = h;
+      *reinterpret_cast<uint32_t *>(lo) = l;
+    }
   }
 }
 
@@ -1534,12 +1626,13 @@ __global__ void pair_table_kernel(const double *G, int nsh, int nq, int gst, int
   }
 }
 
-template <int P, int V>
+template <int P, int V, int KD>
 fei_status launch_tc(const fei_reference *ref, const FwdArgs &a, int64_t grid_work, cudaStream_t s) {
-  using C = TcCfg<P, V>;
+  using C = TcCfg<P, V, KD>;
   const TcImage *im = ref->tc;
   if (!im) return set_error(FEI_ERR_UNSUPPORTED, "no tensor-core image for degree %d", P);
-  FEI_CUDA_TRY(cudaFuncSetAttribute(tc_forward_kernel<P, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::DYN_SMEM),
+  FEI_CUDA_TRY(cudaFuncSetAttribute(tc_forward_kernel<P, V, KD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    C::DYN_SMEM),
                "cudaFuncSetAttribute(tc_forward)");
   int dev, sms;
   FEI_CUDA_TRY(cudaGetDevice(&dev), "cudaGetDevice");
@@ -1547,18 +1640,30 @@ fei_status launch_tc(const fei_reference *ref, const FwdArgs &a, int64_t grid_wo
   const int64_t tiles = (grid_work * C::NSH + 127) / 128;
   int64_t blocks = tiles < sms ? tiles : sms;
   if (blocks < 1) blocks = 1;
-  tc_forward_kernel<P, V><<<(unsigned)blocks, C::NTHREADS, C::DYN_SMEM, s>>>(
-      a, im->img, reinterpret_cast<const float4 *>(im->gp), im->tau);
+  tc_forward_kernel<P, V, KD><<<(unsigned)blocks, C::NTHREADS, C::DYN_SMEM, s>>>(
+      a, im->k[KD].img, reinterpret_cast<const float4 *>(im->k[KD].gp), KD ? 0 : im->tau);
   FEI_CUDA_TRY(cudaGetLastError(), "tc_forward_kernel launch");
   return FEI_OK;
 }
 
-template <int P>
-void tc_dims(int &npad, int &nchunk, int &rowb, int &gst) {
-  npad = TcCfg<P>::NPAD;
-  nchunk = TcCfg<P>::NCHUNK;
-  rowb = TcCfg<P>::ROWB;
-  gst = TcCfg<P>::GST;
+template <int P, int KD>
+void tc_dims(int &npad, int &nchunk, int &rowb, int &gst, int &pp) {
+  npad = TcCfg<P, 0, KD>::NPAD;
+  nchunk = TcCfg<P, 0, KD>::NCHUNK;
+  rowb = TcCfg<P, 0, KD>::ROWB;
+  gst = TcCfg<P, 0, KD>::GST;
+  pp = TcCfg<P, 0, KD>::PP;
+}
+
+template <int KD>
+void tc_dims_of(int p, int &npad, int &nchunk, int &rowb, int &gst, int &pp) {
+  switch (p) {
+    case 3: tc_dims<3, KD>(npad, nchunk, rowb, gst, pp); break;
+    case 4: tc_dims<4, KD>(npad, nchunk, rowb, gst, pp); break;
+    case 5: tc_dims<5, KD>(npad, nchunk, rowb, gst, pp); break;
+    case 6: tc_dims<6, KD>(npad, nchunk, rowb, gst, pp); break;
+    default: tc_dims<7, KD>(npad, nchunk, rowb, gst, pp); break;
+  }
 }
 
 }  // namespace
@@ -1566,27 +1671,10 @@ void tc_dims(int &npad, int &nchunk, int &rowb, int &gst) {
 fei_status build_tc_image(fei_reference *ref) {
   ref->tc = nullptr;
   if (ref->p < 3) return FEI_OK;
-  int npad = 0, nchunk = 0, rowb = 0, gst = 0;
-  switch (ref->p) {
-    case 3: tc_dims<3>(npad, nchunk, rowb, gst); break;
-    case 4: tc_dims<4>(npad, nchunk, rowb, gst); break;
-    case 5: tc_dims<5>(npad, nchunk, rowb, gst); break;
-    case 6: tc_dims<6>(npad, nchunk, rowb, gst); break;
-    case 7: tc_dims<7>(npad, nchunk, rowb, gst); break;
-  }
   TcImage *im = new TcImage();
-  im->npad = npad;
-  im->nchunk = nchunk;
-  im->rowb = rowb;
-  im->img = nullptr;
-  im->gp = nullptr;
+  memset(im, 0, sizeof(*im));
   unsigned long long *dmax = nullptr;
-  const size_t halves = (size_t)nchunk * 2 * npad * (rowb / 2);
-  const int pp = rowb / 16;  // point pairs per chunk
-  const size_t gfloats = (size_t)nchunk * 2 * pp * gst * 4;
-  cudaError_t e = cudaMalloc(&im->img, sizeof(__half) * halves);
-  if (e == cudaSuccess) e = cudaMalloc(&im->gp, sizeof(float) * gfloats);
-  if (e == cudaSuccess) e = cudaMalloc(&dmax, sizeof(unsigned long long));
+  cudaError_t e = cudaMalloc(&dmax, sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMemset(dmax, 0, sizeof(unsigned long long));
   if (e == cudaSuccess) {
     const int n = 4 * ref->nq * ref->nsh;
@@ -1601,18 +1689,38 @@ fei_status build_tc_image(fei_reference *ref) {
     int ex = 0;
     frexp(gmax, &ex);  // gmax <= 2^ex
     im->tau = 14 - ex;
-    image_kernel<<<256, 256>>>(ref->G64, ref->nsh, ref->nq, npad, nchunk, rowb, ldexp(1.0, im->tau), im->img);
-    e = cudaGetLastError();
+  }
+  for (int kd = 0; kd < 2 && e == cudaSuccess; ++kd) {
+    int npad = 0, nchunk = 0, rowb = 0, gst = 0, pp = 0;
+    if (kd == 0) tc_dims_of<0>(ref->p, npad, nchunk, rowb, gst, pp);
+    else tc_dims_of<1>(ref->p, npad, nchunk, rowb, gst, pp);
+    im->npad = npad;
+    im->rowb = rowb;
+    TcOperands &o = im->k[kd];
+    o.nchunk = nchunk;
+    const size_t ibytes = (size_t)nchunk * 2 * npad * rowb;
+    const size_t gfloats = (size_t)nchunk * 2 * pp * gst * 4;
+    e = cudaMalloc(&o.img, ibytes);
+    if (e == cudaSuccess) e = cudaMalloc(&o.gp, sizeof(float) * gfloats);
     if (e == cudaSuccess) {
-      pair_table_kernel<<<256, 256>>>(ref->G64, ref->nsh, ref->nq, gst, nchunk, pp, im->gp);
+      if (kd == 0)
+        image_kernel<0><<<256, 256>>>(ref->G64, ref->nsh, ref->nq, npad, nchunk, rowb, ldexp(1.0, im->tau), o.img);
+      else
+        image_kernel<1><<<256, 256>>>(ref->G64, ref->nsh, ref->nq, npad, nchunk, rowb, 1.0, o.img);
       e = cudaGetLastError();
     }
-    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) {
+      pair_table_kernel<<<256, 256>>>(ref->G64, ref->nsh, ref->nq, gst, nchunk, pp, o.gp);
+      e = cudaGetLastError();
+    }
   }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (dmax) cudaFree(dmax);
   if (e != cudaSuccess) {
-    if (im->img) cudaFree(im->img);
-    if (im->gp) cudaFree(im->gp);
+    for (int kd = 0; kd < 2; ++kd) {
+      if (im->k[kd].img) cudaFree(im->k[kd].img);
+      if (im->k[kd].gp) cudaFree(im->k[kd].gp);
+    }
     delete im;
     return cuda_error(e, "tensor-core image");
   }
@@ -1622,29 +1730,44 @@ fei_status build_tc_image(fei_reference *ref) {
 
 void free_tc_image(fei_reference *ref) {
   if (ref->tc) {
-    cudaFree(ref->tc->img);
-    cudaFree(ref->tc->gp);
+    for (int kd = 0; kd < 2; ++kd) {
+      cudaFree(ref->tc->k[kd].img);
+      cudaFree(ref->tc->k[kd].gp);
+    }
     delete ref->tc;
     ref->tc = nullptr;
   }
 }
 
-int tc_variant_count(int p) { return p >= 3 && p <= 5 ? 2 : p >= 6 && p <= 7 ? 1 : 0; }
+int tc_variant_count(int p, fei_precision prec) {
+  if (prec == FEI_TC_3XTF32) return p >= 3 && p <= 7 ? 1 : 0;
+  return p >= 3 && p <= 5 ? 2 : p >= 6 && p <= 7 ? 1 : 0;
+}
 
 fei_status launch_tc_forward(int p, const fei_reference *ref, const FwdArgs &a, int64_t grid_work, cudaStream_t s,
-                             int variant) {
+                             int variant, fei_precision prec) {
   if (grid_work <= 0) return FEI_OK;
-  if (variant < 0 || variant >= tc_variant_count(p))
+  if (variant < 0 || variant >= tc_variant_count(p, prec))
     return set_error(FEI_ERR_UNSUPPORTED, "tensor-core variant %d for degree %d", variant, p);
+  if (prec == FEI_TC_3XTF32) {
+    switch (p) {
+      case 3: return launch_tc<3, 0, 1>(ref, a, grid_work, s);
+      case 4: return launch_tc<4, 0, 1>(ref, a, grid_work, s);
+      case 5: return launch_tc<5, 0, 1>(ref, a, grid_work, s);
+      case 6: return launch_tc<6, 0, 1>(ref, a, grid_work, s);
+      case 7: return launch_tc<7, 0, 1>(ref, a, grid_work, s);
+    }
+    return set_error(FEI_ERR_UNSUPPORTED, "tensor-core path for degree %d", p);
+  }
   switch (p * 2 + variant) {
-    case 6: return launch_tc<3, 0>(ref, a, grid_work, s);
-    case 7: return launch_tc<3, 1>(ref, a, grid_work, s);
-    case 8: return launch_tc<4, 0>(ref, a, grid_work, s);
-    case 9: return launch_tc<4, 1>(ref, a, grid_work, s);
-    case 10: return launch_tc<5, 0>(ref, a, grid_work, s);
-    case 11: return launch_tc<5, 1>(ref, a, grid_work, s);
-    case 12: return launch_tc<6, 0>(ref, a, grid_work, s);
-    case 14: return launch_tc<7, 0>(ref, a, grid_work, s);
+    case 6: return launch_tc<3, 0, 0>(ref, a, grid_work, s);
+    case 7: return launch_tc<3, 1, 0>(ref, a, grid_work, s);
+    case 8: return launch_tc<4, 0, 0>(ref, a, grid_work, s);
+    case 9: return launch_tc<4, 1, 0>(ref, a, grid_work, s);
+    case 10: return launch_tc<5, 0, 0>(ref, a, grid_work, s);
+    case 11: return launch_tc<5, 1, 0>(ref, a, grid_work, s);
+    case 12: return launch_tc<6, 0, 0>(ref, a, grid_work, s);
+    case 14: return launch_tc<7, 0, 0>(ref, a, grid_work, s);
   }
   return set_error(FEI_ERR_UNSUPPORTED, "tensor-core path for degree %d", p);
 }

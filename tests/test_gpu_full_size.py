@@ -65,11 +65,12 @@ def check(A, bv, st, w, idx, p, tol, Aoff=None, boff=None, degree=None):
         assert np.linalg.norm(b - bb) <= tol * np.linalg.norm(bb), e
 
 
-@pytest.mark.parametrize("name,k", [("p4", 40), ("p7", 8), ("p1m", 64)])
-def test_uniform_workload_full_size(api, name, k):
+@pytest.mark.parametrize("name,k,tc", [("p4", 40, "tc_f16x3"), ("p7", 8, "tc_f16x3"), ("p1m", 64, "tc_f16x3"),
+                                       ("p4", 16, "tc_3xtf32"), ("p7", 4, "tc_3xtf32")])
+def test_uniform_workload_full_size(api, name, k, tc):
     w = inputs.workload(name)
     p = w["p"]
-    prec = "tc_f16x3" if p >= 3 else "fp32"
+    prec = tc if p >= 3 else "fp32"
     g = [dev(w[x]) for x in ("geom", "K", "b", "c", "f")]
     refs = [api.fei_reference_create(p)]
     stream = torch.cuda.Stream()
@@ -77,7 +78,7 @@ def test_uniform_workload_full_size(api, name, k):
         A, bv, st, _ = api.fei_integrate(*g, p=p, precision=prec, refs=refs)
     stream.synchronize()
     n = len(w["geom"])
-    check(A, bv, st, w, sample(n, k, 11), p, 1e-6 if prec == "tc_f16x3" else 1e-5)
+    check(A, bv, st, w, sample(n, k, 11), p, 1e-6 if prec.startswith("tc") else 1e-5)
 
 
 def test_mixed_workload_full_size_plan(api):

@@ -14,7 +14,7 @@ from parity_util import assert_grads_close, worst_conditioned
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-12, "fp32": 1e-5, "tc_f16x3": 1e-6}
+TOL = {"fp64": 1e-12, "fp32": 1e-5, "tc_f16x3": 1e-6, "tc_3xtf32": 1e-6}
 # Gradients: element by element (relative Frobenius of the 18 vertex
 # gradients, and of an element's per-point coefficient gradients) at the
 # bars above, and record by record (one element's vertex gradients, one row
@@ -95,7 +95,7 @@ def test_reference_tables_match_oracle(api, p):
     assert np.max(np.abs(G.numpy() - Go)) < 1e-13 * scale
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32", "tc_f16x3"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "tc_f16x3", "tc_3xtf32"])
 @pytest.mark.parametrize("p", range(1, 8))
 def test_forward_uniform_degree(api, p, precision):
     w = workload_for(p, N_PER_P[p])
@@ -111,21 +111,21 @@ def test_pr1_full_fp64(api):
     assert ea.max() < 1e-12 and eb.max() < 1e-12
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32", "tc_f16x3"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "tc_f16x3", "tc_3xtf32"])
 def test_mixed_degree_batch(api, precision):
     w = inputs.workload("mixed", n_max=240)
     ea, eb = compare(api, w, None, precision, degree=w["degree"])
     assert ea.max() < TOL[precision] and eb.max() < TOL[precision]
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32", "tc_f16x3"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "tc_f16x3", "tc_3xtf32"])
 def test_per_point_coefficients(api, precision):
     w = inputs.workload("diff", n_max=6)
     ea, eb = compare(api, w, 5, precision, per_qp=True)
     assert ea.max() < TOL[precision] and eb.max() < TOL[precision]
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32", "tc_f16x3"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "tc_f16x3", "tc_3xtf32"])
 @pytest.mark.parametrize("p", [1, 4, 7])
 def test_status_flags_and_zero_outputs(api, p, precision):
     w = workload_for(p, 7)
