@@ -37,6 +37,7 @@ WORKLOAD_TEXT = {
     "diff": "differentiation: 20000 prisms (25x20x20), p=5, per-point coefficient fields",
     "p7": "high order: 32768 prisms (32x32x16 grid, jitter 25% h, det J > 0 certified), p=7",
     "p1m": "PR1 recipe at 1 000 000 prisms (100x100x50 grid, jitter 10% h), p=1 (supplementary, store-bound)",
+    "p4sym": "symmetric single degree: the p=4 100000-prism batch with b=0, A_e stored as upper triangles",
 }
 
 
@@ -86,12 +87,13 @@ def quad_bwd_flops_per_element(p):
     return 8 * s * q + 616 * q
 
 
-def bytes_per_element(p, out_bytes, per_qp=False):
+def bytes_per_element(p, out_bytes, per_qp=False, upper=False):
     """Algorithmic HBM bytes: geometry 144 B + coefficients 112 B (per
-    element) or 112 N_q B (per point) + outputs (N_sh^2 + N_sh) * s."""
+    element) or 112 N_q B (per point) + outputs (N_sh^2 + N_sh) * s, with
+    N_sh (N_sh + 1) / 2 values of A_e in the upper-triangle layout."""
     s = nsh(p)
     coef = 112 * (nq(p) if per_qp else 1)
-    return 144 + coef + (s * s + s) * out_bytes
+    return 144 + coef + ((s * (s + 1) // 2 if upper else s * s) + s) * out_bytes
 
 
 def measured_traffic(kernel_key, p, n_elem):
@@ -228,12 +230,27 @@ def cpu_oracle_run(w, n_sample, per_qp):
     return n / dt, cores, n, dt, out
 
 
-def errors_vs_oracle(A, bv, st, ref, n_s):
+def errors_vs_oracle(A, bv, st, ref, n_s, upper_p=None):
     """Per-element relative Frobenius error of A_e (2-norm of b_e) of the
     first n_s elements of a device result against the oracle's, which uses
     the same prefix layout.  Returns max, p99 and mean of A's errors, the
-    max of b's, and whether the statuses agree."""
+    max of b's, and whether the statuses agree.  upper_p: the device result
+    holds each A_e of this uniform degree as its upper triangle (mirrored
+    back to the full matrix for the comparison)."""
     Ao, bo, so, (oA, ob, _) = ref
+    if upper_p is not None:
+        s = nsh(upper_p)
+        su = s * (s + 1) // 2
+        iu = np.triu_indices(s)
+        rows = []
+        for e0 in range(0, n_s, 2048):
+            e1 = min(n_s, e0 + 2048)
+            pk = A[e0 * su:e1 * su].double().cpu().numpy().reshape(-1, su)
+            full = np.zeros((e1 - e0, s, s))
+            full[:, iu[0], iu[1]] = pk
+            full[:, iu[1], iu[0]] = pk
+            rows.append(full.reshape(-1))
+        A = torch_from(np.concatenate(rows))
     offs = np.asarray(oA[: n_s + 1], dtype=np.int64)
     boffs = np.asarray(ob[: n_s + 1], dtype=np.int64)
     ea = np.empty(n_s)
@@ -262,6 +279,11 @@ def errors_vs_oracle(A, bv, st, ref, n_s):
             "mean": float(ea[ok].mean()) if ok.any() else None,
             "b_max": float(eb[ok].max()) if ok.any() else None,
             "status_equal": bool(np.array_equal(st[:n_s].cpu().numpy(), so))}
+
+
+def torch_from(x):
+    import torch
+    return torch.from_numpy(x)
 
 
 def shard_workload(w, rank, world, mode):
@@ -376,6 +398,7 @@ def run_workload(name, args, ctx, headline):
         "world", "rank", "dev", "stream", "flush", "peaks", "peak_src", "live"))
     steps = args.steps if headline else max(2, min(args.steps, args.per_workload_steps))
     w0 = inputs.workload(name, n_max=(args.elements or None) if headline else None)
+    upper = name == "p4sym"  # a symmetric weak form: A_e as upper triangles
     w = shard_workload(w0, rank, world, args.scaling)
     per_qp = bool(w["per_qp"])
     p = w["p"]
@@ -400,7 +423,7 @@ def run_workload(name, args, ctx, headline):
     precision = args.precision if headline else None
     if precision is None:
         precision = "tc_f16x3" if (p is None or p >= 3) else "fp32"
-    layout = api.fei_plan_offsets(deg) if deg is not None else api.uniform_layout(n, p)
+    layout = api.fei_plan_offsets(deg, upper) if deg is not None else api.uniform_layout(n, p, upper)
     refs = [api.fei_reference_create(d) for d in ([p] if p is not None else range(1, 8))]
     out_dtype = torch.float64 if precision == "fp64" else torch.float32
     A = torch.empty(layout.A_total, dtype=out_dtype, device=dev)
@@ -436,7 +459,7 @@ def run_workload(name, args, ctx, headline):
                          out=outs)
         else:
             api.fei_integrate(g["geom"], g["K"], g["b"], g["c"], g["f"], p=p, degree=deg, per_qp=per_qp,
-                              precision=prec, refs=refs, layout=layout, out=outs)
+                              precision=prec, refs=refs, layout=layout, out=outs, upper=upper)
         if grads is not None and prec == precision:
             if mid is not None:
                 mid.record(stream)
@@ -484,14 +507,14 @@ def run_workload(name, args, ctx, headline):
     value = n_job / (ms * 1e-3)
 
     # errors of the timed path's outputs (the last step) against the oracle
-    err = errors_vs_oracle(A, bv, st, ref, n_s) if ref is not None else None
+    err = errors_vs_oracle(A, bv, st, ref, n_s, p if upper else None) if ref is not None else None
 
     # algorithmic flops / bytes of one step
     degs = np.full(n, p) if p is not None else np.asarray(w["degree"])
     counts = np.bincount(degs, minlength=8)
     out_b = 8 if precision == "fp64" else 4
     F = sum(int(counts[d]) * flops_per_element(d) for d in range(1, 8))
-    Bts = sum(int(counts[d]) * bytes_per_element(d, out_b, per_qp) for d in range(1, 8))
+    Bts = sum(int(counts[d]) * bytes_per_element(d, out_b, per_qp, upper) for d in range(1, 8))
     # the dominant kernel and its own duration (CUDA events on its stream):
     # the one kernel of a uniform forward step; the slowest degree of a
     # plan (timed per degree by the plan's tuner above); the adjoint kernel
@@ -514,7 +537,7 @@ def run_workload(name, args, ctx, headline):
             prec_d = precision if (precision != "tc_f16x3" or d >= 3) else "fp32"
             dd = {"kernel": "forward", "ms": tms, "F": int(counts[d]) * flops_per_element(d), "precision": prec_d,
                   "counts": cd}
-            Bd = int(counts[d]) * bytes_per_element(d, out_b, per_qp)
+            Bd = int(counts[d]) * bytes_per_element(d, out_b, per_qp, upper)
             rd = roofline_of(dd, cd, prec_d, peaks, peak_src, live, Bd, tms, d, int(counts[d]), per_qp)
             plan_buckets[f"p{d}"] = {"elements": int(counts[d]), "ms": tms, "bound": rd["bound"],
                                      "achieved": rd["achieved"], "peak": rd["peak"], "frac": rd["frac"]}
@@ -555,7 +578,7 @@ def run_workload(name, args, ctx, headline):
         fp64 = {"elements_per_s": n / (statistics.median(t64) * 1e-3), "ms_per_step": statistics.median(t64),
                 "steps": len(t64), "forward_only": grads is not None}
         if ref is not None:
-            fp64["rel_err_vs_oracle"] = errors_vs_oracle(A64, b64, st64, ref, n_s)
+            fp64["rel_err_vs_oracle"] = errors_vs_oracle(A64, b64, st64, ref, n_s, p if upper else None)
         del A64, b64, st64
         if precision in ("tc_f16x3", "tc_3xtf32") and headline:
             A32 = torch.empty(layout.A_total, dtype=torch.float32, device=dev)
@@ -575,7 +598,7 @@ def run_workload(name, args, ctx, headline):
             fp32_path = {"elements_per_s": n / (statistics.median(t32) * 1e-3),
                          "ms_per_step": statistics.median(t32)}
             if ref is not None:
-                fp32_path["rel_err_vs_oracle"] = errors_vs_oracle(A32, b32, st32, ref, n_s)
+                fp32_path["rel_err_vs_oracle"] = errors_vs_oracle(A32, b32, st32, ref, n_s, p if upper else None)
             del A32, b32, st32
 
     # the other split of the tensor-core contraction on the same batch (the
@@ -604,14 +627,14 @@ def run_workload(name, args, ctx, headline):
         alt_tc = {"precision": alt, "elements_per_s": n / (ma * 1e-3), "ms_per_step": ma,
                   "roofline": roofline_of(da, counts, alt, peaks, peak_src, live, Bts, ma, p, n, per_qp)}
         if ref is not None:
-            alt_tc["rel_err_vs_oracle"] = errors_vs_oracle(Aa, ba, sa, ref, n_s)
+            alt_tc["rel_err_vs_oracle"] = errors_vs_oracle(Aa, ba, sa, ref, n_s, p if upper else None)
         del Aa, ba, sa
 
     # end to end through the public API with host buffers
     e2e = None
-    if headline and not args.no_e2e:
+    if (headline or upper) and not args.no_e2e:
         e2e = end_to_end(args, ctx, w, g, deg, p, per_qp, layout, refs, precision, out_dtype, grads, step, A, bv,
-                         n_job)
+                         n_job, upper)
 
     assembly = None
     if headline and args.assemble and rank == 0 and world == 1:
@@ -644,7 +667,8 @@ def run_workload(name, args, ctx, headline):
     return res
 
 
-def end_to_end(args, ctx, w, g, deg, p, per_qp, layout, refs, precision, out_dtype, grads, step, A, bv, n_job):
+def end_to_end(args, ctx, w, g, deg, p, per_qp, layout, refs, precision, out_dtype, grads, step, A, bv, n_job,
+               upper=False):
     """The same workload through the library's public entry with host
     buffers: pinned inputs, the uploads and downloads inside the timed
     region (fei_integrate_host for a forward batch; copy in, forward +
@@ -673,7 +697,7 @@ def end_to_end(args, ctx, w, g, deg, p, per_qp, layout, refs, precision, out_dty
     def e2e_step():
         if pipe is not None:
             pipe.integrate_host(hin["geom"], hin["K"], hin["b"], hin["c"], hin["f"], p=p, degree=hdeg,
-                                per_qp=per_qp, out=(hA, hb, hst))
+                                per_qp=per_qp, out=(hA, hb, hst), upper=upper)
             return
         for k in hin:
             g[k].copy_(hin[k], non_blocking=True)
@@ -810,7 +834,7 @@ def assembly_measure(api, w, g, deg, refs, precision, flush, steps):
     }
 
 
-PER_WORKLOAD_ORDER = ("pr1", "p1m", "p4", "mixed", "diff", "p7")
+PER_WORKLOAD_ORDER = ("pr1", "p1m", "p4", "p4sym", "mixed", "diff", "p7")
 
 
 def main():

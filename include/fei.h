@@ -89,11 +89,25 @@ typedef enum {
   FEI_COEF_PER_POINT = 1    /* one record per quadrature point            */
 } fei_coef_mode;
 
+/* Layout of each A_e in A_out.  FEI_A_FULL: N_sh x N_sh row-major.
+ * FEI_A_UPPER: for a symmetric weak form (b = 0 and K symmetric, so that
+ * A_e = A_e^T: the Laplacian-type term of Sec. 2, Eq. (1), plus reaction),
+ * only the upper triangle, row by row: row i holds A_e[i][i..N_sh-1], so
+ * A_e[i][j] (j >= i) is at i N_sh - i (i+1) / 2 + j and an element takes
+ * N_sh (N_sh + 1) / 2 values.  Every coefficient record of an element must
+ * have b = 0 and K[k][l] == K[l][k] exactly; an element that does not is
+ * flagged FEI_ERR_INVALID_ARG (outputs zero). */
+typedef enum {
+  FEI_A_FULL = 0,
+  FEI_A_UPPER = 1
+} fei_a_layout;
+
 /* Opaque per-degree reference data (quadrature, basis tables, tensor-core
  * operand images), resident on the device where it was created. */
 typedef struct fei_reference *fei_reference_t;
 
-/* A batch of elements.  All pointers are device pointers.
+/* A batch of elements.  All pointers are device pointers (host pointers for
+ * fei_integrate_host).
  *  geom      double [n_elem][6][3]  vertex coordinates (layout above).
  *  degree    int32  [n_elem] per-element degree, or NULL: every element has
  *            degree uniform_degree.
@@ -108,8 +122,10 @@ typedef struct fei_reference *fei_reference_t;
  *            its end; the Python binding refuses one).
  *  A_offset, b_offset, q_offset  int64 [n_elem + 1] start of element e in
  *            A_out (scalars), b_out, and the per-point records; NULL means
- *            the contiguous layout of a uniform degree (e*N_sh^2, e*N_sh,
- *            e*N_q).  Required when degree != NULL (see fei_plan_offsets). */
+ *            the contiguous layout of a uniform degree (e*S, e*N_sh,
+ *            e*N_q with S = N_sh^2, or N_sh (N_sh + 1) / 2 for FEI_A_UPPER).
+ *            Required when degree != NULL (see fei_plan_offsets).
+ *  a_layout  fei_a_layout of A_out (0 = FEI_A_FULL). */
 typedef struct {
   int64_t n_elem;
   const double *geom;
@@ -123,6 +139,7 @@ typedef struct {
   const int64_t *A_offset;
   const int64_t *b_offset;
   const int64_t *q_offset;
+  int32_t a_layout;
 } fei_batch;
 
 /* Gradient outputs of fei_integrate_backward, same layouts as the inputs
@@ -183,7 +200,8 @@ fei_status fei_integrate(const fei_reference_t *refs, int nrefs,
  * Jacobians are recomputed, not stored.  Precision FEI_FP64 or FEI_FP32
  * (the contraction W = gA G^T in FP64 or FP32; the Jacobian chain in FP64).
  * Elements with a nonzero elem_status from the forward get zero gradients
- * (this call recomputes the status itself). */
+ * (this call recomputes the status itself).  batch->a_layout must be
+ * FEI_A_FULL (FEI_ERR_UNSUPPORTED otherwise). */
 fei_status fei_integrate_backward(const fei_reference_t *refs, int nrefs,
                                   const fei_batch *batch, fei_precision prec,
                                   const void *gA, const void *gb,
@@ -214,6 +232,12 @@ fei_status fei_plan_offsets(const int32_t *degree, int64_t n_elem,
                             int64_t *A_offset, int64_t *b_offset,
                             int64_t *q_offset, int32_t *bad_count,
                             fei_stream_t stream);
+/* The same for A_out in the FEI_A_UPPER layout: A_offset advances by
+ * N_sh (N_sh + 1) / 2 per element. */
+fei_status fei_plan_offsets_upper(const int32_t *degree, int64_t n_elem,
+                                  int64_t *A_offset, int64_t *b_offset,
+                                  int64_t *q_offset, int32_t *bad_count,
+                                  fei_stream_t stream);
 
 /* --------------------------------------------------------------------- */
 /* Plans: a mixed-degree batch as one CUDA graph, with the kernel shape of

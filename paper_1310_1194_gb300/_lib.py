@@ -31,6 +31,9 @@ FEI_TC_3XTF32 = 3
 FEI_COEF_PER_ELEMENT = 0
 FEI_COEF_PER_POINT = 1
 
+FEI_A_FULL = 0
+FEI_A_UPPER = 1
+
 PRECISIONS = {"fp64": FEI_FP64, "fp32": FEI_FP32, "tc_f16x3": FEI_TC_F16X3, "tc_3xtf32": FEI_TC_3XTF32}
 
 FEI_NOALLOC_MAX_ELEM = 262144
@@ -50,6 +53,7 @@ class fei_batch(ctypes.Structure):
         ("A_offset", ctypes.c_void_p),
         ("b_offset", ctypes.c_void_p),
         ("q_offset", ctypes.c_void_p),
+        ("a_layout", ctypes.c_int32),
     ]
 
 
@@ -83,6 +87,7 @@ def _load():
     lib.fei_integrate_backward_quadratic.argtypes = [ref_p, ctypes.c_int, ctypes.POINTER(fei_batch), ctypes.c_int,
                                                      vp, vp, ctypes.POINTER(fei_coef_grad), vp]
     lib.fei_plan_offsets.argtypes = [vp, i64, vp, vp, vp, vp, vp]
+    lib.fei_plan_offsets_upper.argtypes = [vp, i64, vp, vp, vp, vp, vp]
     lib.fei_status_summary.argtypes = [vp, i64, vp, vp]
     lib.fei_sync_status.argtypes = [vp, i64, ctypes.POINTER(i32), ctypes.POINTER(i64), vp]
     lib.fei_integrate_noalloc.argtypes = [ref_p, ctypes.c_int, ctypes.POINTER(fei_batch), ctypes.c_int,
@@ -112,7 +117,7 @@ def _load():
     for name in ("fei_reference_create", "fei_reference_destroy", "fei_reference_info",
                  "fei_reference_copy_table", "fei_integrate", "fei_integrate_backward",
                  "fei_integrate_backward_quadratic",
-                 "fei_plan_offsets", "fei_integrate_noalloc", "fei_plan_create", "fei_plan_destroy",
+                 "fei_plan_offsets", "fei_plan_offsets_upper", "fei_integrate_noalloc", "fei_plan_create", "fei_plan_destroy",
                  "fei_plan_execute", "fei_plan_tune", "fei_plan_choice", "fei_status_summary", "fei_sync_status",
                  "fei_assembly_create", "fei_assembly_destroy", "fei_assembly_info", "fei_assembly_pattern",
                  "fei_assemble", "fei_integrate_assemble", "fei_debug_set_wait_limit", "fei_plan_set_choice",

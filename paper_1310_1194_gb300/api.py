@@ -25,6 +25,32 @@ def nq(p: int) -> int:
     return (p + 1) ** 3
 
 
+def a_size(p: int, upper: bool = False) -> int:
+    """Values of one A_e: N_sh^2, or N_sh (N_sh + 1) / 2 as its upper triangle."""
+    s = nsh(p)
+    return s * (s + 1) // 2 if upper else s * s
+
+
+def unpack_upper(a_upper, p: int):
+    """The full N_sh x N_sh matrices of elements stored as upper triangles
+    (row i holds A[i][i..N_sh-1]): a_upper [..., N_sh (N_sh + 1) / 2] ->
+    [..., N_sh, N_sh], mirrored across the diagonal (a torch tensor or a
+    numpy array; no kernel)."""
+    s = nsh(p)
+    iu = np.triu_indices(s)
+    if isinstance(a_upper, torch.Tensor):
+        out = a_upper.new_zeros(a_upper.shape[:-1] + (s, s))
+        r, c = torch.as_tensor(iu[0], device=a_upper.device), torch.as_tensor(iu[1], device=a_upper.device)
+        out[..., r, c] = a_upper
+        out[..., c, r] = a_upper
+        return out
+    a_upper = np.asarray(a_upper)
+    out = np.zeros(a_upper.shape[:-1] + (s, s), dtype=a_upper.dtype)
+    out[..., iu[0], iu[1]] = a_upper
+    out[..., iu[1], iu[0]] = a_upper
+    return out
+
+
 class Reference:
     """Owning wrapper of a fei_reference_t (reference data of degree p)."""
 
@@ -93,8 +119,9 @@ class Layout:
     q_total: int
 
 
-def fei_plan_offsets(degree: torch.Tensor) -> Layout:
-    """Contiguous offsets of a degree array (computed by a kernel)."""
+def fei_plan_offsets(degree: torch.Tensor, upper: bool = False) -> Layout:
+    """Contiguous offsets of a degree array (computed by a kernel); upper:
+    for A_e stored as upper triangles."""
     degree = _need(degree, "degree", torch.int32)
     n = degree.numel()
     dev = degree.device
@@ -102,8 +129,8 @@ def fei_plan_offsets(degree: torch.Tensor) -> Layout:
     bo = torch.empty(n + 1, dtype=torch.int64, device=dev)
     qo = torch.empty(n + 1, dtype=torch.int64, device=dev)
     bad = torch.zeros(1, dtype=torch.int32, device=dev)
-    check(lib.fei_plan_offsets(_ptr(degree), n, _ptr(Ao), _ptr(bo), _ptr(qo), _ptr(bad), _stream()),
-          "fei_plan_offsets")
+    fn = lib.fei_plan_offsets_upper if upper else lib.fei_plan_offsets
+    check(fn(_ptr(degree), n, _ptr(Ao), _ptr(bo), _ptr(qo), _ptr(bad), _stream()), "fei_plan_offsets")
     tail = torch.stack([Ao[-1], bo[-1], qo[-1], bad[0].to(torch.int64)]).cpu().tolist()
     if tail[3]:
         raise ValueError(f"{tail[3]} elements have a degree outside 1..7")
@@ -131,12 +158,12 @@ def fei_sync_status(status: torch.Tensor):
     return int(worst.value), int(count.value)
 
 
-def uniform_layout(n: int, p: int) -> Layout:
+def uniform_layout(n: int, p: int, upper: bool = False) -> Layout:
     s = nsh(p)
-    return Layout(None, None, None, n * s * s, n * s, n * nq(p))
+    return Layout(None, None, None, n * a_size(p, upper), n * s, n * nq(p))
 
 
-def _batch(geom, K, b, c, f, degree, p, per_qp, layout):
+def _batch(geom, K, b, c, f, degree, p, per_qp, layout, upper=False):
     n = geom.shape[0]
     bt = _lib.fei_batch()
     bt.n_elem = n
@@ -151,6 +178,7 @@ def _batch(geom, K, b, c, f, degree, p, per_qp, layout):
     bt.A_offset = layout.A_offset.data_ptr() if layout.A_offset is not None else None
     bt.b_offset = layout.b_offset.data_ptr() if layout.b_offset is not None else None
     bt.q_offset = layout.q_offset.data_ptr() if layout.q_offset is not None else None
+    bt.a_layout = _lib.FEI_A_UPPER if upper else _lib.FEI_A_FULL
     return bt
 
 
@@ -159,7 +187,7 @@ def _refs_array(refs):
     return arr
 
 
-def _inputs(geom, K, b, c, f, degree, p, per_qp, layout):
+def _inputs(geom, K, b, c, f, degree, p, per_qp, layout, upper=False):
     geom = _need(geom, "geom")
     if geom.dim() != 3 or geom.shape[1:] != (6, 3):
         raise ValueError("geom must be [n, 6, 3]")
@@ -168,12 +196,12 @@ def _inputs(geom, K, b, c, f, degree, p, per_qp, layout):
     if degree is not None:
         _need(degree, "degree", torch.int32)
         if layout is None:
-            layout = fei_plan_offsets(degree)
+            layout = fei_plan_offsets(degree, upper)
     else:
         if p is None:
             raise ValueError("give p or degree")
         if layout is None:
-            layout = uniform_layout(geom.shape[0], p)
+            layout = uniform_layout(geom.shape[0], p, upper)
     # the kernels index the coefficient records by element (or by element
     # and point) without knowing the arrays' lengths, so a short array would
     # be read past its end: its size is checked here
@@ -186,13 +214,14 @@ def _inputs(geom, K, b, c, f, degree, p, per_qp, layout):
 
 
 def fei_integrate(geom, K, b, c, f, p=None, degree=None, per_qp=False, precision="fp32",
-                  refs=None, layout=None, out=None):
+                  refs=None, layout=None, out=None, upper=False):
     """Element matrices and load vectors (forward, Algorithm 1).
 
     Returns (A, b_vec, status, layout): A [A_total] and b_vec [b_total] in
     FP64 for precision "fp64" and FP32 otherwise, laid out by ``layout``;
-    status int32 [n]."""
-    geom, layout = _inputs(geom, K, b, c, f, degree, p, per_qp, layout)
+    status int32 [n].  upper: each A_e as its upper triangle (a symmetric
+    weak form: b = 0 and K symmetric; see unpack_upper)."""
+    geom, layout = _inputs(geom, K, b, c, f, degree, p, per_qp, layout, upper)
     prec = _lib.PRECISIONS[precision]
     dtype = torch.float64 if prec == _lib.FEI_FP64 else torch.float32
     n = geom.shape[0]
@@ -205,7 +234,7 @@ def fei_integrate(geom, K, b, c, f, p=None, degree=None, per_qp=False, precision
         st = torch.empty(n, dtype=torch.int32, device=geom.device)
     else:
         A, bv, st = out
-    bt = _batch(geom, K, b, c, f, degree, p, per_qp, layout)
+    bt = _batch(geom, K, b, c, f, degree, p, per_qp, layout, upper)
     check(lib.fei_integrate(_refs_array(refs), len(refs), ctypes.byref(bt), prec,
                             _ptr(A), _ptr(bv), _ptr(st), _stream()), "fei_integrate")
     return A, bv, st, layout
@@ -276,8 +305,8 @@ class Plan:
                                   _lib.PRECISIONS[precision], ctypes.byref(h)), "fei_plan_create")
         self.handle = h
 
-    def _call(self, fn, name, geom, K, b, c, f, p, degree, per_qp, layout, out):
-        geom, layout = _inputs(geom, K, b, c, f, degree, p, per_qp, layout)
+    def _call(self, fn, name, geom, K, b, c, f, p, degree, per_qp, layout, out, upper=False):
+        geom, layout = _inputs(geom, K, b, c, f, degree, p, per_qp, layout, upper)
         prec = _lib.PRECISIONS[self.precision]
         dtype = torch.float64 if prec == _lib.FEI_FP64 else torch.float32
         n = geom.shape[0]
@@ -287,13 +316,13 @@ class Plan:
             st = torch.empty(n, dtype=torch.int32, device=geom.device)
         else:
             A, bv, st = out
-        bt = _batch(geom, K, b, c, f, degree, p, per_qp, layout)
+        bt = _batch(geom, K, b, c, f, degree, p, per_qp, layout, upper)
         check(fn(self.handle, ctypes.byref(bt), _ptr(A), _ptr(bv), _ptr(st), _stream()), name)
         return A, bv, st, layout
 
-    def execute(self, geom, K, b, c, f, p=None, degree=None, per_qp=False, layout=None, out=None):
+    def execute(self, geom, K, b, c, f, p=None, degree=None, per_qp=False, layout=None, out=None, upper=False):
         return self._call(lib.fei_plan_execute, "fei_plan_execute", geom, K, b, c, f, p, degree, per_qp,
-                          layout, out)
+                          layout, out, upper)
 
     def tune(self, geom, K, b, c, f, p=None, degree=None, per_qp=False, layout=None, out=None, cache=None):
         """Times the candidate kernel shapes of every degree on this batch
@@ -388,18 +417,20 @@ class Pipeline:
         self.slot_bytes, self.max_elem = sb.value, me.value
         self.n_chunks = 0
 
-    def totals(self, n, p=None, degree=None, per_qp=False):
-        """(A_total, b_total, record count) of the packed layout."""
+    def totals(self, n, p=None, degree=None, per_qp=False, upper=False):
+        """(A_total, b_total, record count) of the packed layout (A_e as
+        upper triangles with upper=True)."""
         if degree is None:
             s, q = (p + 1) ** 2 * (p + 2) // 2, (p + 1) ** 3
-            return n * s * s, n * s, n * q if per_qp else n
+            return n * (s * (s + 1) // 2 if upper else s * s), n * s, n * q if per_qp else n
         d = degree.numpy().astype(np.int64)
         ok = (d >= 1) & (d <= 7)
         s = np.where(ok, (d + 1) ** 2 * (d + 2) // 2, 0)
         q = np.where(ok, (d + 1) ** 3, 0)
-        return int((s * s).sum()), int(s.sum()), int(q.sum()) if per_qp else n
+        a = s * (s + 1) // 2 if upper else s * s
+        return int(a.sum()), int(s.sum()), int(q.sum()) if per_qp else n
 
-    def integrate_host(self, geom, K, b, c, f, p=None, degree=None, per_qp=False, out=None):
+    def integrate_host(self, geom, K, b, c, f, p=None, degree=None, per_qp=False, out=None, upper=False):
         geom = _host_f64(geom, "geom")
         if geom.dim() != 3 or geom.shape[1:] != (6, 3):
             raise ValueError("geom must be [n, 6, 3]")
@@ -408,7 +439,7 @@ class Pipeline:
         elif p is None:
             raise ValueError("give p or degree")
         n = geom.shape[0]
-        A_total, b_total, m = self.totals(n, p, degree, per_qp)
+        A_total, b_total, m = self.totals(n, p, degree, per_qp, upper)
         for t, name, width in ((K, "K", 9), (b, "b", 3), (c, "c", 1), (f, "f", 1)):
             _host_f64(t, name)
             if t.numel() != width * m:
@@ -433,6 +464,7 @@ class Pipeline:
         bt.uniform_degree = int(p) if p is not None else 0
         bt.coef_mode = _lib.FEI_COEF_PER_POINT if per_qp else _lib.FEI_COEF_PER_ELEMENT
         bt.K, bt.b, bt.c, bt.f = K.data_ptr(), b.data_ptr(), c.data_ptr(), f.data_ptr()
+        bt.a_layout = _lib.FEI_A_UPPER if upper else _lib.FEI_A_FULL
         nc = ctypes.c_int64()
         check(lib.fei_integrate_host(self.handle, ctypes.byref(bt), _ptr(A), _ptr(bv), _ptr(st),
                                      ctypes.byref(nc), _stream()), "fei_integrate_host")

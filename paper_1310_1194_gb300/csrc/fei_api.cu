@@ -81,7 +81,7 @@ __global__ void bucket_kernel(const int32_t *degree, int64_t n, unsigned avail, 
 }
 
 // Single-block exclusive scan of N_sh^2, N_sh and N_q over the degrees.
-__global__ void __launch_bounds__(1024) offsets_kernel(const int32_t *degree, int64_t n, int64_t *Ao,
+__global__ void __launch_bounds__(1024) offsets_kernel(const int32_t *degree, int64_t n, int upper, int64_t *Ao,
                                                         int64_t *bo, int64_t *qo, int32_t *bad) {
   __shared__ int64_t sA[1024], sb[1024], sq[1024];
   __shared__ int32_t sbad;
@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(1024) offsets_kernel(const int32_t *degree, in
       continue;
     }
     const int64_t s = nsh_of(p);
-    a += s * s;
+    a += a_size(s, upper);
     b += s;
     q += nq_of(p);
   }
@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(1024) offsets_kernel(const int32_t *degree, in
     const int p = degree[e];
     if (p >= 1 && p <= kPMax) {
       const int64_t s = nsh_of(p);
-      a += s * s;
+      a += a_size(s, upper);
       b += s;
       q += nq_of(p);
     }
@@ -173,6 +173,8 @@ fei_status check_batch(const fei_batch *b) {
     return set_error(FEI_ERR_INVALID_ARG, "batch geometry/coefficient pointer is NULL");
   if (b->coef_mode != FEI_COEF_PER_ELEMENT && b->coef_mode != FEI_COEF_PER_POINT)
     return set_error(FEI_ERR_INVALID_ARG, "coef_mode %d", b->coef_mode);
+  if (b->a_layout != FEI_A_FULL && b->a_layout != FEI_A_UPPER)
+    return set_error(FEI_ERR_INVALID_ARG, "a_layout %d", b->a_layout);
   if (b->degree) {
     if (!b->A_offset || !b->b_offset || (b->coef_mode == FEI_COEF_PER_POINT && !b->q_offset))
       return set_error(FEI_ERR_INVALID_ARG, "a degree array needs A_offset, b_offset (and q_offset per point)");
@@ -194,6 +196,7 @@ void fill_fwd(FwdArgs &a, const fei_batch *b, const fei_reference *r, void *A, v
   a.A_off = b->A_offset;
   a.b_off = b->b_offset;
   a.q_off = b->q_offset;
+  a.upper = b->a_layout == FEI_A_UPPER;
   a.A = A;
   a.bv = bv;
   a.status = st;
@@ -336,15 +339,32 @@ extern "C" fei_status fei_sync_status(const int32_t *elem_status, int64_t n_elem
   return FEI_OK;
 }
 
+namespace fei {
+namespace {
+fei_status plan_offsets(const char *who, const int32_t *degree, int64_t n_elem, int upper, int64_t *A_offset,
+                        int64_t *b_offset, int64_t *q_offset, int32_t *bad_count, fei_stream_t stream) {
+  if (!degree && n_elem > 0) return set_error(FEI_ERR_INVALID_ARG, "%s: degree is NULL", who);
+  if (n_elem < 0) return set_error(FEI_ERR_INVALID_ARG, "%s: n_elem < 0", who);
+  if (!A_offset && !b_offset && !q_offset && !bad_count) return FEI_OK;
+  offsets_kernel<<<1, 1024, 0, (cudaStream_t)stream>>>(degree, n_elem, upper, A_offset, b_offset, q_offset,
+                                                        bad_count);
+  FEI_CUDA_TRY(cudaGetLastError(), "offsets_kernel launch");
+  return FEI_OK;
+}
+}  // namespace
+}  // namespace fei
+
 extern "C" fei_status fei_plan_offsets(const int32_t *degree, int64_t n_elem, int64_t *A_offset,
                                        int64_t *b_offset, int64_t *q_offset, int32_t *bad_count,
                                        fei_stream_t stream) {
-  if (!degree && n_elem > 0) return set_error(FEI_ERR_INVALID_ARG, "fei_plan_offsets: degree is NULL");
-  if (n_elem < 0) return set_error(FEI_ERR_INVALID_ARG, "fei_plan_offsets: n_elem < 0");
-  if (!A_offset && !b_offset && !q_offset && !bad_count) return FEI_OK;
-  offsets_kernel<<<1, 1024, 0, (cudaStream_t)stream>>>(degree, n_elem, A_offset, b_offset, q_offset, bad_count);
-  FEI_CUDA_TRY(cudaGetLastError(), "offsets_kernel launch");
-  return FEI_OK;
+  return plan_offsets("fei_plan_offsets", degree, n_elem, 0, A_offset, b_offset, q_offset, bad_count, stream);
+}
+
+extern "C" fei_status fei_plan_offsets_upper(const int32_t *degree, int64_t n_elem, int64_t *A_offset,
+                                             int64_t *b_offset, int64_t *q_offset, int32_t *bad_count,
+                                             fei_stream_t stream) {
+  return plan_offsets("fei_plan_offsets_upper", degree, n_elem, 1, A_offset, b_offset, q_offset, bad_count,
+                      stream);
 }
 
 namespace fei {
@@ -422,6 +442,8 @@ fei_status backward_impl(const char *who, const fei_reference_t *refs, int nrefs
   if (st) return st;
   if (prec != FEI_FP64 && prec != FEI_FP32)
     return set_error(FEI_ERR_UNSUPPORTED, "%s: precision %d (FP64 or FP32 only)", who, (int)prec);
+  if (batch->a_layout != FEI_A_FULL)
+    return set_error(FEI_ERR_UNSUPPORTED, "%s: the adjoint takes the full A_e layout", who);
   if (batch->n_elem == 0) return FEI_OK;
   if ((!quad && (!gA || !gb)) || !g_geom || !g_coef || !g_coef->K || !g_coef->b || !g_coef->c || !g_coef->f)
     return set_error(FEI_ERR_INVALID_ARG, "%s: NULL gradient pointer", who);

@@ -556,6 +556,8 @@ extern "C" fei_status fei_integrate_assemble(fei_assembly_t as, const fei_refere
   bt.b_offset = as->loff;
   batch = &bt;
   if ((st = check_batch(batch))) return st;
+  if (batch->a_layout != FEI_A_FULL)
+    return set_error(FEI_ERR_UNSUPPORTED, "fei_integrate_assemble: assembly takes the full A_e layout");
   size_t vb;
   if ((st = value_type(prec, &vb))) return st;
   if (batch->n_elem != as->n_elem)

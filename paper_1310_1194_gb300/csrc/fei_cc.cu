@@ -169,7 +169,18 @@ __global__ void __launch_bounds__(SmallCfg<T, P>::WPB * 32) cc_small_kernel(FwdA
       }
       // lanes of one element are one aligned group of 32: the whole warp
       const unsigned bad = __ballot_sync(0xffffffffu, !ok);
-      if (k == 0) Ss(sl)[0] = bad ? FEI_ERR_NONFINITE : 0;
+      // upper layout: K symmetric (K01 = K10, K02 = K20, K12 = K21: lanes
+      // 19/21, 20/24, 23/25) and b = 0 (lanes 27-29), per-element records
+      bool sym = true;
+      if (a.upper && a.coef_mode == FEI_COEF_PER_ELEMENT) {
+        const double xk = k >= 18 ? cds(sl)[k - 18] : 0.0;
+        const int c = k - 18;
+        const int partner = c == 1 ? 21 : c == 3 ? 19 : c == 2 ? 24 : c == 6 ? 20 : c == 5 ? 25 : c == 7 ? 23 : k;
+        const double xp = __shfl_sync(0xffffffffu, xk, partner);
+        sym = (c >= 9 && c <= 11) ? xk == 0.0 : xk == xp;
+      }
+      const unsigned nonsym = __ballot_sync(0xffffffffu, !sym);
+      if (k == 0) Ss(sl)[0] = bad ? 2 * FEI_ERR_NONFINITE : (nonsym ? FEI_ERR_INVALID_ARG : 0);
     }
     __syncwarp();
     // element vectors, one component per lane (FP64)
@@ -195,6 +206,7 @@ __global__ void __launch_bounds__(SmallCfg<T, P>::WPB * 32) cc_small_kernel(FwdA
       if (a.coef_mode == FEI_COEF_PER_POINT) {
         const int64_t r = (a.q_off ? a.q_off[e] : e * (int64_t)NQ) + q;
         if (!load_coef(a, r, cq)) pst = FEI_ERR_NONFINITE;
+        else if (a.upper && !coef_symmetric(cq, cq + 9)) pst = FEI_ERR_INVALID_ARG;
         cp = cq;
       }
       pst = merge_status(pst, point_direct<T>(evs(psl), ptv, cp, Ds(psl) + 16 * q));
@@ -221,11 +233,12 @@ __global__ void __launch_bounds__(SmallCfg<T, P>::WPB * 32) cc_small_kernel(FwdA
       const int i = ij / NSH, j = ij - i * NSH;
       const int64_t e = a.list ? (int64_t)a.list[item0 + sl] : item0 + sl;
       const int64_t aoff = out_a(a, item0 + sl, e, NSH);
+      if (a.upper && j < i) continue;  // the upper layout keeps j >= i
       const T *H = Hs(sl);
       T acc = T(0);
 #pragma unroll 4
       for (int k = 0; k < K4; ++k) acc += H[k * NSH + i] * Gs[k * NSH + j];
-      reinterpret_cast<T *>(a.A)[aoff + ij] = Ss(sl)[0] ? T(0) : acc;
+      reinterpret_cast<T *>(a.A)[aoff + a_pos(i, j, NSH, a.upper)] = Ss(sl)[0] ? T(0) : acc;
     }
     for (int idx = lane; idx < nel * NSH; idx += 32) {
       const int sl = idx / NSH, i = idx - sl * NSH;
@@ -303,8 +316,14 @@ __global__ void __launch_bounds__(256) cc_tile_kernel(FwdArgs a) {
       sm.X[tid] = a.geom[18 * e + tid];
       ok = finite64(sm.X[tid]);
     }
-    if (a.coef_mode == FEI_COEF_PER_ELEMENT && tid == 32) ok = load_coef(a, e, sm.cd);
+    bool sym = true;
+    if (a.coef_mode == FEI_COEF_PER_ELEMENT && tid == 32) {
+      ok = load_coef(a, e, sm.cd);
+      sym = !a.upper || coef_symmetric(sm.cd, sm.cd + 9);
+    }
     if (!ok) sm.status = FEI_ERR_NONFINITE;
+    __syncthreads();
+    if (!sym) atomicMax(&sm.status, FEI_ERR_INVALID_ARG);
     __syncthreads();
     if (tid == 0) elem_vectors(sm.X, sm.ev);
     __syncthreads();
@@ -360,6 +379,7 @@ __global__ void __launch_bounds__(256) cc_tile_kernel(FwdArgs a) {
           if (a.coef_mode == FEI_COEF_PER_POINT) {
             const int64_t r = (a.q_off ? a.q_off[e] : e * (int64_t)NQ) + q;
             if (!load_coef(a, r, cq)) pst = FEI_ERR_NONFINITE;
+            else if (a.upper && !coef_symmetric(cq, cq + 9)) pst = FEI_ERR_INVALID_ARG;
             cp = cq;
           }
           T K[9], b[3];
@@ -444,7 +464,7 @@ __global__ void __launch_bounds__(256) cc_tile_kernel(FwdArgs a) {
 #pragma unroll
       for (int c = 0; c < RM; ++c) {
         const int j = cb * BM + tx + 16 * c;
-        if (i < NSH && j < NSH) A[(size_t)i * NSH + j] = st ? T(0) : acc[r][c];
+        if (i < NSH && j < NSH && (!a.upper || j >= i)) A[a_pos(i, j, NSH, a.upper)] = st ? T(0) : acc[r][c];
       }
     }
     if (cb == 0 && tid < BM && brow < NSH) {

@@ -114,9 +114,10 @@ __device__ __forceinline__ int point_status(double s) {
 }
 
 __device__ __forceinline__ int merge_status(int a, int b) {
-  // NONFINITE takes precedence over NEGATIVE_JACOBIAN
+  // NONFINITE takes precedence over NEGATIVE_JACOBIAN, which takes
+  // precedence over INVALID_ARG (a non-symmetric record in the upper layout)
   if (a == FEI_ERR_NONFINITE || b == FEI_ERR_NONFINITE) return FEI_ERR_NONFINITE;
-  return a ? a : b;
+  return a > b ? a : b;
 }
 
 }  // namespace fei

@@ -60,6 +60,8 @@ struct FwdArgs {
   // k N_sh (a list written contiguously in list order), 0 = at e N_sh^2 and
   // e N_sh for element e
   int out_by_item;
+  // 1: A_e as its upper triangle (FEI_A_UPPER), N_sh (N_sh + 1) / 2 values
+  int upper;
   void *A;
   void *bv;
   int32_t *status;
@@ -70,9 +72,20 @@ struct FwdArgs {
   const float *G32T;
 };
 
+// Values of one A_e: N_sh^2, or N_sh (N_sh + 1) / 2 in the upper layout.
+__host__ __device__ __forceinline__ int64_t a_size(int64_t s, bool upper) { return upper ? s * (s + 1) / 2 : s * s; }
+// Position of A_e[i][j] (j >= i in the upper layout) in the element's values.
+__host__ __device__ __forceinline__ int64_t a_pos(int i, int j, int s, bool upper) {
+  return upper ? (int64_t)i * s - (int64_t)i * (i + 1) / 2 + j : (int64_t)i * s + j;
+}
 // Start of work item k (element e) in A and in b (s = N_sh).
 __device__ __forceinline__ int64_t out_a(const FwdArgs &a, int64_t k, int64_t e, int64_t s) {
-  return a.A_off ? a.A_off[e] : (a.out_by_item ? k : e) * s * s;
+  return a.A_off ? a.A_off[e] : (a.out_by_item ? k : e) * a_size(s, a.upper);
+}
+// FEI_A_UPPER needs a symmetric weak form: b = 0 and K = K^T exactly in
+// every coefficient record (K row-major [3][3], b [3], FP64).
+__device__ __forceinline__ bool coef_symmetric(const double *K, const double *b) {
+  return K[1] == K[3] && K[2] == K[6] && K[5] == K[7] && b[0] == 0.0 && b[1] == 0.0 && b[2] == 0.0;
 }
 __device__ __forceinline__ int64_t out_b(const FwdArgs &a, int64_t k, int64_t e, int64_t s) {
   return a.b_off ? a.b_off[e] : (a.out_by_item ? k : e) * s;

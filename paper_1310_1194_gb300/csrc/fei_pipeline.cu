@@ -152,6 +152,7 @@ fei_status copy_out(void *dst, const void *src, int64_t bytes, cudaStream_t s) {
 // no room, as in fei_plan_offsets) and the chunks that fit one slot.
 fei_status plan_chunks(fei_pipeline *pl, const fei_batch *hb) {
   const int64_t n = hb->n_elem;
+  const bool upper = hb->a_layout == FEI_A_UPPER;
   const bool per_point = hb->coef_mode == FEI_COEF_PER_POINT;
   pl->chunks.clear();
   if (hb->degree) {
@@ -166,7 +167,7 @@ fei_status plan_chunks(fei_pipeline *pl, const fei_batch *hb) {
       const int p = hb->degree[e];
       if (p >= 1 && p <= kPMax) {
         const int64_t s = nsh_of(p);
-        a += s * s;
+        a += a_size(s, upper);
         b += s;
         q += nq_of(p);
       }
@@ -177,8 +178,7 @@ fei_status plan_chunks(fei_pipeline *pl, const fei_batch *hb) {
   }
   auto A_at = [&](int64_t e) -> int64_t {
     if (hb->degree) return pl->aoff[e];
-    const int64_t s = nsh_of(hb->uniform_degree);
-    return e * s * s;
+    return e * a_size(nsh_of(hb->uniform_degree), upper);
   };
   auto b_at = [&](int64_t e) -> int64_t { return hb->degree ? pl->boff[e] : e * nsh_of(hb->uniform_degree); };
   auto q_at = [&](int64_t e) -> int64_t {
@@ -294,14 +294,15 @@ fei_status enqueue_chunks(fei_pipeline *pl, const fei_batch *hb, void *A_host, v
     db.geom = in.geom;
     db.uniform_degree = hb->uniform_degree;
     db.coef_mode = hb->coef_mode;
+    db.a_layout = hb->a_layout;
     db.K = in.K;
     db.b = in.b;
     db.c = in.c;
     db.f = in.f;
     if (mixed) {
       db.degree = in.degree;
-      st = fei_plan_offsets(in.degree, ne, in.A_off, in.b_off, per_point ? in.q_off : nullptr, in.bad,
-                            (fei_stream_t)s);
+      st = (hb->a_layout == FEI_A_UPPER ? fei_plan_offsets_upper : fei_plan_offsets)(
+          in.degree, ne, in.A_off, in.b_off, per_point ? in.q_off : nullptr, in.bad, (fei_stream_t)s);
       if (st) return st;
       db.A_offset = in.A_off;
       db.b_offset = in.b_off;

@@ -48,6 +48,14 @@ namespace {
 
 bool tc_path(fei_precision prec, int p) { return tc_precision(prec) && p >= 3; }
 
+// The batch a graph was captured for, field by field (not the padding).
+bool same_batch(const fei_batch &x, const fei_batch &y) {
+  return x.n_elem == y.n_elem && x.geom == y.geom && x.degree == y.degree && x.uniform_degree == y.uniform_degree &&
+         x.coef_mode == y.coef_mode && x.K == y.K && x.b == y.b && x.c == y.c && x.f == y.f &&
+         x.A_offset == y.A_offset && x.b_offset == y.b_offset && x.q_offset == y.q_offset &&
+         x.a_layout == y.a_layout;
+}
+
 int n_candidates(fei_precision prec, int p) { return tc_path(prec, p) ? tc_variant_count(p, prec) : 4; }
 
 // Candidate c of degree p as (variant, grid cap).
@@ -72,6 +80,7 @@ void fill_args(FwdArgs &a, const fei_batch *b, const fei_reference *r, void *A, 
   a.c = b->c;
   a.f = b->f;
   a.A_off = b->A_offset;
+  a.upper = b->a_layout == FEI_A_UPPER;
   a.b_off = b->b_offset;
   a.q_off = b->q_offset;
   a.A = A;
@@ -293,7 +302,7 @@ extern "C" fei_status fei_plan_execute(fei_plan_t plan, const fei_batch *batch, 
   cudaStream_t s = (cudaStream_t)stream;
   // the legacy default stream cannot be captured: launch directly
   if (s == nullptr || s == cudaStreamLegacy) return enqueue_all(plan, batch, A_out, b_out, elem_status, s);
-  const bool same = plan->has_graph && memcmp(&plan->key_batch, batch, sizeof(fei_batch)) == 0 &&
+  const bool same = plan->has_graph && same_batch(plan->key_batch, *batch) &&
                     plan->key_A == A_out && plan->key_b == b_out && plan->key_st == elem_status;
   if (!same) {
     FEI_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");

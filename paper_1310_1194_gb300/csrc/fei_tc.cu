@@ -390,9 +390,7 @@ struct TcCfg {
 template <int P>
 struct TcElem {
   using C = TcCfg<P>;
-  double X[18];
-  double ev[21];          // element vectors A1, B1, A2, B2, C, D1, D2 (FP64)
-  float evf[21];          // the same rounded once to FP32
+  float evf[21];          // element vectors A1, B1, A2, B2, C, D1, D2, rounded once to FP32
   alignas(16) float cf[16];  // the per-element coefficients rounded once to FP32 (14 used)
   float cn[3];            // their norms in the scale bound: sqrt(||K||_1 ||K||_inf), |b|, |c|
   float2 zabg[C::NZ][3];  // w_z (n3.C, n3.D1, n3.D2) per vertical node: FP64 as FP32 hi + lo
@@ -410,9 +408,10 @@ struct TcElem {
 // Per-tile row data handed from the point-operator warps to the producers
 // (load vector, statuses) and to the epilogue (stores of A_e).
 struct TcMeta {
-  int64_t row_off[128];   // start of the row in A_out, -1 for rows past the end
+  int64_t row_off[128];   // start of the row in A_out (minus its first column), -1 past the end
+  int16_t row_lo[128];    // first column stored (the row index in the upper layout, else 0)
   int64_t row_boff[128];  // position of the row in b_out
-  int64_t row_eid[128];   // element id of the row
+  int32_t row_eid[128];   // element id of the row's element at its first row, else -1
   float row_down[128];    // exact scale back of the row's element
   int row_status[128];    // status of the row's element (nonzero: write zeros)
 };
@@ -455,7 +454,7 @@ struct TcAux {
 
 // Per-point coefficient record r (K 9, b 3, c, f) rounded to FP32; returns
 // whether all 14 values are finite (tested on the FP64 bits).
-__device__ __forceinline__ bool load_coef_tc(const FwdArgs &a, int64_t r, float *cf) {
+__device__ __forceinline__ bool load_coef_tc(const FwdArgs &a, int64_t r, float *cf, bool *sym = nullptr) {
   double cd[14];
 #pragma unroll
   for (int k = 0; k < 9; ++k) cd[k] = a.K[9 * r + k];
@@ -469,6 +468,7 @@ __device__ __forceinline__ bool load_coef_tc(const FwdArgs &a, int64_t r, float 
     ok &= finite64(cd[k]);
     cf[k] = (float)cd[k];
   }
+  if (sym) *sym = coef_symmetric(cd, cd + 9);
   return ok;
 }
 
@@ -684,13 +684,22 @@ __global__ void __launch_bounds__(TcCfg<P, V, KD>::NTHREADS, 1)
         // prefetched during the previous tile when this warp knew the element
         const double x = pf_k == kn0 + i ? pf_x : fetch_input(kn0 + i);
         const bool ok = __all_sync(0xffffffffu, finite64(x));
+        // upper layout: a symmetric K (K01 = K10, K02 = K20, K12 = K21: lanes
+        // 19/21, 20/24, 23/25) and b = 0 (lanes 27-29) in the element's record
+        bool sym = true;
+        if (a.upper && a.coef_mode == FEI_COEF_PER_ELEMENT) {
+          const int c = lane - 18;
+          const int partner = c == 1 ? 21 : c == 3 ? 19 : c == 2 ? 24 : c == 6 ? 20 : c == 5 ? 25 : c == 7 ? 23 : lane;
+          const double xp = __shfl_sync(0xffffffffu, x, partner);
+          sym = __all_sync(0xffffffffu, (c >= 9 && c <= 11) ? x == 0.0 : x == xp);
+        }
         if (lane >= 18 && a.coef_mode == FEI_COEF_PER_ELEMENT) E.cf[lane - 18] = (float)x;
         if (lane == 0) {
           E.e = e;
           E.aoff = out_a(a, kn0 + i, e, NSH);
           E.boff = out_b(a, kn0 + i, e, NSH);
           E.qoff = a.q_off ? a.q_off[e] : e * (int64_t)NQ;
-          E.status = ok ? 0 : FEI_ERR_NONFINITE;
+          E.status = ok ? (sym ? 0 : FEI_ERR_INVALID_ARG) : FEI_ERR_NONFINITE;
           E.mbits = 0;
         }
         // element vectors A1, B1, A2, B2, C, D1, D2 (FP64): lane j < 21 forms
@@ -799,7 +808,9 @@ __global__ void __launch_bounds__(TcCfg<P, V, KD>::NTHREADS, 1)
           // the bound reads the coefficient norms after the 16 values
           float cq[19];
           if (a.coef_mode == FEI_COEF_PER_POINT) {
-            if (!load_coef_tc(a, E.qoff + q, cq)) st = FEI_ERR_NONFINITE;
+            bool sym = true;
+            if (!load_coef_tc(a, E.qoff + q, cq, &sym)) st = FEI_ERR_NONFINITE;
+            else if (a.upper && !sym && st == 0) st = FEI_ERR_INVALID_ARG;
             coef_norms(cq, cq + 16);
           } else {
 #pragma unroll
@@ -869,13 +880,15 @@ __global__ void __launch_bounds__(TcCfg<P, V, KD>::NTHREADS, 1)
             const int64_t k = grow / NSH;
             const int ri = (int)(grow - k * NSH);
             const TcElem<P> &E = ax.el[slot_of(k)];
-            M.row_off[r] = E.aoff + (int64_t)ri * NSH;
+            M.row_off[r] = E.aoff + a_pos(ri, 0, NSH, a.upper);
+            M.row_lo[r] = (int16_t)(a.upper ? ri : 0);
             M.row_boff[r] = E.boff + ri;
-            M.row_eid[r] = ri == 0 ? E.e : -1;
+            M.row_eid[r] = ri == 0 ? (int32_t)E.e : -1;
             M.row_down[r] = E.down;
             M.row_status[r] = E.status;
           } else {
             M.row_off[r] = -1;
+            M.row_lo[r] = 0;
             M.row_boff[r] = -1;
             M.row_eid[r] = -1;
             M.row_down[r] = 0.f;
@@ -1286,7 +1299,7 @@ __global__ void __launch_bounds__(TcCfg<P, V, KD>::NTHREADS, 1)
     const int myrow = quarter * 32 + lane;
     // a contiguous output (uniform degree, no element list, 16-byte aligned):
     // the tile's rows of A_e are one range of A
-    const bool contiguous = a.A_off == nullptr && (a.list == nullptr || a.out_by_item) &&
+    const bool contiguous = a.A_off == nullptr && (a.list == nullptr || a.out_by_item) && !a.upper &&
                             (reinterpret_cast<uintptr_t>(a.A) & 15u) == 0u;
     float rreg[C::RREG > 0 ? C::RREG : 1];
     int it = 0;
@@ -1444,15 +1457,17 @@ __global__ void __launch_bounds__(TcCfg<P, V, KD>::NTHREADS, 1)
             for (int r16 = 0; r16 < 32; r16 += 16) {
               float vv[8];
               int64_t oo[8];
+              int lo[8];
   #pragma unroll
               for (int j = 0; j < 8; ++j) {
                 const int rr = r16 + 2 * j;
                 oo[j] = M.row_off[quarter * 32 + rr + half];
+                lo[j] = M.row_lo[quarter * 32 + rr + half];
                 vv[j] = stg[rr + half][lane & 15];
               }
   #pragma unroll
               for (int j = 0; j < 8; ++j)
-                if (oo[j] >= 0 && col < NSH) Aout[oo[j] + col] = vv[j];
+                if (oo[j] >= 0 && col < NSH && col >= lo[j]) Aout[oo[j] + col] = vv[j];
             }
             __syncwarp();
           }
@@ -1629,6 +1644,7 @@ __global__ void pair_table_kernel(const double *G, int nsh, int nq, int gst, int
 template <int P, int V, int KD>
 fei_status launch_tc(const fei_reference *ref, const FwdArgs &a, int64_t grid_work, cudaStream_t s) {
   using C = TcCfg<P, V, KD>;
+  static_assert(sizeof(TcAux<P, V, KD>) + C::DYN_SMEM <= 232448, "shared memory of one block (227 KB)");
   const TcImage *im = ref->tc;
   if (!im) return set_error(FEI_ERR_UNSUPPORTED, "no tensor-core image for degree %d", P);
   FEI_CUDA_TRY(cudaFuncSetAttribute(tc_forward_kernel<P, V, KD>, cudaFuncAttributeMaxDynamicSharedMemorySize,

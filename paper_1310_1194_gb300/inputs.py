@@ -18,6 +18,8 @@ Workloads (all seeded, numpy PCG64):
   certified valid (positive Jacobian determinant), p = 7.
 * ``p1m``   -- 100x100x50 grid (1 000 000 prisms), +-10% h, p = 1: the
   PR1 recipe at a size where the store-bound low-degree path is measurable.
+* ``p4sym`` -- the ``p4`` batch with b = 0: a symmetric weak form (K is
+  symmetric), whose element matrices can be stored as upper triangles.
 
 Coefficients per element: K = Q diag(lam) Q^T with Q from the QR factor of a
 3x3 standard normal matrix (sign-fixed) and lam ~ U[0.5, 2]; b ~ U[-1, 1]^3;
@@ -36,6 +38,7 @@ WORKLOADS = {
     "diff": dict(grid=(25, 20, 20), jitter=0.10, seed=4, p=5),
     "p7": dict(grid=(32, 32, 16), jitter=0.25, seed=5, p=7),
     "p1m": dict(grid=(100, 100, 50), jitter=0.10, seed=6, p=1),
+    "p4sym": dict(grid=(50, 50, 20), jitter=0.10, seed=2, p=4, symmetric=True),
 }
 
 
@@ -227,6 +230,8 @@ def workload(name: str, n_max: int | None = None) -> dict:
     else:
         degree = np.full(n, cfg["p"], dtype=np.int32)
     coef = None if name == "diff" else coefficients(n, cfg["seed"])
+    if coef is not None and cfg.get("symmetric"):
+        coef["b"] = np.zeros_like(coef["b"])
     if n_max is not None and n_max < n:
         geom = geom[:n_max]
         degree = degree[:n_max]

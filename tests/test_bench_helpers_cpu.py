@@ -112,3 +112,37 @@ def test_two_gloo_ranks_integrate_the_job(tmp_path, mode):
     np.testing.assert_array_equal(got["A"], A)
     np.testing.assert_array_equal(got["b"], bv)
     np.testing.assert_array_equal(got["st"], st)
+
+
+def test_errors_vs_oracle_upper_layout():
+    """A device result in the upper-triangle layout is mirrored back before
+    the comparison: the oracle's own symmetric matrices, packed, give zero
+    error; a change in one off-diagonal entry shows in its element only."""
+    bench = load_bench()
+    w = inputs.workload("p4sym", n_max=12)
+    ref = oracle.integrate(w["geom"], w["K"], w["b"], w["c"], w["f"], p=4)
+    Ao, bo, so, _ = ref
+    s = 75
+    iu = np.triu_indices(s)
+    packed = Ao.reshape(12, s, s)[:, iu[0], iu[1]].reshape(-1)
+    e = bench.errors_vs_oracle(torch.from_numpy(packed), torch.from_numpy(bo), torch.from_numpy(so), ref, 12,
+                               upper_p=4)
+    assert e["max"] < 1e-12, e
+    bad = packed.copy()
+    bad[5 * (s * (s + 1) // 2) + 3] += 1.0
+    e = bench.errors_vs_oracle(torch.from_numpy(bad), torch.from_numpy(bo), torch.from_numpy(so), ref, 12,
+                               upper_p=4)
+    assert e["max"] > 1e-3 and e["p99"] > 1e-3 and e["mean"] < e["max"]
+
+
+def test_unpack_upper_mirrors_the_triangle():
+    from paper_1310_1194_gb300 import api
+    rng = np.random.default_rng(0)
+    M = rng.standard_normal((3, 18, 18))
+    M = M + np.swapaxes(M, 1, 2)
+    iu = np.triu_indices(18)
+    packed = M[:, iu[0], iu[1]]
+    assert packed.shape[-1] == api.a_size(2, True) == 171
+    assert np.array_equal(api.unpack_upper(packed, 2), M)
+    t = api.unpack_upper(torch.from_numpy(packed), 2)
+    assert torch.equal(t, torch.from_numpy(M))
