@@ -81,7 +81,16 @@ typedef enum {
    * paper computes in single precision (Sec. 4); split bf16 is not offered:
    * bf16's 8 significant bits need three pieces and six products for the
    * same accuracy.  Degrees 1 and 2 fall back to FEI_FP32.  Output FP32. */
-  FEI_TC_3XTF32 = 3
+  FEI_TC_3XTF32 = 3,
+  /* Sum factorisation on the CUDA cores (degrees >= 3): the basis and the
+   * collapsed rule are tensor products in (u, v, zeta), so each component
+   * of the reference gradient is a sum of one or two products of 1D
+   * factors and the sum over points runs as three short sums, u then v
+   * then zeta, over the 21 pairs of gradient terms (about 7x fewer
+   * multiply-adds than the dense contraction at p = 7).  Geometry and
+   * point operator as FEI_FP32, the sums in FP32.  Degrees 1 and 2 fall
+   * back to FEI_FP32.  Output FP32. */
+  FEI_SF_FP32 = 4
 } fei_precision;
 
 typedef enum {

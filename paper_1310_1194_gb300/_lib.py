@@ -27,6 +27,7 @@ FEI_FP64 = 0
 FEI_FP32 = 1
 FEI_TC_F16X3 = 2
 FEI_TC_3XTF32 = 3
+FEI_SF_FP32 = 4
 
 FEI_COEF_PER_ELEMENT = 0
 FEI_COEF_PER_POINT = 1
@@ -34,7 +35,8 @@ FEI_COEF_PER_POINT = 1
 FEI_A_FULL = 0
 FEI_A_UPPER = 1
 
-PRECISIONS = {"fp64": FEI_FP64, "fp32": FEI_FP32, "tc_f16x3": FEI_TC_F16X3, "tc_3xtf32": FEI_TC_3XTF32}
+PRECISIONS = {"fp64": FEI_FP64, "fp32": FEI_FP32, "tc_f16x3": FEI_TC_F16X3, "tc_3xtf32": FEI_TC_3XTF32,
+              "sf_fp32": FEI_SF_FP32}
 
 FEI_NOALLOC_MAX_ELEM = 262144
 

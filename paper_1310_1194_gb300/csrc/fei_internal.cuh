@@ -11,6 +11,7 @@
 //   tnode double [(p+1)^2][4]    (xi1, xi2, w_tri, 0)  collapsed triangle nodes
 //   point q = iz * (p+1)^2 + t, t = iv * (p+1) + iu, w_q = w_tri[t] w_zeta[iz].
 //   tc    the tensor-core B operand images and paired tables (fei_tc.cu).
+//   sf    FP32 1D factor tables of the sum-factorised path (fei_sf.cu).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -41,6 +42,7 @@ struct fei_reference {
   double *tnode;
   float *G32T;       // [N_q][N_sh][4] the FP32 table with the 4 components adjacent
   fei::TcImage *tc;  // null until built (degree >= 3)
+  float *sf;         // 1D factor tables of the sum-factorised path (degree >= 3), or null
 };
 
 namespace fei {
@@ -148,8 +150,15 @@ fei_status launch_cc_backward(int p, bool fp64, const BwdArgs &a, int64_t grid_w
 // The tensor-core precisions (split fp16 or split TF32 operands).
 inline bool tc_precision(fei_precision prec) { return prec == FEI_TC_F16X3 || prec == FEI_TC_3XTF32; }
 inline bool valid_precision(fei_precision prec) {
-  return prec == FEI_FP64 || prec == FEI_FP32 || tc_precision(prec);
+  return prec == FEI_FP64 || prec == FEI_FP32 || tc_precision(prec) || prec == FEI_SF_FP32;
 }
+// The sum-factorised kernel runs degrees >= 3 (fei_sf.cu); lower degrees
+// of FEI_SF_FP32 run the FEI_FP32 kernels.
+inline bool sf_path(fei_precision prec, int p) { return prec == FEI_SF_FP32 && p >= 3; }
+fei_status launch_sf_forward(int p, const fei_reference *ref, const FwdArgs &a, int64_t grid_work, cudaStream_t s,
+                             int64_t grid_cap = 0);
+fei_status build_sf_tables(fei_reference *ref);
+void free_sf_tables(fei_reference *ref);
 // variant: 0 .. tc_variant_count(p, prec) - 1 (warp-role variants of one
 // kernel); prec: FEI_TC_F16X3 or FEI_TC_3XTF32
 fei_status launch_tc_forward(int p, const fei_reference *ref, const FwdArgs &a, int64_t grid_work,

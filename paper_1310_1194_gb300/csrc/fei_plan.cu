@@ -15,7 +15,9 @@
 // Candidates per degree (what fei_plan_tune times):
 //   tensor-core paths (p >= 3, FEI_TC_F16X3, FEI_TC_3XTF32): the warp-role variants of the
 //     tcgen05 kernel (8 or 16 producer warps), one CTA per SM;
-//   CUDA-core paths (FEI_FP64, FEI_FP32, and p <= 2 under the tensor-core precisions): the
+//   sum-factorised path (p >= 3, FEI_SF_FP32): as many blocks as fit on the
+//     SMs, or one per SM;
+//   CUDA-core paths (FEI_FP64, FEI_FP32, and p <= 2 under the other precisions): the
 //     grid of the grid-stride kernel, 2, 4, 8 or 16 blocks per SM.
 // Every candidate computes the same quantities; variants differ only in the
 // order of a few FP32 additions (load-vector partial sums), so results stay
@@ -56,13 +58,19 @@ bool same_batch(const fei_batch &x, const fei_batch &y) {
          x.a_layout == y.a_layout;
 }
 
-int n_candidates(fei_precision prec, int p) { return tc_path(prec, p) ? tc_variant_count(p, prec) : 4; }
+int n_candidates(fei_precision prec, int p) {
+  return tc_path(prec, p) ? tc_variant_count(p, prec) : sf_path(prec, p) ? 2 : 4;
+}
 
 // Candidate c of degree p as (variant, grid cap).
 void candidate(fei_precision prec, int p, int c, int *variant, int64_t *grid_cap) {
   if (tc_path(prec, p)) {
     *variant = c;
     *grid_cap = 0;
+  } else if (sf_path(prec, p)) {
+    // one element per block: as many blocks as fit, or one per SM
+    *variant = 0;
+    *grid_cap = c == 0 ? 0 : 152;
   } else {
     static const int per_sm[4] = {2, 4, 8, 16};
     *variant = 0;
@@ -102,8 +110,9 @@ fei_status launch_degree(const fei_plan *pl, int p, int variant, int64_t grid_ca
     a.count = pl->counts + p;
     a.list = pl->lists + (int64_t)(p - 1) * pl->max_elem;
   }
-  const fei_status ls = tc_path(pl->prec, p) ? launch_tc_forward(p, r, a, b->n_elem, s, variant, pl->prec)
-                                             : launch_cc_forward(p, pl->prec == FEI_FP64, a, b->n_elem, s, grid_cap);
+  const fei_status ls = tc_path(pl->prec, p)   ? launch_tc_forward(p, r, a, b->n_elem, s, variant, pl->prec)
+                        : sf_path(pl->prec, p) ? launch_sf_forward(p, r, a, b->n_elem, s, grid_cap)
+                                               : launch_cc_forward(p, pl->prec == FEI_FP64, a, b->n_elem, s, grid_cap);
   return ls ? ls : debug_check(s, "forward kernel");
 }
 

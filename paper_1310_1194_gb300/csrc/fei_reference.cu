@@ -230,6 +230,7 @@ extern "C" fei_status fei_reference_create(int p, fei_reference_t *out) {
   }
   if (p >= 3) {
     fei_status st = build_tc_image(r);
+    if (st == FEI_OK) st = build_sf_tables(r);
     if (st != FEI_OK) {
       fei_reference_destroy(r);
       return st;
@@ -242,6 +243,7 @@ extern "C" fei_status fei_reference_create(int p, fei_reference_t *out) {
 extern "C" fei_status fei_reference_destroy(fei_reference_t r) {
   if (!r) return FEI_OK;
   free_tc_image(r);
+  free_sf_tables(r);
   cudaFree(r->pts);
   cudaFree(r->G64);
   cudaFree(r->G32);

@@ -2,7 +2,8 @@
 
 Tolerances (relative Frobenius norm per element, max over the batch; load
 vectors by the 2-norm): FP64 path 1e-12, FP32 path 1e-5, split-precision
-tensor-core path 1e-6, gradients 1e-6 (FP32 contraction) / 1e-10 (FP64).
+tensor-core path 1e-6, sum-factorised FP32 path 1e-5, gradients 1e-6 (FP32
+contraction) / 1e-10 (FP64).
 """
 import numpy as np
 import pytest
@@ -14,7 +15,7 @@ from parity_util import assert_grads_close, worst_conditioned
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-12, "fp32": 1e-5, "tc_f16x3": 1e-6, "tc_3xtf32": 1e-6}
+TOL = {"fp64": 1e-12, "fp32": 1e-5, "tc_f16x3": 1e-6, "tc_3xtf32": 1e-6, "sf_fp32": 1e-5}
 # Gradients: element by element (relative Frobenius of the 18 vertex
 # gradients, and of an element's per-point coefficient gradients) at the
 # bars above, and record by record (one element's vertex gradients, one row
@@ -95,7 +96,7 @@ def test_reference_tables_match_oracle(api, p):
     assert np.max(np.abs(G.numpy() - Go)) < 1e-13 * scale
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32", "tc_f16x3", "tc_3xtf32"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "tc_f16x3", "tc_3xtf32", "sf_fp32"])
 @pytest.mark.parametrize("p", range(1, 8))
 def test_forward_uniform_degree(api, p, precision):
     w = workload_for(p, N_PER_P[p])
@@ -111,21 +112,21 @@ def test_pr1_full_fp64(api):
     assert ea.max() < 1e-12 and eb.max() < 1e-12
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32", "tc_f16x3", "tc_3xtf32"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "tc_f16x3", "tc_3xtf32", "sf_fp32"])
 def test_mixed_degree_batch(api, precision):
     w = inputs.workload("mixed", n_max=240)
     ea, eb = compare(api, w, None, precision, degree=w["degree"])
     assert ea.max() < TOL[precision] and eb.max() < TOL[precision]
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32", "tc_f16x3", "tc_3xtf32"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "tc_f16x3", "tc_3xtf32", "sf_fp32"])
 def test_per_point_coefficients(api, precision):
     w = inputs.workload("diff", n_max=6)
     ea, eb = compare(api, w, 5, precision, per_qp=True)
     assert ea.max() < TOL[precision] and eb.max() < TOL[precision]
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32", "tc_f16x3", "tc_3xtf32"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "tc_f16x3", "tc_3xtf32", "sf_fp32"])
 @pytest.mark.parametrize("p", [1, 4, 7])
 def test_status_flags_and_zero_outputs(api, p, precision):
     w = workload_for(p, 7)
@@ -428,3 +429,58 @@ def test_tc_wait_timeout_reports_status_and_context_survives(api):
     for j in range(len(idx)):
         ao = Ao[j * s * s:(j + 1) * s * s]
         assert np.linalg.norm(Ah[j] - ao) <= 1e-6 * np.linalg.norm(ao)
+
+
+@pytest.mark.parametrize("bprec", ["fp64", "fp32"])
+def test_p5_per_point_gradients_match_central_differences(api, bprec):
+    """The differentiation workload's configuration (p = 5, coefficients per
+    quadrature point): dL/dX and dL/d(K, b, c, f) of L = sum_e u_e^T A_e u_e
+    - u_e^T b_e from the library's adjoints (the quadratic-loss adjoint and
+    the general one through autograd) against central differences of the
+    FP64 GPU forward, per-point values held fixed."""
+    p, n = 5, 3
+    w = inputs.workload("diff", n_max=n)
+    s, q = api.nsh(p), api.nq(p)
+    u = np.random.default_rng(21).standard_normal(n * s)
+    ud = dev(u)
+    g = {k: dev(w[k]) for k in ("geom", "K", "b", "c", "f")}
+
+    def loss(x):
+        A, bv, st, _ = api.fei_integrate(x["geom"], x["K"], x["b"], x["c"], x["f"], p=p, per_qp=True,
+                                         precision="fp64")
+        assert not st.any()
+        Ae = A.view(n, s, s)
+        ue = ud.view(n, s)
+        return float((torch.einsum("ei,eij,ej->", ue, Ae, ue) - (ue * bv.view(n, s)).sum()).item())
+
+    quad = api.fei_integrate_backward_quadratic(g["geom"], g["K"], g["b"], g["c"], g["f"], ud, p=p, per_qp=True,
+                                                precision=bprec)
+    geom = g["geom"].clone().requires_grad_(True)
+    Kt = g["K"].clone().requires_grad_(True)
+    ct = g["c"].clone().requires_grad_(True)
+    A, bv, st = api.integrate(geom, Kt, g["b"], ct, g["f"], p=p, per_qp=True, precision=bprec)
+    L = torch.einsum("ei,eij,ej->", ud.view(n, s).to(A.dtype), A.view(n, s, s), ud.view(n, s).to(A.dtype)) - \
+        (ud.view(n, s).to(bv.dtype) * bv.view(n, s)).sum()
+    L.backward()
+    tol = 1e-6 if bprec == "fp64" else 1e-5
+    checks = [("geom", (0, 1, 2)), ("geom", (2, 4, 0)), ("geom", (1, 3, 1)), ("K", (17, 0, 1)), ("K", (q + 40, 2, 2)),
+              ("b", (2 * q + 7, 1)), ("c", (q + 100,)), ("f", (2 * q + 211,))]
+    names = ("geom", "K", "b", "c", "f")
+    for name, idx in checks:
+        # A_e and b_e are linear in K, b, c and f (the weak form of Sec. 2),
+        # so the central difference is exact there whatever the step: a
+        # unit one keeps the rounding of L (about 1e-16 |L| / h) far below
+        # the smallest gradient checked
+        h = 1e-6 if name == "geom" else 1.0
+        plus = {k: v.clone() for k, v in g.items()}
+        minus = {k: v.clone() for k, v in g.items()}
+        plus[name][idx] += h
+        minus[name][idx] -= h
+        fd = (loss(plus) - loss(minus)) / (2 * h)
+        got_q = float(quad[names.index(name)][idx])
+        scale = float(quad[names.index(name)].abs().max())
+        assert abs(got_q - fd) <= tol * max(abs(fd), 1e-2 * scale), ("quadratic", name, idx, got_q, fd)
+        auto = {"geom": geom, "K": Kt, "c": ct}.get(name)
+        if auto is not None:
+            got_a = float(auto.grad[idx])
+            assert abs(got_a - fd) <= tol * max(abs(fd), 1e-2 * scale), ("autograd", name, idx, got_a, fd)

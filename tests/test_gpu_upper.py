@@ -12,7 +12,7 @@ from paper_1310_1194_gb300 import inputs
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-12, "fp32": 1e-5, "tc_f16x3": 1e-6, "tc_3xtf32": 1e-6}
+TOL = {"fp64": 1e-12, "fp32": 1e-5, "tc_f16x3": 1e-6, "tc_3xtf32": 1e-6, "sf_fp32": 1e-5}
 
 
 @pytest.fixture(scope="module")
@@ -51,7 +51,7 @@ def run(api, w, p=None, degree=None, precision="fp64", per_qp=False, upper=False
     return A.cpu().numpy(), bv.cpu().numpy(), st.cpu().numpy(), lay
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32", "tc_f16x3", "tc_3xtf32"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "tc_f16x3", "tc_3xtf32", "sf_fp32"])
 @pytest.mark.parametrize("p", range(1, 8))
 def test_upper_uniform_matches_oracle_and_full_layout(api, p, precision):
     n = {1: 300, 2: 90, 3: 40, 4: 21, 5: 9, 6: 5, 7: 3}[p]
@@ -79,7 +79,7 @@ def test_upper_uniform_matches_oracle_and_full_layout(api, p, precision):
     assert np.array_equal(np.triu(full[0]), np.triu(Af.reshape(n, s, s)[0]))
 
 
-@pytest.mark.parametrize("precision", ["fp32", "tc_f16x3"])
+@pytest.mark.parametrize("precision", ["fp32", "tc_f16x3", "sf_fp32"])
 def test_upper_mixed_batch_plan_and_per_point(api, precision):
     w = symmetric(inputs.workload("mixed", n_max=120))
     deg = w["degree"]
@@ -110,7 +110,7 @@ def test_upper_mixed_batch_plan_and_per_point(api, precision):
     assert not su.any() and np.array_equal(Au.view(np.uint8), triu_flat(Af, 5).view(np.uint8))
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32", "tc_f16x3", "tc_3xtf32"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "tc_f16x3", "tc_3xtf32", "sf_fp32"])
 @pytest.mark.parametrize("p", [1, 4, 7])
 def test_upper_flags_records_that_are_not_symmetric(api, p, precision):
     w = symmetric(inputs.workload("p7" if p >= 6 else "pr1", n_max=6))
