@@ -70,6 +70,26 @@ def tc_hw_flops(p, precision="tc_f16x3"):
     return 3 * 2 * s * npad * kpad
 
 
+def sf_flops_per_element(p):
+    """Flops per element of the sum-factorised kernel (M = p+1 nodes per
+    direction, T = (p+1)(p+2)/2 triangle functions, 21 pairs of gradient
+    terms, 4 pairs of zeta factors): per pair the u sum M^3 (M + 2 M^2) and
+    the v sum T^2 M (1 + 2 M), the zeta sum 4 T^2 M (M + 2 M^2), the load
+    vector 2 (M^4 + M^2 T + N_sh M) and the geometry 220 N_q."""
+    M, T = p + 1, (p + 1) * (p + 2) // 2
+    TT = T * T
+    pairs = 21 * (M ** 3 * (M + 2 * M * M) + TT * M * (1 + 2 * M))
+    return pairs + 4 * TT * M * (M + 2 * M * M) + 2 * (M ** 4 + M * M * T + nsh(p) * M) + 220 * nq(p)
+
+
+def kernel_flops(counts, precision):
+    """Flops one step's kernels do for the per-degree counts: the sum-
+    factorised kernel's own count at p >= 3 under sf_fp32, the dense
+    contraction's count otherwise."""
+    return sum(int(counts[d]) * (sf_flops_per_element(d) if (precision == "sf_fp32" and d >= 3)
+                                 else flops_per_element(d)) for d in range(1, 8))
+
+
 def bwd_flops_per_element(p):
     """Algorithmic flops of the adjoint per element: W = gA G^T (8 N_sh^2
     N_q), dL/dDt = G_q W_q (32 N_sh N_q), the load-vector adjoint (2 N_sh
@@ -365,6 +385,15 @@ def roofline_of(dom, counts, precision, peaks, peak_src, live, Bts, ms_all, p, n
         hw = {"tensor_tflops": hwF / (ms * 1e-3) / 1e12,
               "frac_of_tensor_peak": hwF / (ms * 1e-3) / 1e12 / tpeak,
               "note": "issued tcgen05 flops: 3 products x 2 x 128-row tiles x N_pad x 4 N_q"}
+    elif precision == "sf_fp32":
+        # the sum-factorised kernel does its own, smaller flop count on the
+        # FP32 FMA pipe; the dense contraction's count over the same time is
+        # reported beside it as the equivalent rate
+        Fk = kernel_flops(counts, precision)
+        bound, peak, unit, achieved = "alu", f32_peak, "TFLOP/s", Fk / (ms * 1e-3) / 1e12
+        peak_note = f32_note + " (sum-factorised flop count)"
+        hw = {"dense_equivalent_tflops": F / (ms * 1e-3) / 1e12,
+              "note": "dense contraction flops (8 N_sh^2 N_q + ...) over the same time"}
     elif precision == "fp32":
         bound, peak, unit, achieved = "alu", f32_peak, "TFLOP/s", F / (ms * 1e-3) / 1e12
         peak_note = f32_note
@@ -422,7 +451,10 @@ def run_workload(name, args, ctx, headline):
 
     precision = args.precision if headline else None
     if precision is None:
-        precision = "tc_f16x3" if (p is None or p >= 3) else "fp32"
+        # the fastest path within 1e-6 of the oracle: the FP32 kernels at
+        # p <= 2, the split tensor-core kernel at p = 3..5, the sum-factorised
+        # kernel at p = 6, 7, and per degree the tuner's pick for a mixed batch
+        precision = "auto" if p is None else "fp32" if p <= 2 else "tc_f16x3" if p <= 5 else "sf_fp32"
     layout = api.fei_plan_offsets(deg, upper) if deg is not None else api.uniform_layout(n, p, upper)
     refs = [api.fei_reference_create(d) for d in ([p] if p is not None else range(1, 8))]
     out_dtype = torch.float64 if precision == "fp64" else torch.float32
@@ -526,21 +558,25 @@ def run_workload(name, args, ctx, headline):
         d_star = max(per_deg, key=per_deg.get)
         c1 = np.zeros(8, dtype=np.int64)
         c1[d_star] = counts[d_star]
+        kernel_prec = {"cuda_core": "fp64" if precision == "fp64" else "fp32",
+                       "tensor_core": "tc_3xtf32" if precision == "tc_3xtf32" else "tc_f16x3",
+                       "sum_factorised": "sf_fp32"}
+        prec_of = {d: kernel_prec[plan.kernel(d)] for d in per_deg}
         dom = {"kernel": f"forward, p={d_star} bucket", "ms": per_deg[d_star],
-               "F": int(counts[d_star]) * flops_per_element(d_star),
-               "precision": precision if (precision != "tc_f16x3" or d_star >= 3) else "fp32", "counts": c1}
+               "F": int(counts[d_star]) * flops_per_element(d_star), "precision": prec_of[d_star], "counts": c1}
         # every bucket against its own roofline (its tuned time, CUDA events)
         plan_buckets = {}
         for d, tms in per_deg.items():
             cd = np.zeros(8, dtype=np.int64)
             cd[d] = counts[d]
-            prec_d = precision if (precision != "tc_f16x3" or d >= 3) else "fp32"
+            prec_d = prec_of[d]
             dd = {"kernel": "forward", "ms": tms, "F": int(counts[d]) * flops_per_element(d), "precision": prec_d,
                   "counts": cd}
             Bd = int(counts[d]) * bytes_per_element(d, out_b, per_qp, upper)
             rd = roofline_of(dd, cd, prec_d, peaks, peak_src, live, Bd, tms, d, int(counts[d]), per_qp)
-            plan_buckets[f"p{d}"] = {"elements": int(counts[d]), "ms": tms, "bound": rd["bound"],
-                                     "achieved": rd["achieved"], "peak": rd["peak"], "frac": rd["frac"]}
+            plan_buckets[f"p{d}"] = {"elements": int(counts[d]), "ms": tms, "kernel": plan.kernel(d),
+                                     "precision": prec_d, "bound": rd["bound"], "achieved": rd["achieved"],
+                                     "peak": rd["peak"], "frac": rd["frac"]}
     elif grads is not None:
         bwd_ms = statistics.median([mids[k].elapsed_time(evs[k][1]) for k in range(steps)])
         fwd_ms = statistics.median([evs[k][0].elapsed_time(mids[k]) for k in range(steps)])
@@ -553,7 +589,7 @@ def run_workload(name, args, ctx, headline):
         else:
             dom = {"kernel": "forward", "ms": fwd_ms, "F": F, "precision": precision, "counts": counts,
                    "adjoint_ms": bwd_ms}
-    roofline = roofline_of(dom, counts, precision, peaks, peak_src, live, Bts, ms, p, n, per_qp)
+    roofline = roofline_of(dom, dom["counts"], dom["precision"], peaks, peak_src, live, Bts, ms, p, n, per_qp)
 
     # the plain FP64 GPU path on the same batch (the comparison the metric
     # asks for), its error against the oracle, and for the headline the
@@ -601,13 +637,18 @@ def run_workload(name, args, ctx, headline):
                 fp32_path["rel_err_vs_oracle"] = errors_vs_oracle(A32, b32, st32, ref, n_s, p if upper else None)
             del A32, b32, st32
 
-    # the other split of the tensor-core contraction on the same batch (the
-    # trade-off between fp16 and TF32 operands: time and error), for the
-    # headline and the p = 7 workload
-    alt_tc = None
-    if (rank == 0 and precision in ("tc_f16x3", "tc_3xtf32") and p is not None and p >= 3 and grads is None
-            and (headline or name == "p7")):
-        alt = "tc_3xtf32" if precision == "tc_f16x3" else "tc_f16x3"
+    # the other paths on the same batch (time, roofline and error): the
+    # other split of the tensor-core contraction for the headline (fp16 or
+    # TF32 operands), and both splits for the p = 7 workload, where the
+    # sum-factorised kernel is the timed path
+    alts = []
+    if rank == 0 and p is not None and p >= 3 and grads is None:
+        if headline and precision in ("tc_f16x3", "tc_3xtf32"):
+            alts = ["tc_3xtf32" if precision == "tc_f16x3" else "tc_f16x3"]
+        elif name == "p7":
+            alts = [x for x in ("tc_f16x3", "tc_3xtf32", "sf_fp32") if x != precision]
+    other = {}
+    for alt in alts:
         Aa = torch.empty(layout.A_total, dtype=torch.float32, device=dev)
         ba = torch.empty(layout.b_total, dtype=torch.float32, device=dev)
         sa = torch.empty(n, dtype=torch.int32, device=dev)
@@ -624,11 +665,12 @@ def run_workload(name, args, ctx, headline):
             ta.append(e0.elapsed_time(e1))
         ma = statistics.median(ta)
         da = {"kernel": "forward", "ms": ma, "F": F, "precision": alt, "counts": counts}
-        alt_tc = {"precision": alt, "elements_per_s": n / (ma * 1e-3), "ms_per_step": ma,
-                  "roofline": roofline_of(da, counts, alt, peaks, peak_src, live, Bts, ma, p, n, per_qp)}
+        other[alt] = {"precision": alt, "elements_per_s": n / (ma * 1e-3), "ms_per_step": ma,
+                      "roofline": roofline_of(da, counts, alt, peaks, peak_src, live, Bts, ma, p, n, per_qp)}
         if ref is not None:
-            alt_tc["rel_err_vs_oracle"] = errors_vs_oracle(Aa, ba, sa, ref, n_s, p if upper else None)
+            other[alt]["rel_err_vs_oracle"] = errors_vs_oracle(Aa, ba, sa, ref, n_s, p if upper else None)
         del Aa, ba, sa
+    alt_tc = other.get("tc_3xtf32" if precision == "tc_f16x3" else "tc_f16x3") if headline else None
 
     # end to end through the public API with host buffers
     e2e = None
@@ -652,6 +694,8 @@ def run_workload(name, args, ctx, headline):
         res["fp32_path"] = fp32_path
     if alt_tc is not None:
         res["other_tc_split"] = alt_tc
+    if other and not headline:
+        res["other_paths"] = other
     if plan_choices is not None:
         res["plan"] = plan_choices
         res["plan_buckets"] = plan_buckets
@@ -922,7 +966,8 @@ def main():
             "metric": metric_name(args), "value": head["elements_per_s"], "unit": "elements/s", "n_gpus": world,
             "steps": head["steps"], "warmup": max(3, args.warmup), "ms_per_step": head["ms_per_step"],
             "higher_is_better": True, "scaling": args.scaling, "vs_baseline": None,
-            "dtype": {"fp64": "f64", "fp32": "f32", "tc_f16x3": "f16x3->f32", "tc_3xtf32": "tf32x3->f32"}[precision],
+            "dtype": {"fp64": "f64", "fp32": "f32", "tc_f16x3": "f16x3->f32", "tc_3xtf32": "tf32x3->f32",
+                      "sf_fp32": "f32", "auto": "f32 (per degree: f32, f16x3->f32 or sum-factorised f32)"}[precision],
             "data": "synthetic",
             "config": {"workload": head["workload"], "precision": precision, "elements": head["elements"],
                        "l2": "256 MB buffer written between timed steps (outside the events); "

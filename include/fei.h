@@ -90,7 +90,14 @@ typedef enum {
    * multiply-adds than the dense contraction at p = 7).  Geometry and
    * point operator as FEI_FP32, the sums in FP32.  Degrees 1 and 2 fall
    * back to FEI_FP32.  Output FP32. */
-  FEI_SF_FP32 = 4
+  FEI_SF_FP32 = 4,
+  /* Per degree, the fastest kernel among those measured within 1e-6 of
+   * the FP64 oracle (relative Frobenius norm per element): the FEI_FP32
+   * kernels for p <= 2, the FEI_TC_F16X3 kernel for p = 3..5 and the
+   * sum-factorised kernel for p = 6, 7 on a direct call; a plan's tuner
+   * times the tensor-core variants and the sum-factorised kernel at every
+   * p >= 3 and keeps the fastest.  Output FP32. */
+  FEI_AUTO = 5
 } fei_precision;
 
 typedef enum {
@@ -284,24 +291,33 @@ fei_status fei_plan_execute(fei_plan_t plan, const fei_batch *batch, void *A_out
  * `batch` on that degree's elements (writing the same outputs a normal call
  * writes), times each with CUDA events (best of two after one warm-up run)
  * and keeps the fastest per degree.  Candidates: the tensor-core kernel's
- * warp-role variants (p >= 3 under FEI_TC_F16X3), or 2/4/8/16 blocks per
+ * warp-role variants (p >= 3 under the tensor-core precisions), the
+ * sum-factorised kernel with as many blocks as fit or one per SM (p >= 3
+ * under FEI_SF_FP32), both of these under FEI_AUTO, or 2/4/8/16 blocks per
  * SM for the CUDA-core kernels.  Synchronous (waits for the stream). */
 fei_status fei_plan_tune(fei_plan_t plan, const fei_batch *batch, void *A_out,
                          void *b_out, int32_t *elem_status, fei_stream_t stream);
 
 /* The plan's choice for degree p (host pointers, any may be NULL):
  * variant index, grid cap in blocks (0 = the kernel's default) and the
- * time fei_plan_tune measured for that degree (ms, -1 if not tuned). */
+ * time fei_plan_tune measured for that degree (ms, -1 if not tuned).
+ * Variants of degree p >= 3: the tensor-core kernel's warp-role variants
+ * 0 .. count - 1 (count: 2 or more, fixed per degree and precision); under
+ * FEI_AUTO the variant equal to that count is the sum-factorised kernel. */
 fei_status fei_plan_choice(fei_plan_t plan, int p, int *variant, int64_t *grid_cap,
                            float *tuned_ms);
 
 /* Sets the choice for degree p, e.g. one that fei_plan_tune measured in an
  * earlier process on the same GPU model (the tuning cache persisted by the
- * caller).  variant: a warp-role variant of the tensor-core kernel (0 ..
- * count - 1 under FEI_TC_F16X3 at p >= 3, else 0); grid_cap: blocks, 0 =
- * the kernel's default.  The plan's graph is recaptured on the next
+ * caller).  variant: as fei_plan_choice reports it (0 where a degree has a
+ * single kernel); grid_cap: blocks, 0 = the kernel's default.  The plan's graph is recaptured on the next
  * fei_plan_execute.  Errors: INVALID_ARG, INVALID_DEGREE. */
 fei_status fei_plan_set_choice(fei_plan_t plan, int p, int variant, int64_t grid_cap);
+
+/* The kernel the plan's current choice runs for degree p (host pointer):
+ * 0 the CUDA-core kernels, 1 the tensor-core kernel, 2 the sum-factorised
+ * kernel.  Errors: INVALID_ARG (NULL plan or kernel), INVALID_DEGREE. */
+fei_status fei_plan_kernel(fei_plan_t plan, int p, int *kernel);
 
 /* Batch-level summary of the per-element statuses (device int32
  * [n_elem], as written by fei_integrate): summary (device int32 [2])

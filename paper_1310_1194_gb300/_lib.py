@@ -28,6 +28,7 @@ FEI_FP32 = 1
 FEI_TC_F16X3 = 2
 FEI_TC_3XTF32 = 3
 FEI_SF_FP32 = 4
+FEI_AUTO = 5
 
 FEI_COEF_PER_ELEMENT = 0
 FEI_COEF_PER_POINT = 1
@@ -36,7 +37,9 @@ FEI_A_FULL = 0
 FEI_A_UPPER = 1
 
 PRECISIONS = {"fp64": FEI_FP64, "fp32": FEI_FP32, "tc_f16x3": FEI_TC_F16X3, "tc_3xtf32": FEI_TC_3XTF32,
-              "sf_fp32": FEI_SF_FP32}
+              "sf_fp32": FEI_SF_FP32, "auto": FEI_AUTO}
+# fei_plan_kernel
+KERNELS = {0: "cuda_core", 1: "tensor_core", 2: "sum_factorised"}
 
 FEI_NOALLOC_MAX_ELEM = 262144
 
@@ -110,6 +113,7 @@ def _load():
                                            vp, vp, vp, vp]
     lib.fei_debug_set_wait_limit.argtypes = [ctypes.c_uint64]
     lib.fei_plan_set_choice.argtypes = [vp, ctypes.c_int, ctypes.c_int, i64]
+    lib.fei_plan_kernel.argtypes = [vp, ctypes.c_int, ctypes.POINTER(i32)]
     lib.fei_pipeline_create.argtypes = [ref_p, ctypes.c_int, ctypes.c_int, i64, ref_p]
     lib.fei_pipeline_destroy.argtypes = [vp]
     lib.fei_pipeline_info.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]
@@ -123,6 +127,7 @@ def _load():
                  "fei_plan_execute", "fei_plan_tune", "fei_plan_choice", "fei_status_summary", "fei_sync_status",
                  "fei_assembly_create", "fei_assembly_destroy", "fei_assembly_info", "fei_assembly_pattern",
                  "fei_assemble", "fei_integrate_assemble", "fei_debug_set_wait_limit", "fei_plan_set_choice",
+                 "fei_plan_kernel",
                  "fei_pipeline_create", "fei_pipeline_destroy", "fei_pipeline_info", "fei_integrate_host"):
         getattr(lib, name).restype = i32
     return lib

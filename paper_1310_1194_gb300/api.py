@@ -347,6 +347,13 @@ class Plan:
               "fei_plan_choice")
         return v.value, g.value, t.value
 
+    def kernel(self, p: int) -> str:
+        """The kernel the current choice runs for degree p: "cuda_core",
+        "tensor_core" or "sum_factorised"."""
+        k = ctypes.c_int32()
+        check(lib.fei_plan_kernel(self.handle, int(p), ctypes.byref(k)), "fei_plan_kernel")
+        return _lib.KERNELS[k.value]
+
     def set_choice(self, p: int, variant: int, grid_cap: int):
         check(lib.fei_plan_set_choice(self.handle, int(p), int(variant), int(grid_cap)), "fei_plan_set_choice")
 

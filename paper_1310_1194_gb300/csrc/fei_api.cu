@@ -209,9 +209,11 @@ void fill_fwd(FwdArgs &a, const fei_batch *b, const fei_reference *r, void *A, v
 
 fei_status launch_forward(int p, fei_precision prec, const fei_reference *r, const FwdArgs &a,
                           int64_t grid_work, cudaStream_t s) {
-  const fei_status st = (tc_precision(prec) && p >= 3) ? launch_tc_forward(p, r, a, grid_work, s, 0, prec)
-                        : sf_path(prec, p)                ? launch_sf_forward(p, r, a, grid_work, s)
-                                                        : launch_cc_forward(p, prec == FEI_FP64, a, grid_work, s);
+  fei_precision run;
+  const KernelKind k = direct_kernel(prec, p, &run);
+  const fei_status st = k == KERNEL_TC   ? launch_tc_forward(p, r, a, grid_work, s, 0, run)
+                        : k == KERNEL_SF ? launch_sf_forward(p, r, a, grid_work, s)
+                                         : launch_cc_forward(p, run == FEI_FP64, a, grid_work, s);
   return st ? st : debug_check(s, "forward kernel");
 }
 

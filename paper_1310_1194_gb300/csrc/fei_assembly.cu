@@ -412,7 +412,7 @@ fei_status build(fei_assembly *as, const int64_t *l2g) {
 
 fei_status value_type(fei_precision prec, size_t *bytes) {
   if (prec == FEI_FP64) *bytes = 8;
-  else if (prec == FEI_FP32 || tc_precision(prec) || prec == FEI_SF_FP32) *bytes = 4;
+  else if (valid_precision(prec)) *bytes = 4;
   else return set_error(FEI_ERR_INVALID_ARG, "precision %d", (int)prec);
   return FEI_OK;
 }

@@ -150,11 +150,22 @@ fei_status launch_cc_backward(int p, bool fp64, const BwdArgs &a, int64_t grid_w
 // The tensor-core precisions (split fp16 or split TF32 operands).
 inline bool tc_precision(fei_precision prec) { return prec == FEI_TC_F16X3 || prec == FEI_TC_3XTF32; }
 inline bool valid_precision(fei_precision prec) {
-  return prec == FEI_FP64 || prec == FEI_FP32 || tc_precision(prec) || prec == FEI_SF_FP32;
+  return prec == FEI_FP64 || prec == FEI_FP32 || tc_precision(prec) || prec == FEI_SF_FP32 || prec == FEI_AUTO;
 }
-// The sum-factorised kernel runs degrees >= 3 (fei_sf.cu); lower degrees
-// of FEI_SF_FP32 run the FEI_FP32 kernels.
-inline bool sf_path(fei_precision prec, int p) { return prec == FEI_SF_FP32 && p >= 3; }
+// The kernels of the forward: CUDA-core (fei_cc.cu), tensor-core
+// (fei_tc.cu) and sum-factorised (fei_sf.cu).  The tensor-core and
+// sum-factorised kernels run degrees >= 3; lower degrees of those
+// precisions run the FEI_FP32 CUDA-core kernels.
+enum KernelKind { KERNEL_CC = 0, KERNEL_TC = 1, KERNEL_SF = 2 };
+// The kernel of degree p under prec on a direct call, and the precision it
+// runs in (FEI_AUTO resolved per degree).
+inline KernelKind direct_kernel(fei_precision prec, int p, fei_precision *run) {
+  if (prec == FEI_AUTO) prec = p <= 2 ? FEI_FP32 : p <= 5 ? FEI_TC_F16X3 : FEI_SF_FP32;
+  *run = prec;
+  if (p >= 3 && tc_precision(prec)) return KERNEL_TC;
+  if (p >= 3 && prec == FEI_SF_FP32) return KERNEL_SF;
+  return KERNEL_CC;
+}
 fei_status launch_sf_forward(int p, const fei_reference *ref, const FwdArgs &a, int64_t grid_work, cudaStream_t s,
                              int64_t grid_cap = 0);
 fei_status build_sf_tables(fei_reference *ref);

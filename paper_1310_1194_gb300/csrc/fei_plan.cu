@@ -17,6 +17,8 @@
 //     tcgen05 kernel (8 or 16 producer warps), one CTA per SM;
 //   sum-factorised path (p >= 3, FEI_SF_FP32): as many blocks as fit on the
 //     SMs, or one per SM;
+//   FEI_AUTO at p >= 3: both of the above (FEI_TC_F16X3 variants and the
+//     sum-factorised kernel), so the fastest kernel within the 1e-6 bar wins;
 //   CUDA-core paths (FEI_FP64, FEI_FP32, and p <= 2 under the other precisions): the
 //     grid of the grid-stride kernel, 2, 4, 8 or 16 blocks per SM.
 // Every candidate computes the same quantities; variants differ only in the
@@ -48,7 +50,25 @@ struct fei_plan {
 namespace fei {
 namespace {
 
-bool tc_path(fei_precision prec, int p) { return tc_precision(prec) && p >= 3; }
+// The kernel of degree p for a plan's variant number, and its precision.
+// Variants: the tensor-core warp-role variants 0 .. tc_variant_count - 1;
+// under FEI_AUTO at p >= 3 one more, the sum-factorised kernel; else 0.
+KernelKind plan_kernel(fei_precision prec, int p, int variant, fei_precision *run) {
+  if (prec == FEI_AUTO && p >= 3) {
+    *run = variant < tc_variant_count(p, FEI_TC_F16X3) ? FEI_TC_F16X3 : FEI_SF_FP32;
+    return *run == FEI_TC_F16X3 ? KERNEL_TC : KERNEL_SF;
+  }
+  return direct_kernel(prec, p, run);
+}
+int n_variants(fei_precision prec, int p) {
+  fei_precision run;
+  if (prec == FEI_AUTO && p >= 3) return tc_variant_count(p, FEI_TC_F16X3) + 1;
+  return direct_kernel(prec, p, &run) == KERNEL_TC ? tc_variant_count(p, run) : 1;
+}
+// The variant a plan starts from (before any tuning).
+int default_variant(fei_precision prec, int p) {
+  return (prec == FEI_AUTO && p >= 6) ? tc_variant_count(p, FEI_TC_F16X3) : 0;
+}
 
 // The batch a graph was captured for, field by field (not the padding).
 bool same_batch(const fei_batch &x, const fei_batch &y) {
@@ -58,19 +78,27 @@ bool same_batch(const fei_batch &x, const fei_batch &y) {
          x.a_layout == y.a_layout;
 }
 
+// Candidates of degree p: every tensor-core variant (grid: one CTA per
+// SM), the sum-factorised kernel with as many blocks as fit or one per SM,
+// the CUDA-core kernels with 2, 4, 8 or 16 blocks per SM.
 int n_candidates(fei_precision prec, int p) {
-  return tc_path(prec, p) ? tc_variant_count(p, prec) : sf_path(prec, p) ? 2 : 4;
+  fei_precision run;
+  const KernelKind k = plan_kernel(prec, p, 0, &run);
+  if (prec == FEI_AUTO && p >= 3) return tc_variant_count(p, FEI_TC_F16X3) + 2;
+  return k == KERNEL_TC ? tc_variant_count(p, run) : k == KERNEL_SF ? 2 : 4;
 }
 
 // Candidate c of degree p as (variant, grid cap).
 void candidate(fei_precision prec, int p, int c, int *variant, int64_t *grid_cap) {
-  if (tc_path(prec, p)) {
+  fei_precision run;
+  const int ntc = (prec == FEI_AUTO && p >= 3) ? tc_variant_count(p, FEI_TC_F16X3) : 0;
+  const KernelKind k = plan_kernel(prec, p, c, &run);
+  if (k == KERNEL_TC) {
     *variant = c;
     *grid_cap = 0;
-  } else if (sf_path(prec, p)) {
-    // one element per block: as many blocks as fit, or one per SM
-    *variant = 0;
-    *grid_cap = c == 0 ? 0 : 152;
+  } else if (k == KERNEL_SF) {
+    *variant = ntc;
+    *grid_cap = c == ntc ? 0 : 152;
   } else {
     static const int per_sm[4] = {2, 4, 8, 16};
     *variant = 0;
@@ -110,9 +138,11 @@ fei_status launch_degree(const fei_plan *pl, int p, int variant, int64_t grid_ca
     a.count = pl->counts + p;
     a.list = pl->lists + (int64_t)(p - 1) * pl->max_elem;
   }
-  const fei_status ls = tc_path(pl->prec, p)   ? launch_tc_forward(p, r, a, b->n_elem, s, variant, pl->prec)
-                        : sf_path(pl->prec, p) ? launch_sf_forward(p, r, a, b->n_elem, s, grid_cap)
-                                               : launch_cc_forward(p, pl->prec == FEI_FP64, a, b->n_elem, s, grid_cap);
+  fei_precision run;
+  const KernelKind k = plan_kernel(pl->prec, p, variant, &run);
+  const fei_status ls = k == KERNEL_TC   ? launch_tc_forward(p, r, a, b->n_elem, s, variant, run)
+                        : k == KERNEL_SF ? launch_sf_forward(p, r, a, b->n_elem, s, grid_cap)
+                                         : launch_cc_forward(p, run == FEI_FP64, a, b->n_elem, s, grid_cap);
   return ls ? ls : debug_check(s, "forward kernel");
 }
 
@@ -218,7 +248,7 @@ extern "C" fei_status fei_plan_create(const fei_reference_t *refs, int nrefs, in
     pl->avail |= 1u << refs[k]->p;
   }
   for (int p = 1; p <= kPMax; ++p) {
-    pl->variant[p] = 0;
+    pl->variant[p] = pl->by_p[p] ? default_variant(prec, p) : 0;
     pl->grid_cap[p] = 0;
     pl->tuned_ms[p] = -1.f;
   }
@@ -359,10 +389,18 @@ extern "C" fei_status fei_plan_choice(fei_plan_t plan, int p, int *variant, int6
   return FEI_OK;
 }
 
+extern "C" fei_status fei_plan_kernel(fei_plan_t plan, int p, int *kernel) {
+  if (!plan || !kernel) return set_error(FEI_ERR_INVALID_ARG, "fei_plan_kernel: NULL plan or kernel");
+  if (p < 1 || p > kPMax) return set_error(FEI_ERR_INVALID_DEGREE, "fei_plan_kernel: degree %d", p);
+  fei_precision run;
+  *kernel = (int)plan_kernel(plan->prec, p, plan->variant[p], &run);
+  return FEI_OK;
+}
+
 extern "C" fei_status fei_plan_set_choice(fei_plan_t plan, int p, int variant, int64_t grid_cap) {
   if (!plan) return set_error(FEI_ERR_INVALID_ARG, "fei_plan_set_choice: plan is NULL");
   if (p < 1 || p > kPMax) return set_error(FEI_ERR_INVALID_DEGREE, "fei_plan_set_choice: degree %d", p);
-  const int nv = tc_path(plan->prec, p) ? tc_variant_count(p, plan->prec) : 1;
+  const int nv = n_variants(plan->prec, p);
   if (variant < 0 || variant >= nv)
     return set_error(FEI_ERR_INVALID_ARG, "fei_plan_set_choice: variant %d for degree %d", variant, p);
   if (grid_cap < 0 || grid_cap > 2147483647LL)

@@ -68,6 +68,8 @@ def test_argument_errors_before_any_cuda_call(lib):
     assert lib.fei_plan_choice(None, 3, None, None, None) == 1
     lib.fei_plan_set_choice.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int64]
     assert lib.fei_plan_set_choice(None, 3, 0, 0) == 1
+    lib.fei_plan_kernel.argtypes = [vp, ctypes.c_int, vp]
+    assert lib.fei_plan_kernel(None, 3, None) == 1
     lib.fei_pipeline_create.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int64, vp]
     out = vp()
     assert lib.fei_pipeline_create(None, 1, 0, 0, ctypes.byref(out)) == 1 and out.value is None

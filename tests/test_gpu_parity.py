@@ -445,13 +445,19 @@ def test_p5_per_point_gradients_match_central_differences(api, bprec):
     ud = dev(u)
     g = {k: dev(w[k]) for k in ("geom", "K", "b", "c", "f")}
 
-    def loss(x):
+    def outputs(x):
         A, bv, st, _ = api.fei_integrate(x["geom"], x["K"], x["b"], x["c"], x["f"], p=p, per_qp=True,
                                          precision="fp64")
         assert not st.any()
-        Ae = A.view(n, s, s)
+        return A.view(n, s, s), bv.view(n, s)
+
+    def loss_difference(plus, minus):
+        # L(plus) - L(minus) from the differences of the outputs: entries the
+        # step does not touch cancel exactly, so the rounding of L itself
+        # (about 1e-16 |L|) does not enter
+        (Ap, bp), (Am, bm) = outputs(plus), outputs(minus)
         ue = ud.view(n, s)
-        return float((torch.einsum("ei,eij,ej->", ue, Ae, ue) - (ue * bv.view(n, s)).sum()).item())
+        return float((torch.einsum("ei,eij,ej->", ue, Ap - Am, ue) - (ue * (bp - bm)).sum()).item())
 
     quad = api.fei_integrate_backward_quadratic(g["geom"], g["K"], g["b"], g["c"], g["f"], ud, p=p, per_qp=True,
                                                 precision=bprec)
@@ -469,14 +475,13 @@ def test_p5_per_point_gradients_match_central_differences(api, bprec):
     for name, idx in checks:
         # A_e and b_e are linear in K, b, c and f (the weak form of Sec. 2),
         # so the central difference is exact there whatever the step: a
-        # unit one keeps the rounding of L (about 1e-16 |L| / h) far below
-        # the smallest gradient checked
+        # unit one keeps the rounding of the outputs small against the step
         h = 1e-6 if name == "geom" else 1.0
         plus = {k: v.clone() for k, v in g.items()}
         minus = {k: v.clone() for k, v in g.items()}
         plus[name][idx] += h
         minus[name][idx] -= h
-        fd = (loss(plus) - loss(minus)) / (2 * h)
+        fd = loss_difference(plus, minus) / (2 * h)
         got_q = float(quad[names.index(name)][idx])
         scale = float(quad[names.index(name)].abs().max())
         assert abs(got_q - fd) <= tol * max(abs(fd), 1e-2 * scale), ("quadratic", name, idx, got_q, fd)

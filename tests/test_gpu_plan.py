@@ -24,7 +24,8 @@ def _mixed(n, seed_name="mixed"):
     return w, g, deg
 
 
-@pytest.mark.parametrize("precision,tol", [("tc_f16x3", 1e-6), ("fp32", 1e-5), ("fp64", 1e-12)])
+@pytest.mark.parametrize("precision,tol", [("tc_f16x3", 1e-6), ("fp32", 1e-5), ("fp64", 1e-12), ("sf_fp32", 1e-5),
+                                           ("auto", 1e-6)])
 def test_plan_matches_integrate_and_oracle(precision, tol):
     from paper_1310_1194_gb300 import api
     w, g, deg = _mixed(700)
@@ -61,6 +62,51 @@ def test_plan_matches_integrate_and_oracle(precision, tol):
         assert v >= 0 and cap >= 0
         if (w["degree"] == p).any():
             assert ms > 0.0
+        kernel = plan.kernel(p)
+        if p <= 2 or precision in ("fp32", "fp64"):
+            assert kernel == "cuda_core"
+        elif precision == "auto":
+            assert kernel in ("tensor_core", "sum_factorised")
+        else:
+            assert kernel == {"tc_f16x3": "tensor_core", "sf_fp32": "sum_factorised"}[precision]
+
+
+def test_auto_precision_resolves_per_degree():
+    """FEI_AUTO on a direct call runs FEI_FP32 at p <= 2, FEI_TC_F16X3 at
+    p = 3..5 and the sum-factorised kernel at p = 6, 7: bit for bit the
+    outputs of those precisions.  Under a plan, the sum-factorised variant
+    (number = the tensor-core variant count) can be chosen by hand."""
+    from paper_1310_1194_gb300 import api, _lib
+    for p, same in ((1, "fp32"), (4, "tc_f16x3"), (5, "tc_f16x3"), (6, "sf_fp32"), (7, "sf_fp32")):
+        w = inputs.workload("p7" if p >= 6 else "pr1", n_max=40 if p >= 6 else 300)
+        g = {k: torch.from_numpy(np.ascontiguousarray(w[k])).cuda() for k in ("geom", "K", "b", "c", "f")}
+        Aa, ba, sa, _ = api.fei_integrate(g["geom"], g["K"], g["b"], g["c"], g["f"], p=p, precision="auto")
+        As, bs, ss, _ = api.fei_integrate(g["geom"], g["K"], g["b"], g["c"], g["f"], p=p, precision=same)
+        torch.cuda.synchronize()
+        assert torch.equal(Aa, As) and torch.equal(ba, bs) and torch.equal(sa, ss), (p, same)
+    n = 40
+    w = inputs.workload("p7", n_max=n)
+    g = {k: torch.from_numpy(np.ascontiguousarray(w[k])).cuda() for k in ("geom", "K", "b", "c", "f")}
+    plan = api.Plan(degrees=[5], max_elem=n, precision="auto")
+    assert plan.kernel(5) == "tensor_core"
+    ntc = 0
+    while True:
+        try:
+            plan.set_choice(5, ntc, 0)
+        except _lib.FeiError:
+            break
+        if plan.kernel(5) == "sum_factorised":
+            break
+        ntc += 1
+    assert ntc >= 2 and plan.kernel(5) == "sum_factorised"
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        Ap, bp, sp, _ = plan.execute(g["geom"], g["K"], g["b"], g["c"], g["f"], p=5)
+        Ar, br, sr, _ = api.fei_integrate(g["geom"], g["K"], g["b"], g["c"], g["f"], p=5, precision="sf_fp32")
+    s.synchronize()
+    assert torch.equal(Ap, Ar) and torch.equal(bp, br)
+    with pytest.raises(_lib.FeiError):
+        plan.set_choice(5, ntc + 1, 0)
 
 
 def test_plan_recapture_new_buffers_and_uniform():
