@@ -452,9 +452,9 @@ def run_workload(name, args, ctx, headline):
     precision = args.precision if headline else None
     if precision is None:
         # the fastest path within 1e-6 of the oracle: the FP32 kernels at
-        # p <= 2, the split tensor-core kernel at p = 3..5, the sum-factorised
-        # kernel at p = 6, 7, and per degree the tuner's pick for a mixed batch
-        precision = "auto" if p is None else "fp32" if p <= 2 else "tc_f16x3" if p <= 5 else "sf_fp32"
+        # p <= 2, the split tensor-core kernel at p = 3, 4, the sum-factorised
+        # kernel at p = 5..7, and per degree the tuner's pick for a mixed batch
+        precision = "auto" if p is None else "fp32" if p <= 2 else "tc_f16x3" if p <= 4 else "sf_fp32"
     layout = api.fei_plan_offsets(deg, upper) if deg is not None else api.uniform_layout(n, p, upper)
     refs = [api.fei_reference_create(d) for d in ([p] if p is not None else range(1, 8))]
     out_dtype = torch.float64 if precision == "fp64" else torch.float32

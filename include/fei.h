@@ -93,8 +93,8 @@ typedef enum {
   FEI_SF_FP32 = 4,
   /* Per degree, the fastest kernel among those measured within 1e-6 of
    * the FP64 oracle (relative Frobenius norm per element): the FEI_FP32
-   * kernels for p <= 2, the FEI_TC_F16X3 kernel for p = 3..5 and the
-   * sum-factorised kernel for p = 6, 7 on a direct call; a plan's tuner
+   * kernels for p <= 2, the FEI_TC_F16X3 kernel for p = 3, 4 and the
+   * sum-factorised kernel for p = 5..7 on a direct call; a plan's tuner
    * times the tensor-core variants and the sum-factorised kernel at every
    * p >= 3 and keeps the fastest.  Output FP32. */
   FEI_AUTO = 5

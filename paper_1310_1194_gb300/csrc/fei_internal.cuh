@@ -160,7 +160,7 @@ enum KernelKind { KERNEL_CC = 0, KERNEL_TC = 1, KERNEL_SF = 2 };
 // The kernel of degree p under prec on a direct call, and the precision it
 // runs in (FEI_AUTO resolved per degree).
 inline KernelKind direct_kernel(fei_precision prec, int p, fei_precision *run) {
-  if (prec == FEI_AUTO) prec = p <= 2 ? FEI_FP32 : p <= 5 ? FEI_TC_F16X3 : FEI_SF_FP32;
+  if (prec == FEI_AUTO) prec = p <= 2 ? FEI_FP32 : p <= 4 ? FEI_TC_F16X3 : FEI_SF_FP32;
   *run = prec;
   if (p >= 3 && tc_precision(prec)) return KERNEL_TC;
   if (p >= 3 && prec == FEI_SF_FP32) return KERNEL_SF;

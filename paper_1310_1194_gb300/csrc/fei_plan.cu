@@ -67,7 +67,7 @@ int n_variants(fei_precision prec, int p) {
 }
 // The variant a plan starts from (before any tuning).
 int default_variant(fei_precision prec, int p) {
-  return (prec == FEI_AUTO && p >= 6) ? tc_variant_count(p, FEI_TC_F16X3) : 0;
+  return (prec == FEI_AUTO && p >= 5) ? tc_variant_count(p, FEI_TC_F16X3) : 0;
 }
 
 // The batch a graph was captured for, field by field (not the padding).

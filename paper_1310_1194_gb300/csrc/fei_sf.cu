@@ -27,7 +27,10 @@
 // p = 7 this is about 5.7 M multiply-adds per element against 41 M for the
 // dense contraction (8 N_sh^2 N_q / 2).
 //
-// One thread block per element (persistent over elements).  Setup: the
+// One thread block per element, persistent over elements: 512 threads and
+// one block per SM at p = 6, 7 (the shared memory of one element), 256
+// threads and three blocks per SM at p <= 5, where several elements in
+// flight hide the latency of each one's short stages.  Setup: the
 // element record is fetched one element ahead into registers; each node
 // thread forms its own Jacobian columns in FP64 from the vertices; the
 // point operators Dt of every point as in the FEI_FP32 path (FP64 w det J,
@@ -249,11 +252,14 @@ template <int P>
 struct SfCfg {
   static constexpr int M = P + 1, T = (P + 1) * (P + 2) / 2, NSH = nsh_of(P), NQ = nq_of(P), NT2 = M * M;
   static constexpr int MZ = sf_mz(P);  // a node index padded for 16-byte loads
-  static constexpr int NTH = P >= 5 ? 512 : 256;
+  static constexpr int NTH = P >= 6 ? 512 : 256;
+  // blocks per SM the register budget is set for: several small elements
+  // in flight per SM hide the latency of each one's short stages
+  static constexpr int MINB = P <= 5 ? 3 : 1;
   static constexpr int TT = T * T;
   static constexpr int NPR = (TT + NTH - 1) / NTH;  // stage-3 (t, t') pairs per thread
   // stage 2: each thread a BR x BC block of (t, t') pairs sharing (m(t), m(t'))
-  static constexpr int BR = P >= 7 ? 2 : 1, BC = P >= 6 ? 2 : 1;
+  static constexpr int BR = P >= 7 ? 2 : 1, BC = (P == 5 || P >= 6) ? 2 : 1;
   static constexpr int NBLK = [] {
     int a = 0, b = 0;
     for (int m = 0; m < M; ++m) a += (M - m + BR - 1) / BR, b += (M - m + BC - 1) / BC;
@@ -321,7 +327,7 @@ __device__ __forceinline__ void t_column_from_vertices(const double *X, double x
 }
 
 template <int P>
-__global__ void __launch_bounds__(SfCfg<P>::NTH, 1) sf_forward_kernel(FwdArgs a, const float *gtab) {
+__global__ void __launch_bounds__(SfCfg<P>::NTH, SfCfg<P>::MINB) sf_forward_kernel(FwdArgs a, const float *gtab) {
   using C = SfCfg<P>;
   constexpr int M = C::M, MZ = C::MZ, T = C::T, NSH = C::NSH, NQ = C::NQ, NT2 = C::NT2, NTH = C::NTH, TT = C::TT;
   constexpr int BR = C::BR, BC = C::BC;

@@ -73,11 +73,12 @@ def test_plan_matches_integrate_and_oracle(precision, tol):
 
 def test_auto_precision_resolves_per_degree():
     """FEI_AUTO on a direct call runs FEI_FP32 at p <= 2, FEI_TC_F16X3 at
-    p = 3..5 and the sum-factorised kernel at p = 6, 7: bit for bit the
-    outputs of those precisions.  Under a plan, the sum-factorised variant
-    (number = the tensor-core variant count) can be chosen by hand."""
+    p = 3, 4 and the sum-factorised kernel at p = 5..7: bit for bit the
+    outputs of those precisions.  Under a plan, a tensor-core variant or the
+    sum-factorised variant (number = the tensor-core variant count) can be
+    chosen by hand."""
     from paper_1310_1194_gb300 import api, _lib
-    for p, same in ((1, "fp32"), (4, "tc_f16x3"), (5, "tc_f16x3"), (6, "sf_fp32"), (7, "sf_fp32")):
+    for p, same in ((1, "fp32"), (3, "tc_f16x3"), (4, "tc_f16x3"), (5, "sf_fp32"), (6, "sf_fp32"), (7, "sf_fp32")):
         w = inputs.workload("p7" if p >= 6 else "pr1", n_max=40 if p >= 6 else 300)
         g = {k: torch.from_numpy(np.ascontiguousarray(w[k])).cuda() for k in ("geom", "K", "b", "c", "f")}
         Aa, ba, sa, _ = api.fei_integrate(g["geom"], g["K"], g["b"], g["c"], g["f"], p=p, precision="auto")
@@ -88,6 +89,8 @@ def test_auto_precision_resolves_per_degree():
     w = inputs.workload("p7", n_max=n)
     g = {k: torch.from_numpy(np.ascontiguousarray(w[k])).cuda() for k in ("geom", "K", "b", "c", "f")}
     plan = api.Plan(degrees=[5], max_elem=n, precision="auto")
+    assert plan.kernel(5) == "sum_factorised"
+    plan.set_choice(5, 0, 0)
     assert plan.kernel(5) == "tensor_core"
     ntc = 0
     while True:
