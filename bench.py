@@ -90,6 +90,15 @@ def kernel_flops(counts, precision):
                                  else flops_per_element(d)) for d in range(1, 8))
 
 
+def fp64_pipe_ops_per_element(p):
+    """FP64-pipe instructions per element of the FP32 path at p <= 2: the 21
+    element-vector components (3 adds, a multiply, a conversion each), per
+    vertical node 36 (the columns c1, c2: 6; n3: 6; n3.C, n3.D1, n3.D2: 9;
+    the w_z products: 3; three FP32-pair splits: 12) and the 14 coefficient
+    conversions."""
+    return 21 * 5 + 36 * (p + 1) + 14
+
+
 def bwd_flops_per_element(p):
     """Algorithmic flops of the adjoint per element: W = gA G^T (8 N_sh^2
     N_q), dL/dDt = G_q W_q (32 N_sh N_q), the load-vector adjoint (2 N_sh
@@ -357,16 +366,27 @@ def roofline_of(dom, counts, precision, peaks, peak_src, live, Bts, ms_all, p, n
         f64_peak = 152 * 2 * 2 * sm_max * 1e6 / 1e12
     if not f32_peak:
         f32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12
-    if low_p:
-        # p <= 2: a few kflops per element against 0.4-0.6 KB of traffic, but
-        # the Jacobian work is FP64 (about 45 FP64 flops per point and 84 per
-        # element for the element vectors on the FP32 paths; everything on
-        # the FP64 path), and at GB300's FP64 rate that, not HBM, binds
-        f64 = (F if precision == "fp64" else sum(int(counts[d]) * (45 * nq(d) + 84) for d in range(1, 3)))
-        bound, peak, unit, achieved = "alu", f64_peak, "TFLOP/s", f64 / (ms * 1e-3) / 1e12
-        peak_note = f64_note + " (the FP64 Jacobian work binds before HBM)"
+    if low_p and precision == "fp64":
+        # the FP64 path at p <= 2: every flop in FP64
+        bound, peak, unit, achieved = "alu", f64_peak, "TFLOP/s", F / (ms * 1e-3) / 1e12
+        peak_note = f64_note
         hw = {"hbm_gbs": Bts / (ms * 1e-3) / 1e9, "hbm_frac": Bts / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
               "hbm_peak_gbs": peaks["hbm_gbs"]}
+    elif low_p:
+        # p <= 2 on the FP32 path: a few kflops per element against 0.4-0.6 KB
+        # of traffic, but reading the FP64 inputs needs FP64 work, and at
+        # GB300's FP64 rate (1/64 of FP32) that, not HBM, binds.  The work is
+        # counted in FP64-pipe instructions per element (the element vectors:
+        # 21 x (3 adds, a multiply, a conversion); per vertical node the
+        # columns, n3 and its three dot products, w_z and the FP32-pair
+        # splits: 36; the 14 coefficient conversions) against the measured
+        # FP64 FMA instruction rate (half the FP64 flop peak)
+        ops = sum(int(counts[d]) * fp64_pipe_ops_per_element(d) for d in range(1, 3))
+        bound, peak, unit, achieved = "alu", f64_peak / 2, "Tinst/s", ops / (ms * 1e-3) / 1e12
+        peak_note = f64_note + " / 2: FP64 pipe instructions (the FP64 input work binds before HBM)"
+        hw = {"hbm_gbs": Bts / (ms * 1e-3) / 1e9, "hbm_frac": Bts / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
+              "hbm_peak_gbs": peaks["hbm_gbs"], "fp64_pipe_ops_per_element": {
+                  str(d): fp64_pipe_ops_per_element(d) for d in range(1, 3) if counts[d]}}
     elif precision in ("tc_f16x3", "tc_3xtf32"):
         # every algorithmic multiply-add is three tensor products (hi*hi,
         # hi*lo, lo*hi), so the peak for algorithmic flops is a third of the

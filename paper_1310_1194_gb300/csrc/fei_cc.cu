@@ -57,73 +57,79 @@ __device__ __forceinline__ bool load_coef(const FwdArgs &a, int64_t r, double *c
   return ok;
 }
 
-// Point operator directly from the element vectors (no node caching).
-template <typename T>
-__device__ __forceinline__ int point_direct(const double *ev, const double *pt, const double *cd,
-                                            T *D) {
+// Point operator directly from the element vectors, FP64 (the FEI_FP64
+// path at p <= 2).
+__device__ __forceinline__ int point_direct64(const double *ev, const double *pt, const double *cd, double *D) {
   double c1[3], c2[3], n3[3], c3[3];
   znode_columns(ev, pt[2], c1, c2, n3);
   tnode_column(ev, pt[0], pt[1], c3);
   const double w = pt[3];
   const double det = dot3(n3, c3);
   const double s = w * det;
-  T K[9], b[3];
-#pragma unroll
-  for (int k = 0; k < 9; ++k) K[k] = (T)cd[k];
-#pragma unroll
-  for (int k = 0; k < 3; ++k) b[k] = (T)cd[9 + k];
-  if constexpr (std::is_same<T, double>::value) {
-    double a0[3], a1[3];
-    cross3(c2, c3, a0);
-    cross3(c3, c1, a1);
-    dt_from_adj<double>(a0, a1, n3, w, s, w / det, K, b, cd[12], cd[13], D);
-  } else {
-    float f1[3], f2[3], f3[3], fn[3], a0[3], a1[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      f1[k] = (float)c1[k];
-      f2[k] = (float)c2[k];
-      f3[k] = (float)c3[k];
-      fn[k] = (float)n3[k];
-    }
-    cross3(f2, f3, a0);
-    cross3(f3, f1, a1);
-    const float wf = (float)w, sf = (float)s;
-    dt_from_adj<float>(a0, a1, fn, wf, sf, wf * wf / sf, K, b, (float)cd[12], (float)cd[13], D);
-  }
+  double a0[3], a1[3];
+  cross3(c2, c3, a0);
+  cross3(c3, c1, a1);
+  dt_from_adj<double>(a0, a1, n3, w, s, w / det, cd, cd + 9, cd[12], cd[13], D);
   return point_status(s);
 }
 
 // ---------------------------------------------------------------------------
 // Low degree (p <= 2): EPW elements per warp (p = 1: four elements of 8
-// points, p = 2: one of 27), so that every lane takes a point in the FP64
-// Jacobian work; lanes then run over the entries of the A_e.
+// points, p = 2: one of 27), so that every lane takes a point; lanes then
+// run over the entries of the A_e.  The FP64 path forms each point's
+// Jacobian in FP64.  The FP32 path keeps FP64 to what reading its inputs
+// needs: the element vectors, and per vertical node the FP64 sums
+// alpha, beta, gamma of det J = alpha + xi1 beta + xi2 gamma (split into
+// FP32 pairs); each point's w det J is then formed in double-FP32
+// arithmetic and rounded once, and the columns and adjugate are FP32.  At
+// p = 1 that is about 200 FP64 instructions per element instead of about
+// 500 with per-point FP64 columns (this part's FP64 rate binds there).
 // ---------------------------------------------------------------------------
 
 // One component (j = vector * 3 + axis) of the element vectors A1, B1, A2,
-// B2, C, D1, D2 from the bottom (P) and top (Q) vertices, FP64.
+// B2, C, D1, D2 from the bottom (P) and top (Q) vertices, FP64:
+// 0.5 ((X_a - X_b) + s (X_c - X_d)) with the vertices a, b, c, d and the
+// sign s of each vector picked by integer selects, so that lanes holding
+// different vectors run the same FP64 instructions (a branch per vector
+// would run every branch's FP64 work in every lane of the warp).
 __device__ __forceinline__ double elem_vec_comp(const double *X, int j) {
   const int v = j / 3, k = j - 3 * v;
-  const double p0 = X[k], p1 = X[3 + k], p2 = X[6 + k], q0 = X[9 + k], q1 = X[12 + k], q2 = X[15 + k];
-  switch (v) {
-    case 0: return 0.5 * ((p1 - p0) + (q1 - q0));
-    case 1: return 0.5 * ((q1 - q0) - (p1 - p0));
-    case 2: return 0.5 * ((p2 - p0) + (q2 - q0));
-    case 3: return 0.5 * ((q2 - q0) - (p2 - p0));
-    case 4: return 0.5 * (q0 - p0);
-    case 5: return 0.5 * ((q1 - p1) - (q0 - p0));
-    default: return 0.5 * ((q2 - p2) - (q0 - p0));
-  }
+  // a | b << 4 | c << 8 | d << 12 | (s + 1) << 16, vertices P0..P2 = 0..2,
+  // Q0..Q2 = 3..5: A1 = (P1-P0) + (Q1-Q0), B1 = (Q1-Q0) - (P1-P0),
+  // A2 = (P2-P0) + (Q2-Q0), B2 = (Q2-Q0) - (P2-P0), C = Q0-P0,
+  // D1 = (Q1-P1) - (Q0-P0), D2 = (Q2-P2) - (Q0-P0), each halved
+  const int code = v == 0 ? (1 | 0 << 4 | 4 << 8 | 3 << 12 | 2 << 16)
+                   : v == 1 ? (4 | 3 << 4 | 1 << 8 | 0 << 12 | 0 << 16)
+                   : v == 2 ? (2 | 0 << 4 | 5 << 8 | 3 << 12 | 2 << 16)
+                   : v == 3 ? (5 | 3 << 4 | 2 << 8 | 0 << 12 | 0 << 16)
+                   : v == 4 ? (3 | 0 << 4 | 0 << 8 | 0 << 12 | 1 << 16)
+                   : v == 5 ? (4 | 1 << 4 | 3 << 8 | 0 << 12 | 0 << 16)
+                            : (5 | 2 << 4 | 3 << 8 | 0 << 12 | 0 << 16);
+  const double xa = X[3 * (code & 15) + k], xb = X[3 * ((code >> 4) & 15) + k];
+  const double xc = X[3 * ((code >> 8) & 15) + k], xd = X[3 * ((code >> 12) & 15) + k];
+  const int sg = code >> 16;  // s + 1
+  const long long t = __double_as_longlong(xc - xd);
+  // s (X_c - X_d) by the sign bit (s = -1) or zero (s = 0): integer work
+  const double st = sg == 1 ? 0.0 : __longlong_as_double(sg == 0 ? t ^ (1LL << 63) : t);
+  return 0.5 * ((xa - xb) + st);
 }
 
 template <typename T, int P>
 struct SmallCfg {
   static constexpr int NSH = nsh_of(P), NQ = nq_of(P), K4 = 4 * NQ;
+  static constexpr int M = P + 1, NT = (P + 1) * (P + 1);
+  static constexpr bool F64 = std::is_same<T, double>::value;
   static constexpr int EPW = 32 / NQ;  // elements per warp
-  static constexpr int WPB = std::is_same<T, double>::value ? 4 : 8;
-  // per element slot: X[18], ev[21], cd[14] (FP64), D[NQ][16], H[K4][NSH] (T), status
+  static constexpr int WPB = F64 ? 4 : 8;
+  // FP32 path, floats per slot: per vertical node w_z (alpha, beta, gamma)
+  // as FP32 pairs [M][6], evf[21], cdf[14], the FP32 columns c1, c2, n3 [M][9]
+  static constexpr int XF = F64 ? 0 : M * 6 + 21 + 14 + M * 9;
+  static_assert((sizeof(double) * (18 + 21 + 14) + sizeof(T) * (NQ * 16 + K4 * NSH)) % 8 == 0,
+                "the FP32 pairs start 8-byte aligned");
+  // per element slot: X[18], ev[21], cd[14] (FP64), D[NQ][16], H[K4][NSH] (T),
+  // the FP32 extras, status
   static constexpr int SLOT_BYTES =
-      ((sizeof(double) * (18 + 21 + 14) + sizeof(T) * (NQ * 16 + K4 * NSH) + 16 + 15) / 16) * 16;
+      ((sizeof(double) * (18 + 21 + 14) + sizeof(T) * (NQ * 16 + K4 * NSH) + 4 * XF + 16 + 15) / 16) * 16;
   static constexpr int WARP_BYTES = EPW * SLOT_BYTES;
   static constexpr int SMEM = ((sizeof(T) * K4 * NSH + 15) / 16) * 16 + WPB * WARP_BYTES;
 };
@@ -131,8 +137,14 @@ struct SmallCfg {
 template <typename T, int P>
 __global__ void __launch_bounds__(SmallCfg<T, P>::WPB * 32) cc_small_kernel(FwdArgs a) {
   using C = SmallCfg<T, P>;
-  constexpr int NSH = C::NSH, NQ = C::NQ, K4 = C::K4, EPW = C::EPW;
+  constexpr int NSH = C::NSH, NQ = C::NQ, K4 = C::K4, EPW = C::EPW, M = C::M, NT = C::NT;
+  constexpr bool F64 = C::F64;
   static_assert(NQ <= 32, "one point per lane");
+  // FP32 path: node tables of the degree, once per block (triangle node:
+  // w_t, w_t xi1, w_t xi2 as FP32 pairs, and w_t, xi1, xi2; vertical node:
+  // zeta and w_z)
+  __shared__ float2 ttab[NT][3];
+  __shared__ float ttabf[NT][3], zf[M], zwf[M];
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *Gs = reinterpret_cast<T *>(smem_raw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -142,10 +154,33 @@ __global__ void __launch_bounds__(SmallCfg<T, P>::WPB * 32) cc_small_kernel(FwdA
   auto cds = [&](int sl) { return Xs(sl) + 39; };
   auto Ds = [&](int sl) { return reinterpret_cast<T *>(Xs(sl) + 53); };
   auto Hs = [&](int sl) { return Ds(sl) + NQ * 16; };
-  auto Ss = [&](int sl) { return reinterpret_cast<int *>(Hs(sl) + K4 * NSH); };
+  // FP32 extras: the FP32 pairs first (Fx is 8-byte aligned: the slot is
+  // 16-byte aligned and every array before it a multiple of 8 bytes), then
+  // evf, cdf, zc
+  auto Fx = [&](int sl) { return reinterpret_cast<float *>(Hs(sl) + K4 * NSH); };
+  auto zabs = [&](int sl) { return reinterpret_cast<float2 *>(Fx(sl)); };
+  auto evfs = [&](int sl) { return Fx(sl) + 6 * M; };
+  auto cdfs = [&](int sl) { return Fx(sl) + 6 * M + 21; };
+  auto zcs = [&](int sl) { return Fx(sl) + 6 * M + 35; };
+  auto Ss = [&](int sl) { return reinterpret_cast<int *>(Fx(sl) + C::XF); };
 
   const T *G = gtab<T>(a);
   for (int k = threadIdx.x; k < K4 * NSH; k += blockDim.x) Gs[k] = G[k];
+  if constexpr (!F64) {
+    for (int t = threadIdx.x; t < NT; t += blockDim.x) {
+      const double x1 = a.tnode[4 * t], x2 = a.tnode[4 * t + 1], wt = a.tnode[4 * t + 2];
+      ttab[t][0] = split_f64(wt);
+      ttab[t][1] = split_f64(wt * x1);
+      ttab[t][2] = split_f64(wt * x2);
+      ttabf[t][0] = (float)wt;
+      ttabf[t][1] = (float)x1;
+      ttabf[t][2] = (float)x2;
+    }
+    for (int iz = threadIdx.x; iz < M; iz += blockDim.x) {
+      zf[iz] = (float)a.znode[2 * iz];
+      zwf[iz] = (float)a.znode[2 * iz + 1];
+    }
+  }
   __syncthreads();
 
   const int64_t items = n_items(a);
@@ -165,6 +200,7 @@ __global__ void __launch_bounds__(SmallCfg<T, P>::WPB * 32) cc_small_kernel(FwdA
         const int c = k - 18;
         const double x = c < 9 ? a.K[9 * e + c] : c < 12 ? a.b[3 * e + (c - 9)] : c == 12 ? a.c[e] : a.f[e];
         cds(sl)[c] = x;
+        if constexpr (!F64) cdfs(sl)[c] = (float)x;
         ok = finite64(x);
       }
       // lanes of one element are one aligned group of 32: the whole warp
@@ -186,30 +222,98 @@ __global__ void __launch_bounds__(SmallCfg<T, P>::WPB * 32) cc_small_kernel(FwdA
     // element vectors, one component per lane (FP64)
     for (int idx = lane; idx < nel * 21; idx += 32) {
       const int sl = idx / 21, j = idx - sl * 21;
-      evs(sl)[j] = elem_vec_comp(Xs(sl), j);
+      const double v = elem_vec_comp(Xs(sl), j);
+      evs(sl)[j] = v;
+      if constexpr (!F64) evfs(sl)[j] = (float)v;
     }
     __syncwarp();
+    if constexpr (!F64) {
+      // per vertical node, three lanes (one per axis k): FP64 n3 = c1 x c2
+      // and w_z (n3.C, n3.D1, n3.D2) as FP32 pairs; the FP32 columns c1, c2
+      // and n3 from the FP32 vectors
+      {
+        const bool act = lane < nel * M * 3;
+        const int sl = act ? lane / (3 * M) : 0, rem = act ? lane - sl * 3 * M : 0;
+        const int iz = rem / 3, k = rem - 3 * iz;
+        const int g0 = lane - k, l1 = g0 + (k + 1) % 3, l2 = g0 + (k + 2) % 3;
+        const double *ev = evs(sl);
+        const double z = a.znode[2 * iz], wz = a.znode[2 * iz + 1];
+        const double c1 = fma(z, ev[3 + k], ev[k]), c2 = fma(z, ev[9 + k], ev[6 + k]);
+        const double c1a = __shfl_sync(0xffffffffu, c1, l1), c1b = __shfl_sync(0xffffffffu, c1, l2);
+        const double c2a = __shfl_sync(0xffffffffu, c2, l1), c2b = __shfl_sync(0xffffffffu, c2, l2);
+        const double n3 = c1a * c2b - c1b * c2a;  // (c1 x c2)_k
+        double al = n3 * ev[12 + k], be = n3 * ev[15 + k], ga = n3 * ev[18 + k];
+        al += __shfl_sync(0xffffffffu, al, l1) + __shfl_sync(0xffffffffu, al, l2);
+        be += __shfl_sync(0xffffffffu, be, l1) + __shfl_sync(0xffffffffu, be, l2);
+        ga += __shfl_sync(0xffffffffu, ga, l1) + __shfl_sync(0xffffffffu, ga, l2);
+        const float *evf = evfs(sl);
+        const float f1 = fmaf(zf[iz], evf[3 + k], evf[k]), f2 = fmaf(zf[iz], evf[9 + k], evf[6 + k]);
+        const float f1a = __shfl_sync(0xffffffffu, f1, l1), f1b = __shfl_sync(0xffffffffu, f1, l2);
+        const float f2a = __shfl_sync(0xffffffffu, f2, l1), f2b = __shfl_sync(0xffffffffu, f2, l2);
+        if (act) {
+          // lane k of the node keeps value k of (alpha, beta, gamma)
+          zabs(sl)[3 * iz + k] = split_f64(wz * (k == 0 ? al : k == 1 ? be : ga));
+          float *zc = zcs(sl) + 9 * iz;
+          zc[k] = f1;
+          zc[3 + k] = f2;
+          zc[6 + k] = f1a * f2b - f1b * f2a;
+        }
+      }
+      __syncwarp();
+    }
     // point operators: lane = (element slot, point)
     const int psl = lane / NQ, q = lane - psl * NQ;
     int pst = 0;
     if (psl < nel) {
       const int64_t e = a.list ? (int64_t)a.list[item0 + psl] : item0 + psl;
-      double ptv[4];
       // quadrature point from the node tables: q = iz*(p+1)^2 + t
-      const int iz = q / ((P + 1) * (P + 1)), t = q % ((P + 1) * (P + 1));
-      ptv[0] = a.tnode[4 * t];
-      ptv[1] = a.tnode[4 * t + 1];
-      ptv[2] = a.znode[2 * iz];
-      ptv[3] = a.tnode[4 * t + 2] * a.znode[2 * iz + 1];
+      const int iz = q / NT, t = q % NT;
       double cq[14];
-      const double *cp = cds(psl);
       if (a.coef_mode == FEI_COEF_PER_POINT) {
         const int64_t r = (a.q_off ? a.q_off[e] : e * (int64_t)NQ) + q;
         if (!load_coef(a, r, cq)) pst = FEI_ERR_NONFINITE;
         else if (a.upper && !coef_symmetric(cq, cq + 9)) pst = FEI_ERR_INVALID_ARG;
-        cp = cq;
       }
-      pst = merge_status(pst, point_direct<T>(evs(psl), ptv, cp, Ds(psl) + 16 * q));
+      const bool perq = a.coef_mode == FEI_COEF_PER_POINT;
+      if constexpr (F64) {
+        const double ptv[4] = {a.tnode[4 * t], a.tnode[4 * t + 1], a.znode[2 * iz],
+                               a.tnode[4 * t + 2] * a.znode[2 * iz + 1]};
+        pst = merge_status(pst, point_direct64(evs(psl), ptv, perq ? cq : cds(psl), Ds(psl) + 16 * q));
+      } else {
+        const float *evf = evfs(psl), *zc = zcs(psl) + 9 * iz;
+        const float2 *zab = zabs(psl) + 3 * iz;
+        // w det J in double-FP32, rounded once
+        const float2 sd = add_ff(add_ff(mul_ff(ttab[t][0], zab[0]), mul_ff(ttab[t][1], zab[1])),
+                                 mul_ff(ttab[t][2], zab[2]));
+        const float sf = sd.x + sd.y;
+        const int sst = !(fabsf(sf) <= 3.402823466e38f) ? FEI_ERR_NONFINITE
+                        : !(sf > 0.f)                    ? FEI_ERR_NEGATIVE_JACOBIAN
+                                                         : 0;
+        float c3[3], a0[3], a1[3], K[9], b[3], cf, ff;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) c3[k] = fmaf(ttabf[t][2], evf[18 + k], fmaf(ttabf[t][1], evf[15 + k], evf[12 + k]));
+        cross3(zc + 3, c3, a0);
+        cross3(c3, zc, a1);
+        if (perq) {
+#pragma unroll
+          for (int k = 0; k < 9; ++k) K[k] = (float)cq[k];
+#pragma unroll
+          for (int k = 0; k < 3; ++k) b[k] = (float)cq[9 + k];
+          cf = (float)cq[12];
+          ff = (float)cq[13];
+        } else {
+          const float *cdf = cdfs(psl);
+#pragma unroll
+          for (int k = 0; k < 9; ++k) K[k] = cdf[k];
+#pragma unroll
+          for (int k = 0; k < 3; ++k) b[k] = cdf[9 + k];
+          cf = cdf[12];
+          ff = cdf[13];
+        }
+        const float wf = ttabf[t][0] * zwf[iz];
+        dt_from_adj<float>(a0, a1, zc + 6, wf, sf, wf * wf / sf, K, b, cf, ff, Ds(psl) + 16 * q);
+        pst = merge_status(pst, sst);
+      }
       if (pst) atomicMax(Ss(psl), pst == FEI_ERR_NONFINITE ? 2 * FEI_ERR_NONFINITE : pst);
     }
     __syncwarp();
@@ -257,6 +361,164 @@ __global__ void __launch_bounds__(SmallCfg<T, P>::WPB * 32) cc_small_kernel(FwdA
     }
     __syncwarp();
   }
+}
+
+// ---------------------------------------------------------------------------
+// p = 1, FP32 path: one thread per element.  A p = 1 element is small (6
+// shape functions, 8 points, 36 entries), so a thread keeps A_e and b_e in
+// registers and runs the points in turn.  With one element per lane, every
+// FP64 instruction of the setup (element vectors, the vertical-node sums
+// of det J) serves 32 elements: this part's FP64 rate is what binds p = 1,
+// and a warp shared by four elements ran most of that work on a few lanes.
+// ---------------------------------------------------------------------------
+constexpr int kP1Threads = 128;
+
+__global__ void __launch_bounds__(kP1Threads, 3) cc_p1_kernel(FwdArgs a) {
+  constexpr int NSH = 6, NQ = 8, M = 2, NT = 4;
+  __shared__ float Gs[4 * NQ * NSH];  // G32 [q][a][i]
+  __shared__ float2 ttab[NT][3];      // w_t, w_t xi1, w_t xi2 as FP32 pairs
+  __shared__ float ttabf[NT][3];      // w_t, xi1, xi2
+  __shared__ float zf[M], zwf[M];
+  __shared__ double zd[M], zwd[M];
+  for (int k = threadIdx.x; k < 4 * NQ * NSH; k += blockDim.x) Gs[k] = a.G32[k];
+  if (threadIdx.x < NT) {
+    const int t = threadIdx.x;
+    const double x1 = a.tnode[4 * t], x2 = a.tnode[4 * t + 1], wt = a.tnode[4 * t + 2];
+    ttab[t][0] = split_f64(wt);
+    ttab[t][1] = split_f64(wt * x1);
+    ttab[t][2] = split_f64(wt * x2);
+    ttabf[t][0] = (float)wt;
+    ttabf[t][1] = (float)x1;
+    ttabf[t][2] = (float)x2;
+  } else if (threadIdx.x >= 32 && threadIdx.x < 32 + M) {
+    const int iz = threadIdx.x - 32;
+    zd[iz] = a.znode[2 * iz];
+    zwd[iz] = a.znode[2 * iz + 1];
+    zf[iz] = (float)zd[iz];
+    zwf[iz] = (float)zwd[iz];
+  }
+  __syncthreads();
+  const int64_t items = n_items(a);
+  for (int64_t item = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; item < items;
+       item += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = a.list ? (int64_t)a.list[item] : item;
+    bool ok = true, sym = true;
+    float ev32[21];   // element vectors rounded once
+    float2 zab[M][3];  // per vertical node w_z (n3.C, n3.D1, n3.D2), FP32 pairs
+    {
+      double X[18], ev[21];
+#pragma unroll
+      for (int k = 0; k < 18; ++k) {
+        X[k] = a.geom[18 * e + k];
+        ok &= finite64(X[k]);
+      }
+      elem_vectors(X, ev);
+#pragma unroll
+      for (int k = 0; k < 21; ++k) ev32[k] = (float)ev[k];
+#pragma unroll
+      for (int iz = 0; iz < M; ++iz) {
+        double c1[3], c2[3], n3[3];
+        znode_columns(ev, zd[iz], c1, c2, n3);
+        zab[iz][0] = split_f64(zwd[iz] * dot3(n3, ev + 12));
+        zab[iz][1] = split_f64(zwd[iz] * dot3(n3, ev + 15));
+        zab[iz][2] = split_f64(zwd[iz] * dot3(n3, ev + 18));
+      }
+    }
+    // FP32 columns c1, c2 and n3 per vertical node
+    float zc[M][9];
+#pragma unroll
+    for (int iz = 0; iz < M; ++iz) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        zc[iz][k] = fmaf(zf[iz], ev32[3 + k], ev32[k]);
+        zc[iz][3 + k] = fmaf(zf[iz], ev32[9 + k], ev32[6 + k]);
+      }
+      cross3(zc[iz], zc[iz] + 3, zc[iz] + 6);
+    }
+    float cf[14];
+    const bool perq = a.coef_mode == FEI_COEF_PER_POINT;
+    if (!perq) {
+      double cd[14];
+      ok &= load_coef(a, e, cd);
+      sym = !a.upper || coef_symmetric(cd, cd + 9);
+#pragma unroll
+      for (int k = 0; k < 14; ++k) cf[k] = (float)cd[k];
+    }
+    int st = !ok ? FEI_ERR_NONFINITE : (!sym ? FEI_ERR_INVALID_ARG : 0);
+    float A[NSH][NSH], bv[NSH];
+#pragma unroll
+    for (int i = 0; i < NSH; ++i) {
+      bv[i] = 0.f;
+#pragma unroll
+      for (int j = 0; j < NSH; ++j) A[i][j] = 0.f;
+    }
+#pragma unroll
+    for (int iz = 0; iz < M; ++iz)
+#pragma unroll 1
+    for (int t = 0; t < NT; ++t) {
+      const int q = iz * NT + t;
+      if (perq) {
+        double cd[14];
+        const int64_t r = (a.q_off ? a.q_off[e] : e * (int64_t)NQ) + q;
+        int pst = 0;
+        if (!load_coef(a, r, cd)) pst = FEI_ERR_NONFINITE;
+        else if (a.upper && !coef_symmetric(cd, cd + 9)) pst = FEI_ERR_INVALID_ARG;
+        st = merge_status(st, pst);
+#pragma unroll
+        for (int k = 0; k < 14; ++k) cf[k] = (float)cd[k];
+      }
+      // w det J in double-FP32, rounded once
+      const float2 sd = add_ff(add_ff(mul_ff(ttab[t][0], zab[iz][0]), mul_ff(ttab[t][1], zab[iz][1])),
+                               mul_ff(ttab[t][2], zab[iz][2]));
+      const float sf = sd.x + sd.y;
+      st = merge_status(st, !(fabsf(sf) <= 3.402823466e38f) ? FEI_ERR_NONFINITE
+                            : !(sf > 0.f)                    ? FEI_ERR_NEGATIVE_JACOBIAN
+                                                             : 0);
+      float c3[3], a0[3], a1[3], D[16];
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+        c3[k] = fmaf(ttabf[t][2], ev32[18 + k], fmaf(ttabf[t][1], ev32[15 + k], ev32[12 + k]));
+      cross3(zc[iz] + 3, c3, a0);
+      cross3(c3, zc[iz], a1);
+      const float wf = ttabf[t][0] * zwf[iz];
+      dt_from_adj<float>(a0, a1, zc[iz] + 6, wf, sf, wf * wf / sf, cf, cf + 9, cf[12], cf[13], D);
+      // A_e += G_q^T Dt_q G_q, b_e += (w det J f) G_q0
+      const float *G = Gs + q * 4 * NSH;
+#pragma unroll
+      for (int i = 0; i < NSH; ++i) {
+        const float g0 = G[i], g1 = G[NSH + i], g2 = G[2 * NSH + i], g3 = G[3 * NSH + i];
+        const float h0 = D[0] * g0;
+        const float h1 = D[1] * g0 + D[4] * g1 + D[7] * g2 + D[10] * g3;
+        const float h2 = D[2] * g0 + D[5] * g1 + D[8] * g2 + D[11] * g3;
+        const float h3 = D[3] * g0 + D[6] * g1 + D[9] * g2 + D[12] * g3;
+#pragma unroll
+        for (int j = 0; j < NSH; ++j)
+          A[i][j] += h0 * G[j] + h1 * G[NSH + j] + h2 * G[2 * NSH + j] + h3 * G[3 * NSH + j];
+        bv[i] += D[13] * g0;
+      }
+    }
+    float *Ao = reinterpret_cast<float *>(a.A) + out_a(a, item, e, NSH);
+#pragma unroll
+    for (int i = 0; i < NSH; ++i)
+#pragma unroll
+      for (int j = 0; j < NSH; ++j)
+        if (!a.upper || j >= i) Ao[a_pos(i, j, NSH, a.upper)] = st ? 0.f : A[i][j];
+    float *bo = reinterpret_cast<float *>(a.bv) + out_b(a, item, e, NSH);
+#pragma unroll
+    for (int i = 0; i < NSH; ++i) bo[i] = st ? 0.f : bv[i];
+    a.status[e] = st;
+  }
+}
+
+fei_status launch_p1(const FwdArgs &a, int64_t grid_work, cudaStream_t s, int64_t grid_cap) {
+  int64_t blocks = (grid_work + kP1Threads - 1) / kP1Threads;
+  const int64_t cap = grid_cap > 0 ? grid_cap : (a.count ? 152 * 8 : 0);
+  if (cap > 0 && blocks > cap) blocks = cap;
+  if (blocks > 2147483647LL) blocks = 2147483647LL;
+  if (blocks < 1) blocks = 1;
+  cc_p1_kernel<<<(unsigned)blocks, kP1Threads, 0, s>>>(a);
+  FEI_CUDA_TRY(cudaGetLastError(), "cc_p1_kernel launch");
+  return FEI_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -507,7 +769,9 @@ fei_status launch_tile(const FwdArgs &a, int64_t grid_work, cudaStream_t s, int6
 template <typename T>
 fei_status launch_typed(int p, const FwdArgs &a, int64_t grid_work, cudaStream_t s, int64_t cap) {
   switch (p) {
-    case 1: return launch_small<T, 1>(a, grid_work, s, cap);
+    case 1:
+      if constexpr (std::is_same<T, float>::value) return launch_p1(a, grid_work, s, cap);
+      return launch_small<T, 1>(a, grid_work, s, cap);
     case 2: return launch_small<T, 2>(a, grid_work, s, cap);
     case 3: return launch_tile<T, 3>(a, grid_work, s, cap);
     case 4: return launch_tile<T, 4>(a, grid_work, s, cap);

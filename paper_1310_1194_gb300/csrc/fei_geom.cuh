@@ -100,6 +100,33 @@ __device__ __forceinline__ void dt_from_adj(const T *a0, const T *a1, const T *a
   D[15] = T(0);
 }
 
+// Double-FP32 arithmetic (w det J on the FP32-class paths, reading the
+// FP64 node sums once per node and forming each point's value in FP32
+// pipes; one FP64 instruction costs tens of FP32 ones on this part).
+// An FP64 value as an unevaluated sum of two FP32 values, hi = rn(x) and
+// lo = rn(x - hi): 48 significant bits, enough for products and sums whose
+// FP32 rounding is taken once at the end.
+__device__ __forceinline__ float2 split_f64(double x) {
+  const float hi = (float)x;
+  return make_float2(hi, (float)(x - (double)hi));
+}
+// a.x b.x + a.y b.x + a.x b.y (the lo * lo term is below 2^-46 relative)
+// as (product, error) with the error of the leading product exact (FMA)
+__device__ __forceinline__ float2 mul_ff(float2 a, float2 b) {
+  const float p = a.x * b.x;
+  float e = fmaf(a.x, b.x, -p);
+  e = fmaf(a.x, b.y, e);
+  e = fmaf(a.y, b.x, e);
+  return make_float2(p, e);
+}
+// sum of two (value, error) pairs, the rounding error of the leading sum
+// kept exactly (Knuth's two-sum)
+__device__ __forceinline__ float2 add_ff(float2 a, float2 b) {
+  const float s = a.x + b.x;
+  const float bb = s - a.x;
+  const float err = (a.x - (s - bb)) + (b.x - bb);
+  return make_float2(s, err + a.y + b.y);
+}
 // Finite test on the exponent bits of an FP64 value (integer pipe: FP64
 // compares run at the FP64 rate, which is low on this part).
 __device__ __forceinline__ bool finite64(double x) {

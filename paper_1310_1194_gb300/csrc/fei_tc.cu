@@ -258,30 +258,6 @@ __device__ __forceinline__ void tmem_ld16_nw(uint32_t taddr, uint32_t *r) {
       : "r"(taddr));
 }
 
-// An FP64 value as an unevaluated sum of two FP32 values, hi = rn(x) and
-// lo = rn(x - hi): 48 significant bits, enough for products and sums whose
-// FP32 rounding is taken once at the end.
-__device__ __forceinline__ float2 split_f64(double x) {
-  const float hi = (float)x;
-  return make_float2(hi, (float)(x - (double)hi));
-}
-// a.x b.x + a.y b.x + a.x b.y (the lo * lo term is below 2^-46 relative)
-// as (product, error) with the error of the leading product exact (FMA)
-__device__ __forceinline__ float2 mul_ff(float2 a, float2 b) {
-  const float p = a.x * b.x;
-  float e = fmaf(a.x, b.x, -p);
-  e = fmaf(a.x, b.y, e);
-  e = fmaf(a.y, b.x, e);
-  return make_float2(p, e);
-}
-// sum of two (value, error) pairs, the rounding error of the leading sum
-// kept exactly (Knuth's two-sum)
-__device__ __forceinline__ float2 add_ff(float2 a, float2 b) {
-  const float s = a.x + b.x;
-  const float bb = s - a.x;
-  const float err = (a.x - (s - bb)) + (b.x - bb);
-  return make_float2(s, err + a.y + b.y);
-}
 __device__ __forceinline__ float exp2i(int k) {  // exact 2^k for |k| < 126
   return __int_as_float((127 + k) << 23);
 }
