@@ -128,20 +128,21 @@ def bytes_per_element(p, out_bytes, per_qp=False, upper=False):
 def measured_traffic(kernel_key, p, n_elem):
     """DRAM bytes of one launch of the dominant kernel from the committed ncu
     capture (profiles/traffic.json, per element, scaled by the elements of
-    this launch), or None when the capture is of another kernel source."""
+    this launch), or None when the capture is of another kernel source or
+    another degree."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "traffic.json")
-    src = os.path.join(ROOT, "paper_1310_1194_gb300", "csrc", "fei_tc.cu")
-    if kernel_key != "tc_forward_kernel" or not os.path.exists(path):
+    if not os.path.exists(path):
         return None
     with open(path) as fh:
         d = json.load(fh)
-    with open(src, "rb") as fh:
-        sha = hashlib.sha256(fh.read()).hexdigest()
-    if d.get("fei_tc_cu_sha256") != sha:
+    rec = d.get(kernel_key)
+    if not rec or str(p) not in rec:
         return None
-    rec = d.get(kernel_key, {}).get(str(p))
-    return None if rec is None else rec["bytes_per_element"] * n_elem
+    with open(os.path.join(ROOT, rec["source"]), "rb") as fh:
+        if hashlib.sha256(fh.read()).hexdigest() != rec["sha256"]:
+            return None
+    return rec[str(p)]["bytes_per_element"] * n_elem
 
 
 def load_peaks():
@@ -421,8 +422,8 @@ def roofline_of(dom, counts, precision, peaks, peak_src, live, Bts, ms_all, p, n
         bound, peak, unit, achieved = "alu", f64_peak, "TFLOP/s", F / (ms * 1e-3) / 1e12
         peak_note = f64_note
     traffic = None
-    if precision == "tc_f16x3" and dom["kernel"] == "forward" and p is not None and p >= 3:
-        traffic = measured_traffic("tc_forward_kernel", p, n)
+    if dom["kernel"] == "forward" and p is not None and p >= 3 and precision in ("tc_f16x3", "sf_fp32"):
+        traffic = measured_traffic("tc_forward_kernel" if precision == "tc_f16x3" else "sf_forward_kernel", p, n)
     r = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
          "traffic": traffic, "peak_source": peak_note, "kernel": dom["kernel"], "kernel_ms": ms,
          "step_hbm_gbs": Bts / (ms_all * 1e-3) / 1e9, "step_hbm_frac": Bts / (ms_all * 1e-3) / 1e9 / peaks["hbm_gbs"],
