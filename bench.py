@@ -972,7 +972,10 @@ def main():
         live = peak_probe.measure()
     except Exception as exc:  # the probe is a measurement aid: report, derive instead
         live = {"error": str(exc)}
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > L2
+    # 1 GiB > 8 x L2: written between steps, it evicts the L2 and keeps the
+    # device busy while the host enqueues the next step, so that the events
+    # around a step time its kernels, not the host's launch path
+    flush = torch.empty(1024 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     ctx = {"world": world, "rank": rank, "local": local, "dev": dev, "stream": stream, "flush": flush,
            "peaks": peaks, "peak_src": peak_src, "live": live if "error" not in live else None}
 
@@ -1001,7 +1004,7 @@ def main():
                       "sf_fp32": "f32", "auto": "f32 (per degree: f32, f16x3->f32 or sum-factorised f32)"}[precision],
             "data": "synthetic",
             "config": {"workload": head["workload"], "precision": precision, "elements": head["elements"],
-                       "l2": "256 MB buffer written between timed steps (outside the events); "
+                       "l2": "1 GiB buffer written between timed steps (outside the events); "
                              "each step also writes its outputs (> L2)",
                        "gflops_algorithmic": head["gflops_algorithmic"],
                        "rel_err_vs_oracle_max": err["max"] if err else None,

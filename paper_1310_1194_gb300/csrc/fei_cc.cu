@@ -373,6 +373,42 @@ __global__ void __launch_bounds__(SmallCfg<T, P>::WPB * 32) cc_small_kernel(FwdA
 // ---------------------------------------------------------------------------
 constexpr int kP1Threads = 128;
 
+// The two p = 1 kernels below (one thread per element for large batches,
+// eight lanes per element for small ones) give the same bits: their
+// FP64 node sums and their sums over points run in one fixed order of
+// rounded operations (the host-memory entry cuts a batch into chunks of
+// any size and must equal the device entry bit for bit).
+//
+// w_z (n3.C, n3.D1, n3.D2) of a vertical node as FP32 pairs, from the
+// columns' components c1[k], c2[k] and C, D1, D2 (FP64): n3_k and its
+// products p_k rounded one by one, value v summed as (p_v + p_v+1) + p_v+2.
+__device__ __forceinline__ double p1_node_sum(const double *n3, const double *w, int v) {
+  const double a = __dmul_rn(n3[v], w[v]), b = __dmul_rn(n3[(v + 1) % 3], w[(v + 1) % 3]);
+  const double c = __dmul_rn(n3[(v + 2) % 3], w[(v + 2) % 3]);
+  return __dadd_rn(__dadd_rn(a, b), c);
+}
+__device__ __forceinline__ double p1_cross_comp(double a1, double a2, double b1, double b2) {
+  return __dsub_rn(__dmul_rn(a1, b2), __dmul_rn(a2, b1));  // a1 b2 - a2 b1
+}
+// One point's contribution to A_e (36 values, row-major) and b_e (6):
+// G_q^T Dt_q G_q and (w det J f) G_q0, every operation rounded in turn.
+__device__ __forceinline__ void p1_point_contrib(const float *D, const float *G, float *c) {
+  constexpr int NSH = 6;
+#pragma unroll
+  for (int i = 0; i < NSH; ++i) {
+    const float g0 = G[i], g1 = G[NSH + i], g2 = G[2 * NSH + i], g3 = G[3 * NSH + i];
+    const float h0 = __fmul_rn(D[0], g0);
+    const float h1 = __fmaf_rn(D[10], g3, __fmaf_rn(D[7], g2, __fmaf_rn(D[4], g1, __fmul_rn(D[1], g0))));
+    const float h2 = __fmaf_rn(D[11], g3, __fmaf_rn(D[8], g2, __fmaf_rn(D[5], g1, __fmul_rn(D[2], g0))));
+    const float h3 = __fmaf_rn(D[12], g3, __fmaf_rn(D[9], g2, __fmaf_rn(D[6], g1, __fmul_rn(D[3], g0))));
+#pragma unroll
+    for (int j = 0; j < NSH; ++j)
+      c[i * NSH + j] = __fmaf_rn(h3, G[3 * NSH + j],
+                                 __fmaf_rn(h2, G[2 * NSH + j], __fmaf_rn(h1, G[NSH + j], __fmul_rn(h0, G[j]))));
+    c[NSH * NSH + i] = __fmul_rn(D[13], g0);
+  }
+}
+
 __global__ void __launch_bounds__(kP1Threads, 3) cc_p1_kernel(FwdArgs a) {
   constexpr int NSH = 6, NQ = 8, M = 2, NT = 4;
   __shared__ float Gs[4 * NQ * NSH];  // G32 [q][a][i]
@@ -418,10 +454,17 @@ __global__ void __launch_bounds__(kP1Threads, 3) cc_p1_kernel(FwdArgs a) {
 #pragma unroll
       for (int iz = 0; iz < M; ++iz) {
         double c1[3], c2[3], n3[3];
-        znode_columns(ev, zd[iz], c1, c2, n3);
-        zab[iz][0] = split_f64(zwd[iz] * dot3(n3, ev + 12));
-        zab[iz][1] = split_f64(zwd[iz] * dot3(n3, ev + 15));
-        zab[iz][2] = split_f64(zwd[iz] * dot3(n3, ev + 18));
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          c1[k] = fma(zd[iz], ev[3 + k], ev[k]);
+          c2[k] = fma(zd[iz], ev[9 + k], ev[6 + k]);
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+          n3[k] = p1_cross_comp(c1[(k + 1) % 3], c1[(k + 2) % 3], c2[(k + 1) % 3], c2[(k + 2) % 3]);
+        zab[iz][0] = split_f64(__dmul_rn(zwd[iz], p1_node_sum(n3, ev + 12, 0)));
+        zab[iz][1] = split_f64(__dmul_rn(zwd[iz], p1_node_sum(n3, ev + 15, 1)));
+        zab[iz][2] = split_f64(__dmul_rn(zwd[iz], p1_node_sum(n3, ev + 18, 2)));
       }
     }
     // FP32 columns c1, c2 and n3 per vertical node
@@ -483,18 +526,13 @@ __global__ void __launch_bounds__(kP1Threads, 3) cc_p1_kernel(FwdArgs a) {
       const float wf = ttabf[t][0] * zwf[iz];
       dt_from_adj<float>(a0, a1, zc[iz] + 6, wf, sf, wf * wf / sf, cf, cf + 9, cf[12], cf[13], D);
       // A_e += G_q^T Dt_q G_q, b_e += (w det J f) G_q0
-      const float *G = Gs + q * 4 * NSH;
+      float c[NSH * NSH + NSH];
+      p1_point_contrib(D, Gs + q * 4 * NSH, c);
 #pragma unroll
       for (int i = 0; i < NSH; ++i) {
-        const float g0 = G[i], g1 = G[NSH + i], g2 = G[2 * NSH + i], g3 = G[3 * NSH + i];
-        const float h0 = D[0] * g0;
-        const float h1 = D[1] * g0 + D[4] * g1 + D[7] * g2 + D[10] * g3;
-        const float h2 = D[2] * g0 + D[5] * g1 + D[8] * g2 + D[11] * g3;
-        const float h3 = D[3] * g0 + D[6] * g1 + D[9] * g2 + D[12] * g3;
 #pragma unroll
-        for (int j = 0; j < NSH; ++j)
-          A[i][j] += h0 * G[j] + h1 * G[NSH + j] + h2 * G[2 * NSH + j] + h3 * G[3 * NSH + j];
-        bv[i] += D[13] * g0;
+        for (int j = 0; j < NSH; ++j) A[i][j] = __fadd_rn(A[i][j], c[i * NSH + j]);
+        bv[i] = __fadd_rn(bv[i], c[NSH * NSH + i]);
       }
     }
     float *Ao = reinterpret_cast<float *>(a.A) + out_a(a, item, e, NSH);
@@ -510,7 +548,205 @@ __global__ void __launch_bounds__(kP1Threads, 3) cc_p1_kernel(FwdArgs a) {
   }
 }
 
+// p = 1, FP32 path, small batches: eight lanes per element (one per
+// point), so that a batch that fills only part of the GPU (4096 prisms:
+// 32 blocks of the kernel above) is not bound by one thread walking its
+// eight points in turn.  The FP64 work is spread over the lanes (three
+// element-vector components per lane, three lanes per vertical node for
+// the node sums), each lane forms its point's contribution to A_e and b_e
+// in registers, and a butterfly over the eight lanes adds them up.
+__global__ void __launch_bounds__(kP1Threads) cc_p1_small_kernel(FwdArgs a) {
+  constexpr int NSH = 6, NQ = 8, M = 2, NT = 4;
+  __shared__ float Gs[4 * NQ * NSH];  // G32 [q][a][i]
+  __shared__ float2 ttab[NT][3];
+  __shared__ float ttabf[NT][3];
+  __shared__ float zf[M], zwf[M];
+  __shared__ double zd[M], zwd[M];
+  for (int k = threadIdx.x; k < 4 * NQ * NSH; k += blockDim.x) Gs[k] = a.G32[k];
+  if (threadIdx.x < NT) {
+    const int t = threadIdx.x;
+    const double x1 = a.tnode[4 * t], x2 = a.tnode[4 * t + 1], wt = a.tnode[4 * t + 2];
+    ttab[t][0] = split_f64(wt);
+    ttab[t][1] = split_f64(wt * x1);
+    ttab[t][2] = split_f64(wt * x2);
+    ttabf[t][0] = (float)wt;
+    ttabf[t][1] = (float)x1;
+    ttabf[t][2] = (float)x2;
+  } else if (threadIdx.x >= 32 && threadIdx.x < 32 + M) {
+    const int iz = threadIdx.x - 32;
+    zd[iz] = a.znode[2 * iz];
+    zwd[iz] = a.znode[2 * iz + 1];
+    zf[iz] = (float)zd[iz];
+    zwf[iz] = (float)zwd[iz];
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, g = lane & 7, gbase = lane & 24;
+  const int64_t items = n_items(a);
+  const int64_t groups = (int64_t)gridDim.x * (blockDim.x / 8);
+  // every lane of the warp runs every iteration (the shuffles need the
+  // whole warp); a group past the end computes on a clamped element and
+  // stores nothing
+  const int64_t first = (int64_t)blockIdx.x * (blockDim.x / 8) + (threadIdx.x >> 3);
+  const int64_t warp_first = first - (lane >> 3);
+  for (int64_t it0 = warp_first; it0 < items; it0 += groups) {
+    const int64_t item = it0 + (lane >> 3);
+    const bool live = item < items;
+    const int64_t e = live ? (a.list ? (int64_t)a.list[item] : item) : (a.list ? (int64_t)a.list[0] : 0);
+    // vertices: lane g checks coordinates g, g + 8, g + 16 (the group's AND
+    // below); the element-vector components g, g + 8, g + 16 read theirs
+    // from global memory (the group's 144 bytes, cached), in FP64
+    const double *X = a.geom + 18 * e;
+    bool ok = finite64(X[g]) && finite64(X[g + 8]) && (g >= 2 || finite64(X[g + 16]));
+    double evm[3];
+    float evfm[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const int j = g + 8 * r;
+      evm[r] = elem_vec_comp(X, j < 21 ? j : 20);
+      evfm[r] = (float)evm[r];
+    }
+    float ev32[21];
+#pragma unroll
+    for (int j = 0; j < 21; ++j) ev32[j] = __shfl_sync(0xffffffffu, evfm[j / 8], gbase + (j & 7));
+    auto ev64 = [&](int j) { return __shfl_sync(0xffffffffu, evm[j / 8], gbase + (j & 7)); };
+    // node sums: lanes 0..5 of the group, three per vertical node
+    float2 zab[M][3];
+    {
+      const int iz = g < 3 ? 0 : 1, k = g < 6 ? g - 3 * iz : 0;
+      const int l1 = gbase + 3 * iz + (k + 1) % 3, l2 = gbase + 3 * iz + (k + 2) % 3;
+      // components k of A1, B1, A2, B2, C, D1, D2 (the shuffles run in all lanes)
+      double e0 = ev64(0), e1 = ev64(1), e2 = ev64(2), e3 = ev64(3), e4 = ev64(4), e5 = ev64(5);
+      double e6 = ev64(6), e7 = ev64(7), e8 = ev64(8), e9 = ev64(9), e10 = ev64(10), e11 = ev64(11);
+      double e12 = ev64(12), e13 = ev64(13), e14 = ev64(14), e15 = ev64(15), e16 = ev64(16), e17 = ev64(17);
+      double e18 = ev64(18), e19 = ev64(19), e20 = ev64(20);
+      const double A1 = k == 0 ? e0 : k == 1 ? e1 : e2, B1 = k == 0 ? e3 : k == 1 ? e4 : e5;
+      const double A2 = k == 0 ? e6 : k == 1 ? e7 : e8, B2 = k == 0 ? e9 : k == 1 ? e10 : e11;
+      const double Cc = k == 0 ? e12 : k == 1 ? e13 : e14, D1 = k == 0 ? e15 : k == 1 ? e16 : e17;
+      const double D2 = k == 0 ? e18 : k == 1 ? e19 : e20;
+      const double z = zd[iz], wz = zwd[iz];
+      const double c1 = fma(z, B1, A1), c2 = fma(z, B2, A2);
+      const double c1a = __shfl_sync(0xffffffffu, c1, l1), c1b = __shfl_sync(0xffffffffu, c1, l2);
+      const double c2a = __shfl_sync(0xffffffffu, c2, l1), c2b = __shfl_sync(0xffffffffu, c2, l2);
+      const double n3 = p1_cross_comp(c1a, c1b, c2a, c2b);
+      // lane k of the node keeps value k, summed as (p_k + p_k+1) + p_k+2
+      const double pa = __dmul_rn(n3, Cc), pb = __dmul_rn(n3, D1), pc = __dmul_rn(n3, D2);
+      const double s_al = __dadd_rn(__dadd_rn(pa, __shfl_sync(0xffffffffu, pa, l1)), __shfl_sync(0xffffffffu, pa, l2));
+      const double s_be = __dadd_rn(__dadd_rn(pb, __shfl_sync(0xffffffffu, pb, l1)), __shfl_sync(0xffffffffu, pb, l2));
+      const double s_ga = __dadd_rn(__dadd_rn(pc, __shfl_sync(0xffffffffu, pc, l1)), __shfl_sync(0xffffffffu, pc, l2));
+      const float2 mine = split_f64(__dmul_rn(wz, k == 0 ? s_al : k == 1 ? s_be : s_ga));
+#pragma unroll
+      for (int n = 0; n < M; ++n)
+#pragma unroll
+        for (int v = 0; v < 3; ++v) {
+          zab[n][v].x = __shfl_sync(0xffffffffu, mine.x, gbase + 3 * n + v);
+          zab[n][v].y = __shfl_sync(0xffffffffu, mine.y, gbase + 3 * n + v);
+        }
+    }
+    // coefficients: components g and g + 8 per lane, shared in FP32
+    float cf[14];
+    const bool perq = a.coef_mode == FEI_COEF_PER_POINT;
+    bool sym = true;
+    if (!perq) {
+      float cm[2];
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        const int c = g + 8 * r;
+        double x = 0.0;
+        if (c < 14) x = c < 9 ? a.K[9 * e + c] : c < 12 ? a.b[3 * e + c - 9] : c == 12 ? a.c[e] : a.f[e];
+        ok &= finite64(x);
+        cm[r] = (float)x;
+      }
+#pragma unroll
+      for (int c = 0; c < 14; ++c) cf[c] = __shfl_sync(0xffffffffu, cm[c / 8], gbase + (c & 7));
+      if (a.upper) {
+        // K symmetric and b = 0, compared in FP64 (as the other kernels)
+        const double k01 = a.K[9 * e + 1], k10 = a.K[9 * e + 3], k02 = a.K[9 * e + 2], k20 = a.K[9 * e + 6];
+        const double k12 = a.K[9 * e + 5], k21 = a.K[9 * e + 7];
+        sym = k01 == k10 && k02 == k20 && k12 == k21 && a.b[3 * e] == 0.0 && a.b[3 * e + 1] == 0.0 &&
+              a.b[3 * e + 2] == 0.0;
+      }
+    }
+    // the point of this lane
+    const int q = g, iz = q / NT, t = q - iz * NT;
+    int st = 0;
+    if (perq) {
+      double cd[14];
+      const int64_t r = (a.q_off ? a.q_off[e] : e * (int64_t)NQ) + q;
+      if (!load_coef(a, r, cd)) st = FEI_ERR_NONFINITE;
+      else if (a.upper && !coef_symmetric(cd, cd + 9)) st = FEI_ERR_INVALID_ARG;
+#pragma unroll
+      for (int k = 0; k < 14; ++k) cf[k] = (float)cd[k];
+    }
+    const float2 *zq = iz ? zab[1] : zab[0];
+    const float2 sd = add_ff(add_ff(mul_ff(ttab[t][0], zq[0]), mul_ff(ttab[t][1], zq[1])), mul_ff(ttab[t][2], zq[2]));
+    const float sf = sd.x + sd.y;
+    st = merge_status(st, !(fabsf(sf) <= 3.402823466e38f) ? FEI_ERR_NONFINITE
+                          : !(sf > 0.f)                    ? FEI_ERR_NEGATIVE_JACOBIAN
+                                                           : 0);
+    float zc[9];
+    {
+      const float zz = zf[iz];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        zc[k] = fmaf(zz, ev32[3 + k], ev32[k]);
+        zc[3 + k] = fmaf(zz, ev32[9 + k], ev32[6 + k]);
+      }
+      cross3(zc, zc + 3, zc + 6);
+    }
+    float c3[3], a0[3], a1[3], D[16];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) c3[k] = fmaf(ttabf[t][2], ev32[18 + k], fmaf(ttabf[t][1], ev32[15 + k], ev32[12 + k]));
+    cross3(zc + 3, c3, a0);
+    cross3(c3, zc, a1);
+    const float wf = ttabf[t][0] * zwf[iz];
+    dt_from_adj<float>(a0, a1, zc + 6, wf, sf, wf * wf / sf, cf, cf + 9, cf[12], cf[13], D);
+    float c[NSH * NSH + NSH];  // this point's G_q^T Dt_q G_q, then its share of b
+    p1_point_contrib(D, Gs + q * 4 * NSH, c);
+    // the sums over the group's points in point order (q = lane), as the
+    // one-thread kernel adds them
+    float A[NSH * NSH + NSH];
+#pragma unroll
+    for (int v = 0; v < NSH * NSH + NSH; ++v) A[v] = 0.f;
+#pragma unroll
+    for (int qq = 0; qq < NQ; ++qq)
+#pragma unroll
+      for (int v = 0; v < NSH * NSH + NSH; ++v) A[v] = __fadd_rn(A[v], __shfl_sync(0xffffffffu, c[v], gbase + qq));
+    int code = st == FEI_ERR_NONFINITE ? 2 * FEI_ERR_NONFINITE : st;
+    if (!ok) code = 2 * FEI_ERR_NONFINITE;  // any lane's coordinate or coefficient
+    else if (!sym && code == 0) code = FEI_ERR_INVALID_ARG;
+#pragma unroll
+    for (int off = 4; off >= 1; off >>= 1) code = max(code, __shfl_xor_sync(0xffffffffu, code, off));
+    const int fst = code == 2 * FEI_ERR_NONFINITE ? FEI_ERR_NONFINITE : code;
+    if (live) {
+      float *Ao = reinterpret_cast<float *>(a.A) + out_a(a, item, e, NSH);
+      float *bo = reinterpret_cast<float *>(a.bv) + out_b(a, item, e, NSH);
+#pragma unroll
+      for (int v = 0; v < NSH * NSH + NSH; ++v) {
+        if ((v & 7) != g) continue;
+        if (v < NSH * NSH) {
+          const int i = v / NSH, j = v - i * NSH;
+          if (!a.upper || j >= i) Ao[a_pos(i, j, NSH, a.upper)] = fst ? 0.f : A[v];
+        } else {
+          bo[v - NSH * NSH] = fst ? 0.f : A[v];
+        }
+      }
+      if (g == 0) a.status[e] = fst;
+    }
+  }
+}
+
+// Below this many elements the batch fills little of the GPU with one
+// thread per element, and eight lanes per element finish sooner.
+constexpr int64_t kP1SmallBatch = 16384;
+
 fei_status launch_p1(const FwdArgs &a, int64_t grid_work, cudaStream_t s, int64_t grid_cap) {
+  if (!a.count && grid_work <= kP1SmallBatch) {
+    int64_t blocks = (grid_work * 8 + kP1Threads - 1) / kP1Threads;
+    if (grid_cap > 0 && blocks > grid_cap) blocks = grid_cap;
+    cc_p1_small_kernel<<<(unsigned)blocks, kP1Threads, 0, s>>>(a);
+    FEI_CUDA_TRY(cudaGetLastError(), "cc_p1_small_kernel launch");
+    return FEI_OK;
+  }
   int64_t blocks = (grid_work + kP1Threads - 1) / kP1Threads;
   const int64_t cap = grid_cap > 0 ? grid_cap : (a.count ? 152 * 8 : 0);
   if (cap > 0 && blocks > cap) blocks = cap;

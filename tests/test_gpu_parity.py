@@ -489,3 +489,36 @@ def test_p5_per_point_gradients_match_central_differences(api, bprec):
         if auto is not None:
             got_a = float(auto.grad[idx])
             assert abs(got_a - fd) <= tol * max(abs(fd), 1e-2 * scale), ("autograd", name, idx, got_a, fd)
+
+
+@pytest.mark.parametrize("upper", [False, True])
+def test_p1_small_and_large_batches_give_the_same_bits(api, upper):
+    """At p = 1 the FP32 path runs eight lanes per element for small batches
+    and one thread per element for large ones; both give the same bits (the
+    host-memory entry cuts a batch into chunks of any size), and the oracle
+    agrees with both."""
+    w = inputs.workload("p1m", n_max=20000)
+    if upper:
+        K = np.asarray(w["K"]).reshape(-1, 3, 3)
+        w = dict(w, K=np.ascontiguousarray((0.5 * (K + np.swapaxes(K, 1, 2))).reshape(w["K"].shape)),
+                 b=np.zeros_like(w["b"]))
+    big = api.fei_integrate(dev(w["geom"]), dev(w["K"]), dev(w["b"]), dev(w["c"]), dev(w["f"]), p=1,
+                            precision="fp32", upper=upper)
+    m = 3001
+    small = api.fei_integrate(dev(w["geom"][:m]), dev(w["K"][:m]), dev(w["b"][:m]), dev(w["c"][:m]),
+                              dev(w["f"][:m]), p=1, precision="fp32", upper=upper)
+    torch.cuda.synchronize()
+    s = api.a_size(1, upper)
+    Ab, bb, sb = (x.cpu().numpy() for x in big[:3])
+    As, bs, ss = (x.cpu().numpy() for x in small[:3])
+    assert not sb.any() and not ss.any()
+    assert np.array_equal(As.view(np.uint8), Ab[:m * s].view(np.uint8))
+    assert np.array_equal(bs.view(np.uint8), bb[:m * 6].view(np.uint8))
+    idx = np.array([0, 1234, 3000])
+    Ao, bo, so, _ = oracle.integrate(w["geom"][idx], w["K"][idx], w["b"][idx], w["c"][idx], w["f"][idx], p=1)
+    full = As.reshape(m, s).astype(np.float64)
+    if upper:
+        full = api.unpack_upper(full, 1).reshape(m, 36)
+    for k, e in enumerate(idx):
+        ref = Ao[36 * k:36 * (k + 1)]
+        assert np.linalg.norm(full[e] - ref) <= 1e-6 * np.linalg.norm(ref)
