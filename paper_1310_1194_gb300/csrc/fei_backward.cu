@@ -49,7 +49,7 @@ struct BwdCfg {
   static constexpr size_t OFF_END = ((OFF_GSF + sizeof(T) * NQ + 15) / 16) * 16;
   // the sums over points reuse the dynamic area: per warp 35 values x 32
   // lanes (rows padded to 33) in FP64
-  static constexpr size_t RED_BYTES = sizeof(double) * 8 * 35 * 33;
+  static constexpr size_t RED_BYTES = F32 ? sizeof(float) * 35 * 256 : sizeof(double) * 8 * 35 * 33;
   static constexpr size_t SMEM = OFF_END > RED_BYTES ? OFF_END : RED_BYTES;
 };
 
@@ -80,6 +80,197 @@ __device__ __forceinline__ bool load_coef_b(const BwdArgs &a, int64_t r, double 
   cd[13] = a.f[r];
   ok &= finite64(cd[12]) && finite64(cd[13]);
   return ok;
+}
+
+// An FP32 value as FP64, exactly, by moving its fields (normal numbers;
+// zero, subnormals, infinities and NaN through the conversion instruction):
+// integer work instead of this part's slow FP64 pipe.
+__device__ __forceinline__ double f32_to_f64(float x) {
+  const uint32_t u = __float_as_uint(x), ex = (u >> 23) & 0xffu;
+  if (ex == 0u || ex == 0xffu) return (double)x;
+  const uint32_t hi = (u & 0x80000000u) | ((ex + 896u) << 20) | ((u & 0x7fffffu) >> 3);
+  return __hiloint2double((int)hi, (int)((u & 7u) << 29));
+}
+// (s, e) with s + e = a + b exactly (Knuth's two-sum), FP32.
+__device__ __forceinline__ float2 two_sum_f(float a, float b) {
+  const float s = a + b, bb = s - a;
+  return make_float2(s, (a - (s - bb)) + (b - bb));
+}
+// x + y for unevaluated FP32 pairs (hi, lo), normalised.
+__device__ __forceinline__ float2 add_pair_f(float2 x, float2 y) {
+  const float2 s = two_sum_f(x.x, y.x);
+  const float lo = s.y + x.y + y.y;
+  const float hi = s.x + lo;
+  return make_float2(hi, lo - (hi - s.x));
+}
+
+// The chain of the FP32 adjoint to the coefficients and the vertices, one
+// thread per point (two at p >= 6), from dL/dDt (gD) and dL/d(w det J f)
+// (gsf) of every point.  det J and w det J come from the FP64 node columns;
+// the rest runs in FP32 (the contraction that produced gD is FP32 too).
+// The sums over points of the 21 element-vector and 14 coefficient
+// gradients: each thread adds its points' terms in FP32, then the 256
+// partial sums of each value are added as unevaluated FP32 pairs
+// (two-sum, 2^-44 relative), in a fixed order, and stored in sm as FP64.
+template <int P>
+__device__ __forceinline__ void chain_f32(const BwdArgs &a, BwdStatic &sm, const float *gD, const float *gsf,
+                                          int64_t qoff, float *red) {
+  constexpr int NQ = nq_of(P), NT = (P + 1) * (P + 1);
+  const int tid = threadIdx.x;
+  float acc[35];
+#pragma unroll
+  for (int k = 0; k < 35; ++k) acc[k] = 0.f;
+  int pst = 0;
+  const bool perq = a.coef_mode == FEI_COEF_PER_POINT;
+  for (int q = tid; q < NQ; q += 256) {
+    const int iz = q / NT, t = q - iz * NT;
+    const double *c1 = sm.zc1[iz], *c2 = sm.zc2[iz], *n3 = sm.zn3[iz], *c3 = sm.tc3[t];
+    const double w64 = sm.zw[iz] * sm.tw[t];
+    const double det64 = dot3(n3, c3);
+    const double s64 = w64 * det64;
+    pst = merge_status(pst, point_status(s64));
+    double cq[14];
+    const double *cp = sm.cd;
+    if (perq) {
+      if (!load_coef_b(a, qoff + q, cq)) pst = FEI_ERR_NONFINITE;
+      cp = cq;
+    }
+    float K[9], bvec[3];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) K[k] = (float)cp[k];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) bvec[k] = (float)cp[9 + k];
+    const float cc = (float)cp[12], ff = (float)cp[13];
+    float adj[3][3], cx1[3], cx2[3], cx3[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      cx1[k] = (float)c1[k];
+      cx2[k] = (float)c2[k];
+      cx3[k] = (float)c3[k];
+      adj[2][k] = (float)n3[k];
+    }
+    cross3(cx2, cx3, adj[0]);
+    cross3(cx3, cx1, adj[1]);
+    const float gD00 = gD[q * 16 + 0];
+    float gD0[3], gDm[3][3];
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+      gD0[l] = gD[q * 16 + 1 + l];
+#pragma unroll
+      for (int m = 0; m < 3; ++m) gDm[l][m] = gD[q * 16 + 4 * (l + 1) + (m + 1)];
+    }
+    const float gs = gsf[q];
+    const float w = (float)w64, det = (float)det64, s = (float)s64;
+    const float wd = w / det, wdd = wd / det;
+    float Ka[3][3], Kta[3][3];
+#pragma unroll
+    for (int m = 0; m < 3; ++m)
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        Ka[m][r] = K[3 * r] * adj[m][0] + K[3 * r + 1] * adj[m][1] + K[3 * r + 2] * adj[m][2];
+        Kta[m][r] = K[r] * adj[m][0] + K[3 + r] * adj[m][1] + K[6 + r] * adj[m][2];
+      }
+    float U[3][3], V[3][3], Tm[3][3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        U[r][k] = gDm[r][0] * Ka[0][k] + gDm[r][1] * Ka[1][k] + gDm[r][2] * Ka[2][k];
+        V[r][k] = gDm[0][r] * Kta[0][k] + gDm[1][r] * Kta[1][k] + gDm[2][r] * Kta[2][k];
+        Tm[r][k] = gDm[r][0] * adj[0][k] + gDm[r][1] * adj[1][k] + gDm[r][2] * adj[2][k];
+      }
+    // coefficient gradients at this point: dL/dK = (w / det) adj^T gDm adj,
+    // dL/db = w adj^T gD0, dL/dc = w det gD00, dL/df = w det gs
+    float gco[14];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        gco[3 * r + c] = wd * (adj[0][r] * Tm[0][c] + adj[1][r] * Tm[1][c] + adj[2][r] * Tm[2][c]);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) gco[9 + k] = w * (gD0[0] * adj[0][k] + gD0[1] * adj[1][k] + gD0[2] * adj[2][k]);
+    gco[12] = s * gD00;
+    gco[13] = s * gs;
+    if (perq) {
+      const int64_t r = qoff + q;
+#pragma unroll
+      for (int k = 0; k < 9; ++k) a.gK[9 * r + k] = f32_to_f64(gco[k]);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) a.gbc[3 * r + k] = f32_to_f64(gco[9 + k]);
+      a.gc[r] = f32_to_f64(gco[12]);
+      a.gf[r] = f32_to_f64(gco[13]);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 14; ++k) acc[21 + k] += gco[k];
+    }
+    // through det J and the adjugate rows: with the quadratic form
+    // sum_lm gDm[l][m] adj_l K adj_m^T = sum_{l,r} adj[l][r] U[l][r]
+    float quad = 0.f;
+#pragma unroll
+    for (int l = 0; l < 3; ++l) quad += adj[l][0] * U[l][0] + adj[l][1] * U[l][1] + adj[l][2] * U[l][2];
+    const float gdet = w * (cc * gD00 + ff * gs) - wdd * quad;
+    float gadj[3][3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) gadj[r][k] = w * gD0[r] * bvec[k] + wd * (U[r][k] + V[r][k]);
+    float gc1[3] = {0, 0, 0}, gc2[3] = {0, 0, 0}, gc3[3], tmp[3], gn3[3];
+    cross3(cx3, gadj[0], gc2);  // adj0 = c2 x c3
+    cross3(gadj[0], cx2, gc3);
+    cross3(cx1, gadj[1], tmp);  // adj1 = c3 x c1
+#pragma unroll
+    for (int k = 0; k < 3; ++k) gc3[k] += tmp[k];
+    cross3(gadj[1], cx3, gc1);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      gn3[k] = gadj[2][k] + gdet * cx3[k];  // adj2 = n3, det = n3 . c3
+      gc3[k] += gdet * adj[2][k];
+    }
+    cross3(cx2, gn3, tmp);  // n3 = c1 x c2
+#pragma unroll
+    for (int k = 0; k < 3; ++k) gc1[k] += tmp[k];
+    cross3(gn3, cx1, tmp);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) gc2[k] += tmp[k];
+    const float z = (float)sm.zz[iz], x1 = (float)sm.txi[t][0], x2 = (float)sm.txi[t][1];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      acc[0 + k] += gc1[k];
+      acc[3 + k] += z * gc1[k];
+      acc[6 + k] += gc2[k];
+      acc[9 + k] += z * gc2[k];
+      acc[12 + k] += gc3[k];
+      acc[15 + k] += x1 * gc3[k];
+      acc[18 + k] += x2 * gc3[k];
+    }
+  }
+  if (pst) atomicMax(&sm.status, pst);
+  __syncthreads();  // every point's dL/dDt has been read: the area is free
+  // red [35][256]: each thread's partial sums
+#pragma unroll
+  for (int k = 0; k < 35; ++k) red[k * 256 + tid] = acc[k];
+  __syncthreads();
+  // value k = pass * 32 + tid / 8: eight lanes add 32 partials each as
+  // FP32 pairs, then combine across the eight lanes (fixed order)
+  const int nval = a.coef_mode == FEI_COEF_PER_ELEMENT ? 35 : 21;
+  for (int pass = 0; pass < 2; ++pass) {
+    const int k = pass * 32 + (tid >> 3), sub = tid & 7;
+    float2 v = make_float2(0.f, 0.f);
+    if (k < nval) {
+      for (int j = 0; j < 32; ++j) v = add_pair_f(v, make_float2(red[k * 256 + sub + 8 * j], 0.f));
+    }
+#pragma unroll
+    for (int off = 4; off >= 1; off >>= 1) {
+      const float2 o = make_float2(__shfl_xor_sync(0xffffffffu, v.x, off), __shfl_xor_sync(0xffffffffu, v.y, off));
+      v = add_pair_f(v, o);
+    }
+    if (k < nval && sub == 0) {
+      const double d = f32_to_f64(v.x) + f32_to_f64(v.y);
+      if (k < 21) sm.gev[k] = d;
+      else sm.gcoef[k - 21] = d;
+    }
+  }
+  __syncthreads();
 }
 
 template <typename T, int P, bool Q>
@@ -254,6 +445,9 @@ __global__ void __launch_bounds__(256, 2) cc_backward_kernel(BwdArgs a) {
 
     }  // !Q
 
+    if constexpr (C::F32) {
+      chain_f32<P>(a, sm, gD, gsf, qoff, reinterpret_cast<float *>(dsm));
+    } else {
     // The chain to the coefficients and the vertices, one thread per point.
     // det J, w det J, w / det J and the sums over points are FP64; the 3 x 3
     // products that carry dL/dDt through the adjugate run in the contraction's
@@ -426,6 +620,7 @@ __global__ void __launch_bounds__(256, 2) cc_backward_kernel(BwdArgs a) {
       else sm.gcoef[tid - 21] = v;
     }
     __syncthreads();
+    }
     const int st = sm.status;
     // element vectors -> vertices (transpose of elem_vectors)
     if (tid < 3) {
