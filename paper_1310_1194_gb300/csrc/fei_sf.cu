@@ -252,14 +252,14 @@ template <int P>
 struct SfCfg {
   static constexpr int M = P + 1, T = (P + 1) * (P + 2) / 2, NSH = nsh_of(P), NQ = nq_of(P), NT2 = M * M;
   static constexpr int MZ = sf_mz(P);  // a node index padded for 16-byte loads
-  static constexpr int NTH = P >= 6 ? 512 : 256;
+  static constexpr int NTH = P >= 7 ? 512 : P == 6 ? 416 : 256;
   // blocks per SM the register budget is set for: several small elements
   // in flight per SM hide the latency of each one's short stages
   static constexpr int MINB = P <= 5 ? 3 : 1;
   static constexpr int TT = T * T;
   static constexpr int NPR = (TT + NTH - 1) / NTH;  // stage-3 (t, t') pairs per thread
   // stage 2: each thread a BR x BC block of (t, t') pairs sharing (m(t), m(t'))
-  static constexpr int BR = P >= 7 ? 2 : 1, BC = (P == 5 || P >= 6) ? 2 : 1;
+  static constexpr int BR = P >= 6 ? 2 : 1, BC = P >= 5 ? 2 : 1;
   static constexpr int NBLK = [] {
     int a = 0, b = 0;
     for (int m = 0; m < M; ++m) a += (M - m + BR - 1) / BR, b += (M - m + BC - 1) / BC;
