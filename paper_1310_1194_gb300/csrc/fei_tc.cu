@@ -162,6 +162,13 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t
                : "memory");
 }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// 8-byte asynchronous copy global -> shared (cp.async, both 8-byte aligned);
+// complete for this thread after cp_async_wait_all
+__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 // shared -> global bulk copy (16-byte aligned addresses, size a multiple of 16)
 __device__ __forceinline__ void bulk_s2g(void *dst, uint32_t src, uint32_t bytes) {
   asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(src), "r"(bytes)
@@ -175,22 +182,34 @@ __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wa
 __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_commit(uint32_t mbar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
-}
-// KD = 0: kind::f16 (fp16 A and B), KD = 1: kind::tf32.
+// MMAs and commits are executed by the whole warp and issued by one
+// elected lane (elect.sync elects the lowest active lane, the same lane each
+// time, so that its commits track all of these MMAs).  A warp-uniform MMA
+// loop lets the compiler keep the operands in uniform registers; a loop in
+// lane 0 alone moved them from per-thread registers at every MMA and, next
+// to warps busy with FP32 work, issued one MMA per 3-10 tensor-pipe times.
+// KD = 0: kind::f16 (fp16 A and B), KD = 1: kind::tf32.  A and B from
+// shared memory by descriptor.
 template <int KD>
-__device__ __forceinline__ void tc_mma_ss(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+__device__ __forceinline__ void tc_mma_ss_w(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
   if constexpr (KD == 0)
     asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+        "{\n .reg .pred p, e;\n setp.ne.b32 p, %4, 0;\n elect.sync _|e, 0xffffffff;\n"
+        " @e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
         "l"(a), "l"(b), "r"(idesc), "r"(acc)
         : "memory");
   else
     asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+        "{\n .reg .pred p, e;\n setp.ne.b32 p, %4, 0;\n elect.sync _|e, 0xffffffff;\n"
+        " @e tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
         "l"(a), "l"(b), "r"(idesc), "r"(acc)
         : "memory");
+}
+__device__ __forceinline__ void tc_commit_w(uint32_t mbar) {
+  asm volatile(
+      "{\n .reg .pred e;\n elect.sync _|e, 0xffffffff;\n"
+      " @e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n}\n" ::"r"(mbar)
+      : "memory");
 }
 // x rounded to TF32 (10 fraction bits, nearest, ties away), as FP32 bits
 __device__ __forceinline__ uint32_t tf32_rna(float x) {
@@ -202,15 +221,17 @@ __device__ __forceinline__ uint32_t tf32_rna(float x) {
 // row; two consecutive fp16 K values, or one TF32 value, per 32-bit column),
 // B from shared memory by descriptor.
 template <int KD>
-__device__ __forceinline__ void tc_mma_ts(uint32_t d, uint32_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+__device__ __forceinline__ void tc_mma_ts_w(uint32_t d, uint32_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
   if constexpr (KD == 0)
     asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d),
+        "{\n .reg .pred p, e;\n setp.ne.b32 p, %4, 0;\n elect.sync _|e, 0xffffffff;\n"
+        " @e tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d),
         "r"(a), "l"(b), "r"(idesc), "r"(acc)
         : "memory");
   else
     asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d),
+        "{\n .reg .pred p, e;\n setp.ne.b32 p, %4, 0;\n elect.sync _|e, 0xffffffff;\n"
+        " @e tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d),
         "r"(a), "l"(b), "r"(idesc), "r"(acc)
         : "memory");
 }
@@ -312,7 +333,7 @@ struct TcCfg {
   static constexpr int TMEM_COLS = TS ? 512 : (3 * NPAD <= 256 ? 256 : 512);
   static constexpr int EMAX = (128 + NSH - 1) / NSH + 1;  // elements a tile can touch
   static constexpr int NSLOT = EMAX + 1;  // element slots: a tile's elements plus the one it shares
-  static constexpr int NDW = P == 7 ? 2 : P == 6 || P == 5 ? 4 : 6;  // point-operator warps
+  static constexpr int NDW = P == 7 ? 2 : P == 6 || P == 5 ? 4 : V == 1 ? 6 : 8;  // point-operator warps
   static constexpr int NPW = V == 1 ? 16 : 8;  // producer warps
   static constexpr int NEW = 4;  // epilogue warps
   static constexpr int W_DW = 2, W_PW = W_DW + NDW, W_EW = W_PW + NPW;
@@ -398,6 +419,11 @@ struct TcAux {
   uint64_t full[C::STAGES];   // producers wrote A of the stage
   uint64_t bfull[C::STAGES];  // B of the stage landed
   uint64_t empty[C::STAGES];  // MMAs of the stage completed
+  // GS: the table rows of a stage have their own hand-off, released by the
+  // producers once they have read them, so that the next chunk's rows are
+  // copied while the MMAs of this one still run
+  uint64_t gfull[C::STAGES];   // table rows of the stage landed
+  uint64_t gempty[C::STAGES];  // producers done with them
   uint64_t dfull[C::DRING];   // point operators of a chunk ready
   uint64_t dempty[C::DRING];  // producers done with them
   uint64_t part_full[3];      // partial accumulator ready for promotion
@@ -414,12 +440,18 @@ struct TcAux {
   float2 ttab[C::NT][3];     // (w_t, w_t xi1, w_t xi2) per triangle node: FP64 as FP32 hi + lo
   float ttabf[C::NT][3];     // (w_t, xi1, xi2) in FP32
   float ztabf[C::NZ][2];     // (zeta, w_z) in FP32
+  float2 ztab2[C::NZ][2];    // (zeta, w_z) as FP32 hi + lo
+  // inputs of the next tile's first new element of each point-operator warp
+  // (copied with cp.async while the current tile is processed)
+  double pf_buf[C::NDW][32];
   // point operators of a chunk, [tile-relative element][k'][point pair]:
   // float4 k' of pair (q, q+1) is (c_2k'(q), c_2k'(q+1), c_2k'+1(q),
   // c_2k'+1(q+1)) for the 14 values c_0..c_13 of a point (Dt by rows, then
   // w det J f), i.e. the pairs the producers feed to packed FP32 FMAs;
-  // consecutive pairs are consecutive 16-byte words (broadcast loads)
-  float4 Dc[C::DRING][C::EMAX][7][C::PP];
+  // consecutive pairs are consecutive 16-byte words (broadcast loads); one
+  // word of padding per element, so that a warp whose rows span two
+  // elements reads their words from different banks
+  float4 Dc[C::DRING][C::EMAX][7 * C::PP + 1];
   TcMeta meta[2];
   float bsum[2][C::PP][128];
   alignas(16) float stg[C::NEW][32][17];  // epilogue transpose staging
@@ -555,6 +587,8 @@ __global__ void __launch_bounds__(TcCfg<P, V, KD>::NTHREADS, 1)
       mbar_init(smem_u32(&ax.full[s]), C::NPW);
       mbar_init(smem_u32(&ax.bfull[s]), 1);
       mbar_init(smem_u32(&ax.empty[s]), 1);
+      mbar_init(smem_u32(&ax.gfull[s]), 1);
+      mbar_init(smem_u32(&ax.gempty[s]), C::NPW);
     }
     for (int k = 0; k < DR; ++k) {
       mbar_init(smem_u32(&ax.dfull[k]), 1);
@@ -592,6 +626,8 @@ __global__ void __launch_bounds__(TcCfg<P, V, KD>::NTHREADS, 1)
   for (int z = tid; z < NZ; z += blockDim.x) {
     ax.ztabf[z][0] = (float)a.znode[2 * z];
     ax.ztabf[z][1] = (float)a.znode[2 * z + 1];
+    ax.ztab2[z][0] = split_f64(a.znode[2 * z]);
+    ax.ztab2[z][1] = split_f64(a.znode[2 * z + 1]);
   }
   tc_fence_before();
   __syncthreads();
@@ -620,17 +656,18 @@ __global__ void __launch_bounds__(TcCfg<P, V, KD>::NTHREADS, 1)
     // loaded while the current tile's point operators are formed (lanes
     // 0-17 a vertex coordinate, 18-31 a per-element coefficient)
     int64_t pf_k = -1;
-    double pf_x = 0.0;
-    auto fetch_input = [&](int64_t k) {
+    double *const pf_slot = &ax.pf_buf[warp - C::W_DW][lane];
+    // this lane's input of work item k (null: none)
+    auto input_ptr = [&](int64_t k) -> const double * {
       const int64_t e = a.list ? (int64_t)a.list[k] : k;
-      double x = 0.0;
-      if (lane < 18) {
-        x = a.geom[18 * e + lane];
-      } else if (a.coef_mode == FEI_COEF_PER_ELEMENT) {
-        const int j = lane - 18;
-        x = j < 9 ? a.K[9 * e + j] : j < 12 ? a.b[3 * e + (j - 9)] : j == 12 ? a.c[e] : a.f[e];
-      }
-      return x;
+      if (lane < 18) return a.geom + 18 * e + lane;
+      if (a.coef_mode != FEI_COEF_PER_ELEMENT) return nullptr;
+      const int j = lane - 18;
+      return j < 9 ? a.K + 9 * e + j : j < 12 ? a.b + 3 * e + (j - 9) : j == 12 ? a.c + e : a.f + e;
+    };
+    auto fetch_input = [&](int64_t k) {
+      const double *src = input_ptr(k);
+      return src ? *src : 0.0;
     };
     for (int64_t tile = t_begin; tile < t_end; ++tile, ++it) {
       // the point-operator warps leave together (they share named barriers)
@@ -658,18 +695,26 @@ __global__ void __launch_bounds__(TcCfg<P, V, KD>::NTHREADS, 1)
         const int64_t e = a.list ? (int64_t)a.list[kn0 + i] : kn0 + i;
         // geometry (lanes 0-17) and per-element coefficients (lanes 18-31),
         // prefetched during the previous tile when this warp knew the element
-        const double x = pf_k == kn0 + i ? pf_x : fetch_input(kn0 + i);
+        double x;
+        if (pf_k == kn0 + i) {
+          cp_async_wait_all();
+          x = *pf_slot;
+        } else {
+          x = fetch_input(kn0 + i);
+        }
         const bool ok = __all_sync(0xffffffffu, finite64(x));
         // upper layout: a symmetric K (K01 = K10, K02 = K20, K12 = K21: lanes
         // 19/21, 20/24, 23/25) and b = 0 (lanes 27-29) in the element's record
+        // (compared on the bits, +0 and -0 equal)
         bool sym = true;
         if (a.upper && a.coef_mode == FEI_COEF_PER_ELEMENT) {
           const int c = lane - 18;
           const int partner = c == 1 ? 21 : c == 3 ? 19 : c == 2 ? 24 : c == 6 ? 20 : c == 5 ? 25 : c == 7 ? 23 : lane;
-          const double xp = __shfl_sync(0xffffffffu, x, partner);
-          sym = __all_sync(0xffffffffu, (c >= 9 && c <= 11) ? x == 0.0 : x == xp);
+          const unsigned long long xb = (unsigned long long)__double_as_longlong(x);
+          const unsigned long long pb = __shfl_sync(0xffffffffu, xb, partner);
+          sym = __all_sync(0xffffffffu, (c >= 9 && c <= 11) ? (xb << 1) == 0ull : (xb == pb || ((xb | pb) << 1) == 0ull));
         }
-        if (lane >= 18 && a.coef_mode == FEI_COEF_PER_ELEMENT) E.cf[lane - 18] = (float)x;
+        if (lane >= 18 && a.coef_mode == FEI_COEF_PER_ELEMENT) E.cf[lane - 18] = f64_to_f32_bits(x);
         if (lane == 0) {
           E.e = e;
           E.aoff = out_a(a, kn0 + i, e, NSH);
@@ -678,39 +723,66 @@ __global__ void __launch_bounds__(TcCfg<P, V, KD>::NTHREADS, 1)
           E.status = ok ? (sym ? 0 : FEI_ERR_INVALID_ARG) : FEI_ERR_NONFINITE;
           E.mbits = 0;
         }
-        // element vectors A1, B1, A2, B2, C, D1, D2 (FP64): lane j < 21 forms
+        // Element vectors A1, B1, A2, B2, C, D1, D2: lane j < 21 forms
         // component k = j % 3 of vector j / 3 as (X_a - X_b) +- (X_c - X_d)
-        // over vertices a, b, c, d, halved, from the lanes holding them
-        double ev;
-        {
-          const int v = lane < 21 ? lane / 3 : 0, k = lane < 21 ? lane % 3 : 0;
-          // vertices (a, b, c, d) of vector v, 3 bits each, 12 bits per
-          // vector, in an immediate (a table in memory would be a local load)
-          //   A1 (1,0,4,3)  B1 (4,3,1,0)  A2 (2,0,5,3)  B2 (5,3,2,0)
-          //   C  (3,0,0,0)  D1 (4,1,3,0)  D2 (5,2,3,0)
-          constexpr unsigned long long kTab =
-              (0x223ull << 0) | (0x8C8ull << 12) | (0x42Bull << 24) | (0xAD0ull << 36) | (0x600ull << 48);
-          constexpr unsigned long long kTab2 = (0x858ull << 0) | (0xA98ull << 12);  // D1, D2
-          constexpr unsigned kNeg = 0x6Au;  // B1, B2, D1, D2 subtract
-          const unsigned tv = (unsigned)((v < 5 ? kTab >> (12 * v) : kTab2 >> (12 * (v - 5))) & 0xFFFu);
-          const double xa = __shfl_sync(0xffffffffu, x, 3 * ((tv >> 9) & 7u) + k);
-          const double xb = __shfl_sync(0xffffffffu, x, 3 * ((tv >> 6) & 7u) + k);
-          const double xc = __shfl_sync(0xffffffffu, x, 3 * ((tv >> 3) & 7u) + k);
-          const double xd = __shfl_sync(0xffffffffu, x, 3 * (tv & 7u) + k);
-          const double t1 = xa - xb, t2 = xc - xd;
-          ev = 0.5 * (((kNeg >> v) & 1u) ? t1 - t2 : t1 + t2);
-          if (lane < 21) E.evf[lane] = (float)ev;
-        }
-        // vertical nodes (lanes 3 iz + k): c1, c2 and n3 = c1 x c2 in FP64 and
-        // w_z (n3.C, n3.D1, n3.D2), so that w det J = w_t (..) is FP64; the
-        // FP32 columns and their norms from the FP32 element vectors
-        {
-          const bool act = lane < 3 * NZ;
-          const int iz = act ? lane / 3 : 0, k = act ? lane % 3 : 0;
+        // over vertices a, b, c, d, halved, from the lanes holding them.
+        // Vertical nodes (lanes 3 iz + k): c1, c2, n3 = c1 x c2 and w_z (n3.C,
+        // n3.D1, n3.D2), from which w det J = w_t (..) follows at every point.
+        // The vertex differences in FP64 (two independent subtractions, exact
+        // to 2^-53 of the difference however far the element is from the
+        // origin), split from their bit fields into FP32 pairs; the rest in
+        // double-FP32 arithmetic (two-sum and FMA products, about 2^-46
+        // relative): a dependent FP64 instruction takes hundreds of cycles on
+        // this part, an FP32 one a few.  Differences outside 2^-60 <= |d| <
+        // 2^60 (other than 0) take the same steps in FP64.
+        const int v = lane < 21 ? lane / 3 : 0, kv = lane < 21 ? lane % 3 : 0;
+        // vertices (a, b, c, d) of vector v, 3 bits each, 12 bits per
+        // vector, in an immediate (a table in memory would be a local load)
+        //   A1 (1,0,4,3)  B1 (4,3,1,0)  A2 (2,0,5,3)  B2 (5,3,2,0)
+        //   C  (3,0,0,0)  D1 (4,1,3,0)  D2 (5,2,3,0)
+        constexpr unsigned long long kTab =
+            (0x223ull << 0) | (0x8C8ull << 12) | (0x42Bull << 24) | (0xAD0ull << 36) | (0x600ull << 48);
+        constexpr unsigned long long kTab2 = (0x858ull << 0) | (0xA98ull << 12);  // D1, D2
+        constexpr unsigned kNeg = 0x6Au;  // B1, B2, D1, D2 subtract
+        const unsigned tv = (unsigned)((v < 5 ? kTab >> (12 * v) : kTab2 >> (12 * (v - 5))) & 0xFFFu);
+        const int la = 3 * ((tv >> 9) & 7u) + kv, lb = 3 * ((tv >> 6) & 7u) + kv;
+        const int lc = 3 * ((tv >> 3) & 7u) + kv, ld = 3 * (tv & 7u) + kv;
+        const bool subtract = (kNeg >> v) & 1u;
+        const bool act = lane < 3 * NZ;
+        const int iz = act ? lane / 3 : 0, k = act ? lane % 3 : 0;
+        const int g0 = lane - k, l1 = g0 + (k + 1) % 3, l2 = g0 + (k + 2) % 3;
+        const double xa = __shfl_sync(0xffffffffu, x, la), xb = __shfl_sync(0xffffffffu, x, lb);
+        const double xc = __shfl_sync(0xffffffffu, x, lc), xd = __shfl_sync(0xffffffffu, x, ld);
+        const double t1 = xa - xb, t2 = xc - xd;
+        bool r1 = true, r2 = true;
+        const float2 t1s = split_f64_bits(t1, &r1), t2s = split_f64_bits(t2, &r2);
+        float evf;  // the element vector value of this lane in FP32
+        if (__all_sync(0xffffffffu, lane >= 21 || (r1 && r2))) {
+          auto shfl2 = [](float2 q, int src) {
+            return make_float2(__shfl_sync(0xffffffffu, q.x, src), __shfl_sync(0xffffffffu, q.y, src));
+          };
+          float2 ev = norm_ff(add_ff(t1s, subtract ? neg_ff(t2s) : t2s));
+          ev = make_float2(0.5f * ev.x, 0.5f * ev.y);
+          evf = ev.x;
+          const float2 z2 = ax.ztab2[iz][0], wz2 = ax.ztab2[iz][1];
+          const float2 c1 = norm_ff(add_ff(shfl2(ev, k), mul_ff(z2, shfl2(ev, 3 + k))));
+          const float2 c2 = norm_ff(add_ff(shfl2(ev, 6 + k), mul_ff(z2, shfl2(ev, 9 + k))));
+          const float2 c1a = shfl2(c1, l1), c1b = shfl2(c1, l2), c2a = shfl2(c2, l1), c2b = shfl2(c2, l2);
+          const float2 n3 = norm_ff(add_ff(mul_ff(c1a, c2b), neg_ff(mul_ff(c1b, c2a))));  // (c1 x c2)_k
+          float2 ab = mul_ff(n3, shfl2(ev, 12 + k));
+          float2 bb = mul_ff(n3, shfl2(ev, 15 + k));
+          float2 gb = mul_ff(n3, shfl2(ev, 18 + k));
+          ab = norm_ff(add_ff(ab, add_ff(shfl2(ab, l1), shfl2(ab, l2))));
+          bb = norm_ff(add_ff(bb, add_ff(shfl2(bb, l1), shfl2(bb, l2))));
+          gb = norm_ff(add_ff(gb, add_ff(shfl2(gb, l1), shfl2(gb, l2))));
+          // lane k of the node stores value k
+          if (act) E.zabg[iz][k] = norm_ff(mul_ff(wz2, k == 0 ? ab : k == 1 ? bb : gb));
+        } else {
+          const double ev = 0.5 * (subtract ? t1 - t2 : t1 + t2);
+          evf = (float)ev;
           const double z = a.znode[2 * iz], wz = a.znode[2 * iz + 1];
           const double c1 = fma(z, __shfl_sync(0xffffffffu, ev, 3 + k), __shfl_sync(0xffffffffu, ev, k));
           const double c2 = fma(z, __shfl_sync(0xffffffffu, ev, 9 + k), __shfl_sync(0xffffffffu, ev, 6 + k));
-          const int g0 = lane - k, l1 = g0 + (k + 1) % 3, l2 = g0 + (k + 2) % 3;
           const double c1a = __shfl_sync(0xffffffffu, c1, l1), c1b = __shfl_sync(0xffffffffu, c1, l2);
           const double c2a = __shfl_sync(0xffffffffu, c2, l1), c2b = __shfl_sync(0xffffffffu, c2, l2);
           const double n3 = c1a * c2b - c1b * c2a;  // (c1 x c2)_k
@@ -720,9 +792,11 @@ __global__ void __launch_bounds__(TcCfg<P, V, KD>::NTHREADS, 1)
           ab += __shfl_sync(0xffffffffu, ab, l1) + __shfl_sync(0xffffffffu, ab, l2);
           bb += __shfl_sync(0xffffffffu, bb, l1) + __shfl_sync(0xffffffffu, bb, l2);
           gb += __shfl_sync(0xffffffffu, gb, l1) + __shfl_sync(0xffffffffu, gb, l2);
-          // lane k of the node stores value k, split into FP32 hi + lo
           if (act) E.zabg[iz][k] = split_f64(wz * (k == 0 ? ab : k == 1 ? bb : gb));
-          const float evf = (float)ev;
+        }
+        if (lane < 21) E.evf[lane] = evf;
+        // the FP32 node columns and their norms from the FP32 element vectors
+        {
           const float zf = ax.ztabf[iz][0];
           const float f1 = fmaf(zf, __shfl_sync(0xffffffffu, evf, 3 + k), __shfl_sync(0xffffffffu, evf, k));
           const float f2 = fmaf(zf, __shfl_sync(0xffffffffu, evf, 9 + k), __shfl_sync(0xffffffffu, evf, 6 + k));
@@ -841,8 +915,13 @@ __global__ void __launch_bounds__(TcCfg<P, V, KD>::NTHREADS, 1)
         if (k1n > items - 1) k1n = items - 1;
         const int64_t kf = k1 + 1 + (warp - C::W_DW);
         if (kf <= k1n) {
+          // an asynchronous copy: a plain load into a register that lives on
+          // held the warp at the next use of that register
           pf_k = kf;
-          pf_x = fetch_input(kf);
+          const double *src = input_ptr(kf);
+          if (src) cp_async8(pf_slot, src);
+          else *pf_slot = 0.0;
+          cp_async_commit();
         }
       }
       // row data of this tile (double-buffered by tile parity)
@@ -893,7 +972,7 @@ __global__ void __launch_bounds__(TcCfg<P, V, KD>::NTHREADS, 1)
             const TcElem<P> &E = ax.el[sl];
             // value k of this point: float4 k/2 of its pair, component
             // 2 (k % 2) + (the point's position in the pair)
-            float *D1 = reinterpret_cast<float *>(&ax.Dc[dr][el][0][qq >> 1]) + (qq & 1);
+            float *D1 = reinterpret_cast<float *>(&ax.Dc[dr][el][qq >> 1]) + (qq & 1);
             float cv[14];
             if (q < NQ && E.status == 0) {
               float cq[16];
@@ -929,6 +1008,7 @@ __global__ void __launch_bounds__(TcCfg<P, V, KD>::NTHREADS, 1)
         if (td < cn && ok) mbar_arrive(smem_u32(&ax.dfull[(it * NCH + c0 + td) % DR]));
       }
     }
+    cp_async_wait_all();  // a prefetch not consumed (an aborted block) has landed
   } else if (warp >= C::W_PW && warp < C::W_EW && C::TS) {
     // ========================================================= producers (TS)
     // A thread owns one row of the tile (its tensor-memory lane: warp w
@@ -978,18 +1058,18 @@ __global__ void __launch_bounds__(TcCfg<P, V, KD>::NTHREADS, 1)
             gb[j] = __ldg(gp + (size_t)((c * 2 + 1) * C::PP + pp0 + j) * GST + ri);
           }
         }
-        // A columns free (the stage's MMAs completed: with the table in the
-        // stage, its copy landing implies that), point operators ready
+        // point operators ready, the table rows landed (GS) and the A
+        // columns free (the MMAs of the chunk S before completed)
         bool ok = mbar_wait(smem_u32(&ax.dfull[dr]), ud & 1u, abort_flag);
-        if constexpr (C::GS) ok = ok && mbar_wait(smem_u32(&ax.bfull[s]), u & 1u, abort_flag);
-        else ok = ok && mbar_wait(smem_u32(&ax.empty[s]), (u & 1u) ^ 1u, abort_flag);
+        if constexpr (C::GS) ok = ok && mbar_wait(smem_u32(&ax.gfull[s]), u & 1u, abort_flag);
+        ok = ok && mbar_wait(smem_u32(&ax.empty[s]), (u & 1u) ^ 1u, abort_flag);
         ok = __all_sync(0xffffffffu, ok);
         if (!ok) break;
         tc_fence_after();
         const float4 *Gs = reinterpret_cast<const float4 *>(dsm_raw + (stageG(s) - smem_u32(dsm_raw)));
         // a point pair is 8 K values: 4 columns of fp16 pairs, or 8 of TF32
         const uint32_t acol = tmem + lane_base + (uint32_t)(C::ABASE + s * C::ACOLS + pp0 * 8 / C::VPC);
-        const float4 *D4 = &ax.Dc[dr][rel][0][pp0];
+        const float4 *D4 = &ax.Dc[dr][rel][pp0];
         // two pairs at a time: 8 columns of hi and 8 of lo per tcgen05.st
         // (holding all pairs' values until one wider store raised the
         // register peak above the budget)
@@ -1068,6 +1148,7 @@ __global__ void __launch_bounds__(TcCfg<P, V, KD>::NTHREADS, 1)
         __syncwarp();
         if (lane == 0) {
           mbar_arrive(smem_u32(&ax.dempty[dr]));
+          if (C::GS) mbar_arrive(smem_u32(&ax.gempty[s]));
           mbar_arrive(smem_u32(&ax.full[s]));
         }
       }
@@ -1147,12 +1228,11 @@ __global__ void __launch_bounds__(TcCfg<P, V, KD>::NTHREADS, 1)
             gb[k] = __ldg(gp + (size_t)((c * 2 + 1) * C::PP + pp) * GST + ri[k]);
           }
         }
-        // A slot free, point operators ready (and the table chunk landed:
-        // the copy engine fills a stage only after its MMAs completed, so
-        // with the table in the stage that wait also frees the A slot)
+        // point operators ready, the table chunk landed (GS) and the A slot
+        // free (the MMAs of the chunk S before completed)
         bool ok = mbar_wait(smem_u32(&ax.dfull[dr]), ud & 1u, abort_flag);
-        if constexpr (C::GS) ok = ok && mbar_wait(smem_u32(&ax.bfull[s]), u & 1u, abort_flag);
-        else ok = ok && mbar_wait(smem_u32(&ax.empty[s]), (u & 1u) ^ 1u, abort_flag);
+        if constexpr (C::GS) ok = ok && mbar_wait(smem_u32(&ax.gfull[s]), u & 1u, abort_flag);
+        ok = ok && mbar_wait(smem_u32(&ax.empty[s]), (u & 1u) ^ 1u, abort_flag);
         ok = __all_sync(0xffffffffu, ok);
         if (!ok) break;
         if constexpr (!C::GS) {
@@ -1179,7 +1259,7 @@ __global__ void __launch_bounds__(TcCfg<P, V, KD>::NTHREADS, 1)
         for (int k = 0; k < RT; ++k) {
           if (rel[k] != cur) {
             cur = rel[k];
-            const float4 *D4 = &ax.Dc[dr][cur][0][pp];
+            const float4 *D4 = &ax.Dc[dr][cur][pp];
 #pragma unroll
             for (int j = 0; j < 7; ++j) {
               const float4 d = D4[j * C::PP];
@@ -1240,6 +1320,7 @@ __global__ void __launch_bounds__(TcCfg<P, V, KD>::NTHREADS, 1)
         __syncwarp();
         if (lane == 0) {
           mbar_arrive(smem_u32(&ax.dempty[dr]));
+          if (C::GS) mbar_arrive(smem_u32(&ax.gempty[s]));
           mbar_arrive(smem_u32(&ax.full[s]));
         }
       }
@@ -1463,22 +1544,34 @@ __global__ void __launch_bounds__(TcCfg<P, V, KD>::NTHREADS, 1)
         for (int c = 0; c < NCH; ++c) {
           const int g = it * NCH + c, s = g % S;
           const uint32_t u = (uint32_t)(g / S);
+          // the table rows once the producers have read the chunk S before
+          // (they are needed first, and that happens before its MMAs end)
+          if (C::GS) {
+            if (!mbar_wait(smem_u32(&ax.gempty[s]), (u & 1u) ^ 1u, abort_flag)) {
+              ok = false;
+              break;
+            }
+            const uint32_t gbar = smem_u32(&ax.gfull[s]);
+            mbar_expect_tx(gbar, (uint32_t)C::G_BYTES);
+            bulk_g2s(stageG(s), gp + (size_t)c * 2 * C::PP * C::GST, (uint32_t)C::G_BYTES, gbar);
+          }
+          // the B operand once the MMAs of the chunk S before completed
           if (!mbar_wait(smem_u32(&ax.empty[s]), (u & 1u) ^ 1u, abort_flag)) {
             ok = false;
             break;
           }
           const uint32_t bar = smem_u32(&ax.bfull[s]);
-          const uint32_t gbytes = C::GS ? (uint32_t)C::G_BYTES : 0u;
-          mbar_expect_tx(bar, 2u * C::B_BYTES + gbytes);
+          mbar_expect_tx(bar, 2u * C::B_BYTES);
           bulk_g2s(stageB(s), img + (size_t)c * 2 * C::B_BYTES, 2u * C::B_BYTES, bar);
-          if (C::GS) bulk_g2s(stageG(s), gp + (size_t)c * 2 * C::PP * C::GST, gbytes, bar);
         }
         if (!ok) break;
       }
     }
   } else {
     // ================================================================ MMA issue
-    if (lane == 0) {
+    // The whole warp runs the loop and its waits; one elected lane issues
+    // the MMAs and the commits (tc_mma_ts_w, tc_commit_w).
+    {
       constexpr uint32_t IDESC = idesc_mma(128, C::NMMA, KD);
       bool ok = true;
       uint32_t unit = 0;
@@ -1487,20 +1580,21 @@ __global__ void __launch_bounds__(TcCfg<P, V, KD>::NTHREADS, 1)
         for (int c0 = 0; c0 < NCH && ok; c0 += C::UC) {
           const int cn = NCH - c0 < C::UC ? NCH - c0 : C::UC;
           int st[C::UC];
-          for (int j = 0; j < cn && ok; ++j) {
+          for (int j = 0; j < cn; ++j) {
             const int g = it * NCH + c0 + j;
             st[j] = g % S;
             const uint32_t u = (uint32_t)(g / S);
-            ok = mbar_wait(smem_u32(&ax.bfull[st[j]]), u & 1u, abort_flag) &&
+            ok = ok && mbar_wait(smem_u32(&ax.bfull[st[j]]), u & 1u, abort_flag) &&
                  mbar_wait(smem_u32(&ax.full[st[j]]), u & 1u, abort_flag);
           }
+          ok = __all_sync(0xffffffffu, ok);
           if (!ok) break;
           tc_fence_after();
 #pragma unroll
           for (int nh = 0; nh < C::NHALF; ++nh) {
             const uint32_t pb = unit % C::NPART, k = unit / C::NPART;
             ++unit;
-            ok = mbar_wait(smem_u32(&ax.promo_done[pb]), (k & 1u) ^ 1u, abort_flag);
+            ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&ax.promo_done[pb]), (k & 1u) ^ 1u, abort_flag));
             if (!ok) break;
             tc_fence_after();
             const uint32_t d = tmem + pb * C::NMMA;
@@ -1514,9 +1608,9 @@ __global__ void __launch_bounds__(TcCfg<P, V, KD>::NTHREADS, 1)
                 for (int kk = 0; kk < C::KSL; ++kk) {
                   const uint32_t boff = (uint32_t)(nh * C::NMMA * ROWB + kk * 32);
                   const uint64_t Bh = sw_desc<ROWB>(bh + boff), Bl = sw_desc<ROWB>(bl + boff);
-                  tc_mma_ts<KD>(d, ah + kk * 8, Bh, IDESC, (j | kk) != 0);
-                  tc_mma_ts<KD>(d, ah + kk * 8, Bl, IDESC, 1u);
-                  tc_mma_ts<KD>(d, alo + kk * 8, Bh, IDESC, 1u);
+                  tc_mma_ts_w<KD>(d, ah + kk * 8, Bh, IDESC, (j | kk) != 0);
+                  tc_mma_ts_w<KD>(d, ah + kk * 8, Bl, IDESC, 1u);
+                  tc_mma_ts_w<KD>(d, alo + kk * 8, Bh, IDESC, 1u);
                 }
               } else {
                 const uint32_t ah = stageA(st[j], 0), alo = stageA(st[j], 1);
@@ -1525,24 +1619,25 @@ __global__ void __launch_bounds__(TcCfg<P, V, KD>::NTHREADS, 1)
                   const uint32_t boff = (uint32_t)(nh * C::NMMA * ROWB + kk * 32);
                   const uint64_t Ah = sw_desc<ROWB>(ah + kk * 32), Al = sw_desc<ROWB>(alo + kk * 32);
                   const uint64_t Bh = sw_desc<ROWB>(bh + boff), Bl = sw_desc<ROWB>(bl + boff);
-                  tc_mma_ss<KD>(d, Ah, Bh, IDESC, (j | kk) != 0);
-                  tc_mma_ss<KD>(d, Ah, Bl, IDESC, 1u);
-                  tc_mma_ss<KD>(d, Al, Bh, IDESC, 1u);
+                  tc_mma_ss_w<KD>(d, Ah, Bh, IDESC, (j | kk) != 0);
+                  tc_mma_ss_w<KD>(d, Ah, Bl, IDESC, 1u);
+                  tc_mma_ss_w<KD>(d, Al, Bh, IDESC, 1u);
                 }
               }
             }
-            tc_commit(smem_u32(&ax.part_full[pb]));
+            tc_commit_w(smem_u32(&ax.part_full[pb]));
           }
           if (ok)
-            for (int j = 0; j < cn; ++j) tc_commit(smem_u32(&ax.empty[st[j]]));
+            for (int j = 0; j < cn; ++j) tc_commit_w(smem_u32(&ax.empty[st[j]]));
         }
       }
       if (!ok) {
         // make sure no MMA is in flight before the block leaves
-        tc_commit(smem_u32(&ax.drain));
+        tc_commit_w(smem_u32(&ax.drain));
         const uint64_t t0 = global_ns();
         while (!mbar_try_wait(smem_u32(&ax.drain), 0) && global_ns() - t0 < kWaitLimitNs) {
         }
+        __syncwarp();
       }
     }
   }

@@ -522,3 +522,26 @@ def test_p1_small_and_large_batches_give_the_same_bits(api, upper):
     for k, e in enumerate(idx):
         ref = Ao[36 * k:36 * (k + 1)]
         assert np.linalg.norm(full[e] - ref) <= 1e-6 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("precision", ["tc_f16x3", "tc_3xtf32", "fp32"])
+@pytest.mark.parametrize("p", [3, 4])
+def test_far_and_tiny_coordinates(api, p, precision):
+    """Element set-up of the tensor-core path on coordinates that stress
+    it: elements moved 1e4 and 1e6 from the origin (vertex differences far
+    below the coordinates), and elements with an edge of length 1e-20 along
+    one axis (a vertex difference outside the range of the exact FP32 split,
+    so the element takes the FP64 steps) mixed into one batch.  Parity
+    with the oracle at the same bar as the plain workload."""
+    w = workload_for(p, 24)
+    geom = w["geom"].copy().reshape(24, 6, 3)
+    geom[0:8] += np.array([1.0e4, -3.0e4, 2.0e4])
+    geom[8:16] += np.array([-1.0e6, 0.0, 0.5e6])
+    # vertices 0 and 3 (one vertical edge) share x and y, and vertex 3's y
+    # moves by 1e-20: the difference X_3 - X_0 has a y component of 1e-20
+    geom[16:24:2, 3, :2] = geom[16:24:2, 0, :2]
+    geom[16:24:2, 3, 1] += 1e-20 if p == 3 else -1e-20
+    w = dict(w, geom=np.ascontiguousarray(geom.reshape(w["geom"].shape)))
+    ea, eb = compare(api, w, p, precision)
+    assert ea.max() < TOL[precision], (p, precision, ea.max())
+    assert eb.max() < TOL[precision], (p, precision, eb.max())
