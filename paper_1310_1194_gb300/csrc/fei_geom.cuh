@@ -26,6 +26,7 @@
 #pragma once
 
 #include <math.h>
+#include <string.h>
 
 #include "fei_internal.cuh"
 
@@ -140,8 +141,9 @@ __device__ __forceinline__ float2 neg_ff(float2 a) { return make_float2(-a.x, -a
 // only: hi = x with the significand cut to 24 bits (exact), lo = the next
 // 29 bits rounded to 24, so hi + lo = x to 2^-47 relative.  in_range is false
 // (and the pair meaningless) outside 2^-60 <= |x| < 2^60, except x = +-0.
-__device__ __forceinline__ float2 split_f64_bits(double x, bool *in_range) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+__host__ __device__ inline float2 split_f64_bits(double x, bool *in_range) {
+  unsigned long long b;
+  memcpy(&b, &x, 8);
   const unsigned h = (unsigned)(b >> 32), l = (unsigned)b;
   const int E = (int)((h >> 20) & 0x7ffu) - 1023;
   const unsigned sgn = h & 0x80000000u;
@@ -151,24 +153,30 @@ __device__ __forceinline__ float2 split_f64_bits(double x, bool *in_range) {
   }
   *in_range = E >= -60 && E < 60;
   const int ef = *in_range ? E + 127 : 127;
-  const float hi = __uint_as_float(sgn | ((unsigned)ef << 23) | ((h & 0xfffffu) << 3) | (l >> 29));
-  // m[28:0] 2^(E - 52): the 29 low bits as an integer, scaled by 2^-52 and
-  // 2^E (both exact)
-  const float lo = __uint2float_rn(l & 0x1fffffffu) * 2.220446049250313e-16f * __uint_as_float((unsigned)ef << 23);
+  const unsigned hb = sgn | ((unsigned)ef << 23) | ((h & 0xfffffu) << 3) | (l >> 29), sb = (unsigned)ef << 23;
+  float hi, scale;
+  memcpy(&hi, &hb, 4);
+  memcpy(&scale, &sb, 4);
+  // m[28:0] 2^(E - 52): the 29 low bits as an integer (rounded to 24),
+  // scaled by 2^-52 and 2^E (both exact)
+  const float lo = (float)(l & 0x1fffffffu) * 2.220446049250313e-16f * scale;
   return make_float2(hi, sgn ? -lo : lo);
 }
 // FP64 -> FP32 rounded to nearest (ties to even) from the bit fields, for
 // a finite x whose FP32 result is normal or overflows; other magnitudes
 // take the conversion instruction (which runs on the FP64 pipe).
-__device__ __forceinline__ float f64_to_f32_bits(double x) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+__host__ __device__ inline float f64_to_f32_bits(double x) {
+  unsigned long long b;
+  memcpy(&b, &x, 8);
   const unsigned h = (unsigned)(b >> 32), l = (unsigned)b;
   const int e = (int)((h >> 20) & 0x7ffu) - 1023 + 127;
   if (e < 1 || e > 254) return (float)x;
   unsigned r = (h & 0x80000000u) | ((unsigned)e << 23) | ((h & 0xfffffu) << 3) | (l >> 29);
   const unsigned rest = l & 0x1fffffffu;  // the 29 bits cut off
   r += (rest > 0x10000000u || (rest == 0x10000000u && (r & 1u))) ? 1u : 0u;  // a carry raises the exponent
-  return __uint_as_float(r);
+  float f;
+  memcpy(&f, &r, 4);
+  return f;
 }
 // Finite test on the exponent bits of an FP64 value (integer pipe: FP64
 // compares run at the FP64 rate, which is low on this part).

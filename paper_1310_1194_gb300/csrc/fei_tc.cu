@@ -421,9 +421,12 @@ struct TcAux {
   uint64_t empty[C::STAGES];  // MMAs of the stage completed
   // GS: the table rows of a stage have their own hand-off, released by the
   // producers once they have read them, so that the next chunk's rows are
-  // copied while the MMAs of this one still run
-  uint64_t gfull[C::STAGES];   // table rows of the stage landed
-  uint64_t gempty[C::STAGES];  // producers done with them
+  // copied while the MMAs of this one still run.  gfull also takes the
+  // commit of the MMAs of the chunk S before (the A columns free), so the
+  // producers wait on one barrier for both; the copy warp stands in for
+  // that commit at the first use of a stage.
+  uint64_t gfull[C::STAGES];   // table rows of the stage landed, A columns free
+  uint64_t gempty[C::STAGES];  // producers done with the table rows
   uint64_t dfull[C::DRING];   // point operators of a chunk ready
   uint64_t dempty[C::DRING];  // producers done with them
   uint64_t part_full[3];      // partial accumulator ready for promotion
@@ -587,7 +590,7 @@ __global__ void __launch_bounds__(TcCfg<P, V, KD>::NTHREADS, 1)
       mbar_init(smem_u32(&ax.full[s]), C::NPW);
       mbar_init(smem_u32(&ax.bfull[s]), 1);
       mbar_init(smem_u32(&ax.empty[s]), 1);
-      mbar_init(smem_u32(&ax.gfull[s]), 1);
+      mbar_init(smem_u32(&ax.gfull[s]), 2);
       mbar_init(smem_u32(&ax.gempty[s]), C::NPW);
     }
     for (int k = 0; k < DR; ++k) {
@@ -734,7 +737,9 @@ __global__ void __launch_bounds__(TcCfg<P, V, KD>::NTHREADS, 1)
         // double-FP32 arithmetic (two-sum and FMA products, about 2^-46
         // relative): a dependent FP64 instruction takes hundreds of cycles on
         // this part, an FP32 one a few.  Differences outside 2^-60 <= |d| <
-        // 2^60 (other than 0) take the same steps in FP64.
+        // 2^60 (other than 0) take the same steps in FP64.  (The differences
+        // by 64-bit integer arithmetic on the bit fields took longer than the
+        // one FP64 latency.)
         const int v = lane < 21 ? lane / 3 : 0, kv = lane < 21 ? lane % 3 : 0;
         // vertices (a, b, c, d) of vector v, 3 bits each, 12 bits per
         // vector, in an immediate (a table in memory would be a local load)
@@ -1058,11 +1063,11 @@ __global__ void __launch_bounds__(TcCfg<P, V, KD>::NTHREADS, 1)
             gb[j] = __ldg(gp + (size_t)((c * 2 + 1) * C::PP + pp0 + j) * GST + ri);
           }
         }
-        // point operators ready, the table rows landed (GS) and the A
-        // columns free (the MMAs of the chunk S before completed)
+        // point operators ready, the A columns free (the MMAs of the chunk S
+        // before completed) and, with GS, the table rows landed
         bool ok = mbar_wait(smem_u32(&ax.dfull[dr]), ud & 1u, abort_flag);
         if constexpr (C::GS) ok = ok && mbar_wait(smem_u32(&ax.gfull[s]), u & 1u, abort_flag);
-        ok = ok && mbar_wait(smem_u32(&ax.empty[s]), (u & 1u) ^ 1u, abort_flag);
+        else ok = ok && mbar_wait(smem_u32(&ax.empty[s]), (u & 1u) ^ 1u, abort_flag);
         ok = __all_sync(0xffffffffu, ok);
         if (!ok) break;
         tc_fence_after();
@@ -1228,11 +1233,11 @@ __global__ void __launch_bounds__(TcCfg<P, V, KD>::NTHREADS, 1)
             gb[k] = __ldg(gp + (size_t)((c * 2 + 1) * C::PP + pp) * GST + ri[k]);
           }
         }
-        // point operators ready, the table chunk landed (GS) and the A slot
-        // free (the MMAs of the chunk S before completed)
+        // point operators ready, the A slot free (the MMAs of the chunk S
+        // before completed) and, with GS, the table chunk landed
         bool ok = mbar_wait(smem_u32(&ax.dfull[dr]), ud & 1u, abort_flag);
         if constexpr (C::GS) ok = ok && mbar_wait(smem_u32(&ax.gfull[s]), u & 1u, abort_flag);
-        ok = ok && mbar_wait(smem_u32(&ax.empty[s]), (u & 1u) ^ 1u, abort_flag);
+        else ok = ok && mbar_wait(smem_u32(&ax.empty[s]), (u & 1u) ^ 1u, abort_flag);
         ok = __all_sync(0xffffffffu, ok);
         if (!ok) break;
         if constexpr (!C::GS) {
@@ -1552,6 +1557,7 @@ __global__ void __launch_bounds__(TcCfg<P, V, KD>::NTHREADS, 1)
               break;
             }
             const uint32_t gbar = smem_u32(&ax.gfull[s]);
+            if (g < S) mbar_arrive(gbar);  // no MMAs before the first use
             mbar_expect_tx(gbar, (uint32_t)C::G_BYTES);
             bulk_g2s(stageG(s), gp + (size_t)c * 2 * C::PP * C::GST, (uint32_t)C::G_BYTES, gbar);
           }
@@ -1628,7 +1634,10 @@ __global__ void __launch_bounds__(TcCfg<P, V, KD>::NTHREADS, 1)
             tc_commit_w(smem_u32(&ax.part_full[pb]));
           }
           if (ok)
-            for (int j = 0; j < cn; ++j) tc_commit_w(smem_u32(&ax.empty[st[j]]));
+            for (int j = 0; j < cn; ++j) {
+              tc_commit_w(smem_u32(&ax.empty[st[j]]));
+              if (C::GS) tc_commit_w(smem_u32(&ax.gfull[st[j]]));
+            }
         }
       }
       if (!ok) {
