@@ -108,6 +108,14 @@ def bwd_flops_per_element(p):
     return 8 * s * s * q + 34 * s * q + 600 * q
 
 
+def adj_tc_hw_flops(p):
+    """Issued tensor flops of the tensor-core adjoint per element: three
+    products of M = 128-row tiles of (q, b) (ceil(4 N_q / 128) of them),
+    N = N_sh padded to 16 and K = N_sh padded to 32."""
+    s, q = nsh(p), nq(p)
+    return 3 * 2 * ((4 * q + 127) // 128) * 128 * ((s + 15) // 16 * 16) * ((s + 31) // 32 * 32)
+
+
 def quad_bwd_flops_per_element(p):
     """Algorithmic flops of the quadratic-loss adjoint per element: v_q =
     G_q u (8 N_sh N_q), the outer products (16 N_q) and the per-point chain
@@ -402,10 +410,16 @@ def roofline_of(dom, counts, precision, peaks, peak_src, live, Bts, ms_all, p, n
             tpeak, tnote = peaks["bf16_tflops"] * 1.1 / 2.25, f"TF32: bf16 peak ({peak_src}) x nominal 1.1/2.25"
         bound, peak, unit, achieved = "tensor", tpeak / 3, "TFLOP/s", F / (ms * 1e-3) / 1e12
         peak_note = tnote + " / 3"
-        hwF = sum(int(counts[d]) * tc_hw_flops(d, precision) for d in range(3, 8))
+        if dom["kernel"].startswith("adjoint"):
+            hwF = sum(int(counts[d]) * adj_tc_hw_flops(d) for d in range(3, 6))
+            hw_note = ("issued tcgen05 flops of W^T: 3 products x 2 x 128-row tiles of (q, b) x N_sh pad 16 x "
+                       "N_sh pad 32; the time includes the FP32 chain kernel")
+        else:
+            hwF = sum(int(counts[d]) * tc_hw_flops(d, precision) for d in range(3, 8))
+            hw_note = "issued tcgen05 flops: 3 products x 2 x 128-row tiles x N_pad x 4 N_q"
         hw = {"tensor_tflops": hwF / (ms * 1e-3) / 1e12,
               "frac_of_tensor_peak": hwF / (ms * 1e-3) / 1e12 / tpeak,
-              "note": "issued tcgen05 flops: 3 products x 2 x 128-row tiles x N_pad x 4 N_q"}
+              "note": hw_note}
     elif precision == "sf_fp32":
         # the sum-factorised kernel does its own, smaller flop count on the
         # FP32 FMA pipe; the dense contraction's count over the same time is
@@ -430,6 +444,8 @@ def roofline_of(dom, counts, precision, peaks, peak_src, live, Bts, ms_all, p, n
          "hardware": hw}
     if "fwd_ms" in dom:
         r["forward_ms"] = dom["fwd_ms"]
+    if "fp32_adjoint_ms" in dom:
+        r["fp32_cuda_core_adjoint_ms"] = dom["fp32_adjoint_ms"]
     if "adjoint_ms" in dom:
         r["adjoint_ms"] = dom["adjoint_ms"]
         r["adjoint"] = "quadratic loss (gA never formed)"
@@ -505,8 +521,11 @@ def run_workload(name, args, ctx, headline):
             grads = ((uu[:, :, None] * uu[:, None, :]).reshape(-1).to(torch.float32), (-u).to(torch.float32))
         else:
             grads = (u,)
+    # the general adjoint: W = gA G^T on the tensor cores (split fp16) at a
+    # uniform degree 3..5, else the FP32 CUDA-core adjoint
+    bwd_prec = "tc_f16x3" if (grads is not None and len(grads) == 2 and deg is None and p in (3, 4, 5)) else "fp32"
 
-    def step(prec=precision, outs=(A, bv, st), mid=None):
+    def step(prec=precision, outs=(A, bv, st), mid=None, bprec=None):
         if plan is not None and prec == precision:
             plan.execute(g["geom"], g["K"], g["b"], g["c"], g["f"], degree=deg, per_qp=per_qp, layout=layout,
                          out=outs)
@@ -518,7 +537,8 @@ def run_workload(name, args, ctx, headline):
                 mid.record(stream)
             if len(grads) == 2:
                 api.fei_integrate_backward(g["geom"], g["K"], g["b"], g["c"], g["f"], grads[0], grads[1], p=p,
-                                           degree=deg, per_qp=per_qp, precision="fp32", refs=refs, layout=layout)
+                                           degree=deg, per_qp=per_qp, precision=bprec or bwd_prec, refs=refs,
+                                           layout=layout)
             else:
                 api.fei_integrate_backward_quadratic(g["geom"], g["K"], g["b"], g["c"], g["f"], grads[0], p=p,
                                                      degree=deg, per_qp=per_qp, precision="fp32", refs=refs,
@@ -602,8 +622,22 @@ def run_workload(name, args, ctx, headline):
         bwd_ms = statistics.median([mids[k].elapsed_time(evs[k][1]) for k in range(steps)])
         fwd_ms = statistics.median([evs[k][0].elapsed_time(mids[k]) for k in range(steps)])
         if len(grads) == 2:
-            dom = {"kernel": "adjoint (fp32 contraction, fp64 chain)", "ms": bwd_ms,
-                   "F": n * bwd_flops_per_element(p), "precision": "fp32", "counts": counts, "fwd_ms": fwd_ms}
+            kname = ("adjoint (tensor-core W^T = G gA^T in split fp16, FP32 chain)" if bwd_prec == "tc_f16x3"
+                     else "adjoint (FP32 CUDA-core contraction, FP32 chain)")
+            dom = {"kernel": kname, "ms": bwd_ms, "F": n * bwd_flops_per_element(p), "precision": bwd_prec,
+                   "counts": counts, "fwd_ms": fwd_ms}
+            if bwd_prec == "tc_f16x3" and rank == 0:
+                # the FP32 CUDA-core adjoint on the same cotangents, for comparison
+                tb = []
+                for k in range(min(steps, 3)):
+                    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+                    flush.fill_(float(k))
+                    e0.record(stream)
+                    step(mid=e1, bprec="fp32")
+                    e2.record(stream)
+                    torch.cuda.synchronize()
+                    tb.append(e1.elapsed_time(e2))
+                dom["fp32_adjoint_ms"] = statistics.median(tb)
         elif bwd_ms > fwd_ms:
             dom = {"kernel": "quadratic-loss adjoint (fp32 G u, fp64 chain)", "ms": bwd_ms,
                    "F": n * quad_bwd_flops_per_element(p), "precision": "fp32", "counts": counts, "fwd_ms": fwd_ms}

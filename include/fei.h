@@ -213,8 +213,16 @@ fei_status fei_integrate(const fei_reference_t *refs, int nrefs,
  * vertex coordinates g_geom [n_elem][6][3] (FP64) and the coefficients
  * (g_coef, same layout and mode as the inputs, FP64).  Per-point
  * coefficient values are held fixed when differentiating by the geometry.
- * Jacobians are recomputed, not stored.  Precision FEI_FP64 or FEI_FP32
- * (the contraction W = gA G^T in FP64 or FP32; the Jacobian chain in FP64).
+ * Jacobians are recomputed, not stored.  Precision: FEI_FP64 (all FP64);
+ * FEI_FP32 (the contraction W = gA G^T in FP32 on the CUDA cores, the chain
+ * in FP32 with det J from FP64 node sums); FEI_TC_F16X3 or FEI_AUTO with a
+ * uniform degree 3..5: dL/dDt_q = G_q gA G_q^T with W^T = G gA^T on the
+ * tensor cores (each gA row split into fp16 hi + lo with its own
+ * power-of-two scale, three products per K slice) and the FP32 chain, in
+ * chunks of 8192 elements (FEI_ADJOINT_CHUNK in the environment overrides
+ * it) with 64 N_q bytes of scratch per element allocated stream-ordered on
+ * the stream; every other precision and case runs as FEI_FP32.  gA and gb
+ * are FP32 for every precision but FEI_FP64.
  * Elements with a nonzero elem_status from the forward get zero gradients
  * (this call recomputes the status itself).  batch->a_layout must be
  * FEI_A_FULL (FEI_ERR_UNSUPPORTED otherwise). */

@@ -594,7 +594,9 @@ class _IntegrateFn(torch.autograd.Function):
     def backward(ctx, gA, gb, _gst):
         geom, K, bc, c, f = ctx.saved_tensors
         p, degree, per_qp, precision, layout = ctx.cfg
-        bprec = "fp64" if precision == "fp64" else "fp32"
+        # the tensor-core adjoint where the forward ran the split fp16 path
+        # (the library runs it at a uniform degree 3..5, else the FP32 one)
+        bprec = "fp64" if precision == "fp64" else "tc_f16x3" if precision in ("tc_f16x3", "auto") else "fp32"
         dt = torch.float64 if bprec == "fp64" else torch.float32
         gA = torch.zeros(layout.A_total, dtype=dt, device=geom.device) if gA is None else gA.to(dt).contiguous()
         gb = torch.zeros(layout.b_total, dtype=dt, device=geom.device) if gb is None else gb.to(dt).contiguous()

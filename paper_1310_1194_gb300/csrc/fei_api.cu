@@ -436,6 +436,15 @@ namespace {
 
 // Shared by the general adjoint (gA, gb given) and the quadratic-loss
 // adjoint (u given, gA = u u^T and gb = -u implied).
+// elements per launch pair of the tensor-core adjoint (its scratch: 64 N_q
+// bytes per element, 14 MB per 1024 elements at p = 5); FEI_ADJOINT_CHUNK
+// in the environment (a positive integer) overrides it
+int64_t adjoint_chunk() {
+  const char *v = getenv("FEI_ADJOINT_CHUNK");
+  const long long c = v ? atoll(v) : 0;
+  return c > 0 ? (int64_t)c : 8192;
+}
+
 fei_status backward_impl(const char *who, const fei_reference_t *refs, int nrefs, const fei_batch *batch,
                          fei_precision prec, const void *gA, const void *gb, const double *u, double *g_geom,
                          const fei_coef_grad *g_coef, fei_stream_t stream) {
@@ -443,8 +452,11 @@ fei_status backward_impl(const char *who, const fei_reference_t *refs, int nrefs
   const bool quad = u != nullptr;
   fei_status st = check_batch(batch);
   if (st) return st;
-  if (prec != FEI_FP64 && prec != FEI_FP32)
-    return set_error(FEI_ERR_UNSUPPORTED, "%s: precision %d (FP64 or FP32 only)", who, (int)prec);
+  if (!valid_precision(prec)) return set_error(FEI_ERR_INVALID_ARG, "%s: precision %d", who, (int)prec);
+  // FEI_TC_F16X3 (and FEI_AUTO): W on the tensor cores for a uniform degree
+  // 3..5 and the general adjoint; every other case of a precision other
+  // than FEI_FP64 runs the FEI_FP32 adjoint
+  const bool want_tc = prec == FEI_TC_F16X3 || prec == FEI_AUTO;
   if (batch->a_layout != FEI_A_FULL)
     return set_error(FEI_ERR_UNSUPPORTED, "%s: the adjoint takes the full A_e layout", who);
   if (batch->n_elem == 0) return FEI_OK;
@@ -484,6 +496,30 @@ fei_status backward_impl(const char *who, const fei_reference_t *refs, int nrefs
     a.G32 = r->G32;
     a.znode = r->znode;
     a.tnode = r->tnode;
+    if (want_tc && !quad && tc_adjoint_ready(r)) {
+      // dL/dDt of a chunk of elements on the tensor cores into a scratch
+      // array (stream-ordered allocation), then the FP32 chain reads it
+      const int64_t n = batch->n_elem, cmax = adjoint_chunk(), chunk = n < cmax ? n : cmax;
+      float *gDs = nullptr;
+      FEI_CUDA_TRY(cudaMallocAsync((void **)&gDs, sizeof(float) * (size_t)chunk * r->nq * 16, s),
+                   "cudaMallocAsync(adjoint scratch)");
+      for (int64_t e0 = 0; e0 < n && !st; e0 += chunk) {
+        const int64_t cnt = n - e0 < chunk ? n - e0 : chunk;
+        st = launch_tc_adjoint(p, r, reinterpret_cast<const float *>(gA), batch->A_offset, e0, cnt, gDs, s);
+        if (!st) st = debug_check(s, "tensor-core adjoint kernel");
+        if (st) break;
+        BwdArgs ac = a;
+        ac.n_work = cnt;
+        ac.e0 = e0;
+        ac.gDpre = gDs;
+        st = launch_cc_backward(p, false, ac, cnt, s, false);
+        if (!st) st = debug_check(s, "backward kernel");
+      }
+      const cudaError_t fe = cudaFreeAsync(gDs, s);
+      if (st) return st;
+      FEI_CUDA_TRY(fe, "cudaFreeAsync(adjoint scratch)");
+      return FEI_OK;
+    }
     st = launch_cc_backward(p, prec == FEI_FP64, a, batch->n_elem, s, quad);
     return st ? st : debug_check(s, "backward kernel");
   }

@@ -291,7 +291,7 @@ __global__ void __launch_bounds__(256, 2) cc_backward_kernel(BwdArgs a) {
   const int64_t items = a.count ? (int64_t)(*a.count) : a.n_work;
 
   for (int64_t item = blockIdx.x; item < items; item += gridDim.x) {
-    const int64_t e = a.list ? (int64_t)a.list[item] : item;
+    const int64_t e = a.list ? (int64_t)a.list[item] : a.e0 + item;
     const int64_t aoff = a.A_off ? a.A_off[e] : e * (int64_t)(NSH * NSH);
     const int64_t boff = a.b_off ? a.b_off[e] : e * (int64_t)NSH;
     const int64_t qoff = a.q_off ? a.q_off[e] : e * (int64_t)NQ;
@@ -359,8 +359,15 @@ __global__ void __launch_bounds__(256, 2) cc_backward_kernel(BwdArgs a) {
       __syncthreads();
     }
     if constexpr (!Q) {
-    // zero the dL/dDt accumulators; dL/d(w det f) per point
-    for (int k = tid; k < NQ * 16; k += 256) gD[k] = T(0);
+    // zero the dL/dDt accumulators (or take them from the tensor-core
+    // adjoint); dL/d(w det f) per point
+    const bool pre = C::F32 && a.gDpre != nullptr;
+    if (pre) {
+      const float *src = a.gDpre + (size_t)item * NQ * 16;
+      for (int k = tid; k < NQ * 16; k += 256) gD[k] = (T)src[k];
+    } else {
+      for (int k = tid; k < NQ * 16; k += 256) gD[k] = T(0);
+    }
     for (int q = tid; q < NQ; q += 256) {
       T s = T(0);
       for (int i = 0; i < NSH; ++i) s += gbg[boff + i] * Gg[(size_t)(4 * q) * NSH + i];
@@ -369,7 +376,7 @@ __global__ void __launch_bounds__(256, 2) cc_backward_kernel(BwdArgs a) {
     __syncthreads();
 
     // dL/dDt_q = G_q gA G_q^T, row block by row block
-    for (int r0 = 0; r0 < NSH; r0 += BI) {
+    for (int r0 = 0; r0 < (pre ? 0 : NSH); r0 += BI) {
       for (int k = tid; k < BI * NSHP; k += 256) {
         const int ii = k / NSHP, j = k - ii * NSHP;
         gAs[k] = (r0 + ii < NSH && j < NSH) ? gAg[aoff + (int64_t)(r0 + ii) * NSH + j] : T(0);

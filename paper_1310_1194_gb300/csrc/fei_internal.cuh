@@ -104,6 +104,10 @@ struct BwdArgs {
   const void *gA;
   const void *gb;
   const double *u;  // quadratic-loss adjoint: u_e at b_off[e] (else unused)
+  // general adjoint with dL/dDt precomputed (FEI_FP32 chain only): gDpre
+  // [n_work][N_q][16] for the work items, element e0 + item (no list)
+  const float *gDpre;
+  int64_t e0;
   double *g_geom;
   double *gK, *gbc, *gc, *gf;
   const double *G64;
@@ -175,6 +179,12 @@ void free_sf_tables(fei_reference *ref);
 fei_status launch_tc_forward(int p, const fei_reference *ref, const FwdArgs &a, int64_t grid_work,
                              cudaStream_t s, int variant, fei_precision prec);
 int tc_variant_count(int p, fei_precision prec);
+// Tensor-core adjoint (fei_tc.cu, p = 3..5, uniform degree): gD [count][N_q]
+// [16] = dL/dDt_q of the elements e0 .. e0 + count - 1, from gA (FP32, at
+// A_off[e] or e N_sh^2) with W^T = G gA^T on the tensor cores (split fp16).
+bool tc_adjoint_ready(const fei_reference *ref);  // degree 3..5 and its image built
+fei_status launch_tc_adjoint(int p, const fei_reference *ref, const float *gA, const int64_t *A_off, int64_t e0,
+                             int64_t count, float *gD, cudaStream_t s);
 fei_status build_tc_image(fei_reference *ref);
 void free_tc_image(fei_reference *ref);
 

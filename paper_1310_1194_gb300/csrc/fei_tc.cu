@@ -90,6 +90,12 @@ struct TcOperands {
 struct TcImage {
   TcOperands k[2];
   int npad, rowb, tau;
+  // adjoint A operand (p = 3..5): G 2^tau by rows (q, b), K = j, split into
+  // fp16 hi/lo, [M tile][K chunk][hi, lo][128 rows][64 bytes] swizzled
+  unsigned char *aimg;
+  // the FP32 table for the adjoint epilogue: [N_q][N_pad] float4 (G of the
+  // four components a at (q, i)), zero for i >= N_sh
+  float4 *gq4p;
 };
 
 namespace {
@@ -234,6 +240,11 @@ __device__ __forceinline__ void tc_mma_ts_w(uint32_t d, uint32_t a, uint64_t b, 
         " @e tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d),
         "r"(a), "l"(b), "r"(idesc), "r"(acc)
         : "memory");
+}
+// 16 bytes to shared memory at a shared-window address
+__device__ __forceinline__ void st_shared_v4(uint32_t addr, const uint32_t *v) {
+  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3])
+               : "memory");
 }
 // 32 lanes x 8 columns of 32-bit values from registers (thread t = lane t)
 __device__ __forceinline__ void tmem_st8u(uint32_t taddr, const uint32_t *v) {
@@ -1665,6 +1676,366 @@ __global__ void __launch_bounds__(TcCfg<P, V, KD>::NTHREADS, 1)
 }
 
 // ---------------------------------------------------------------------------
+// Tensor-core adjoint: dL/dDt from W^T = G gA^T, element by element
+// ---------------------------------------------------------------------------
+// For one element, W^T[(q,b)][i] = sum_j G[q][b][j] gA[i][j] (the transpose
+// of W = gA G^T of the reverse pass, Sec. 2 with the weak form of Eq. (2)) is
+// a product with M = 4 N_q rows (q, b) of the table (A operand: the same for
+// every element, split G 2^tau streamed by the copy lane), N = N_sh rows of
+// gA (B operand: each row split into fp16 hi/lo with its own power-of-two
+// scale by the producer warps) and K = N_sh (j).  Three products per K slice
+// (hi hi + hi lo + lo hi) into partial accumulators of at most four K slices,
+// as in the forward.  The epilogue thread of TMEM lane (q, b) adds the
+// partials and forms dL/dDt_q[a][b] = sum_i G[q][a][i] W^T[(q,b)][i] from its
+// own columns, so no reduction crosses lanes; the result goes to a scratch
+// array [element][N_q][16] that the chain of the FP32 adjoint reads.
+template <int P>
+struct TaCfg {
+  static constexpr int NSH = nsh_of(P), NQ = nq_of(P);
+  static constexpr int K = (NSH + 31) / 32 * 32;     // K padded to whole 64-byte rows
+  static constexpr int NKC = K / 32;                 // K chunks, one 64-byte row each
+  static constexpr int KS = K / 16;                  // MMA K slices
+  static constexpr int NPAD = (NSH + 15) / 16 * 16;  // MMA N
+  static constexpr int NMT = (4 * NQ + 127) / 128;   // M tiles of 128 rows (q, b)
+  static constexpr int SPP = 4;                      // K slices per partial accumulator
+  static constexpr int NPK = (KS + SPP - 1) / SPP;   // partials per M tile
+  static constexpr int NBUF = 2;                     // accumulator buffers (M tiles in flight)
+  static constexpr int ACC_COLS = NPK * NPAD;
+  static constexpr int TMEM_COLS = NBUF * ACC_COLS <= 32 ? 32 : NBUF * ACC_COLS <= 64 ? 64
+                                   : NBUF * ACC_COLS <= 128 ? 128 : NBUF * ACC_COLS <= 256 ? 256 : 512;
+  static constexpr int A_TILE = 128 * 64;            // hi or lo of one K chunk of an M tile
+  static constexpr int A_STAGE = 2 * A_TILE;
+  static constexpr int NSTG = 4;                     // A stages
+  static constexpr int B_TILE = NPAD * 64;
+  static constexpr int B_BUF = NKC * 2 * B_TILE;     // [K chunk][hi, lo][NPAD rows][64 bytes]
+  static constexpr int NB = 2;                       // B buffers (elements in flight)
+  static constexpr int NRS = 4;                      // row-scale sets (producers run <= 2 elements ahead)
+  static constexpr int DYN_SMEM = NSTG * A_STAGE + NB * B_BUF + 1024;
+  // producer warps; epilogue warps, two per tensor-memory lane quarter,
+  // each pair splitting the columns
+  static constexpr int NPW = 4, NEW = 8;
+  static constexpr int W_PW = 2, W_EW = W_PW + NPW;
+  static constexpr int NTHREADS = (2 + NPW + NEW) * 32;
+  static constexpr int NCB = NPAD / 16, NCB0 = (NCB + 1) / 2;  // column blocks; the first half's share
+  static_assert(NBUF * ACC_COLS <= 512, "tensor memory");
+  static_assert(NPAD <= 256 && NPAD % 16 == 0, "MMA N");
+  static_assert(NPAD % 8 == 0 && B_TILE % 1024 == 0, "swizzle atoms of the B tiles");
+  static_assert(K / 8 <= 16, "a row's 16-byte chunks fit in 16 lanes");
+  static_assert(NEW == 8, "two groups of four consecutive epilogue warps cover the TMEM lane quarters");
+};
+
+template <int P>
+struct TaAux {
+  using C = TaCfg<P>;
+  uint64_t afull[C::NSTG], aempty[C::NSTG];
+  uint64_t bfull[C::NB], bempty[C::NB];
+  uint64_t accfull[C::NBUF], accempty[C::NBUF];
+  // the row scales of an element written (the epilogue reads them; a slot
+  // is rewritten four elements later, when the epilogue is past it)
+  uint64_t rsfull[C::NRS];
+  uint64_t drain;
+  uint32_t tmem_base;
+  int abort_flag;
+  float rs[C::NRS][C::NPAD];  // 2^-s of each gA row (its split scale)
+  float4 comb[2][4][32];      // second-half epilogue sums, by tile parity, quarter and lane
+};
+
+// gD [count][N_q][16] (FP32, dL/dDt_q[a][b] at 4 a + b) for the elements
+// e0 .. e0 + count - 1 of the batch (no list: uniform degree).
+template <int P>
+__global__ void __launch_bounds__(TaCfg<P>::NTHREADS, 1)
+    tc_adjoint_kernel(const float *gA, const int64_t *A_off, int64_t e0, int64_t count, const unsigned char *aimg,
+                      const float4 *gq4, int tau, float *gD) {
+  using C = TaCfg<P>;
+  constexpr int NSH = C::NSH, NQ = C::NQ, NPAD = C::NPAD, NKC = C::NKC, NMT = C::NMT, S = C::NSTG;
+  extern __shared__ __align__(1024) unsigned char dsm_raw[];
+  __shared__ TaAux<P> ax;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t dbase = (smem_u32(dsm_raw) + 1023u) & ~1023u;
+  auto stageA = [&](int s) { return dbase + (uint32_t)(s * C::A_STAGE); };
+  auto bufB = [&](int bb) { return dbase + (uint32_t)(S * C::A_STAGE + bb * C::B_BUF); };
+  volatile int *abort_flag = &ax.abort_flag;
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(smem_u32(&ax.afull[s]), 1);
+      mbar_init(smem_u32(&ax.aempty[s]), 1);
+    }
+    for (int k = 0; k < C::NB; ++k) {
+      mbar_init(smem_u32(&ax.bfull[k]), C::NPW);
+      mbar_init(smem_u32(&ax.bempty[k]), 1);
+    }
+    for (int k = 0; k < C::NBUF; ++k) {
+      mbar_init(smem_u32(&ax.accfull[k]), 1);
+      mbar_init(smem_u32(&ax.accempty[k]), C::NEW);
+    }
+    for (int k = 0; k < C::NRS; ++k) mbar_init(smem_u32(&ax.rsfull[k]), C::NPW);
+    mbar_init(smem_u32(&ax.drain), 1);
+    ax.abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&ax.tmem_base)),
+                 "r"(C::TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = ax.tmem_base;
+  // this block's elements: b, b + grid, ... (local index k, element e0 + k)
+  const int64_t kfirst = blockIdx.x, kstep = gridDim.x;
+
+  if (warp == 0) {
+    // ============================================================ A stream
+    if (lane == 0) {
+      uint32_t g = 0;
+      bool ok = true;
+      for (int64_t k = kfirst; k < count && ok; k += kstep)
+        for (int m = 0; m < NMT && ok; ++m)
+          for (int kc = 0; kc < NKC; ++kc, ++g) {
+            const int s = (int)(g % S);
+            const uint32_t u = g / S;
+            if (!mbar_wait(smem_u32(&ax.aempty[s]), (u & 1u) ^ 1u, abort_flag)) {
+              ok = false;
+              break;
+            }
+            const uint32_t bar = smem_u32(&ax.afull[s]);
+            mbar_expect_tx(bar, (uint32_t)C::A_STAGE);
+            bulk_g2s(stageA(s), aimg + (size_t)(m * NKC + kc) * C::A_STAGE, (uint32_t)C::A_STAGE, bar);
+          }
+    }
+  } else if (warp == 1) {
+    // ================================================================ MMA
+    constexpr uint32_t IDESC = idesc_mma(128, NPAD, 0);
+    bool ok = true;
+    uint32_t g = 0, tile = 0;
+    int it = 0;
+    for (int64_t k = kfirst; k < count && ok; k += kstep, ++it) {
+      const int bb = it % C::NB;
+      ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&ax.bfull[bb]), (uint32_t)(it / C::NB) & 1u, abort_flag));
+      if (!ok) break;
+      tc_fence_after();
+      const uint32_t bh0 = bufB(bb);
+      for (int m = 0; m < NMT && ok; ++m, ++tile) {
+        const int buf = (int)(tile % C::NBUF);
+        ok = __all_sync(0xffffffffu,
+                        mbar_wait(smem_u32(&ax.accempty[buf]), ((tile / C::NBUF) & 1u) ^ 1u, abort_flag));
+        if (!ok) break;
+        tc_fence_after();
+        const uint32_t d = tmem + (uint32_t)(buf * C::ACC_COLS);
+        for (int kc = 0; kc < NKC; ++kc, ++g) {
+          const int s = (int)(g % S);
+          ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&ax.afull[s]), (g / S) & 1u, abort_flag));
+          if (!ok) break;
+          tc_fence_after();
+#pragma unroll
+          for (int kk = 0; kk < 2; ++kk) {
+            const int ks = kc * 2 + kk;
+            const uint32_t dp = d + (uint32_t)((ks / C::SPP) * NPAD);
+            const uint32_t first = (ks % C::SPP) == 0 ? 0u : 1u;
+            const uint64_t Ah = sw_desc<64>(stageA(s) + kk * 32), Al = sw_desc<64>(stageA(s) + C::A_TILE + kk * 32);
+            const uint64_t Bh = sw_desc<64>(bh0 + (uint32_t)((kc * 2) * C::B_TILE + kk * 32));
+            const uint64_t Bl = sw_desc<64>(bh0 + (uint32_t)((kc * 2 + 1) * C::B_TILE + kk * 32));
+            tc_mma_ss_w<0>(dp, Ah, Bh, IDESC, first);
+            tc_mma_ss_w<0>(dp, Ah, Bl, IDESC, 1u);
+            tc_mma_ss_w<0>(dp, Al, Bh, IDESC, 1u);
+          }
+          tc_commit_w(smem_u32(&ax.aempty[s]));
+        }
+        if (ok) tc_commit_w(smem_u32(&ax.accfull[buf]));
+      }
+      if (ok) tc_commit_w(smem_u32(&ax.bempty[bb]));
+    }
+    if (!ok) {
+      // no MMA in flight when the block leaves
+      tc_commit_w(smem_u32(&ax.drain));
+      const uint64_t t0 = global_ns();
+      while (!mbar_try_wait(smem_u32(&ax.drain), 0) && global_ns() - t0 < kWaitLimitNs) {
+      }
+      __syncwarp();
+    }
+  } else if (warp < C::W_EW) {
+    // ========================================================== producers
+    // 16 lanes per row, lane c the row's K values 8 c .. 8 c + 7; a warp two
+    // rows at a time.  Each row is scaled by 2^s (s from its largest
+    // magnitude, so that it is at most 2^14) and split into fp16 hi + lo.
+    const int pw = warp - C::W_PW, half = lane >> 4, c8 = lane & 15;
+    const int64_t cw = (int64_t)NSH * NSH;
+    int it = 0;
+    for (int64_t k = kfirst; k < count; k += kstep, ++it) {
+      const int bb = it % C::NB;
+      const bool ok =
+          __all_sync(0xffffffffu, mbar_wait(smem_u32(&ax.bempty[bb]), ((uint32_t)(it / C::NB) & 1u) ^ 1u, abort_flag));
+      if (!ok) break;
+      const int64_t e = e0 + k;
+      const float *row0 = gA + (A_off ? A_off[e] : e * cw);
+      float *rs = ax.rs[it % C::NRS];
+      const uint32_t b0 = bufB(bb);
+#pragma unroll 4
+      for (int r = 2 * pw + half; r < NPAD; r += 2 * C::NPW) {
+        float v[8];
+        float mx = 0.f;
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          const int j = 8 * c8 + t;
+          v[t] = (r < NSH && j < NSH) ? __ldg(row0 + (int64_t)r * NSH + j) : 0.f;
+          mx = fmaxf(mx, fabsf(v[t]));
+        }
+#pragma unroll
+        for (int o = 1; o < 16; o <<= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        int ex = 0;
+        if (mx > 0.f && mx <= 3.402823466e38f) (void)frexpf(mx, &ex);  // mx <= 2^ex
+        int sc = 14 - ex;
+        sc = sc > 100 ? 100 : (sc < -100 ? -100 : sc);
+        const float up = exp2i(sc / 2) * exp2i(sc - sc / 2);
+        if (c8 == 0) rs[r] = exp2i(-(sc / 2)) * exp2i(-(sc - sc / 2));
+        uint32_t hv[4], lv[4];
+#pragma unroll
+        for (int t = 0; t < 8; t += 2) {
+          const float x0 = v[t] * up, x1 = v[t + 1] * up;
+          const __half2 h = __floats2half2_rn(x0, x1);
+          const float2 rr = split_residual(h, x0, x1);
+          const __half2 l = __floats2half2_rn(rr.x, rr.y);
+          memcpy(&hv[t / 2], &h, 4);
+          memcpy(&lv[t / 2], &l, 4);
+        }
+        if (8 * c8 < C::K) {
+          const int kc = c8 >> 2, un = c8 & 3;
+          const uint32_t off = sw_off<64>(r, un);
+          st_shared_v4(b0 + (uint32_t)((kc * 2) * C::B_TILE) + off, hv);
+          st_shared_v4(b0 + (uint32_t)((kc * 2 + 1) * C::B_TILE) + off, lv);
+        }
+      }
+      // the B operand is read by the tensor core (async proxy)
+      fence_proxy_async();
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(smem_u32(&ax.bfull[bb]));
+        mbar_arrive(smem_u32(&ax.rsfull[it % C::NRS]));
+      }
+    }
+  } else {
+    // =========================================================== epilogue
+    // Warp w of the group: lane quarter w & 3, column half (w - W_EW) / 4.
+    // The second half leaves its sums in shared memory (by tile parity)
+    // and the first half, after a named barrier of the pair, stores.
+    const int quarter = warp & 3, ch = (warp - C::W_EW) >> 2;
+    const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
+    const int r = quarter * 32 + lane;
+    const int cb0 = ch == 0 ? 0 : C::NCB0, cb1 = ch == 0 ? C::NCB0 : C::NCB;
+    const float down = exp2i(-tau);
+    uint32_t tile = 0;
+    int it = 0;
+    bool ok = true;
+    for (int64_t k = kfirst; k < count && ok; k += kstep, ++it) {
+      const float *rs = ax.rs[it % C::NRS];
+      ok = __all_sync(0xffffffffu,
+                      mbar_wait(smem_u32(&ax.rsfull[it % C::NRS]), (uint32_t)(it / C::NRS) & 1u, abort_flag));
+      if (!ok) break;
+      for (int m = 0; m < NMT; ++m, ++tile) {
+        const int buf = (int)(tile % C::NBUF);
+        ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&ax.accfull[buf]), (tile / C::NBUF) & 1u, abort_flag));
+        if (!ok) break;
+        tc_fence_after();
+        const int qb = 128 * m + r, q = qb >> 2, b = qb & 3;
+        const bool valid = q < NQ;
+        const float4 *g4 = gq4 + (size_t)(valid ? q : 0) * NPAD;
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 1
+        for (int cb = cb0; cb < cb1; ++cb) {
+          // the table values first (no condition: the table is padded), so
+          // that their latency overlaps the tensor-memory loads
+          float4 gv[16];
+#pragma unroll
+          for (int k2 = 0; k2 < 16; ++k2) gv[k2] = __ldg(g4 + 16 * cb + k2);
+          uint32_t pv[C::NPK][16];
+#pragma unroll
+          for (int pk = 0; pk < C::NPK; ++pk)
+            tmem_ld16_nw(tmem + lane_base + (uint32_t)(buf * C::ACC_COLS + pk * NPAD + 16 * cb), pv[pk]);
+          tmem_wait_ld();
+#pragma unroll
+          for (int k2 = 0; k2 < 16; ++k2) {
+            float w = __uint_as_float(pv[0][k2]);
+#pragma unroll
+            for (int pk = 1; pk < C::NPK; ++pk) w += __uint_as_float(pv[pk][k2]);
+            w *= rs[16 * cb + k2];
+            acc[0] = fmaf(gv[k2].x, w, acc[0]);
+            acc[1] = fmaf(gv[k2].y, w, acc[1]);
+            acc[2] = fmaf(gv[k2].z, w, acc[2]);
+            acc[3] = fmaf(gv[k2].w, w, acc[3]);
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&ax.accempty[buf]));
+        if (ch == 1) ax.comb[tile & 1][quarter][lane] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+        named_bar(1 + quarter, 64);
+        if (ch == 0 && valid) {
+          const float4 o2 = ax.comb[tile & 1][quarter][lane];
+          float *o = gD + ((size_t)k * NQ + q) * 16 + b;
+          o[0] = (acc[0] + o2.x) * down;
+          o[4] = (acc[1] + o2.y) * down;
+          o[8] = (acc[2] + o2.z) * down;
+          o[12] = (acc[3] + o2.w) * down;
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  // an aborted block marks its elements with NaN, which the chain carries
+  // into their gradients
+  if (*abort_flag) {
+    const float nan = __int_as_float(0x7fc00000);
+    for (int64_t k = kfirst; k < count; k += kstep)
+      for (int t = tid; t < NQ * 16; t += blockDim.x) gD[(size_t)k * NQ * 16 + t] = nan;
+    const uint64_t t0 = global_ns();  // in-flight bulk copies land within microseconds
+    while (global_ns() - t0 < 200000ull) {
+    }
+  }
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::TMEM_COLS) : "memory");
+  }
+}
+
+// Adjoint epilogue table: out[q][i] = (G[q][0][i], .., G[q][3][i]) in FP32,
+// zero for i >= nsh (i < npad).
+__global__ void adj_table_kernel(const double *G, int nsh, int nq, int npad, float4 *out) {
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < nq * npad; idx += gridDim.x * blockDim.x) {
+    const int q = idx / npad, i = idx - q * npad;
+    float v[4] = {0.f, 0.f, 0.f, 0.f};
+    if (i < nsh)
+      for (int a = 0; a < 4; ++a) v[a] = (float)G[(size_t)(4 * q + a) * nsh + i];
+    out[idx] = make_float4(v[0], v[1], v[2], v[3]);
+  }
+}
+
+// Adjoint A image: x = G[q][b][j] 2^tau at row (q, b) = 128 m + r, K value
+// j = 32 kc + t, split into fp16 hi + lo at its swizzled position.
+__global__ void adj_image_kernel(const double *G, int nsh, int nq, int nmt, int nkc, double scale,
+                                 unsigned char *img) {
+  const int64_t total = (int64_t)nmt * nkc * 128 * 32;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int t = (int)(idx % 32);
+    const int r = (int)((idx / 32) % 128);
+    const int kc = (int)((idx / (32 * 128)) % nkc);
+    const int m = (int)(idx / (32 * 128 * (int64_t)nkc));
+    const int qb = 128 * m + r, q = qb >> 2, b = qb & 3, j = 32 * kc + t;
+    const double x = (q < nq && j < nsh) ? G[(size_t)(4 * q + b) * nsh + j] * scale : 0.0;
+    const uint32_t byte = sw_off<64>(r, (2 * t) >> 4) + ((2 * t) & 15);
+    unsigned char *base = img + (size_t)(m * nkc + kc) * 2 * (128 * 64);
+    const __half h = __double2half(x);
+    const __half l = __double2half(x - (double)__half2float(h));
+    *reinterpret_cast<__half *>(base + byte) = h;
+    *reinterpret_cast<__half *>(base + 128 * 64 + byte) = l;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // B operand image: G * 2^tau split into fp16 hi/lo, K-major swizzled rows
 // ---------------------------------------------------------------------------
 __global__ void gmax_kernel(const double *G, int n, unsigned long long *out) {
@@ -1742,6 +2113,26 @@ fei_status launch_tc(const fei_reference *ref, const FwdArgs &a, int64_t grid_wo
   return FEI_OK;
 }
 
+template <int P>
+fei_status launch_ta(const fei_reference *ref, const float *gA, const int64_t *A_off, int64_t e0, int64_t count,
+                     float *gD, cudaStream_t s) {
+  using C = TaCfg<P>;
+  static_assert(sizeof(TaAux<P>) + C::DYN_SMEM <= 232448, "shared memory of one block (227 KB)");
+  const TcImage *im = ref->tc;
+  if (!im || !im->aimg || !im->gq4p)
+    return set_error(FEI_ERR_UNSUPPORTED, "no tensor-core adjoint image for degree %d", P);
+  FEI_CUDA_TRY(cudaFuncSetAttribute(tc_adjoint_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::DYN_SMEM),
+               "cudaFuncSetAttribute(tc_adjoint)");
+  int dev, sms;
+  FEI_CUDA_TRY(cudaGetDevice(&dev), "cudaGetDevice");
+  FEI_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "cudaDeviceGetAttribute");
+  const int64_t blocks = count < sms ? count : sms;
+  tc_adjoint_kernel<P><<<(unsigned)blocks, C::NTHREADS, C::DYN_SMEM, s>>>(
+      gA, A_off, e0, count, im->aimg, im->gq4p, im->tau, gD);
+  FEI_CUDA_TRY(cudaGetLastError(), "tc_adjoint_kernel launch");
+  return FEI_OK;
+}
+
 template <int P, int KD>
 void tc_dims(int &npad, int &nchunk, int &rowb, int &gst, int &pp) {
   npad = TcCfg<P, 0, KD>::NPAD;
@@ -1749,6 +2140,14 @@ void tc_dims(int &npad, int &nchunk, int &rowb, int &gst, int &pp) {
   rowb = TcCfg<P, 0, KD>::ROWB;
   gst = TcCfg<P, 0, KD>::GST;
   pp = TcCfg<P, 0, KD>::PP;
+}
+
+void ta_dims_of(int p, int &nmt, int &nkc) {
+  switch (p) {
+    case 3: nmt = TaCfg<3>::NMT, nkc = TaCfg<3>::NKC; break;
+    case 4: nmt = TaCfg<4>::NMT, nkc = TaCfg<4>::NKC; break;
+    default: nmt = TaCfg<5>::NMT, nkc = TaCfg<5>::NKC; break;
+  }
 }
 
 template <int KD>
@@ -1810,6 +2209,21 @@ fei_status build_tc_image(fei_reference *ref) {
       e = cudaGetLastError();
     }
   }
+  if (e == cudaSuccess && ref->p <= 5) {
+    int nmt = 0, nkc = 0;
+    ta_dims_of(ref->p, nmt, nkc);
+    const int npad = (ref->nsh + 15) / 16 * 16;
+    e = cudaMalloc(&im->aimg, (size_t)nmt * nkc * 2 * 128 * 64);
+    if (e == cudaSuccess) e = cudaMalloc(&im->gq4p, sizeof(float4) * (size_t)ref->nq * npad);
+    if (e == cudaSuccess) {
+      adj_image_kernel<<<256, 256>>>(ref->G64, ref->nsh, ref->nq, nmt, nkc, ldexp(1.0, im->tau), im->aimg);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+      adj_table_kernel<<<256, 256>>>(ref->G64, ref->nsh, ref->nq, npad, im->gq4p);
+      e = cudaGetLastError();
+    }
+  }
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (dmax) cudaFree(dmax);
   if (e != cudaSuccess) {
@@ -1817,6 +2231,8 @@ fei_status build_tc_image(fei_reference *ref) {
       if (im->k[kd].img) cudaFree(im->k[kd].img);
       if (im->k[kd].gp) cudaFree(im->k[kd].gp);
     }
+    if (im->aimg) cudaFree(im->aimg);
+    if (im->gq4p) cudaFree(im->gq4p);
     delete im;
     return cuda_error(e, "tensor-core image");
   }
@@ -1830,9 +2246,26 @@ void free_tc_image(fei_reference *ref) {
       cudaFree(ref->tc->k[kd].img);
       cudaFree(ref->tc->k[kd].gp);
     }
+    if (ref->tc->aimg) cudaFree(ref->tc->aimg);
+    if (ref->tc->gq4p) cudaFree(ref->tc->gq4p);
     delete ref->tc;
     ref->tc = nullptr;
   }
+}
+
+bool tc_adjoint_ready(const fei_reference *ref) {
+  return ref->p >= 3 && ref->p <= 5 && ref->tc && ref->tc->aimg && ref->tc->gq4p;
+}
+
+fei_status launch_tc_adjoint(int p, const fei_reference *ref, const float *gA, const int64_t *A_off, int64_t e0,
+                             int64_t count, float *gD, cudaStream_t s) {
+  if (count <= 0) return FEI_OK;
+  switch (p) {
+    case 3: return launch_ta<3>(ref, gA, A_off, e0, count, gD, s);
+    case 4: return launch_ta<4>(ref, gA, A_off, e0, count, gD, s);
+    case 5: return launch_ta<5>(ref, gA, A_off, e0, count, gD, s);
+  }
+  return set_error(FEI_ERR_UNSUPPORTED, "tensor-core adjoint for degree %d", p);
 }
 
 int tc_variant_count(int p, fei_precision prec) {

@@ -27,7 +27,7 @@ TOL = {"fp64": 1e-12, "fp32": 1e-5, "tc_f16x3": 1e-6, "tc_3xtf32": 1e-6, "sf_fp3
 # that error relative to it (1.3e-6 measured at p = 5); 1e-5 bounds this
 # with margin and still fails any record that is wrong (an index or sign
 # mistake is an O(1) error).
-TOL_GRAD_REC = {"fp64": 1e-10, "fp32": 1e-5}
+TOL_GRAD_REC = {"fp64": 1e-10, "fp32": 1e-5, "tc_f16x3": 1e-5}
 # elements per degree: several thread blocks / tiles and a ragged tail
 N_PER_P = {1: 517, 2: 133, 3: 45, 4: 21, 5: 9, 6: 5, 7: 3}
 
@@ -183,10 +183,13 @@ def test_invalid_degree_reported(api):
     assert ei.value.status == 2
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32", 1e-6)])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32", 1e-6), ("tc_f16x3", 1e-6)])
 @pytest.mark.parametrize("p,per_qp", [(1, False), (2, False), (3, False), (4, False), (5, True), (6, False),
                                      (7, False)])
 def test_backward_matches_oracle_adjoint(api, p, per_qp, precision, tol):
+    """The general adjoint against the oracle's, element by element and record
+    by record.  tc_f16x3 forms dL/dDt on the tensor cores at p = 3..5 and
+    runs the FP32 adjoint at the other degrees."""
     w = inputs.workload("diff", n_max=3) if per_qp else inputs.workload("p7", n_max=4)
     n = len(w["geom"])
     s = api.nsh(p)
@@ -197,7 +200,7 @@ def test_backward_matches_oracle_adjoint(api, p, per_qp, precision, tol):
     out = api.fei_integrate_backward(dev(w["geom"]), dev(w["K"]), dev(w["b"]), dev(w["c"]), dev(w["f"]),
                                      dev(gA, dt), dev(gb, dt), p=p, per_qp=per_qp, precision=precision)
     torch.cuda.synchronize()
-    if precision == "fp32":  # the oracle sees the same rounded cotangents
+    if precision != "fp64":  # the oracle sees the same rounded cotangents
         gA = gA.astype(np.float32).astype(np.float64)
         gb = gb.astype(np.float32).astype(np.float64)
     ref = oracle.integrate_backward(w["geom"], w["K"], w["b"], w["c"], w["f"], gA, gb, p=p, per_qp=per_qp)
@@ -545,3 +548,33 @@ def test_far_and_tiny_coordinates(api, p, precision):
     ea, eb = compare(api, w, p, precision)
     assert ea.max() < TOL[precision], (p, precision, ea.max())
     assert eb.max() < TOL[precision], (p, precision, eb.max())
+
+
+@pytest.mark.parametrize("p,per_qp", [(3, False), (4, False), (5, True)])
+def test_tc_adjoint_blocks_and_chunks(api, monkeypatch, p, per_qp):
+    """The tensor-core adjoint over more elements than thread blocks (each
+    block's pipeline runs several elements: B buffers, A stages and
+    accumulator buffers wrap) and over several launch chunks (the chain reads
+    the scratch at an element offset), with cotangents whose rows differ by
+    orders of magnitude (each gA row has its own split scale: over six
+    orders, one scale per element would leave the small rows about 18 bits
+    of fp16 hi + lo instead of 22)."""
+    n = {3: 400, 4: 170, 5: 160}[p]
+    w = inputs.workload("diff", n_max=n) if per_qp else inputs.workload("p7", n_max=n)
+    n = len(w["geom"])
+    s = api.nsh(p)
+    rng = np.random.default_rng(100 + p)
+    row_scale = 10.0 ** rng.integers(-3, 4, size=(n, s, 1))
+    gA = (rng.standard_normal((n, s, s)) * row_scale).reshape(-1)
+    gb = rng.standard_normal(n * s)
+    monkeypatch.setenv("FEI_ADJOINT_CHUNK", "64")
+    out = api.fei_integrate_backward(dev(w["geom"]), dev(w["K"]), dev(w["b"]), dev(w["c"]), dev(w["f"]),
+                                     dev(gA, torch.float32), dev(gb, torch.float32), p=p, per_qp=per_qp,
+                                     precision="tc_f16x3")
+    torch.cuda.synchronize()
+    gA = gA.astype(np.float32).astype(np.float64)
+    gb = gb.astype(np.float32).astype(np.float64)
+    ref = oracle.integrate_backward(w["geom"], w["K"], w["b"], w["c"], w["f"], gA, gb, p=p, per_qp=per_qp)
+    got = [t.cpu().numpy() for t in out]
+    assert_grads_close(got, ref, n, per_qp, np.full(n, api.nq(p)), 1e-6, TOL_GRAD_REC["tc_f16x3"],
+                       where=f"p={p} tc_f16x3, {n} elements in chunks of 64")
