@@ -63,6 +63,127 @@ struct BwdStatic {
   double gcoef[14]; // per-element coefficient gradient
   int status;
 };
+// FP32 path: node tables of the block (once) and per element the FP32
+// element vectors, node columns and node sums of det J (FP32 pairs), the
+// coefficients in FP32 and the element-vector gradients as FP32 pairs
+struct BwdTablesF32 {
+  float2 ttab2[64][3];  // (w_t, w_t xi1, w_t xi2) as FP32 hi + lo
+  float ttabf[64][3];   // (w_t, xi1, xi2)
+  float2 ztab2[8][2];   // (zeta, w_z) as FP32 hi + lo
+  float ztabf[8][2];    // (zeta, w_z)
+  float evf[21];
+  float cdf[14];
+  float zc1f[8][3], zc2f[8][3], zn3f[8][3];
+  float2 zabg[8][3];    // w_z (n3.C, n3.D1, n3.D2)
+  float tc3f[64][3];
+  float2 gev2[21];
+  // for single roundings of c3, w and det J: the element vectors and the
+  // node sums (n3.C, n3.D1, n3.D2) as FP32 pairs, xi1, xi2 as pairs
+  float2 ev2[21];
+  float2 zsum[8][3];
+  float2 txi2[64][2];
+};
+// the block's static shared data: the FP32 tables only in FP32 kernels (the
+// FP64 kernel at p = 7 needs the room for its dynamic area)
+template <bool F32>
+struct BwdShared : BwdStatic {};
+template <>
+struct BwdShared<true> : BwdStatic, BwdTablesF32 {};
+
+__device__ __forceinline__ int point_status_f(float s) {
+  if (!(fabsf(s) <= 3.402823466e38f)) return FEI_ERR_NONFINITE;
+  if (!(s > 0.f)) return FEI_ERR_NEGATIVE_JACOBIAN;
+  return 0;
+}
+
+// FP32 path, warp 0: the element vectors (lanes 0-20, component k = j % 3 of
+// vector j / 3) and the vertical-node quantities (lanes 3 iz + k: c1, c2,
+// n3 = c1 x c2 and w_z (n3.C, n3.D1, n3.D2)).  The vertex differences in
+// FP64 (two independent subtractions), split from their bit fields into
+// FP32 pairs, the rest in double-FP32 arithmetic: a dependent FP64
+// instruction takes hundreds of cycles on this part, an FP32 one a few.
+// Differences outside 2^-60 <= |d| < 2^60 (other than 0) take the same
+// steps in FP64.
+template <int P>
+__device__ __forceinline__ void bwd_elem_setup_f32(BwdShared<true> &sm, int lane) {
+  constexpr int NZ = P + 1;
+  const double x = lane < 18 ? sm.X[lane] : 0.0;
+  const int v = lane < 21 ? lane / 3 : 0, kv = lane < 21 ? lane % 3 : 0;
+  // vertices (a, b, c, d) of vector v, 3 bits each, 12 bits per vector:
+  //   A1 (1,0,4,3)  B1 (4,3,1,0)  A2 (2,0,5,3)  B2 (5,3,2,0)
+  //   C  (3,0,0,0)  D1 (4,1,3,0)  D2 (5,2,3,0)
+  // each (X_a - X_b) +- (X_c - X_d), halved
+  constexpr unsigned long long kTab =
+      (0x223ull << 0) | (0x8C8ull << 12) | (0x42Bull << 24) | (0xAD0ull << 36) | (0x600ull << 48);
+  constexpr unsigned long long kTab2 = (0x858ull << 0) | (0xA98ull << 12);  // D1, D2
+  constexpr unsigned kNeg = 0x6Au;  // B1, B2, D1, D2 subtract
+  const unsigned tv = (unsigned)((v < 5 ? kTab >> (12 * v) : kTab2 >> (12 * (v - 5))) & 0xFFFu);
+  const int la = 3 * ((tv >> 9) & 7u) + kv, lb = 3 * ((tv >> 6) & 7u) + kv;
+  const int lc = 3 * ((tv >> 3) & 7u) + kv, ld = 3 * (tv & 7u) + kv;
+  const bool subtract = (kNeg >> v) & 1u;
+  const bool act = lane < 3 * NZ;
+  const int iz = act ? lane / 3 : 0, k = act ? lane % 3 : 0;
+  const int g0 = lane - k, l1 = g0 + (k + 1) % 3, l2 = g0 + (k + 2) % 3;
+  const double xa = __shfl_sync(0xffffffffu, x, la), xb = __shfl_sync(0xffffffffu, x, lb);
+  const double xc = __shfl_sync(0xffffffffu, x, lc), xd = __shfl_sync(0xffffffffu, x, ld);
+  const double t1 = xa - xb, t2 = xc - xd;
+  bool r1 = true, r2 = true;
+  const float2 t1s = split_f64_bits(t1, &r1), t2s = split_f64_bits(t2, &r2);
+  float evf;
+  if (__all_sync(0xffffffffu, lane >= 21 || (r1 && r2))) {
+    auto shfl2 = [](float2 q, int src) {
+      return make_float2(__shfl_sync(0xffffffffu, q.x, src), __shfl_sync(0xffffffffu, q.y, src));
+    };
+    float2 ev = norm_ff(add_ff(t1s, subtract ? neg_ff(t2s) : t2s));
+    ev = make_float2(0.5f * ev.x, 0.5f * ev.y);
+    evf = ev.x;
+    const float2 z2 = sm.ztab2[iz][0], wz2 = sm.ztab2[iz][1];
+    const float2 c1 = norm_ff(add_ff(shfl2(ev, k), mul_ff(z2, shfl2(ev, 3 + k))));
+    const float2 c2 = norm_ff(add_ff(shfl2(ev, 6 + k), mul_ff(z2, shfl2(ev, 9 + k))));
+    const float2 c1a = shfl2(c1, l1), c1b = shfl2(c1, l2), c2a = shfl2(c2, l1), c2b = shfl2(c2, l2);
+    const float2 n3 = norm_ff(add_ff(mul_ff(c1a, c2b), neg_ff(mul_ff(c1b, c2a))));
+    float2 ab = mul_ff(n3, shfl2(ev, 12 + k));
+    float2 bb = mul_ff(n3, shfl2(ev, 15 + k));
+    float2 gb = mul_ff(n3, shfl2(ev, 18 + k));
+    ab = norm_ff(add_ff(ab, add_ff(shfl2(ab, l1), shfl2(ab, l2))));
+    bb = norm_ff(add_ff(bb, add_ff(shfl2(bb, l1), shfl2(bb, l2))));
+    gb = norm_ff(add_ff(gb, add_ff(shfl2(gb, l1), shfl2(gb, l2))));
+    if (lane < 21) sm.ev2[lane] = ev;
+    if (act) {
+      const float2 sk = k == 0 ? ab : k == 1 ? bb : gb;
+      sm.zsum[iz][k] = sk;
+      sm.zabg[iz][k] = norm_ff(mul_ff(wz2, sk));
+      sm.zc1f[iz][k] = c1.x;
+      sm.zc2f[iz][k] = c2.x;
+      sm.zn3f[iz][k] = n3.x;
+    }
+  } else {
+    const double ev = 0.5 * (subtract ? t1 - t2 : t1 + t2);
+    evf = (float)ev;
+    const double z = sm.zz[iz], wz = sm.zw[iz];
+    const double c1 = fma(z, __shfl_sync(0xffffffffu, ev, 3 + k), __shfl_sync(0xffffffffu, ev, k));
+    const double c2 = fma(z, __shfl_sync(0xffffffffu, ev, 9 + k), __shfl_sync(0xffffffffu, ev, 6 + k));
+    const double c1a = __shfl_sync(0xffffffffu, c1, l1), c1b = __shfl_sync(0xffffffffu, c1, l2);
+    const double c2a = __shfl_sync(0xffffffffu, c2, l1), c2b = __shfl_sync(0xffffffffu, c2, l2);
+    const double n3 = c1a * c2b - c1b * c2a;
+    double ab = n3 * __shfl_sync(0xffffffffu, ev, 12 + k);
+    double bb = n3 * __shfl_sync(0xffffffffu, ev, 15 + k);
+    double gb = n3 * __shfl_sync(0xffffffffu, ev, 18 + k);
+    ab += __shfl_sync(0xffffffffu, ab, l1) + __shfl_sync(0xffffffffu, ab, l2);
+    bb += __shfl_sync(0xffffffffu, bb, l1) + __shfl_sync(0xffffffffu, bb, l2);
+    gb += __shfl_sync(0xffffffffu, gb, l1) + __shfl_sync(0xffffffffu, gb, l2);
+    if (lane < 21) sm.ev2[lane] = split_f64(ev);
+    if (act) {
+      const double sk = k == 0 ? ab : k == 1 ? bb : gb;
+      sm.zsum[iz][k] = split_f64(sk);
+      sm.zabg[iz][k] = split_f64(wz * sk);
+      sm.zc1f[iz][k] = (float)c1;
+      sm.zc2f[iz][k] = (float)c2;
+      sm.zn3f[iz][k] = (float)n3;
+    }
+  }
+  if (lane < 21) sm.evf[lane] = evf;
+}
 
 __device__ __forceinline__ bool load_coef_b(const BwdArgs &a, int64_t r, double *cd) {
   bool ok = true;
@@ -113,7 +234,7 @@ __device__ __forceinline__ float2 add_pair_f(float2 x, float2 y) {
 // partial sums of each value are added as unevaluated FP32 pairs
 // (two-sum, 2^-44 relative), in a fixed order, and stored in sm as FP64.
 template <int P>
-__device__ __forceinline__ void chain_f32(const BwdArgs &a, BwdStatic &sm, const float *gD, const float *gsf,
+__device__ __forceinline__ void chain_f32(const BwdArgs &a, BwdShared<true> &sm, const float *gD, const float *gsf,
                                           int64_t qoff, float *red) {
   constexpr int NQ = nq_of(P), NT = (P + 1) * (P + 1);
   const int tid = threadIdx.x;
@@ -124,30 +245,42 @@ __device__ __forceinline__ void chain_f32(const BwdArgs &a, BwdStatic &sm, const
   const bool perq = a.coef_mode == FEI_COEF_PER_POINT;
   for (int q = tid; q < NQ; q += 256) {
     const int iz = q / NT, t = q - iz * NT;
-    const double *c1 = sm.zc1[iz], *c2 = sm.zc2[iz], *n3 = sm.zn3[iz], *c3 = sm.tc3[t];
-    const double w64 = sm.zw[iz] * sm.tw[t];
-    const double det64 = dot3(n3, c3);
-    const double s64 = w64 * det64;
-    pst = merge_status(pst, point_status(s64));
-    double cq[14];
-    const double *cp = sm.cd;
+    // w det J = w_t (a + xi1 b + xi2 g) from the node sums in double-FP32,
+    // rounded once
+    const float2 wp = mul_ff(sm.ztab2[iz][1], sm.ttab2[t][0]);
+    const float w = wp.x + wp.y;
+    const float2 sd = add_ff(add_ff(mul_ff(sm.ttab2[t][0], sm.zabg[iz][0]), mul_ff(sm.ttab2[t][1], sm.zabg[iz][1])),
+                             mul_ff(sm.ttab2[t][2], sm.zabg[iz][2]));
+    const float s = sd.x + sd.y;
+    // det J = a + xi1 b + xi2 g from the node sums, rounded once
+    const float2 dd = add_ff(add_ff(sm.zsum[iz][0], mul_ff(sm.txi2[t][0], sm.zsum[iz][1])),
+                             mul_ff(sm.txi2[t][1], sm.zsum[iz][2]));
+    const float det = dd.x + dd.y;
+    pst = merge_status(pst, point_status_f(s));
+    // coefficients in FP32 (converted from the bit fields)
+    float cf[14];
     if (perq) {
+      double cq[14];
       if (!load_coef_b(a, qoff + q, cq)) pst = FEI_ERR_NONFINITE;
-      cp = cq;
+#pragma unroll
+      for (int k = 0; k < 14; ++k) cf[k] = f64_to_f32_bits(cq[k]);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 14; ++k) cf[k] = sm.cdf[k];
     }
     float K[9], bvec[3];
 #pragma unroll
-    for (int k = 0; k < 9; ++k) K[k] = (float)cp[k];
+    for (int k = 0; k < 9; ++k) K[k] = cf[k];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) bvec[k] = (float)cp[9 + k];
-    const float cc = (float)cp[12], ff = (float)cp[13];
+    for (int k = 0; k < 3; ++k) bvec[k] = cf[9 + k];
+    const float cc = cf[12], ff = cf[13];
     float adj[3][3], cx1[3], cx2[3], cx3[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      cx1[k] = (float)c1[k];
-      cx2[k] = (float)c2[k];
-      cx3[k] = (float)c3[k];
-      adj[2][k] = (float)n3[k];
+      cx1[k] = sm.zc1f[iz][k];
+      cx2[k] = sm.zc2f[iz][k];
+      cx3[k] = sm.tc3f[t][k];
+      adj[2][k] = sm.zn3f[iz][k];
     }
     cross3(cx2, cx3, adj[0]);
     cross3(cx3, cx1, adj[1]);
@@ -160,7 +293,6 @@ __device__ __forceinline__ void chain_f32(const BwdArgs &a, BwdStatic &sm, const
       for (int m = 0; m < 3; ++m) gDm[l][m] = gD[q * 16 + 4 * (l + 1) + (m + 1)];
     }
     const float gs = gsf[q];
-    const float w = (float)w64, det = (float)det64, s = (float)s64;
     const float wd = w / det, wdd = wd / det;
     float Ka[3][3], Kta[3][3];
 #pragma unroll
@@ -232,7 +364,7 @@ __device__ __forceinline__ void chain_f32(const BwdArgs &a, BwdStatic &sm, const
     cross3(gn3, cx1, tmp);
 #pragma unroll
     for (int k = 0; k < 3; ++k) gc2[k] += tmp[k];
-    const float z = (float)sm.zz[iz], x1 = (float)sm.txi[t][0], x2 = (float)sm.txi[t][1];
+    const float z = sm.ztabf[iz][0], x1 = sm.ttabf[t][1], x2 = sm.ttabf[t][2];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       acc[0 + k] += gc1[k];
@@ -266,8 +398,12 @@ __device__ __forceinline__ void chain_f32(const BwdArgs &a, BwdStatic &sm, const
     }
     if (k < nval && sub == 0) {
       const double d = f32_to_f64(v.x) + f32_to_f64(v.y);
-      if (k < 21) sm.gev[k] = d;
-      else sm.gcoef[k - 21] = d;
+      if (k < 21) {
+        sm.gev[k] = d;
+        sm.gev2[k] = v;
+      } else {
+        sm.gcoef[k - 21] = d;
+      }
     }
   }
   __syncthreads();
@@ -278,7 +414,7 @@ __global__ void __launch_bounds__(256, 2) cc_backward_kernel(BwdArgs a) {
   using C = BwdCfg<T, P, Q>;
   constexpr int NSH = C::NSH, NQ = C::NQ, NT = C::NT, BI = C::BI, QC = C::QC, KC = C::KC, NSHP = C::NSHP;
   extern __shared__ __align__(16) unsigned char dsm[];
-  __shared__ BwdStatic sm;
+  __shared__ BwdShared<C::F32> sm;
   T *gAs = reinterpret_cast<T *>(dsm + C::OFF_GA);
   T *Gc = reinterpret_cast<T *>(dsm + C::OFF_GC);
   T *Wc = reinterpret_cast<T *>(dsm + C::OFF_W);
@@ -289,6 +425,36 @@ __global__ void __launch_bounds__(256, 2) cc_backward_kernel(BwdArgs a) {
   const T *gAg = reinterpret_cast<const T *>(a.gA);
   const T *gbg = reinterpret_cast<const T *>(a.gb);
   const int64_t items = a.count ? (int64_t)(*a.count) : a.n_work;
+  // node tables of the degree, once per block (FP64 node data; the FP32
+  // path's FP32 copies and pairs)
+  for (int t = tid; t < NT; t += 256) {
+    const double x1 = a.tnode[4 * t], x2 = a.tnode[4 * t + 1], wt = a.tnode[4 * t + 2];
+    sm.txi[t][0] = x1;
+    sm.txi[t][1] = x2;
+    sm.tw[t] = wt;
+    if constexpr (C::F32) {
+      sm.ttab2[t][0] = split_f64(wt);
+      sm.ttab2[t][1] = split_f64(wt * x1);
+      sm.ttab2[t][2] = split_f64(wt * x2);
+      sm.txi2[t][0] = split_f64(x1);
+      sm.txi2[t][1] = split_f64(x2);
+      sm.ttabf[t][0] = (float)wt;
+      sm.ttabf[t][1] = (float)x1;
+      sm.ttabf[t][2] = (float)x2;
+    }
+  }
+  for (int z = tid; z < C::NZ; z += 256) {
+    const double zz = a.znode[2 * z], zw = a.znode[2 * z + 1];
+    sm.zz[z] = zz;
+    sm.zw[z] = zw;
+    if constexpr (C::F32) {
+      sm.ztab2[z][0] = split_f64(zz);
+      sm.ztab2[z][1] = split_f64(zw);
+      sm.ztabf[z][0] = (float)zz;
+      sm.ztabf[z][1] = (float)zw;
+    }
+  }
+  __syncthreads();
 
   for (int64_t item = blockIdx.x; item < items; item += gridDim.x) {
     const int64_t e = a.list ? (int64_t)a.list[item] : a.e0 + item;
@@ -307,27 +473,38 @@ __global__ void __launch_bounds__(256, 2) cc_backward_kernel(BwdArgs a) {
     if (a.coef_mode == FEI_COEF_PER_ELEMENT && tid == 32) ok = load_coef_b(a, e, sm.cd);
     if (!ok) sm.status = FEI_ERR_NONFINITE;
     __syncthreads();
-    if (tid == 0) elem_vectors(sm.X, sm.ev);
-    __syncthreads();
-    if (tid < C::NZ) {
-      const double z = a.znode[2 * tid];
-      znode_columns(sm.ev, z, sm.zc1[tid], sm.zc2[tid], sm.zn3[tid]);
-      sm.zz[tid] = z;
-      sm.zw[tid] = a.znode[2 * tid + 1];
-    } else if (tid >= 32 && tid < 32 + NT) {
-      const int t = tid - 32;
-      const double x1 = a.tnode[4 * t], x2 = a.tnode[4 * t + 1];
-      tnode_column(sm.ev, x1, x2, sm.tc3[t]);
-      sm.txi[t][0] = x1;
-      sm.txi[t][1] = x2;
-      sm.tw[t] = a.tnode[4 * t + 2];
+    if constexpr (C::F32) {
+      // element vectors and vertical-node data (warp 0, double-FP32), the
+      // per-element coefficients in FP32; then the triangle-node columns
+      // c3 = C + xi1 D1 + xi2 D2 in double-FP32, rounded once
+      if (tid < 32) bwd_elem_setup_f32<P>(sm, tid);
+      else if (tid < 46 && a.coef_mode == FEI_COEF_PER_ELEMENT) sm.cdf[tid - 32] = f64_to_f32_bits(sm.cd[tid - 32]);
+      __syncthreads();
+      for (int j = tid; j < 3 * NT; j += 256) {
+        const int t = j / 3, k = j - 3 * t;
+        const float2 c3 = add_ff(add_ff(sm.ev2[12 + k], mul_ff(sm.txi2[t][0], sm.ev2[15 + k])),
+                                 mul_ff(sm.txi2[t][1], sm.ev2[18 + k]));
+        sm.tc3f[t][k] = c3.x + c3.y;
+      }
+    } else {
+      if (tid == 0) elem_vectors(sm.X, sm.ev);
+      __syncthreads();
+      if (tid < C::NZ) {
+        znode_columns(sm.ev, sm.zz[tid], sm.zc1[tid], sm.zc2[tid], sm.zn3[tid]);
+      } else if (tid >= 32 && tid < 32 + NT) {
+        const int t = tid - 32;
+        tnode_column(sm.ev, sm.txi[t][0], sm.txi[t][1], sm.tc3[t]);
+      }
     }
     if constexpr (Q) {
       // L_e = u^T A_e u - u^T b_e: with v_q = G_q u (4 values per point),
       // dL/dDt_q = v_q v_q^T and dL/d(w det f)_q = -v_q[0] (row 0 of G_q
       // is phi), so gA = u u^T is never formed.  One warp per point.
       T *us = gAs;
-      for (int i = tid; i < NSH; i += 256) us[i] = (T)a.u[boff + i];
+      for (int i = tid; i < NSH; i += 256) {
+        if constexpr (C::F32) us[i] = f64_to_f32_bits(a.u[boff + i]);
+        else us[i] = a.u[boff + i];
+      }
       __syncthreads();
       const int warp = tid >> 5, lane = tid & 31;
       constexpr int NI = (NSH + 31) / 32;  // table entries per lane and row
@@ -630,7 +807,29 @@ __global__ void __launch_bounds__(256, 2) cc_backward_kernel(BwdArgs a) {
     }
     const int st = sm.status;
     // element vectors -> vertices (transpose of elem_vectors)
-    if (tid < 3) {
+    if constexpr (C::F32) {
+     if (tid < 18) {
+      // vertex component (vertex tid / 3, coordinate tid % 3) from the
+      // element-vector gradients as FP32 pairs: signed sums of up to 7
+      // terms (rows of the transpose), halved
+      const int vx = tid / 3, k = tid - 3 * vx;
+      // signs of (A1, B1, A2, B2, C, D1, D2) for P0, P1, P2, Q0, Q1, Q2,
+      // two bits each (0: none, 1: +, 2: -)
+      const unsigned sg = vx == 0 ? 0x1666u : vx == 1 ? 0x809u : vx == 2 ? 0x2090u : vx == 3 ? 0x29AAu
+                          : vx == 4 ? 0x405u : 0x1050u;
+      float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int c = 0; c < 7; ++c) {
+        const unsigned b = (sg >> (2 * c)) & 3u;
+        if (b) {
+          const float2 g = sm.gev2[3 * c + k];
+          acc = add_pair_f(acc, b == 1u ? g : make_float2(-g.x, -g.y));
+        }
+      }
+      const double val = 0.5 * (f32_to_f64(acc.x) + f32_to_f64(acc.y));
+      a.g_geom[18 * e + 3 * vx + k] = st ? 0.0 : val;
+     }
+    } else if (tid < 3) {
       const int k = tid;
       const double *g = sm.gev;
       const double gA1 = g[0 + k], gB1 = g[3 + k], gA2 = g[6 + k], gB2 = g[9 + k];
@@ -674,6 +873,7 @@ __global__ void __launch_bounds__(256, 2) cc_backward_kernel(BwdArgs a) {
 template <typename T, int P, bool Q>
 fei_status launch_bwd(const BwdArgs &a, int64_t grid_work, cudaStream_t s) {
   using C = BwdCfg<T, P, Q>;
+  static_assert(sizeof(BwdShared<C::F32>) + C::SMEM <= 232448, "shared memory of one block (227 KB)");
   FEI_CUDA_TRY(cudaFuncSetAttribute(cc_backward_kernel<T, P, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)C::SMEM),
                "cudaFuncSetAttribute(cc_backward)");
