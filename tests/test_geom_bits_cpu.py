@@ -5,6 +5,7 @@ arithmetic and numpy's FP64 -> FP32 rounding:
   split_f64_bits(x)  x as hi + lo to 2^-47 of |x|, flagged outside
                      [2^-60, 2^60) (0 excepted)
   f64_to_f32_bits(x) FP64 -> FP32 rounded to nearest even, bit for bit
+                     (normal, overflow, subnormal, zero, NaN)
 """
 import os
 import shutil
@@ -62,8 +63,15 @@ def test_f64_to_f32_bits_rounds_like_numpy(harness):
     ties = [float(np.uint32(f + k).view(np.float32)) + 2.0 ** -24 for k in range(4)]
     edge = [3.4028234663852886e38, 3.4028235677973366e38, 3.5e38, -3.5e38, 1e-39, -1e-45, 1.1754943508222875e-38,
             0.0, -0.0, 1e300]
-    x = np.concatenate([x, ties, edge])
+    # subnormal FP32 results across the whole range, with halfway cases
+    sub = rng.uniform(0, 1.2e-38, 2000) * rng.choice([-1, 1], 2000)
+    tiny = np.array([2.0 ** -149, 2.0 ** -150, 3 * 2.0 ** -151, 2.0 ** -151, 1.5 * 2.0 ** -149, 2.5 * 2.0 ** -149,
+                     (1 - 2.0 ** -25) * 2.0 ** -126, -(2.0 ** -126) * (1 - 2.0 ** -24), 1e-320, -1e-300])
+    x = np.concatenate([x, ties, edge, sub, tiny])
     ok, got, _ = harness(2, x)
-    with np.errstate(over="ignore"):
+    with np.errstate(over="ignore", under="ignore"):
         want = x.astype(np.float32)
     assert np.array_equal(got.view(np.uint32), want.view(np.uint32))
+    # NaN stays NaN
+    ok, got, _ = harness(2, np.array([np.nan, -np.inf, np.inf]))
+    assert np.isnan(got[0]) and got[1] == -np.inf and got[2] == np.inf
