@@ -370,8 +370,8 @@ fei_status fei_sync_status(const int32_t *elem_status, int64_t n_elem, int32_t *
  * leaves its contents behind (the call clears the counts it needs); calls
  * whose work overlaps on the GPU race on it, so order them on one stream.
  * The first call on a device with a degree array looks the array's address
- * up (cudaGetSymbolAddress) and keeps it: make that call before any stream
- * capture starts; the kept address does not survive cudaDeviceReset. */
+ * up (cudaGetSymbolAddress) and keeps it for later calls; the kept address
+ * does not survive cudaDeviceReset. */
 fei_status fei_integrate_noalloc(const fei_reference_t *refs, int nrefs,
                                  const fei_batch *batch, fei_precision prec,
                                  void *A_out, void *b_out, int32_t *elem_status,

@@ -23,9 +23,8 @@
 //    but two calls whose work overlaps on the GPU (different streams without
 //    ordering between them) race on the array and give wrong results;
 //  - the first call on a device looks up the array's device address
-//    (cudaGetSymbolAddress) and keeps it for the life of the process --
-//    make that first call before any stream capture begins.  The kept
-//    address is not valid after cudaDeviceReset on that device.
+//    (cudaGetSymbolAddress) and keeps it for the life of the process.  The
+//    kept address is not valid after cudaDeviceReset on that device.
 #include "fei_internal.cuh"
 
 #include <mutex>
