@@ -243,6 +243,35 @@ def test_autograd_matches_central_differences(api):
         assert abs(got - fd) <= 1e-6 * max(1.0, abs(fd)), (idx, got, fd)
 
 
+@pytest.mark.parametrize("precision", ["tc_f16x3", "auto"])
+def test_autograd_split_precision_uses_the_tensor_core_adjoint(api, precision):
+    """integrate() with a split-precision forward at p = 4: its backward runs
+    the tensor-core adjoint (gA from torch's autograd, a general cotangent,
+    not u u^T), and the gradients of a loss with general weights on A and b
+    match the FP64 autograd gradients element by element within the FP32
+    bar."""
+    p, n = 4, 40
+    w = inputs.workload("p7", n_max=n)
+    s = api.nsh(p)
+    rng = np.random.default_rng(11)
+    WA = torch.from_numpy(rng.standard_normal((n, s, s))).cuda()
+    Wb = torch.from_numpy(rng.standard_normal((n, s))).cuda()
+
+    def grads(prec):
+        geom = dev(w["geom"]).clone().requires_grad_(True)
+        K = dev(w["K"]).clone().requires_grad_(True)
+        A, bv, st = api.integrate(geom, K, dev(w["b"]), dev(w["c"]), dev(w["f"]), p=p, precision=prec)
+        L = (A.double().view(n, s, s) * WA).sum() + (bv.double().view(n, s) * Wb).sum()
+        L.backward()
+        return geom.grad.cpu().numpy(), K.grad.cpu().numpy()
+
+    g64, k64 = grads("fp64")
+    g, k = grads(precision)
+    eg = np.linalg.norm((g - g64).reshape(n, -1), axis=1) / np.linalg.norm(g64.reshape(n, -1), axis=1)
+    ek = np.linalg.norm((k - k64).reshape(n, -1), axis=1) / np.linalg.norm(k64.reshape(n, -1), axis=1)
+    assert eg.max() < 1e-5 and ek.max() < 1e-5, (eg.max(), ek.max())
+
+
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32", 1e-6)])
 @pytest.mark.parametrize("p,per_qp", [(1, False), (4, False), (5, True), (7, False)])
 def test_quadratic_adjoint_matches_oracle(api, p, per_qp, precision, tol):
