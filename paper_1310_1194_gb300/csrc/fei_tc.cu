@@ -366,8 +366,11 @@ struct TcCfg {
   // row stride of the paired table: odd with GS, so that the 8 pairs of a
   // row group fall into different 16-byte bank groups of shared memory
   static constexpr int GST = GS ? (NSH | 1) : NSH;
-  static constexpr int DRING = 8;  // chunks of point operators ahead
-  static constexpr int DB = 4;     // chunks of point operators per round
+  // chunks of point operators ahead, and per round (one wait and one pass
+  // of the point-operator warps for several chunks): at p = 4 a whole tile
+  // (8 chunks) per round on a 16-chunk ring, 4.3 % faster than rounds of 4
+  static constexpr int DRING = P == 4 ? 16 : 8;
+  static constexpr int DB = P == 4 ? 8 : 4;
   static constexpr int A_BYTES = 128 * ROWB;
   static constexpr int B_BYTES = NPAD * ROWB;
   static constexpr int G_BYTES = GS ? PPC * GST * 16 : 0;
