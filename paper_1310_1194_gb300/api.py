@@ -242,7 +242,12 @@ def fei_integrate(geom, K, b, c, f, p=None, degree=None, per_qp=False, precision
 
 def fei_integrate_backward(geom, K, b, c, f, gA, gb, p=None, degree=None, per_qp=False,
                            precision="fp64", refs=None, layout=None):
-    """Gradients of <gA, A> + <gb, b>: (g_geom, gK, gb_coef, gc, gf), FP64."""
+    """Gradients of <gA, A> + <gb, b>: (g_geom, gK, gb_coef, gc, gf), FP64.
+
+    precision: "fp64" (gA, gb FP64; all FP64), "fp32" (gA, gb FP32; the FP32
+    adjoint), "tc_f16x3" or "auto" (gA, gb FP32; at a uniform degree 3..5
+    dL/dDt is formed on the tensor cores, elsewhere the FP32 adjoint runs);
+    other split precisions run the FP32 adjoint."""
     geom, layout = _inputs(geom, K, b, c, f, degree, p, per_qp, layout)
     prec = _lib.PRECISIONS[precision]
     dtype = torch.float64 if prec == _lib.FEI_FP64 else torch.float32
